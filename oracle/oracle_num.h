@@ -1,0 +1,132 @@
+/*
+ * Numeric oracle kernels, instantiated by oracle.c for ORC_T = double and
+ * ORC_T = double complex (complex symmetric: plain transposes only).
+ * TEST INFRASTRUCTURE ONLY (see oracle.c).
+ */
+
+/*
+ * Left-looking pivot-free LDL^T on a given elimination-closed pattern
+ * (Section 2.1's LDL^T simplification of the LU form; Section 4: no
+ * pivoting, symmetric permutation only).  L is unit lower triangular,
+ * stored strictly below the diagonal on lcp/lri; D on the diagonal.
+ *
+ *   for j = 0..n-1:
+ *     w = A(j:n, j)                                  (rows {j} U struct(j))
+ *     for every k < j with L_jk != 0:  w(i) -= L_ik d_k L_jk,  i in {j} U struct(k), i >= j
+ *     d_j = w(j);   L_ij = w(i) / d_j  for i in struct(j)
+ *
+ * Returns 0, or -(j+1) if d_j is zero or not finite (first such column), or
+ * -(n+1) if A has an entry outside {j} U struct(j).
+ */
+int ORC_SFX(orc_ldlt)(int32_t n, const int64_t* cp, const int32_t* ri, const ORC_T* av,
+                      const int64_t* lcp, const int32_t* lri, ORC_T* lv, ORC_T* d) {
+  /* row lists of L: for each row j the (column k, position p) with lri[p] == j */
+  int64_t nnzl = lcp[n];
+  int64_t* rp = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  for (int64_t p = 0; p < nnzl; ++p) rp[lri[p] + 1]++;
+  for (int32_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+  int32_t* rk = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnzl > 0 ? nnzl : 1));
+  int64_t* rpos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnzl > 0 ? nnzl : 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int32_t i = 0; i < n; ++i) fill[i] = rp[i];
+  for (int32_t k = 0; k < n; ++k)
+    for (int64_t p = lcp[k]; p < lcp[k + 1]; ++p) {
+      rk[fill[lri[p]]] = k;
+      rpos[fill[lri[p]]++] = p;
+    }
+  ORC_T* w = (ORC_T*)calloc((size_t)(n > 0 ? n : 1), sizeof(ORC_T));
+  char* in = (char*)calloc((size_t)(n > 0 ? n : 1), 1);      /* membership of {j} U struct(j) */
+  int status = 0;
+  for (int32_t j = 0; j < n && status == 0; ++j) {
+    in[j] = 1;
+    for (int64_t p = lcp[j]; p < lcp[j + 1]; ++p) in[lri[p]] = 1;
+    for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
+      if (!in[ri[p]]) { status = -(n + 1); break; }
+      w[ri[p]] = av[p];
+    }
+    if (status) break;
+    for (int64_t q = rp[j]; q < rp[j + 1]; ++q) {
+      int32_t k = rk[q];
+      int64_t pj = rpos[q];                   /* position of L_jk in column k */
+      ORC_T f = lv[pj] * d[k];
+      for (int64_t p = pj; p < lcp[k + 1]; ++p) w[lri[p]] -= lv[p] * f;
+    }
+    d[j] = w[j];
+    w[j] = 0;
+    in[j] = 0;
+    if (ORC_ISBAD(d[j])) status = -(j + 1);
+    for (int64_t p = lcp[j]; p < lcp[j + 1]; ++p) {
+      lv[p] = w[lri[p]] / d[j];
+      w[lri[p]] = 0;
+      in[lri[p]] = 0;
+    }
+  }
+  free(rp); free(rk); free(rpos); free(fill); free(w); free(in);
+  return status;
+}
+
+/*
+ * Selected inversion, column form of Eqs. (11)-(13) (Algorithm 1 with
+ * one-column supernodes; Lhat = L because L_jj = 1; Uhat = Lhat^T by Eq. 14;
+ * U_jj^{-1} L_jj^{-1} = 1/d_j).  For j = n-1 down to 0 with C = struct(j):
+ *
+ *   X_ij = - sum_{k in C} X_{max(i,k), min(i,k)} L_kj      (i in C)    step 2
+ *   X_jj = 1/d_j - sum_{i in C} L_ij X_ij                               step 3
+ *
+ * X is stored on the same pattern as L (xv) plus its diagonal (xd).  The
+ * entries X_{a,b} (a > b, both in C) are found by a merge walk of C against
+ * struct(b): C ∩ (b, n) ⊆ struct(b) holds for elimination-closed patterns.
+ * The double sum is visited once per unordered pair {a, b} and credited to
+ * both rows (X is symmetric).  Returns 0, or -(j+1) if the walk for column j
+ * fails (pattern not closed).
+ */
+int ORC_SFX(orc_selinv)(int32_t n, const int64_t* lcp, const int32_t* lri, const ORC_T* lv,
+                        const ORC_T* d, ORC_T* xv, ORC_T* xd) {
+  ORC_T* y = (ORC_T*)calloc((size_t)(n > 0 ? n : 1), sizeof(ORC_T));
+  int status = 0;
+  for (int32_t j = n - 1; j >= 0 && status == 0; --j) {
+    int64_t p0 = lcp[j], r = lcp[j + 1] - lcp[j];
+    const int32_t* C = lri + p0;
+    const ORC_T* Lj = lv + p0;
+    for (int64_t a = 0; a < r; ++a) y[a] = 0;
+    for (int64_t b = 0; b < r && status == 0; ++b) {
+      int32_t k = C[b];
+      ORC_T lkj = Lj[b];
+      y[b] += xd[k] * lkj;                    /* pair (k, k) */
+      int64_t q = lcp[k], qend = lcp[k + 1];
+      for (int64_t a = b + 1; a < r; ++a) {   /* pairs (C[a], k), C[a] > k */
+        while (q < qend && lri[q] != C[a]) ++q;
+        if (q == qend) { status = -(j + 1); break; }
+        ORC_T x = xv[q];
+        y[a] += x * lkj;
+        y[b] += x * Lj[a];
+      }
+    }
+    ORC_T acc = 0;
+    for (int64_t a = 0; a < r; ++a) {
+      xv[p0 + a] = -y[a];
+      acc += Lj[a] * xv[p0 + a];
+    }
+    xd[j] = 1.0 / d[j] - acc;
+  }
+  free(y);
+  return status;
+}
+
+/*
+ * Solve A x = b with A = L D L^T (in place on b): L z = b, z /= d, L^T x = z.
+ * This is the direct inversion of Eq. (6) one right-hand side at a time,
+ * used to check columns of the inverse.
+ */
+int ORC_SFX(orc_solve)(int32_t n, const int64_t* lcp, const int32_t* lri, const ORC_T* lv,
+                       const ORC_T* d, ORC_T* b) {
+  for (int32_t j = 0; j < n; ++j)
+    for (int64_t p = lcp[j]; p < lcp[j + 1]; ++p) b[lri[p]] -= lv[p] * b[j];
+  for (int32_t j = 0; j < n; ++j) b[j] /= d[j];
+  for (int32_t j = n - 1; j >= 0; --j) {
+    ORC_T acc = b[j];
+    for (int64_t p = lcp[j]; p < lcp[j + 1]; ++p) acc -= lv[p] * b[lri[p]];
+    b[j] = acc;
+  }
+  return 0;
+}
