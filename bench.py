@@ -1,0 +1,301 @@
+"""Benchmark: selected inversion of the 80^3 7-point grid Laplacian (n =
+512,000, FP64) on one GB300, level-scheduled vs one supernode per launch.
+
+One step = one full selected inversion (normalisation pass + every level
+of the top-down sweep, Algorithm 3) of the already factored matrix, inputs
+resident in HBM.  Factorisation and symbolic analysis happen once, before
+the timed region (the paper times the phases separately, Section 4.2).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the plain column selected inversion) on a bounded sample of the same
+workload family instead.  Multi-GPU (torchrun) runs independent replicas:
+the method has no exchange step on one matrix in this design.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "selinv ms & FP64 TFLOP/s (frac of peak), batched vs plain, err<=1e-10"
+# FP64 peak measured on this machine's GB300: cuBLAS DGEMM 8192^3 (torch.matmul
+# float64) and mma.sync m8n8k4 f64 throughput both ~1.10 TFLOP/s; see
+# profiles/fp64_peak_gb300.md.
+FP64_PEAK_TFLOPS = 1.10
+WORKLOAD = ("grid3d_80: 80^3 7-point Laplacian, n=512000, diag 6+U(0.01,0.1), geometric nested "
+            "dissection, relaxed supernodes of width <= 128, FP64")
+# Oracle sample for the CPU baseline: the same grid family at a size the
+# scalar oracle finishes in about 10-30 s.
+CPU_SAMPLE_SIDE = 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=80)
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample_tflops(side=CPU_SAMPLE_SIDE):
+    """Time the oracle's column selected inversion (its factorisation done
+    first, untimed) on the side^3 member of the workload family; return
+    (TFLOP/s by the algorithmic count of that instance, seconds, flops)."""
+    import oracle
+    import synth
+    p = synth.config1(side)
+    sym = oracle.analyse(p.n, p.colptr, p.rowind, 128, 1)
+    lcp, lri = oracle.supernodal_pattern(p.n, sym["sn_start"], sym["rcount"], sym["rrows"])
+    lv, d = oracle.ldlt(p.n, sym["colptr"], sym["rowind"], p.values, lcp, lri)
+    s = np.diff(sym["sn_start"]).astype(float)
+    r = sym["rcount"].astype(float)
+    flops = float(np.sum(2 * r * r * s + 3 * r * s * s + 2.0 / 3.0 * s ** 3))
+    t0 = time.perf_counter()
+    oracle.selinv(p.n, lcp, lri, lv, d)
+    dt = time.perf_counter() - t0
+    return flops / dt / 1e12, dt, flops
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    sample = (f"oracle column selected inversion (single thread, factorisation untimed) of the "
+              f"{CPU_SAMPLE_SIDE}^3 member of the same 7-point grid family (n={CPU_SAMPLE_SIDE ** 3}); "
+              f"TFLOP/s by the supernodal algorithmic flop count of that instance")
+    for _ in range(args.warmup):
+        oracle_sample_tflops()
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, dt, fl = oracle_sample_tflops()
+        vals.append(v)
+        secs.append(dt)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].isdigit():
+                    rows.append(f)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [int(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": int(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace('.', '').isdigit())
+                if any(r[3].replace('.', '').isdigit() for r in rows) else None}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import synth
+    import paper_1404_0447_gb300 as P
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.load_library()
+
+    prob = synth.config1(args.side)
+    h = P.SelInv(prob.n, prob.colptr, prob.rowind, max_sn_width=128, relax=P.RELAX_AMALG)
+    info = h.info
+    flops = info["flops_selinv"]
+    vals = torch.tensor(prob.values, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        h.factor(vals, stream=stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(mode, steps, record=False):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        if record:
+            h.set_timing(True)
+        e0.record(stream)
+        for _ in range(steps):
+            h.selinv(mode, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        kt = h.get_timing() if record else None
+        if record:
+            h.set_timing(False)
+        return ms, kt
+
+    # warm-up (level schedule, also captures nothing)
+    for _ in range(args.warmup):
+        h.selinv(P.LEVEL, stream=stream)
+    torch.cuda.synchronize()
+
+    # headline: level-scheduled sweep, kernel classes bracketed by events
+    with ClockSampler(local) as clk:
+        ms, (kms, kl) = timed(P.LEVEL, args.steps, record=True)
+    clocks = clk.summary()
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+
+    # graph-replayed level schedule and the plain one-supernode-per-launch schedule
+    h.selinv(P.GRAPH, stream=stream)
+    torch.cuda.synchronize()
+    ms_graph, _ = timed(P.GRAPH, max(1, args.steps))
+    ms_plain = None
+    if not args.no_plain:
+        h.selinv(P.PLAIN, stream=stream)
+        torch.cuda.synchronize()
+        ms_plain, _ = timed(P.PLAIN, max(1, args.plain_steps))
+
+    # end to end through host buffers: values H2D, factor, selinv, X panels D2H
+    e2e = None
+    if not args.no_e2e:
+        host_vals = torch.tensor(prob.values, dtype=torch.float64).pin_memory()
+        host_out = torch.empty(info["panel_entries"], dtype=torch.float64).pin_memory()
+        dev_vals = torch.empty_like(vals)
+        xbuf = torch.empty(info["panel_entries"], dtype=torch.float64, device=dev)
+        for it in range(2):
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                dev_vals.copy_(host_vals, non_blocking=True)
+                h.factor(dev_vals, stream=stream)
+                h.selinv(P.LEVEL, stream=stream)
+                h._check(h._lib.pselinv_get_panels(h._h, 0, P.ctypes.c_void_p(xbuf.data_ptr()),
+                                                   P._stream_ptr(stream)))
+                host_out.copy_(xbuf, non_blocking=True)
+            stream.synchronize()
+            t_e2e = time.perf_counter() - t0
+        e2e = {"value": flops / t_e2e / 1e12 * world, "unit": "TFLOP/s", "ms_per_step": 1e3 * t_e2e,
+               "h2d_bytes_per_step": int(host_vals.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
+               "includes": "pinned H2D of A's values, pselinv_factor, pselinv_selinv, D2H of the X panels"}
+
+    value = flops * world / (ms * 1e-3) / 1e12
+    # roofline of the dominant kernel (step 2, X_{C,K} = -X_{C,C} Lhat): algorithmic
+    # flops per launch over its event-timed average launch duration
+    g1_launches = max(1, int(kl[1]) // args.steps)
+    g1_ms_launch = kms[1] / args.steps / g1_launches
+    g1_flops_launch = info["flops_gemm1"] / g1_launches
+    achieved = g1_flops_launch / (g1_ms_launch * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "kernel": "k_gemm1 (step 2, FP64 DMMA m8n8k4)", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "measured cuBLAS DGEMM / DMMA throughput on this pool's GB300 (FP64 has no entry "
+                               "in MEASURED_PEAKS.json)",
+                "traffic": None, "launches_per_step": g1_launches,
+                "whole_step_frac": value / world / FP64_PEAK_TFLOPS}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, fl = oracle_sample_tflops()
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "seconds": dt,
+               "sample": f"oracle column selected inversion, 1 thread, on the {CPU_SAMPLE_SIDE}^3 member of the "
+                         f"same grid family ({fl:.3e} algorithmic flops)"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": prob.n, "nnz_a_lower": info["nnz_a"],
+                           "nnz_l": info["nnz_l"], "supernodes": info["nsn"], "levels": info["nlevels"],
+                           "flops_per_step": flops, "schedule": "level (one grouped launch per kernel per level)",
+                           "batched_ms": ms, "graph_ms": ms_graph, "plain_ms": ms_plain,
+                           "speedup_batched_vs_plain": ms_plain / ms if ms_plain else None,
+                           "kernel_ms_per_step": {"normalise": kms[0] / args.steps, "step2_gemm1": kms[1] / args.steps,
+                                                  "step3_partials": kms[2] / args.steps,
+                                                  "step3_finish": kms[3] / args.steps},
+                           "l2": "no flush: the X panels (%.1f GB) exceed L2 (129 MB)" % (info["panel_entries"] * 8 / 1e9),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(sum(kl)), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * pselinv -- supernodal selected inversion of sparse symmetric matrices on
+ * one NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * Method: L. Lin, M. Jacquelin, C. Yang, "PSelInv -- A Distributed Memory
+ * Parallel Algorithm for Selected Inversion: the Symmetric Case"
+ * (arXiv 1404.0447).  Given A = L D L^T (pivot-free, symmetric permutation
+ * only; Section 4), the library computes every entry of A^{-1} on the
+ * pattern of L + L^T (Section 1, Eq. 1 and the superset remark that
+ * follows it) by the supernodal recurrence of Algorithm 1 in the symmetric
+ * form of Eq. 14:
+ *
+ *   step 1  Lhat_{C,K} = L_{C,K} (L_{K,K})^{-1}
+ *   step 2  X_{C,K}    = - X_{C,C} Lhat_{C,K}
+ *   step 3  X_{K,K}    = L_{K,K}^{-T} D_K^{-1} L_{K,K}^{-1} - Lhat_{C,K}^T X_{C,K},
+ *           then X_{K,K} <- (X_{K,K} + X_{K,K}^T) / 2   (end of Section 2.1)
+ *   step 4  X_{K,C} = X_{C,K}^T (not stored: lower triangle only)
+ *
+ * supernodes taken level by level in the priority order of Algorithm 2.
+ * Complex matrices are complex symmetric: all transposes are plain.
+ *
+ * Conventions for every entry point:
+ *  - Status: 0 = PSELINV_OK, < 0 = error (PSELINV_ERR_*).  After an error,
+ *    pselinv_last_error(handle) returns a message (and, for a bad pivot,
+ *    the column).  No entry point aborts or traps.
+ *  - Host pointers ("h_") are read during the call and may be freed after
+ *    it returns; device pointers ("d_") must stay valid until the work
+ *    enqueued on the given stream has completed.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default).
+ *  - Values are laid out batch-major: member b of a batch of B matrices
+ *    sharing one pattern starts at b * nnz (elements of the dtype).
+ *  - complex128 values are interleaved (re, im) pairs of doubles.
+ *  - There is no CPU fallback: without a usable GPU the numeric entry
+ *    points return PSELINV_ERR_CUDA.
+ *  - A handle may be used by one host thread at a time.
+ */
+#ifndef PSELINV_H
+#define PSELINV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PSELINV_OK 0
+#define PSELINV_ERR_ARG (-1)        /* bad argument (null pointer, size, option) */
+#define PSELINV_ERR_NOT_LOWER (-2)  /* pattern is not lower CSC, sorted, diagonal first */
+#define PSELINV_ERR_ZERO_PIVOT (-3) /* a pivot d_j is exactly zero */
+#define PSELINV_ERR_NONFINITE (-4)  /* a pivot d_j is Inf or NaN */
+#define PSELINV_ERR_OOM (-5)        /* device allocation failed */
+#define PSELINV_ERR_CUDA (-6)       /* CUDA runtime error or no device */
+#define PSELINV_ERR_TIMEOUT (-7)    /* a bounded device wait ran out */
+#define PSELINV_ERR_STATE (-8)      /* call out of order (e.g. selinv before factor) */
+
+/* value types */
+#define PSELINV_F64 0
+#define PSELINV_C128 1
+
+/* supernode relaxation (Section 2.1: width cap plus merging of nearly
+   identical patterns) */
+#define PSELINV_RELAX_NONE 0  /* fundamental supernodes, split at the width cap */
+#define PSELINV_RELAX_AMALG 1 /* merge child into parent (rule in pselinv_analyze) */
+
+/* selected-inversion schedules (Algorithm 3 and Section 3.3) */
+#define PSELINV_PLAIN 0 /* one supernode per launch, reverse postorder */
+#define PSELINV_LEVEL 1 /* one grouped launch per kernel per level of Algorithm 2 */
+#define PSELINV_GRAPH 2 /* the LEVEL sequence captured once into a CUDA graph and replayed */
+
+typedef struct pselinv_handle pselinv_handle;
+
+typedef struct {
+  int32_t dtype;          /* PSELINV_F64 or PSELINV_C128 */
+  int32_t batch;          /* B >= 1 matrices sharing the pattern (e.g. poles H - z_l I) */
+  int32_t max_sn_width;   /* width cap w_max, 1..128; 0 means 128 */
+  int32_t relax;          /* PSELINV_RELAX_NONE or PSELINV_RELAX_AMALG */
+  int32_t small_cutoff;   /* reserved for the small/large path switch; < 0 = automatic */
+  int32_t debug_checks;   /* nonzero: kernels bounds-check every index and report */
+  int64_t spin_limit_ns;  /* limit for bounded device waits; <= 0 = 1e9 */
+} pselinv_opts;
+
+/* Sizes and work counts of an analysed handle. */
+typedef struct {
+  int64_t n;              /* matrix order */
+  int64_t nnz_a;          /* entries of A's lower triangle (diagonal included) */
+  int64_t nnz_l;          /* entries of the supernodal L pattern, lower, diagonal included */
+  int64_t panel_entries;  /* sum over supernodes of (s + r) * s: one panel array */
+  int64_t relidx_len;     /* relative-index entries */
+  int32_t nsn;            /* supernodes */
+  int32_t nlevels;        /* priority lists of Algorithm 2 */
+  int32_t max_width;      /* widest supernode */
+  int32_t batch;
+  int64_t max_r;          /* largest |C| */
+  double flops_selinv;    /* sum_K 2 r^2 s + 3 r s^2 + 2/3 s^3 (real flops per matrix; x4 for complex) */
+  double flops_gemm1;     /* sum_K 2 r^2 s */
+  double bytes_selinv;    /* algorithmic HBM bytes of one selinv (per matrix) */
+  int64_t device_bytes;   /* device memory the handle holds (after factor) */
+} pselinv_info;
+
+/* Read-only view of the symbolic analysis, owned by the handle (valid until
+   pselinv_destroy).  Supernodes are numbered in column order; all arrays
+   are host memory. */
+typedef struct {
+  int64_t n;
+  int32_t nsn;
+  int32_t nlevels;
+  const int32_t* perm;      /* [n] internal index k is user index perm[k] (user perm then postorder) */
+  const int32_t* parent;    /* [n] column elimination tree (Section 2.2), -1 = root */
+  const int32_t* sn_start;  /* [nsn+1] first column of each supernode */
+  const int32_t* sn_parent; /* [nsn] supernodal tree, -1 = root */
+  const int32_t* sigma;     /* [nsn] priority numbers of Algorithm 2 (1 = root) */
+  const int64_t* rowptr;    /* [nsn+1] offsets into rows */
+  const int32_t* rows;      /* R(K): sorted rows below supernode K (the set C of Alg. 1) */
+  const int64_t* panel_off; /* [nsn+1] element offset of each (s+r) x s column-major panel */
+  const int64_t* relptr;    /* [nsn+1] offsets into relidx */
+  const int32_t* relidx;    /* relative indices, see pselinv_analyze */
+  const int32_t* nblk;      /* [nsn] ancestor blocks of each C */
+  const int32_t* level_ptr; /* [nlevels+1] offsets into level_sn */
+  const int32_t* level_sn;  /* [nsn] supernodes of level k (k = 0 is sigma 1), costliest first */
+} pselinv_symbolic;
+
+/* Fill *o with defaults: F64, batch 1, w_max 128, RELAX_AMALG, automatic
+   cutoff, no debug checks, 1 s spin limit. */
+void pselinv_default_opts(pselinv_opts* o);
+
+/*
+ * Symbolic analysis (host only; no device work until pselinv_factor).
+ * Section 2.1 (supernodes), Section 2.2 (elimination tree), Algorithm 1
+ * step 0 (the sets C), Algorithm 2 (priority lists).
+ *
+ * n                order of A (1 <= n < 2^31)
+ * h_colptr[n+1]    lower-CSC column pointers of A (int64)
+ * h_rowind[nnz]    row indices, sorted inside each column, diagonal first
+ * h_perm[n]        optional symmetric ordering (internal k = user h_perm[k]);
+ *                  NULL = identity.  The elimination tree is then postordered
+ *                  (children in increasing order) and that postorder is
+ *                  composed into the ordering.
+ * opts             NULL = defaults
+ * out              receives the handle (caller destroys it)
+ *
+ * Supernode rule: (1) fundamental supernodes: column j+1 joins j's
+ * supernode iff parent(j) = j+1, j is j+1's only child and
+ * |struct(j)| = |struct(j+1)| + 1; (2) with RELAX_AMALG, walking the
+ * supernodes in column order, the current node K merges into the next node
+ * P if P contains parent(last(K)), width(K)+width(P) <= w_max and either
+ * the merged width is <= 8 or its explicit zeros are <= 5% of its stored
+ * entries (a node of width s with r rows below stores s(s+1)/2 + s r);
+ * (3) nodes wider than w_max are split into chunks of w_max from the left.
+ *
+ * Relative indices: for supernode K with rows below C (|C| = r), split C
+ * into maximal runs lying in one supernode J ("blocks"); for a block
+ * starting at position p and every i in [p, r) the entry is the position of
+ * C[i] in J's panel rows (J's columns, then R(J)); blocks and supernodes
+ * are concatenated in order.
+ *
+ * Errors: ERR_ARG (null pointers, n out of range, bad options),
+ * ERR_NOT_LOWER (pattern not lower CSC / unsorted / missing diagonal /
+ * perm not a permutation).
+ */
+int pselinv_analyze(int64_t n, const int64_t* h_colptr, const int32_t* h_rowind,
+                    const int32_t* h_perm, const pselinv_opts* opts, pselinv_handle** out);
+
+/*
+ * Numeric factorisation A = L D L^T on the device (supernodal, level by
+ * level from the leaves; no pivoting, Section 4).  Not the optimisation
+ * target of this library; it produces the input of the selected inversion.
+ *
+ * d_values   device, batch x nnz_a values of A's lower CSC in the user's
+ *            order (dtype of the handle)
+ * Errors: ERR_ZERO_PIVOT / ERR_NONFINITE (first bad column, in internal
+ * order, reported by pselinv_last_error), ERR_OOM, ERR_CUDA.  The call
+ * synchronises the stream once at the end to read the pivot status.
+ */
+int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream);
+
+/*
+ * Selected inversion (Algorithm 3's normalisation pass, then steps 2-3 of
+ * Algorithm 1 for every supernode, top-down in the priority order of
+ * Algorithm 2).  The result stays in the handle's X panels (same layout as
+ * the L panels: per supernode an (s + r) x s column-major block, rows = the
+ * supernode's columns then R(K); the s x s diagonal block is full and
+ * symmetric).  mode: PSELINV_PLAIN, PSELINV_LEVEL or PSELINV_GRAPH.
+ * Enqueues work only; no host synchronisation.  ERR_STATE before factor.
+ */
+int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream);
+
+/*
+ * Copy panels to caller memory: which = 0 for X (after selinv), 1 for L
+ * (after factor; unit diagonal not stored, D on the diagonal positions).
+ * d_out: device, batch x panel_entries elements of the dtype.
+ */
+int pselinv_get_panels(pselinv_handle* h, int32_t which, void* d_out, void* stream);
+
+/*
+ * Gather the selected inverse at the positions of A's lower CSC in the
+ * user's order (the requested set of Eq. 1): d_out[b * nnz_a + q] =
+ * (A_b^{-1})_{i,j} for the q-th stored entry (i, j).  Device pointer,
+ * batch x nnz_a elements.  This is also the gradient of log det A with
+ * respect to each stored entry read as a full-matrix entry.
+ */
+int pselinv_get_selected(pselinv_handle* h, void* d_out, void* stream);
+
+/*
+ * log det A = sum_j log d_j (Section 2.1's LDL^T).  h_out (host) receives
+ * per batch member two doubles: F64 -> (sum log|d_j|, number of negative
+ * pivots); C128 -> (real, imaginary) of the sum of principal logs.
+ * Synchronises the stream.
+ */
+int pselinv_logdet(pselinv_handle* h, double* h_out, void* stream);
+
+/*
+ * Adjoint of the selected inversion: given G (device, batch x
+ * panel_entries, same panel layout as X; only the lower-triangle entries
+ * of each panel are read, G symmetric), returns in d_gradA (device,
+ * batch x nnz_a, user order) the values of -(X G X) at A's stored
+ * positions, i.e. the gradient of <G, X> (bilinear pairing over the full
+ * symmetric selected pattern) with respect to each stored entry read as a
+ * full-matrix entry.  Requires a prior selinv.  Uses L and D, recomputes
+ * Lhat; reverse sweep leaves -> root, then the LDL^T adjoint root -> leaves.
+ */
+int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, void* d_gradA, void* stream);
+
+/*
+ * Kernel timing of the selected inversion (measurement support, no paper
+ * counterpart beyond Section 4.2's per-phase timings).  enable != 0 makes
+ * every later pselinv_selinv in PLAIN or LEVEL mode record CUDA events on
+ * its stream around each kernel class; pselinv_get_timing waits for them
+ * and returns in h_ms[PSELINV_NTIMERS] the summed milliseconds since the
+ * previous pselinv_get_timing (or enable), in h_launches[PSELINV_NTIMERS]
+ * the kernel launches per class, and resets both.  GRAPH mode does not
+ * record.  Classes:
+ *   0 normalisation (diagonal inverses, Lhat)   1 step 2 (X_{C,K})
+ *   2 step 3 partial products                    3 step 3 finish (symmetrise)
+ */
+#define PSELINV_NTIMERS 4
+int pselinv_set_timing(pselinv_handle* h, int32_t enable);
+int pselinv_get_timing(pselinv_handle* h, double* h_ms, int64_t* h_launches);
+
+int pselinv_get_info(const pselinv_handle* h, pselinv_info* info);
+int pselinv_export_symbolic(const pselinv_handle* h, pselinv_symbolic* view);
+
+/* Frees everything the handle owns; NULL is allowed. */
+void pselinv_destroy(pselinv_handle* h);
+
+/* Message for the last error on h (or on the last failed analyze if h is
+   NULL); never NULL. */
+const char* pselinv_last_error(const pselinv_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSELINV_H */

@@ -1,0 +1,213 @@
+"""Python binding of the pselinv C ABI (include/pselinv.h).
+
+Argument marshalling only: every step of the factorisation and of the
+selected inversion runs in the library's CUDA kernels.  PyTorch provides
+device memory and streams.  There is no CPU fallback: if the compiled
+library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpselinv.so")
+
+PSELINV_OK = 0
+ERRORS = {-1: "ERR_ARG", -2: "ERR_NOT_LOWER", -3: "ERR_ZERO_PIVOT", -4: "ERR_NONFINITE",
+          -5: "ERR_OOM", -6: "ERR_CUDA", -7: "ERR_TIMEOUT", -8: "ERR_STATE"}
+F64, C128 = 0, 1
+RELAX_NONE, RELAX_AMALG = 0, 1
+PLAIN, LEVEL, GRAPH = 0, 1, 2
+
+EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_factor", "pselinv_selinv",
+            "pselinv_get_panels", "pselinv_get_selected", "pselinv_logdet", "pselinv_selinv_adjoint",
+            "pselinv_set_timing", "pselinv_get_timing", "pselinv_get_info", "pselinv_export_symbolic",
+            "pselinv_destroy", "pselinv_last_error"]
+
+
+class PselinvError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("batch", ctypes.c_int32), ("max_sn_width", ctypes.c_int32),
+                ("relax", ctypes.c_int32), ("small_cutoff", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
+                ("spin_limit_ns", ctypes.c_int64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz_a", ctypes.c_int64), ("nnz_l", ctypes.c_int64),
+                ("panel_entries", ctypes.c_int64), ("relidx_len", ctypes.c_int64), ("nsn", ctypes.c_int32),
+                ("nlevels", ctypes.c_int32), ("max_width", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("max_r", ctypes.c_int64), ("flops_selinv", ctypes.c_double), ("flops_gemm1", ctypes.c_double),
+                ("bytes_selinv", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+_P32 = ctypes.POINTER(ctypes.c_int32)
+_P64 = ctypes.POINTER(ctypes.c_int64)
+
+
+class Symbolic(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nsn", ctypes.c_int32), ("nlevels", ctypes.c_int32),
+                ("perm", _P32), ("parent", _P32), ("sn_start", _P32), ("sn_parent", _P32), ("sigma", _P32),
+                ("rowptr", _P64), ("rows", _P32), ("panel_off", _P64), ("relptr", _P64), ("relidx", _P32),
+                ("nblk", _P32), ("level_ptr", _P32), ("level_sn", _P32)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load the compiled library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"pselinv library not built ({LIB_PATH} missing); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    L.pselinv_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.pselinv_default_opts.restype = None
+    L.pselinv_analyze.argtypes = [ctypes.c_int64, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
+    L.pselinv_factor.argtypes = [vp, vp, vp]
+    L.pselinv_selinv.argtypes = [vp, ctypes.c_int32, vp]
+    L.pselinv_get_panels.argtypes = [vp, ctypes.c_int32, vp, vp]
+    L.pselinv_get_selected.argtypes = [vp, vp, vp]
+    L.pselinv_logdet.argtypes = [vp, vp, vp]
+    L.pselinv_selinv_adjoint.argtypes = [vp, vp, vp, vp]
+    L.pselinv_set_timing.argtypes = [vp, ctypes.c_int32]
+    L.pselinv_get_timing.argtypes = [vp, vp, vp]
+    L.pselinv_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.pselinv_export_symbolic.argtypes = [vp, ctypes.POINTER(Symbolic)]
+    L.pselinv_destroy.argtypes = [vp]
+    L.pselinv_destroy.restype = None
+    L.pselinv_last_error.argtypes = [vp]
+    L.pselinv_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load_library().pselinv_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class SelInv:
+    """One analysed pattern (and its device state).
+
+    ``SelInv(n, colptr, rowind, perm=None, **opts)`` runs pselinv_analyze on
+    host numpy arrays.  ``factor(values)`` takes a CUDA tensor of
+    batch x nnz values (user order), ``selinv(mode)`` enqueues the selected
+    inversion, ``panels()`` / ``selected()`` return CUDA tensors.
+    """
+
+    def __init__(self, n, colptr, rowind, perm=None, **opts):
+        self._lib = load_library()
+        self.opts = default_opts(**opts)
+        cp = np.ascontiguousarray(colptr, np.int64)
+        ri = np.ascontiguousarray(rowind, np.int32)
+        pp = None if perm is None else np.ascontiguousarray(perm, np.int32)
+        h = ctypes.c_void_p()
+        rc = self._lib.pselinv_analyze(int(n), _ptr(cp), _ptr(ri), None if pp is None else _ptr(pp),
+                                       ctypes.byref(self.opts), ctypes.byref(h))
+        if rc != PSELINV_OK:
+            raise PselinvError(rc, self._lib.pselinv_last_error(None).decode())
+        self._h = h
+        self.n = int(n)
+
+    def _check(self, rc):
+        if rc != PSELINV_OK:
+            raise PselinvError(rc, self._lib.pselinv_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pselinv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- introspection ----
+    @property
+    def info(self) -> dict:
+        inf = Info()
+        self._check(self._lib.pselinv_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in Info._fields_}
+
+    def symbolic(self) -> dict:
+        v = Symbolic()
+        self._check(self._lib.pselinv_export_symbolic(self._h, ctypes.byref(v)))
+        n, nsn, nl = v.n, v.nsn, v.nlevels
+
+        def arr(p, k):
+            return np.ctypeslib.as_array(p, shape=(k,)).copy() if k > 0 else np.zeros(0, np.int64)
+
+        rowptr = arr(v.rowptr, nsn + 1)
+        relptr = arr(v.relptr, nsn + 1)
+        return dict(n=n, nsn=nsn, nlevels=nl, perm=arr(v.perm, n), parent=arr(v.parent, n),
+                    sn_start=arr(v.sn_start, nsn + 1), sn_parent=arr(v.sn_parent, nsn),
+                    sigma=arr(v.sigma, nsn), rowptr=rowptr, rows=arr(v.rows, int(rowptr[-1])),
+                    panel_off=arr(v.panel_off, nsn + 1), relptr=relptr, relidx=arr(v.relidx, int(relptr[-1])),
+                    nblk=arr(v.nblk, nsn), level_ptr=arr(v.level_ptr, nl + 1), level_sn=arr(v.level_sn, nsn))
+
+    # ---- numeric ----
+    def factor(self, values, stream=None):
+        import torch
+        assert values.is_cuda and values.dtype == torch.float64 and values.is_contiguous()
+        self._check(self._lib.pselinv_factor(self._h, ctypes.c_void_p(values.data_ptr()), _stream_ptr(stream)))
+
+    def selinv(self, mode=LEVEL, stream=None):
+        self._check(self._lib.pselinv_selinv(self._h, int(mode), _stream_ptr(stream)))
+
+    def panels(self, which=0, stream=None):
+        import torch
+        out = torch.empty(self.opts.batch * self.info["panel_entries"], dtype=torch.float64, device="cuda")
+        self._check(self._lib.pselinv_get_panels(self._h, int(which), ctypes.c_void_p(out.data_ptr()),
+                                                 _stream_ptr(stream)))
+        return out.view(self.opts.batch, -1)
+
+    def selected(self, out=None, stream=None):
+        import torch
+        nnz = self.info["nnz_a"]
+        if out is None:
+            out = torch.empty(self.opts.batch * nnz, dtype=torch.float64, device="cuda")
+        self._check(self._lib.pselinv_get_selected(self._h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out.view(self.opts.batch, nnz)
+
+    def set_timing(self, enable=True):
+        self._check(self._lib.pselinv_set_timing(self._h, 1 if enable else 0))
+
+    def get_timing(self):
+        """(ms per kernel class, launches per class) since the last call; classes:
+        normalisation, step 2, step 3 partial products, step 3 finish."""
+        ms = np.zeros(4, np.float64)
+        ln = np.zeros(4, np.int64)
+        self._check(self._lib.pselinv_get_timing(self._h, _ptr(ms), _ptr(ln)))
+        return ms, ln
+
+    def logdet(self, stream=None):
+        out = np.zeros(2 * self.opts.batch, np.float64)
+        self._check(self._lib.pselinv_logdet(self._h, _ptr(out), _stream_ptr(stream)))
+        return out.reshape(self.opts.batch, 2)

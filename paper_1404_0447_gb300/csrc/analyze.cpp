@@ -1,0 +1,482 @@
+// Host symbolic analysis for the supernodal selected inversion.
+//
+//  - elimination tree (Section 2.2; column version), postorder;
+//  - column counts |struct(j)| by row-subtree traversal;
+//  - supernode partition (Section 2.1: fundamental supernodes, relaxed by
+//    merging and a width cap; the rule is spelled out in pselinv.h);
+//  - supernodal rows R(K) (the set C of Algorithm 1, step 0) by the
+//    supernodal recursion R(K) = (A rows of K U R(children)) beyond K;
+//  - priority lists of Algorithm 2;
+//  - relative indices of each C inside its ancestor supernodes (Section 3.1's
+//    non-contiguous row lists), the per-column gather descriptors and the
+//    value map from A's entries into the panels;
+//  - task lists of the grouped launches and the work counts.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "internal.h"
+
+namespace psi {
+namespace {
+
+int fail(pselinv_handle* h, int code, const std::string& msg) {
+  h->err = msg;
+  return code;
+}
+
+// Lower pattern of P A P^T with, for every entry, its position in the
+// caller's arrays.
+struct Pattern {
+  std::vector<int64_t> cp;
+  std::vector<int32_t> ri;
+  std::vector<int64_t> src;
+};
+
+Pattern permute_pattern(int64_t n, const int64_t* cp, const int32_t* ri,
+                        const std::vector<int32_t>& inv) {
+  Pattern P;
+  const int64_t nnz = cp[n];
+  P.cp.assign(n + 1, 0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
+      int32_t a = inv[ri[p]], b = inv[j];
+      P.cp[std::min(a, b) + 1]++;
+    }
+  for (int64_t j = 0; j < n; ++j) P.cp[j + 1] += P.cp[j];
+  P.ri.resize(nnz);
+  P.src.resize(nnz);
+  std::vector<int64_t> next(P.cp.begin(), P.cp.end() - 1);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
+      int32_t a = inv[ri[p]], b = inv[j];
+      int64_t q = next[std::min(a, b)]++;
+      P.ri[q] = std::max(a, b);
+      P.src[q] = p;
+    }
+  // sort every column by row (columns are short; insertion sort on pairs)
+  for (int64_t j = 0; j < n; ++j) {
+    for (int64_t p = P.cp[j] + 1; p < P.cp[j + 1]; ++p) {
+      int32_t r = P.ri[p];
+      int64_t s = P.src[p];
+      int64_t q = p - 1;
+      while (q >= P.cp[j] && P.ri[q] > r) {
+        P.ri[q + 1] = P.ri[q];
+        P.src[q + 1] = P.src[q];
+        --q;
+      }
+      P.ri[q + 1] = r;
+      P.src[q + 1] = s;
+    }
+  }
+  return P;
+}
+
+// Row lists of a lower pattern (the columns j < i with (i, j) stored).
+void row_lists(int64_t n, const Pattern& P, std::vector<int64_t>& rp, std::vector<int32_t>& rc) {
+  rp.assign(n + 1, 0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = P.cp[j] + 1; p < P.cp[j + 1]; ++p) rp[P.ri[p] + 1]++;
+  for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+  rc.resize(rp[n]);
+  std::vector<int64_t> next(rp.begin(), rp.end() - 1);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = P.cp[j] + 1; p < P.cp[j + 1]; ++p) rc[next[P.ri[p]]++] = (int32_t)j;
+}
+
+// Elimination tree with a disjoint-set forest: scanning rows in order, each
+// A_ij (j < i) joins the set holding j -- whose current tree root becomes a
+// child of i -- to i's set.
+std::vector<int32_t> etree(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& rc) {
+  std::vector<int32_t> parent(n, -1), ds(n), top(n);
+  auto find = [&](int32_t x) {
+    while (ds[x] != x) {
+      ds[x] = ds[ds[x]];  // path halving
+      x = ds[x];
+    }
+    return x;
+  };
+  for (int64_t i = 0; i < n; ++i) {
+    ds[i] = (int32_t)i;
+    top[i] = (int32_t)i;
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+      int32_t set = find(rc[q]);
+      int32_t root = top[set];
+      if (root != i) {
+        parent[root] = (int32_t)i;
+        int32_t mine = find((int32_t)i);
+        ds[set] = mine;
+        top[mine] = (int32_t)i;
+      }
+    }
+  }
+  return parent;
+}
+
+// Postorder (children in increasing order, roots in increasing order) by a
+// stackless threaded walk over first-child / next-sibling links.
+std::vector<int32_t> postorder(int64_t n, const std::vector<int32_t>& parent) {
+  std::vector<int32_t> first(n, -1), sib(n, -1), roots;
+  for (int64_t j = n - 1; j >= 0; --j) {
+    if (parent[j] >= 0) {
+      sib[j] = first[parent[j]];
+      first[parent[j]] = (int32_t)j;
+    }
+  }
+  for (int64_t j = 0; j < n; ++j)
+    if (parent[j] < 0) roots.push_back((int32_t)j);
+  std::vector<int32_t> post;
+  post.reserve(n);
+  for (int32_t r : roots) {
+    int32_t v = r;
+    while (first[v] >= 0) v = first[v];
+    for (;;) {
+      post.push_back(v);
+      if (v == r) break;
+      if (sib[v] >= 0) {
+        v = sib[v];
+        while (first[v] >= 0) v = first[v];
+      } else {
+        v = parent[v];
+      }
+    }
+  }
+  return post;
+}
+
+double sn_flops(double s, double r) { return 2 * r * r * s + 3 * r * s * s + 2.0 / 3.0 * s * s * s; }
+
+}  // namespace
+
+int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
+            const int32_t* uperm) {
+  if (n < 1 || n >= (int64_t)1 << 31) return fail(h, PSELINV_ERR_ARG, "n out of range");
+  if (!cp || !ri) return fail(h, PSELINV_ERR_ARG, "null pattern pointer");
+  if (cp[0] != 0) return fail(h, PSELINV_ERR_NOT_LOWER, "colptr[0] != 0");
+  for (int64_t j = 0; j < n; ++j) {
+    if (cp[j + 1] <= cp[j]) return fail(h, PSELINV_ERR_NOT_LOWER, "empty column (missing diagonal)");
+    if (ri[cp[j]] != j) return fail(h, PSELINV_ERR_NOT_LOWER, "diagonal not first in column " + std::to_string(j));
+    for (int64_t p = cp[j] + 1; p < cp[j + 1]; ++p)
+      if (ri[p] <= ri[p - 1] || ri[p] >= n)
+        return fail(h, PSELINV_ERR_NOT_LOWER, "rows not increasing / out of range in column " + std::to_string(j));
+  }
+  const pselinv_opts& o = h->opts;
+  const int wcap = o.max_sn_width == 0 ? kMaxWidth : o.max_sn_width;
+  if (wcap < 1 || wcap > kMaxWidth) return fail(h, PSELINV_ERR_ARG, "max_sn_width must be 0..128");
+  if (o.relax != PSELINV_RELAX_NONE && o.relax != PSELINV_RELAX_AMALG)
+    return fail(h, PSELINV_ERR_ARG, "bad relax mode");
+
+  h->n = n;
+  h->nnz_a = cp[n];
+  std::vector<int32_t> perm(n), inv(n, -1);
+  if (uperm) {
+    for (int64_t k = 0; k < n; ++k) {
+      int32_t u = uperm[k];
+      if (u < 0 || u >= n || inv[u] >= 0) return fail(h, PSELINV_ERR_NOT_LOWER, "perm is not a permutation");
+      inv[u] = (int32_t)k;
+      perm[k] = u;
+    }
+  } else {
+    std::iota(perm.begin(), perm.end(), 0);
+    std::iota(inv.begin(), inv.end(), 0);
+  }
+
+  // ---- elimination tree and postorder ----
+  Pattern P = permute_pattern(n, cp, ri, inv);
+  std::vector<int64_t> rp;
+  std::vector<int32_t> rc;
+  row_lists(n, P, rp, rc);
+  std::vector<int32_t> parent = etree(n, rp, rc);
+  std::vector<int32_t> post = postorder(n, parent);
+  bool ident = true;
+  for (int64_t k = 0; k < n && ident; ++k) ident = post[k] == k;
+  if (!ident) {
+    std::vector<int32_t> perm2(n);
+    for (int64_t k = 0; k < n; ++k) perm2[k] = perm[post[k]];
+    perm.swap(perm2);
+    for (int64_t k = 0; k < n; ++k) inv[perm[k]] = (int32_t)k;
+    P = permute_pattern(n, cp, ri, inv);
+    row_lists(n, P, rp, rc);
+    parent = etree(n, rp, rc);
+  }
+
+  // ---- column counts by row subtrees ----
+  std::vector<int64_t> cnt(n, 0);
+  {
+    std::vector<int32_t> mark(n, -1);
+    for (int64_t i = 0; i < n; ++i) {
+      mark[i] = (int32_t)i;
+      for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+        for (int32_t k = rc[q]; mark[k] != i; k = parent[k]) {
+          cnt[k]++;
+          mark[k] = (int32_t)i;
+        }
+    }
+  }
+
+  // ---- supernodes ----
+  std::vector<int32_t> nchild(n, 0);
+  for (int64_t j = 0; j < n; ++j)
+    if (parent[j] >= 0) nchild[parent[j]]++;
+  std::vector<int32_t> fund;
+  for (int64_t j = 0; j < n; ++j) {
+    bool joins = j > 0 && parent[j - 1] == j && nchild[j] == 1 && cnt[j - 1] == cnt[j] + 1;
+    if (!joins) fund.push_back((int32_t)j);
+  }
+  fund.push_back((int32_t)n);
+  // true entries of columns [a, b): sum of 1 + |struct(j)|
+  std::vector<int64_t> tpre(n + 1, 0);
+  for (int64_t j = 0; j < n; ++j) tpre[j + 1] = tpre[j] + 1 + cnt[j];
+  std::vector<int32_t> merged;
+  if (o.relax == PSELINV_RELAX_AMALG) {
+    const int64_t nf = (int64_t)fund.size() - 1;
+    int32_t cur = fund[0];
+    for (int64_t t = 0; t < nf; ++t) {
+      const int32_t last = fund[t + 1] - 1;
+      bool take = false;
+      if (t + 1 < nf) {
+        const int32_t pf = fund[t + 1], pl = fund[t + 2] - 1;
+        const int32_t par = parent[last];
+        if (par >= pf && par <= pl) {
+          const int64_t s = pl - cur + 1;
+          const int64_t stored = s * (s + 1) / 2 + s * cnt[pl];
+          const int64_t zeros = stored - (tpre[pl + 1] - tpre[cur]);
+          take = s <= wcap && (s <= 8 || 20 * zeros <= stored);
+        }
+      }
+      if (!take) {
+        merged.push_back(cur);
+        if (t + 1 < nf) cur = fund[t + 1];
+      }
+    }
+    merged.push_back((int32_t)n);
+  } else {
+    merged = fund;
+  }
+  std::vector<int32_t>& ss = h->sn_start;
+  ss.clear();
+  for (size_t t = 0; t + 1 < merged.size(); ++t)
+    for (int32_t c = merged[t]; c < merged[t + 1]; c += wcap) ss.push_back(c);
+  ss.push_back((int32_t)n);
+  const int32_t nsn = (int32_t)ss.size() - 1;
+  h->nsn = nsn;
+  std::vector<int32_t> col2sn(n);
+  for (int32_t k = 0; k < nsn; ++k)
+    for (int32_t j = ss[k]; j < ss[k + 1]; ++j) col2sn[j] = k;
+
+  // ---- supernodal rows R(K) and parents ----
+  h->rowptr.assign(nsn + 1, 0);
+  h->rows.clear();
+  h->sn_parent.assign(nsn, -1);
+  {
+    std::vector<std::vector<int32_t>> kids(nsn);
+    std::vector<int32_t> mark(n, -1), buf;
+    for (int32_t k = 0; k < nsn; ++k) {
+      const int32_t f = ss[k], l = ss[k + 1] - 1;
+      buf.clear();
+      for (int32_t j = f; j <= l; ++j)
+        for (int64_t p = P.cp[j] + 1; p < P.cp[j + 1]; ++p) {
+          int32_t i = P.ri[p];
+          if (i > l && mark[i] != k) { mark[i] = k; buf.push_back(i); }
+        }
+      for (int32_t c : kids[k])
+        for (int64_t p = h->rowptr[c]; p < h->rowptr[c + 1]; ++p) {
+          int32_t i = h->rows[p];
+          if (i > l && mark[i] != k) { mark[i] = k; buf.push_back(i); }
+        }
+      std::sort(buf.begin(), buf.end());
+      h->rows.insert(h->rows.end(), buf.begin(), buf.end());
+      h->rowptr[k + 1] = (int64_t)h->rows.size();
+      if (!buf.empty()) {
+        h->sn_parent[k] = col2sn[buf[0]];
+        kids[h->sn_parent[k]].push_back(k);
+      }
+    }
+  }
+
+  // ---- metadata, work counts, priority lists (Algorithm 2) ----
+  h->meta.assign(nsn, SnMeta{});
+  h->panel_off.assign(nsn + 1, 0);
+  std::vector<double> cost(nsn);
+  h->flops_selinv = h->flops_gemm1 = h->bytes_selinv = 0;
+  h->nnz_l = 0;
+  h->max_r = 0;
+  h->max_width = 0;
+  int64_t lhat = 0, linv = 0;
+  for (int32_t k = 0; k < nsn; ++k) {
+    SnMeta& m = h->meta[k];
+    m.f = ss[k];
+    m.s = ss[k + 1] - ss[k];
+    m.r = (int32_t)(h->rowptr[k + 1] - h->rowptr[k]);
+    m.nchunk = (m.r + kChunkRows - 1) / kChunkRows;
+    m.panel = h->panel_off[k];
+    h->panel_off[k + 1] = h->panel_off[k] + (int64_t)(m.s + m.r) * m.s;
+    m.lhat = lhat;
+    lhat += (int64_t)m.r * m.s;
+    m.linv = linv;
+    linv += (int64_t)m.s * m.s;
+    m.desc = h->rowptr[k];
+    const double s = m.s, r = m.r;
+    cost[k] = sn_flops(s, r);
+    h->flops_selinv += cost[k];
+    h->flops_gemm1 += 2 * r * r * s;
+    h->nnz_l += (int64_t)m.s * (m.s + 1) / 2 + (int64_t)m.s * m.r;
+    h->max_r = std::max<int64_t>(h->max_r, m.r);
+    h->max_width = std::max(h->max_width, m.s);
+  }
+  h->panel_total = h->panel_off[nsn];
+  h->lhat_total = lhat;
+  h->linv_total = linv;
+  h->sigma.assign(nsn, 0);
+  for (int32_t k = nsn - 1; k >= 0; --k)
+    h->sigma[k] = h->sn_parent[k] < 0 ? 1 : h->sigma[h->sn_parent[k]] + 1;
+  int32_t nl = 0;
+  for (int32_t k = 0; k < nsn; ++k) nl = std::max(nl, h->sigma[k]);
+  h->nlevels = nl;
+  h->level_ptr.assign(nl + 1, 0);
+  for (int32_t k = 0; k < nsn; ++k) h->level_ptr[h->sigma[k]]++;
+  for (int32_t l = 0; l < nl; ++l) h->level_ptr[l + 1] += h->level_ptr[l];
+  h->level_sn.assign(nsn, 0);
+  {
+    std::vector<int32_t> next(h->level_ptr.begin(), h->level_ptr.end() - 1);
+    for (int32_t k = 0; k < nsn; ++k) h->level_sn[next[h->sigma[k] - 1]++] = k;
+    for (int32_t l = 0; l < nl; ++l)
+      std::stable_sort(h->level_sn.begin() + h->level_ptr[l], h->level_sn.begin() + h->level_ptr[l + 1],
+                       [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  }
+
+  // ---- relative indices, gather descriptors ----
+  struct Blk {
+    int32_t k, j, p;
+    int64_t out;
+  };
+  std::vector<Blk> blks;
+  h->relptr.assign(nsn + 1, 0);
+  h->nblk.assign(nsn, 0);
+  int64_t tot = 0;
+  for (int32_t k = 0; k < nsn; ++k) {
+    const int32_t* C = h->rows.data() + h->rowptr[k];
+    const int32_t r = h->meta[k].r;
+    for (int32_t p = 0; p < r;) {
+      int32_t j = col2sn[C[p]];
+      int32_t q = p;
+      while (q < r && col2sn[C[q]] == j) ++q;
+      blks.push_back({k, j, p, tot});
+      tot += r - p;
+      h->nblk[k]++;
+      p = q;
+    }
+    h->relptr[k + 1] = tot;
+  }
+  h->relidx.assign(tot, -1);
+  h->desc.assign(h->rowptr[nsn], ColDesc{0, 0});
+  {
+    // bucket the blocks by their ancestor J, then fill with a position map of J
+    std::vector<int64_t> bptr(nsn + 1, 0);
+    for (const Blk& b : blks) bptr[b.j + 1]++;
+    for (int32_t k = 0; k < nsn; ++k) bptr[k + 1] += bptr[k];
+    std::vector<int32_t> order(blks.size());
+    std::vector<int64_t> next(bptr.begin(), bptr.end() - 1);
+    for (size_t t = 0; t < blks.size(); ++t) order[next[blks[t].j]++] = (int32_t)t;
+    std::vector<int32_t> pos(n, -1);
+    for (int32_t j = 0; j < nsn; ++j) {
+      if (bptr[j] == bptr[j + 1]) continue;
+      const SnMeta& mj = h->meta[j];
+      for (int32_t c = 0; c < mj.s; ++c) pos[mj.f + c] = c;
+      for (int32_t t = 0; t < mj.r; ++t) pos[h->rows[h->rowptr[j] + t]] = mj.s + t;
+      for (int64_t t = bptr[j]; t < bptr[j + 1]; ++t) {
+        const Blk& b = blks[order[t]];
+        const int32_t* C = h->rows.data() + h->rowptr[b.k];
+        const int32_t r = h->meta[b.k].r;
+        for (int32_t i = b.p; i < r; ++i) {
+          int32_t v = pos[C[i]];
+          if (v < 0) return fail(h, PSELINV_ERR_NOT_LOWER, "internal: structure not closed");
+          h->relidx[b.out + (i - b.p)] = v;
+        }
+        for (int32_t i = b.p; i < r && col2sn[C[i]] == j; ++i) {
+          ColDesc& d = h->desc[h->rowptr[b.k] + i];
+          d.col = mj.panel + (int64_t)(C[i] - mj.f) * (mj.s + mj.r);
+          d.rel = b.out - b.p;
+        }
+      }
+      for (int32_t c = 0; c < mj.s; ++c) pos[mj.f + c] = -1;
+      for (int32_t t = 0; t < mj.r; ++t) pos[h->rows[h->rowptr[j] + t]] = -1;
+    }
+  }
+  for (int32_t k = 0; k < nsn; ++k) {
+    const double s = h->meta[k].s, r = h->meta[k].r;
+    h->bytes_selinv += 8.0 * (r * (r + 1) / 2 + 2 * (s + r) * s) + 4.0 * (h->relptr[k + 1] - h->relptr[k]);
+  }
+
+  // ---- value map: A's stored entries -> panel offsets ----
+  h->valmap.assign(h->nnz_a, -1);
+  for (int64_t j = 0; j < n; ++j) {
+    const SnMeta& m = h->meta[col2sn[j]];
+    const int32_t* R = h->rows.data() + h->rowptr[col2sn[j]];
+    const int32_t ld = m.s + m.r;
+    for (int64_t p = P.cp[j]; p < P.cp[j + 1]; ++p) {
+      const int32_t i = P.ri[p];
+      int64_t pos;
+      if (i < m.f + m.s) {
+        pos = i - m.f;
+      } else {
+        const int32_t* it = std::lower_bound(R, R + m.r, i);
+        if (it == R + m.r || *it != i) return fail(h, PSELINV_ERR_NOT_LOWER, "internal: entry outside L");
+        pos = m.s + (it - R);
+      }
+      h->valmap[P.src[p]] = m.panel + (j - m.f) * (int64_t)ld + pos;
+    }
+  }
+
+  // ---- task lists ----
+  auto build = [&](TaskList& tl, auto&& emit) {
+    tl.tasks.clear();
+    tl.per_level.assign(nl, Range{});
+    tl.per_sn.assign(nsn, Range{});
+    for (int32_t l = 0; l < nl; ++l) {
+      tl.per_level[l].begin = (int64_t)tl.tasks.size();
+      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+        int32_t k = h->level_sn[t];
+        tl.per_sn[k].begin = (int64_t)tl.tasks.size();
+        emit(k, tl.tasks);
+        tl.per_sn[k].end = (int64_t)tl.tasks.size();
+      }
+      tl.per_level[l].end = (int64_t)tl.tasks.size();
+    }
+  };
+  auto rect = [&](int32_t k, std::vector<Task>& out) {  // r x s output tiles
+    const SnMeta& m = h->meta[k];
+    for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
+      for (int32_t n0 = 0; n0 < m.s; n0 += kTileN) out.push_back({k, m0, n0, 0});
+  };
+  build(h->t_lhat, rect);
+  build(h->t_gemm1, rect);
+  build(h->t_trsm, rect);
+  build(h->t_gemm2, [&](int32_t k, std::vector<Task>& out) {
+    const SnMeta& m = h->meta[k];
+    for (int32_t c = 0; c < m.nchunk; ++c)
+      for (int32_t m0 = 0; m0 < m.s; m0 += kTileM)
+        for (int32_t n0 = 0; n0 < m.s; n0 += kTileN) out.push_back({k, m0, n0, c});
+  });
+  build(h->t_schur, [&](int32_t k, std::vector<Task>& out) {
+    const SnMeta& m = h->meta[k];
+    for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
+      for (int32_t n0 = 0; n0 <= m0; n0 += kTileM) out.push_back({k, m0, n0, 0});
+  });
+  // level-local offsets of the step-3 partial products
+  h->part_max = 0;
+  for (int32_t l = 0; l < nl; ++l) {
+    int64_t off = 0;
+    for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+      SnMeta& m = h->meta[h->level_sn[t]];
+      m.part = off;
+      off += (int64_t)m.nchunk * m.s * m.s;
+    }
+    h->part_max = std::max(h->part_max, off);
+  }
+  h->perm = perm;
+  h->parent = parent;
+  return PSELINV_OK;
+}
+
+}  // namespace psi

@@ -1,0 +1,454 @@
+// C ABI of the pselinv library: handle lifetime, device buffers, the
+// factorisation and selected-inversion schedules, results and errors.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_last_err = "no error";
+constexpr int kStatusWords = 8;   // [0] first bad pivot column, [1] kind, rest spare
+constexpr int kStatusUnset = 0x7f7f7f7f;
+
+int set_err(pselinv_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  g_last_err = msg;
+  return code;
+}
+
+int cuda_err(pselinv_handle* h, cudaError_t e, const char* where) {
+  return set_err(h, e == cudaErrorMemoryAllocation ? PSELINV_ERR_OOM : PSELINV_ERR_CUDA,
+                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PSI_CUDA(h, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_err((h), e_, #call); \
+  } while (0)
+
+size_t elem_size(const pselinv_handle* h) { return h->opts.dtype == PSELINV_C128 ? 16 : 8; }
+
+psi::Sizes sizes(const pselinv_handle* h) {
+  psi::Sizes s;
+  s.panel = h->panel_total;
+  s.lhat = h->lhat_total;
+  s.linv = h->linv_total;
+  s.n = h->n;
+  s.part = h->part_max;
+  s.batch = h->opts.batch;
+  return s;
+}
+
+template <class T>
+int upload(pselinv_handle* h, void** dst, const std::vector<T>& v) {
+  size_t bytes = sizeof(T) * (v.empty() ? 1 : v.size());
+  PSI_CUDA(h, cudaMalloc(dst, bytes));
+  h->device_bytes += (int64_t)bytes;
+  if (!v.empty()) PSI_CUDA(h, cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return PSELINV_OK;
+}
+
+int alloc(pselinv_handle* h, void** dst, int64_t bytes) {
+  if (bytes < 16) bytes = 16;
+  PSI_CUDA(h, cudaMalloc(dst, (size_t)bytes));
+  h->device_bytes += bytes;
+  return PSELINV_OK;
+}
+
+void free_device(pselinv_handle* h) {
+  void** ptrs[] = {&h->d_meta, &h->d_desc, &h->d_relidx, &h->d_valmap, &h->d_tasks, &h->d_levelsn,
+                   &h->d_L,    &h->d_X,    &h->d_D,      &h->d_lhat,   &h->d_linv,  &h->d_part, &h->d_status};
+  for (void** p : ptrs) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  for (void* e : h->ev_pool) cudaEventDestroy((cudaEvent_t)e);
+  h->ev_pool.clear();
+  h->ev_used = 0;
+  h->ev_spans.clear();
+  if (h->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);
+  if (h->graph_stream) cudaStreamDestroy((cudaStream_t)h->graph_stream);
+  h->graph_exec = h->graph_stream = nullptr;
+  h->dev_sym = false;
+  h->device_bytes = 0;
+}
+
+int ensure_device(pselinv_handle* h) {
+  if (h->dev_sym) return PSELINV_OK;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) return set_err(h, PSELINV_ERR_CUDA, "no CUDA device available");
+  PSI_CUDA(h, cudaGetDevice(&h->device));
+  PSI_CUDA(h, psi::setup_kernels());
+  int rc;
+  if ((rc = upload(h, &h->d_meta, h->meta))) return rc;
+  if ((rc = upload(h, &h->d_desc, h->desc))) return rc;
+  if ((rc = upload(h, &h->d_relidx, h->relidx))) return rc;
+  if ((rc = upload(h, &h->d_valmap, h->valmap))) return rc;
+  if ((rc = upload(h, &h->d_levelsn, h->level_sn))) return rc;
+  std::vector<psi::Task> all;
+  h->off_lhat = (int64_t)all.size();
+  all.insert(all.end(), h->t_lhat.tasks.begin(), h->t_lhat.tasks.end());
+  h->off_gemm1 = (int64_t)all.size();
+  all.insert(all.end(), h->t_gemm1.tasks.begin(), h->t_gemm1.tasks.end());
+  h->off_gemm2 = (int64_t)all.size();
+  all.insert(all.end(), h->t_gemm2.tasks.begin(), h->t_gemm2.tasks.end());
+  h->off_trsm = (int64_t)all.size();
+  all.insert(all.end(), h->t_trsm.tasks.begin(), h->t_trsm.tasks.end());
+  h->off_schur = (int64_t)all.size();
+  all.insert(all.end(), h->t_schur.tasks.begin(), h->t_schur.tasks.end());
+  if ((rc = upload(h, &h->d_tasks, all))) return rc;
+  const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
+  if ((rc = alloc(h, &h->d_L, B * h->panel_total * es))) return rc;
+  if ((rc = alloc(h, &h->d_X, B * h->panel_total * es))) return rc;
+  if ((rc = alloc(h, &h->d_D, B * h->n * es))) return rc;
+  if ((rc = alloc(h, &h->d_lhat, B * h->lhat_total * es))) return rc;
+  if ((rc = alloc(h, &h->d_linv, B * h->linv_total * es))) return rc;
+  if ((rc = alloc(h, &h->d_part, B * h->part_max * es))) return rc;
+  if ((rc = alloc(h, &h->d_status, sizeof(int) * kStatusWords + sizeof(double) * 2 * B))) return rc;
+  h->dev_sym = true;
+  return PSELINV_OK;
+}
+
+const psi::Task* tasks_at(const pselinv_handle* h, int64_t base, int64_t off) {
+  return (const psi::Task*)h->d_tasks + base + off;
+}
+
+// Optional event bracketing of one kernel class (pselinv_set_timing).
+struct Timer {
+  pselinv_handle* h;
+  cudaStream_t st;
+  bool on;
+  size_t slot(int* rc) {
+    if (h->ev_used == h->ev_pool.size()) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) {
+        *rc = cuda_err(h, err, "cudaEventCreate");
+        return 0;
+      }
+      h->ev_pool.push_back((void*)e);
+    }
+    return h->ev_used++;
+  }
+  // run f() (which enqueues `count` launches of class cls) between two events
+  template <class F>
+  int run(int cls, int64_t count, F&& f) {
+    if (count <= 0) return PSELINV_OK;
+    int rc = PSELINV_OK;
+    size_t a = 0, b = 0;
+    if (on) {
+      a = slot(&rc);
+      if (rc) return rc;
+      PSI_CUDA(h, cudaEventRecord((cudaEvent_t)h->ev_pool[a], st));
+    }
+    PSI_CUDA(h, f());
+    if (on) {
+      b = slot(&rc);
+      if (rc) return rc;
+      PSI_CUDA(h, cudaEventRecord((cudaEvent_t)h->ev_pool[b], st));
+      h->ev_spans.push_back({cls, {a, b}});
+    }
+    h->launches[cls] += count;
+    return PSELINV_OK;
+  }
+};
+
+// Enqueue one schedule of the selected inversion on stream st.
+int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record) {
+  const psi::Sizes sz = sizes(h);
+  const auto* meta = (const psi::SnMeta*)h->d_meta;
+  const auto* desc = (const psi::ColDesc*)h->d_desc;
+  const auto* rel = (const int32_t*)h->d_relidx;
+  const auto* lsn = (const int32_t*)h->d_levelsn;
+  double* X = (double*)h->d_X;
+  double* Lhat = (double*)h->d_lhat;
+  double* part = (double*)h->d_part;
+  Timer tm{h, st, record};
+  int rc;
+  const int64_t nlhat = (int64_t)h->t_lhat.tasks.size();
+  rc = tm.run(0, 1 + (nlhat > 0), [&] {
+    return psi::launch_normalise(meta, h->nsn, tasks_at(h, h->off_lhat, 0), nlhat, (const double*)h->d_L,
+                                 (const double*)h->d_D, (double*)h->d_linv, Lhat, X, h->max_width, sz, st);
+  });
+  if (rc) return rc;
+  auto step = [&](const int32_t* sns, int nsn_step, psi::Range r1, psi::Range r2) {
+    int e;
+    if ((e = tm.run(1, r1.end > r1.begin, [&] {
+           return psi::launch_gemm1(meta, tasks_at(h, h->off_gemm1, r1.begin), r1.end - r1.begin, desc, rel, Lhat,
+                                    X, sz, st);
+         })))
+      return e;
+    if ((e = tm.run(2, r2.end > r2.begin, [&] {
+           return psi::launch_gemm2(meta, tasks_at(h, h->off_gemm2, r2.begin), r2.end - r2.begin, Lhat, X, part,
+                                    sz, st);
+         })))
+      return e;
+    return tm.run(3, nsn_step > 0, [&] { return psi::launch_diag_final(meta, sns, nsn_step, part, X, sz, st); });
+  };
+  if (mode == PSELINV_PLAIN) {
+    // one supernode per launch, reverse postorder (descending index)
+    std::vector<int32_t> pos(h->nsn);
+    for (int32_t t = 0; t < h->nsn; ++t) pos[h->level_sn[t]] = t;
+    for (int32_t k = h->nsn - 1; k >= 0; --k)
+      if ((rc = step(lsn + pos[k], 1, h->t_gemm1.per_sn[k], h->t_gemm2.per_sn[k]))) return rc;
+  } else {
+    for (int32_t l = 0; l < h->nlevels; ++l)
+      if ((rc = step(lsn + h->level_ptr[l], h->level_ptr[l + 1] - h->level_ptr[l], h->t_gemm1.per_level[l],
+                     h->t_gemm2.per_level[l])))
+        return rc;
+  }
+  return PSELINV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pselinv_default_opts(pselinv_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->dtype = PSELINV_F64;
+  o->batch = 1;
+  o->max_sn_width = psi::kMaxWidth;
+  o->relax = PSELINV_RELAX_AMALG;
+  o->small_cutoff = -1;
+  o->debug_checks = 0;
+  o->spin_limit_ns = 1000000000LL;
+}
+
+int pselinv_analyze(int64_t n, const int64_t* h_colptr, const int32_t* h_rowind, const int32_t* h_perm,
+                    const pselinv_opts* opts, pselinv_handle** out) {
+  if (!out) return set_err(nullptr, PSELINV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  auto* h = new pselinv_handle();
+  if (opts)
+    h->opts = *opts;
+  else
+    pselinv_default_opts(&h->opts);
+  if (h->opts.dtype != PSELINV_F64 && h->opts.dtype != PSELINV_C128) {
+    delete h;
+    return set_err(nullptr, PSELINV_ERR_ARG, "dtype must be PSELINV_F64 or PSELINV_C128");
+  }
+  if (h->opts.dtype == PSELINV_C128) {
+    delete h;
+    return set_err(nullptr, PSELINV_ERR_ARG, "complex128 values are not supported by this build");
+  }
+  if (h->opts.batch < 1 || h->opts.batch > 65535) {
+    delete h;
+    return set_err(nullptr, PSELINV_ERR_ARG, "batch must be 1..65535");
+  }
+  int rc = psi::analyze(h, n, h_colptr, h_rowind, h_perm);
+  if (rc != PSELINV_OK) {
+    g_last_err = h->err;
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return PSELINV_OK;
+}
+
+int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream) {
+  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
+  if (!d_values) return set_err(h, PSELINV_ERR_ARG, "values pointer is NULL");
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const psi::Sizes sz = sizes(h);
+  const int64_t B = h->opts.batch;
+  h->factored = h->inverted = false;
+  PSI_CUDA(h, cudaMemsetAsync(h->d_L, 0, sizeof(double) * B * h->panel_total, st));
+  PSI_CUDA(h, cudaMemsetAsync(h->d_status, 0x7f, sizeof(int), st));
+  PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + 1, 0, sizeof(int) * (kStatusWords - 1), st));
+  PSI_CUDA(h, psi::launch_scatter_values((const double*)d_values, (const int64_t*)h->d_valmap, h->nnz_a,
+                                         (double*)h->d_L, sz, st));
+  const auto* meta = (const psi::SnMeta*)h->d_meta;
+  const auto* lsn = (const int32_t*)h->d_levelsn;
+  for (int32_t l = h->nlevels - 1; l >= 0; --l) {
+    const psi::Range rt = h->t_trsm.per_level[l], rs = h->t_schur.per_level[l];
+    PSI_CUDA(h, psi::launch_factor_level(meta, lsn + h->level_ptr[l], h->level_ptr[l + 1] - h->level_ptr[l],
+                                         tasks_at(h, h->off_trsm, rt.begin), rt.end - rt.begin,
+                                         tasks_at(h, h->off_schur, rs.begin), rs.end - rs.begin,
+                                         (const psi::ColDesc*)h->d_desc, (const int32_t*)h->d_relidx,
+                                         (double*)h->d_L, (double*)h->d_D, (double*)h->d_linv,
+                                         (double*)h->d_lhat, h->max_width, sz, (int*)h->d_status, st));
+  }
+  int status[2];
+  PSI_CUDA(h, cudaMemcpyAsync(status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
+  PSI_CUDA(h, cudaStreamSynchronize(st));
+  if (status[0] != kStatusUnset) {
+    const int code = status[1] == 1 ? PSELINV_ERR_ZERO_PIVOT : PSELINV_ERR_NONFINITE;
+    return set_err(h, code, std::string(status[1] == 1 ? "zero" : "non-finite") + " pivot at column " +
+                                std::to_string(status[0]) + " (internal order)");
+  }
+  h->factored = true;
+  return PSELINV_OK;
+}
+
+int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream) {
+  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
+  if (mode != PSELINV_PLAIN && mode != PSELINV_LEVEL && mode != PSELINV_GRAPH)
+    return set_err(h, PSELINV_ERR_ARG, "bad selinv mode");
+  if (!h->factored) return set_err(h, PSELINV_ERR_STATE, "selinv called before a successful factor");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mode != PSELINV_GRAPH) {
+    int rc = enqueue_selinv(h, mode, st, h->timing);
+    if (rc) return rc;
+  } else {
+    if (!h->graph_exec) {
+      cudaStream_t cs;
+      PSI_CUDA(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      h->graph_stream = cs;
+      PSI_CUDA(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      int64_t before[4];
+      std::memcpy(before, h->launches, sizeof(before));
+      int rc = enqueue_selinv(h, PSELINV_LEVEL, cs, false);
+      for (int q = 0; q < 4; ++q) {
+        h->graph_launches[q] = h->launches[q] - before[q];
+        h->launches[q] = before[q];
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(cs, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_err(h, e, "cudaStreamEndCapture");
+      cudaGraphExec_t ex;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_err(h, e, "cudaGraphInstantiate");
+      h->graph_exec = ex;
+    }
+    PSI_CUDA(h, cudaGraphLaunch((cudaGraphExec_t)h->graph_exec, st));
+    for (int q = 0; q < 4; ++q) h->launches[q] += h->graph_launches[q];
+  }
+  h->inverted = true;
+  return PSELINV_OK;
+}
+
+int pselinv_get_panels(pselinv_handle* h, int32_t which, void* d_out, void* stream) {
+  if (!h || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (which != 0 && which != 1) return set_err(h, PSELINV_ERR_ARG, "which must be 0 (X) or 1 (L)");
+  if (which == 0 && !h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
+  if (which == 1 && !h->factored) return set_err(h, PSELINV_ERR_STATE, "no factor yet");
+  const size_t bytes = elem_size(h) * (size_t)h->opts.batch * (size_t)h->panel_total;
+  PSI_CUDA(h, cudaMemcpyAsync(d_out, which == 0 ? h->d_X : h->d_L, bytes, cudaMemcpyDeviceToDevice,
+                              (cudaStream_t)stream));
+  return PSELINV_OK;
+}
+
+int pselinv_get_selected(pselinv_handle* h, void* d_out, void* stream) {
+  if (!h || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
+  PSI_CUDA(h, psi::launch_gather_values((const double*)h->d_X, (const int64_t*)h->d_valmap, h->nnz_a,
+                                        (double*)d_out, sizes(h), (cudaStream_t)stream));
+  return PSELINV_OK;
+}
+
+int pselinv_logdet(pselinv_handle* h, double* h_out, void* stream) {
+  if (!h || !h_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (!h->factored) return set_err(h, PSELINV_ERR_STATE, "no factor yet");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* dev = (double*)((int*)h->d_status + kStatusWords);
+  PSI_CUDA(h, psi::launch_logdet((const double*)h->d_D, h->n, dev, h->opts.batch, st));
+  PSI_CUDA(h, cudaMemcpyAsync(h_out, dev, sizeof(double) * 2 * h->opts.batch, cudaMemcpyDeviceToHost, st));
+  PSI_CUDA(h, cudaStreamSynchronize(st));
+  return PSELINV_OK;
+}
+
+int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, void* d_gradA, void* stream) {
+  (void)d_G;
+  (void)d_gradA;
+  (void)stream;
+  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
+  return set_err(h, PSELINV_ERR_STATE, "selinv_adjoint is not available in this build");
+}
+
+int pselinv_set_timing(pselinv_handle* h, int32_t enable) {
+  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
+  h->timing = enable != 0;
+  h->ev_used = 0;
+  h->ev_spans.clear();
+  for (int q = 0; q < 4; ++q) h->launches[q] = 0;
+  return PSELINV_OK;
+}
+
+int pselinv_get_timing(pselinv_handle* h, double* h_ms, int64_t* h_launches) {
+  if (!h || !h_ms || !h_launches) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  double ms[PSELINV_NTIMERS] = {0, 0, 0, 0};
+  for (const auto& sp : h->ev_spans) {
+    cudaEvent_t a = (cudaEvent_t)h->ev_pool[sp.second.first], b = (cudaEvent_t)h->ev_pool[sp.second.second];
+    PSI_CUDA(h, cudaEventSynchronize(b));
+    float t = 0.f;
+    PSI_CUDA(h, cudaEventElapsedTime(&t, a, b));
+    ms[sp.first] += t;
+  }
+  for (int q = 0; q < PSELINV_NTIMERS; ++q) {
+    h_ms[q] = ms[q];
+    h_launches[q] = h->launches[q];
+    h->launches[q] = 0;
+  }
+  h->ev_used = 0;
+  h->ev_spans.clear();
+  return PSELINV_OK;
+}
+
+int pselinv_get_info(const pselinv_handle* h, pselinv_info* info) {
+  if (!h || !info) return PSELINV_ERR_ARG;
+  info->n = h->n;
+  info->nnz_a = h->nnz_a;
+  info->nnz_l = h->nnz_l;
+  info->panel_entries = h->panel_total;
+  info->relidx_len = (int64_t)h->relidx.size();
+  info->nsn = h->nsn;
+  info->nlevels = h->nlevels;
+  info->max_width = h->max_width;
+  info->batch = h->opts.batch;
+  info->max_r = h->max_r;
+  info->flops_selinv = h->flops_selinv;
+  info->flops_gemm1 = h->flops_gemm1;
+  info->bytes_selinv = h->bytes_selinv;
+  info->device_bytes = h->device_bytes;
+  return PSELINV_OK;
+}
+
+int pselinv_export_symbolic(const pselinv_handle* h, pselinv_symbolic* v) {
+  if (!h || !v) return PSELINV_ERR_ARG;
+  v->n = h->n;
+  v->nsn = h->nsn;
+  v->nlevels = h->nlevels;
+  v->perm = h->perm.data();
+  v->parent = h->parent.data();
+  v->sn_start = h->sn_start.data();
+  v->sn_parent = h->sn_parent.data();
+  v->sigma = h->sigma.data();
+  v->rowptr = h->rowptr.data();
+  v->rows = h->rows.data();
+  v->panel_off = h->panel_off.data();
+  v->relptr = h->relptr.data();
+  v->relidx = h->relidx.data();
+  v->nblk = h->nblk.data();
+  v->level_ptr = h->level_ptr.data();
+  v->level_sn = h->level_sn.data();
+  return PSELINV_OK;
+}
+
+void pselinv_destroy(pselinv_handle* h) {
+  if (!h) return;
+  free_device(h);
+  delete h;
+}
+
+const char* pselinv_last_error(const pselinv_handle* h) {
+  if (h) return h->err.empty() ? "no error" : h->err.c_str();
+  return g_last_err.c_str();
+}
+
+}  // extern "C"

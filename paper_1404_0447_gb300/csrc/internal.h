@@ -1,0 +1,126 @@
+// Internal declarations of the pselinv library (host analysis, device
+// kernels and the C ABI glue).  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pselinv.h"
+
+namespace psi {
+
+// Per-supernode metadata, mirrored on the device.  Element offsets are per
+// batch member; member b adds b * (total size of that array).
+struct SnMeta {
+  int32_t f;       // first column
+  int32_t s;       // width
+  int32_t r;       // |C| = rows below the diagonal block
+  int32_t nchunk;  // row chunks of the step-3 product Lhat^T X_{C,K}
+  int64_t panel;   // offset of the (s + r) x s column-major panel (ld = s + r)
+  int64_t lhat;    // offset of Lhat_{C,K} (r x s, ld = r) in the normalised-factor buffer
+  int64_t linv;    // offset of (L_KK)^{-1} (s x s, ld = s)
+  int64_t desc;    // offset of this supernode's r column descriptors
+  int64_t part;    // level-local offset of the step-3 partial products (nchunk * s * s)
+};
+
+// Where column k of X_{C,C} (k-th row of C) lives: element offset of that
+// column inside its supernode J's panel, and the index into relidx such
+// that relidx[rel + i] is the row position of C[i] in J's panel for every
+// i >= the start of k's block.
+struct ColDesc {
+  int64_t col;
+  int64_t rel;
+};
+
+// One unit of work of a grouped launch.  Meaning of m0/n0/c per kernel:
+//   tile kernels: output tile origin (m0, n0); c = row chunk (step-3 product) or 0
+struct Task {
+  int32_t sn;
+  int32_t m0;
+  int32_t n0;
+  int32_t c;
+};
+
+// Contiguous task ranges [begin, end) for a level and for a supernode.
+struct Range {
+  int64_t begin = 0, end = 0;
+};
+
+constexpr int kMaxWidth = 128;   // widest supernode the kernels accept
+constexpr int kChunkRows = 512;  // rows per step-3 partial product
+constexpr int kTileM = 64;       // output tile rows of the grouped GEMMs
+constexpr int kTileN = 64;       // output tile columns
+
+struct TaskList {
+  std::vector<Task> tasks;
+  std::vector<Range> per_level;  // indexed by level (0 = root level)
+  std::vector<Range> per_sn;     // indexed by supernode
+};
+
+}  // namespace psi
+
+struct pselinv_handle {
+  pselinv_opts opts{};
+  std::string err;
+
+  // ---- symbolic (host) ----
+  int64_t n = 0;
+  int64_t nnz_a = 0;
+  int32_t nsn = 0;
+  int32_t nlevels = 0;
+  std::vector<int32_t> perm, parent, sn_start, sn_parent, sigma, level_ptr, level_sn;
+  std::vector<int32_t> rows, relidx, nblk;
+  std::vector<int64_t> rowptr, panel_off, relptr;
+  std::vector<int64_t> valmap;  // user entry q -> panel offset of (i, j), i >= j internal
+  std::vector<psi::SnMeta> meta;
+  std::vector<psi::ColDesc> desc;
+  int64_t panel_total = 0, lhat_total = 0, linv_total = 0, part_max = 0;
+  int64_t nnz_l = 0, max_r = 0;
+  int32_t max_width = 0;
+  double flops_selinv = 0, flops_gemm1 = 0, bytes_selinv = 0;
+
+  // task lists (levels in priority order; supernodes of a level costliest first)
+  psi::TaskList t_lhat;   // normalisation tiles (all supernodes)
+  psi::TaskList t_gemm1;  // step 2 tiles
+  psi::TaskList t_gemm2;  // step 3 partial-product tiles
+  psi::TaskList t_trsm;   // factorisation: off-diagonal panel solve tiles
+  psi::TaskList t_schur;  // factorisation: Schur-complement update tiles
+
+  // ---- device state ----
+  int device = -1;
+  bool dev_sym = false;     // symbolic arrays uploaded
+  bool factored = false;
+  bool inverted = false;
+  void* d_meta = nullptr;
+  void* d_desc = nullptr;
+  void* d_relidx = nullptr;
+  void* d_valmap = nullptr;
+  void* d_tasks = nullptr;  // all task arrays back to back
+  int64_t off_lhat = 0, off_gemm1 = 0, off_gemm2 = 0, off_trsm = 0, off_schur = 0;
+  void* d_levelsn = nullptr;
+  void* d_L = nullptr;      // L panels (unit diagonal implied; D on the diagonal slots)
+  void* d_X = nullptr;      // X panels
+  void* d_D = nullptr;      // pivots, batch x n
+  void* d_lhat = nullptr;   // normalised factor / factor scratch
+  void* d_linv = nullptr;   // inverses of the diagonal blocks
+  void* d_part = nullptr;   // step-3 partial products (level-local)
+  void* d_status = nullptr; // device status words
+  int64_t device_bytes = 0;
+  void* graph_exec = nullptr;  // cudaGraphExec_t of the LEVEL schedule
+  void* graph_stream = nullptr;
+
+  // optional kernel timing (pselinv_set_timing)
+  bool timing = false;
+  std::vector<void*> ev_pool;              // cudaEvent_t, reused
+  size_t ev_used = 0;
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_spans;  // class, (start, stop) event slots
+  int64_t launches[4] = {0, 0, 0, 0};
+  int64_t graph_launches[4] = {0, 0, 0, 0};  // kernels in the captured graph, per class
+};
+
+namespace psi {
+// analyze.cpp
+int analyze(pselinv_handle* h, int64_t n, const int64_t* colptr, const int32_t* rowind,
+            const int32_t* perm);
+}  // namespace psi

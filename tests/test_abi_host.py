@@ -1,0 +1,112 @@
+"""Host-side checks of the C-ABI library (no GPU work): the library loads,
+exports every symbol the header declares, and its symbolic analysis matches
+the oracle's bit for bit (elimination tree, supernodes, supernodal tree,
+Algorithm 2 priorities, row lists, relative indices)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as g
+    g.build_library()
+    import paper_1404_0447_gb300 as P
+    return P
+
+
+def test_exports_every_declared_symbol(P):
+    hdr = open(os.path.join(ROOT, "include", "pselinv.h")).read()
+    declared = set(re.findall(r"\b(pselinv_[a-z_]+)\s*\(", hdr))
+    lib = P.load_library()
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared == set(P.EXPORTED)
+
+
+def _compare(P, n, cp, ri, wmax, relax, perm=None):
+    h = P.SelInv(n, cp, ri, perm=perm, max_sn_width=wmax, relax=relax)
+    s = h.symbolic()
+    if perm is not None:
+        cp2, ri2, _, _ = synth.permute_lower(n, cp, ri, np.zeros(len(ri)), perm)
+    else:
+        cp2, ri2 = cp, ri
+    o = oracle.analyse(n, cp2, ri2, wmax, 1 if relax else 0)
+    base = np.arange(n) if perm is None else np.asarray(perm)
+    assert np.array_equal(s["perm"], base[o["post"]])
+    for a, b in [("parent", "parent"), ("sn_start", "sn_start"), ("sn_parent", "sn_parent"),
+                 ("sigma", "sigma"), ("rows", "rrows"), ("relidx", "relidx"), ("nblk", "nblk")]:
+        assert np.array_equal(np.asarray(s[a], np.int64), np.asarray(o[b], np.int64)), a
+    assert np.array_equal(np.diff(s["rowptr"]), o["rcount"])
+    # levels are the sets of Algorithm 2
+    for lv in range(s["nlevels"]):
+        members = s["level_sn"][s["level_ptr"][lv]:s["level_ptr"][lv + 1]]
+        assert np.all(o["sigma"][members] == lv + 1)
+    info = h.info
+    sw = np.diff(o["sn_start"]).astype(np.int64)
+    assert info["panel_entries"] == int(np.sum((sw + o["rcount"]) * sw))
+    return h
+
+
+@pytest.mark.parametrize("wmax,relax", [(128, 0), (16, 1), (128, 1), (5, 1)])
+def test_structure_parity_grids(P, wmax, relax):
+    for prob in (synth.config0(), synth.config1(side=11), synth.grid_problem((7, 9, 5), .1, 1, 3)):
+        _compare(P, prob.n, prob.colptr, prob.rowind, wmax, relax)
+
+
+def test_structure_parity_random_perm_and_postorder(P):
+    rng = np.random.default_rng(4)
+    for trial in range(6):
+        n = 30 + 17 * trial
+        mask = np.triu(rng.random((n, n)) < 0.06, 1)
+        rows, cols = np.nonzero(mask.T)
+        cp, ri, _ = synth.lower_csc_from_coo(
+            n, np.r_[np.arange(n), rows], np.r_[np.arange(n), cols], np.ones(n + rows.size))
+        perm = rng.permutation(n)
+        _compare(P, n, cp, ri, 8, 1, perm=perm)
+
+
+def test_structure_parity_block_matrix(P):
+    n, cp, ri, hv, z = synth.dg_block_matrix((3, 3, 2), 6, 1, seed=1)
+    perm = synth.block_nd_order((3, 3, 2), 6)
+    cp2, ri2, _, _ = synth.permute_lower(n, cp, ri, hv, perm)
+    _compare(P, n, cp2, ri2, 32, 1)
+
+
+def test_analyze_rejects_bad_input(P):
+    cp = np.array([0, 2, 3], np.int64)
+    ri = np.array([1, 0, 1], np.int32)           # diagonal not first in column 0
+    with pytest.raises(P.PselinvError) as e:
+        P.SelInv(2, cp, ri)
+    assert e.value.code == -2
+    cp = np.array([0, 1, 2], np.int64)
+    ri = np.array([0, 1], np.int32)
+    with pytest.raises(P.PselinvError) as e:
+        P.SelInv(2, cp, ri, perm=np.array([0, 0]))
+    assert e.value.code == -2
+    with pytest.raises(P.PselinvError) as e:
+        P.SelInv(2, cp, ri, max_sn_width=500)
+    assert e.value.code == -1
+
+
+def test_figure1_partition_levels_match_algorithm2(P):
+    """The library's priority lists on the Figure 1 pattern (its own
+    supernodes) agree with Algorithm 2 applied by the oracle."""
+    from tests.test_oracle_pins import _read_fig1, lower_from_dense
+    part, blocks, fill, snp, levels = _read_fig1()
+    n = int(part[-1])
+    M = np.zeros((n, n), bool)
+    for k in range(len(part) - 1):
+        M[part[k]:part[k + 1], part[k]:part[k + 1]] = True
+    for br, bc, rows in blocks:
+        M[np.ix_(rows, range(part[bc - 1], part[bc]))] = True
+    M = M | M.T
+    cp, ri, v = lower_from_dense(np.where(M, 1.0, 0.0))
+    _compare(P, n, cp, ri, 128, 0)
