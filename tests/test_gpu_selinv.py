@@ -212,7 +212,8 @@ def test_full_size_80cubed_against_closed_form_and_trace(P):
         for _ in range(2):
             c = int(rng.integers(0, sw)); rr = int(rng.integers(c, sw + len(R)))
             pos.append(s["panel_off"][k] + c * (sw + len(R)) + rr)
-            pairs.append((s["perm"][rowsK[rr]], s["perm"][f + c]))
+            # internal index -> ND-ordered input (library perm) -> natural grid index
+            pairs.append((p.perm[s["perm"][rowsK[rr]]], p.perm[s["perm"][f + c]]))
     got = X[torch.tensor(np.array(pos), device="cuda")].cpu().numpy()
     want = oracle.grid_inverse_entries(p.dims, 0.055, np.array(pairs))
     scale = float(torch.max(torch.abs(X)).item())
