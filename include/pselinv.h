@@ -240,6 +240,38 @@ int pselinv_get_timing(pselinv_handle* h, double* h_ms, int64_t* h_launches);
 int pselinv_get_info(const pselinv_handle* h, pselinv_info* info);
 int pselinv_export_symbolic(const pselinv_handle* h, pselinv_symbolic* view);
 
+/*
+ * Allocation-free inverse of a batch of small dense blocks from their LDL^T
+ * factors: d_M[b] = L_b^{-T} D_b^{-1} L_b^{-1} (= A_b^{-1} when A_b = L_b D_b
+ * L_b^T), the diagonal-block term of step 3 above.  The paper has no
+ * counterpart: this exists for callers that may not call cudaMalloc or
+ * cudaFree (cudaFree synchronises the device and cudaMalloc can stall) --
+ * code running inside another framework's memory pool or under a fixed
+ * memory budget, loops that must never block on the allocator.  It calls no
+ * allocating routine; its only scratch (the L^{-1} blocks) is a file-scope
+ * device array of 2^21 doubles (16 MiB) that every GPU loading this library
+ * holds until the process exits.
+ *
+ * s         block order, 1..128
+ * count     number of blocks; count * s * s must be <= 2^21, else ERR_ARG
+ * d_L       device, count blocks of s x s column-major (ld s); only the
+ *           strictly lower triangle is read (unit diagonal implied), so the
+ *           L panel of pselinv_get_panels(which = 1) of a single-supernode
+ *           matrix can be passed as is
+ * d_d       device, count x s pivots
+ * d_M       device, count x s x s output, full symmetric, column-major
+ * The first call on each device looks up the scratch array's device address
+ * and sets a kernel attribute for that device; make that first call before
+ * any stream capture.  All calls share the one scratch array: calls that can
+ * overlap on the GPU (different streams, or different host threads) race on
+ * it and must be serialised by the caller.  Every call writes all scratch
+ * it reads, so nothing needs clearing between calls.  Enqueues work on
+ * stream; no synchronisation.  Errors: ERR_ARG (sizes, NULL), ERR_CUDA;
+ * message via pselinv_last_error(NULL).
+ */
+int pselinv_block_inverse_static(int32_t s, int32_t count, const double* d_L, const double* d_d, double* d_M,
+                                 void* stream);
+
 /* Frees everything the handle owns; NULL is allowed. */
 void pselinv_destroy(pselinv_handle* h);
 

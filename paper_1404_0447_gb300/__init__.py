@@ -25,7 +25,7 @@ PLAIN, LEVEL, GRAPH = 0, 1, 2
 EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_factor", "pselinv_selinv",
             "pselinv_get_panels", "pselinv_get_selected", "pselinv_logdet", "pselinv_selinv_adjoint",
             "pselinv_set_timing", "pselinv_get_timing", "pselinv_get_info", "pselinv_export_symbolic",
-            "pselinv_destroy", "pselinv_last_error"]
+            "pselinv_destroy", "pselinv_last_error", "pselinv_block_inverse_static"]
 
 
 class PselinvError(RuntimeError):
@@ -89,6 +89,7 @@ def load_library():
     L.pselinv_destroy.restype = None
     L.pselinv_last_error.argtypes = [vp]
     L.pselinv_last_error.restype = ctypes.c_char_p
+    L.pselinv_block_inverse_static.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -211,3 +212,24 @@ class SelInv:
         out = np.zeros(2 * self.opts.batch, np.float64)
         self._check(self._lib.pselinv_logdet(self._h, _ptr(out), _stream_ptr(stream)))
         return out.reshape(self.opts.batch, 2)
+
+
+def block_inverse_static(L, d, out=None, stream=None):
+    """pselinv_block_inverse_static: M_b = L_b^{-T} D_b^{-1} L_b^{-1} for a
+    batch of dense s x s blocks (CUDA float64 tensors, L: [count, s, s] or
+    [count, s*s] column-major, d: [count, s]) without any allocation inside
+    the library.  ``out`` (same shape as L) is allocated here by torch when
+    not given."""
+    import torch
+    lib = load_library()
+    count, s = d.shape
+    assert L.is_cuda and d.is_cuda and L.dtype == torch.float64 and d.dtype == torch.float64
+    assert L.is_contiguous() and d.is_contiguous() and L.numel() == count * s * s
+    if out is None:
+        out = torch.empty(count, s * s, dtype=torch.float64, device=L.device)
+    rc = lib.pselinv_block_inverse_static(int(s), int(count), ctypes.c_void_p(L.data_ptr()),
+                                          ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                          _stream_ptr(stream))
+    if rc != PSELINV_OK:
+        raise PselinvError(rc, lib.pselinv_last_error(None).decode())
+    return out

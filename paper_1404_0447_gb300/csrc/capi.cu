@@ -209,6 +209,11 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record) {
 
 }  // namespace
 
+namespace psi {
+// Error text for entry points that have no handle (read by pselinv_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_last_err = msg; }
+}  // namespace psi
+
 extern "C" {
 
 void pselinv_default_opts(pselinv_opts* o) {
