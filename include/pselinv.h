@@ -202,6 +202,16 @@ int pselinv_get_panels(pselinv_handle* h, int32_t which, void* d_out, void* stre
 int pselinv_get_selected(pselinv_handle* h, void* d_out, void* stream);
 
 /*
+ * Gradient of log det A with respect to the stored values of A's lower CSC
+ * in the user's order: d log det A = tr(A^{-1} dA), and a stored
+ * off-diagonal value stands for both A_ij and A_ji, so
+ * d_out[b * nnz_a + q] = X_jj for a diagonal entry and 2 X_ij for an
+ * off-diagonal one (X = A_b^{-1} from the last pselinv_selinv; plain
+ * transpose for complex symmetric A).  Device pointer, batch x nnz_a.
+ */
+int pselinv_logdet_grad(pselinv_handle* h, void* d_out, void* stream);
+
+/*
  * log det A = sum_j log d_j (Section 2.1's LDL^T).  h_out (host) receives
  * per batch member two doubles: F64 -> (sum log|d_j|, number of negative
  * pivots); C128 -> (real, imaginary) of the sum of principal logs.

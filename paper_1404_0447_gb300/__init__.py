@@ -23,7 +23,8 @@ RELAX_NONE, RELAX_AMALG = 0, 1
 PLAIN, LEVEL, GRAPH = 0, 1, 2
 
 EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_factor", "pselinv_selinv",
-            "pselinv_get_panels", "pselinv_get_selected", "pselinv_logdet", "pselinv_selinv_adjoint",
+            "pselinv_get_panels", "pselinv_get_selected", "pselinv_logdet_grad", "pselinv_logdet",
+            "pselinv_selinv_adjoint",
             "pselinv_set_timing", "pselinv_get_timing", "pselinv_get_info", "pselinv_export_symbolic",
             "pselinv_destroy", "pselinv_last_error", "pselinv_block_inverse_static"]
 
@@ -80,6 +81,7 @@ def load_library():
     L.pselinv_get_panels.argtypes = [vp, ctypes.c_int32, vp, vp]
     L.pselinv_get_selected.argtypes = [vp, vp, vp]
     L.pselinv_logdet.argtypes = [vp, vp, vp]
+    L.pselinv_logdet_grad.argtypes = [vp, vp, vp]
     L.pselinv_selinv_adjoint.argtypes = [vp, vp, vp, vp]
     L.pselinv_set_timing.argtypes = [vp, ctypes.c_int32]
     L.pselinv_get_timing.argtypes = [vp, vp, vp]
@@ -174,9 +176,14 @@ class SelInv:
                     nblk=arr(v.nblk, nsn), level_ptr=arr(v.level_ptr, nl + 1), level_sn=arr(v.level_sn, nsn))
 
     # ---- numeric ----
-    def factor(self, values, stream=None):
+    @property
+    def torch_dtype(self):
         import torch
-        assert values.is_cuda and values.dtype == torch.float64 and values.is_contiguous()
+        return torch.complex128 if self.opts.dtype == C128 else torch.float64
+
+    def factor(self, values, stream=None):
+        assert values.is_cuda and values.dtype == self.torch_dtype and values.is_contiguous()
+        assert values.numel() == self.opts.batch * self.info["nnz_a"]
         self._check(self._lib.pselinv_factor(self._h, ctypes.c_void_p(values.data_ptr()), _stream_ptr(stream)))
 
     def selinv(self, mode=LEVEL, stream=None):
@@ -184,7 +191,7 @@ class SelInv:
 
     def panels(self, which=0, stream=None):
         import torch
-        out = torch.empty(self.opts.batch * self.info["panel_entries"], dtype=torch.float64, device="cuda")
+        out = torch.empty(self.opts.batch * self.info["panel_entries"], dtype=self.torch_dtype, device="cuda")
         self._check(self._lib.pselinv_get_panels(self._h, int(which), ctypes.c_void_p(out.data_ptr()),
                                                  _stream_ptr(stream)))
         return out.view(self.opts.batch, -1)
@@ -193,8 +200,17 @@ class SelInv:
         import torch
         nnz = self.info["nnz_a"]
         if out is None:
-            out = torch.empty(self.opts.batch * nnz, dtype=torch.float64, device="cuda")
+            out = torch.empty(self.opts.batch * nnz, dtype=self.torch_dtype, device="cuda")
         self._check(self._lib.pselinv_get_selected(self._h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out.view(self.opts.batch, nnz)
+
+    def logdet_grad(self, out=None, stream=None):
+        """d log det A / d (stored lower values): X_jj on the diagonal, 2 X_ij off it."""
+        import torch
+        nnz = self.info["nnz_a"]
+        if out is None:
+            out = torch.empty(self.opts.batch * nnz, dtype=self.torch_dtype, device="cuda")
+        self._check(self._lib.pselinv_logdet_grad(self._h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out.view(self.opts.batch, nnz)
 
     def set_timing(self, enable=True):
@@ -233,3 +249,42 @@ def block_inverse_static(L, d, out=None, stream=None):
     if rc != PSELINV_OK:
         raise PselinvError(rc, lib.pselinv_last_error(None).decode())
     return out
+
+
+def _autograd():
+    import torch
+
+    class LogDet(torch.autograd.Function):
+        """log det A(values) for real symmetric A (sum log|d_j| of the LDL^T
+        pivots).  backward = the selected inverse at A's stored positions
+        (pselinv_logdet_grad), scaled by the incoming gradient."""
+
+        @staticmethod
+        def forward(ctx, values, handle, mode):
+            handle.factor(values.detach().contiguous())
+            ld = handle.logdet()
+            ctx.handle, ctx.mode = handle, mode
+            return torch.tensor(ld[:, 0], dtype=torch.float64, device=values.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            h = ctx.handle
+            h.selinv(ctx.mode)
+            return h.logdet_grad() * g[:, None], None, None
+
+    return LogDet
+
+
+_LogDet = None
+
+
+def logdet(values, handle, mode=LEVEL):
+    """Differentiable log det of the batch of real symmetric matrices whose
+    lower-CSC values are ``values`` ([batch, nnz] or [nnz]) on the pattern
+    analysed by ``handle``; returns a [batch] tensor."""
+    global _LogDet
+    if _LogDet is None:
+        _LogDet = _autograd()
+    v = values if values.dim() == 2 else values.unsqueeze(0)
+    out = _LogDet.apply(v, handle, mode)
+    return out if values.dim() == 2 else out[0]

@@ -410,6 +410,8 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
 
   // ---- value map: A's stored entries -> panel offsets ----
   h->valmap.assign(h->nnz_a, -1);
+  h->diagmask.assign(h->nnz_a, 0);
+  for (int64_t j = 0; j < n; ++j) h->diagmask[cp[j]] = 1;  // diagonal first in every column
   for (int64_t j = 0; j < n; ++j) {
     const SnMeta& m = h->meta[col2sn[j]];
     const int32_t* R = h->rows.data() + h->rowptr[col2sn[j]];
@@ -429,39 +431,60 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
   }
 
   // ---- task lists ----
-  auto build = [&](TaskList& tl, auto&& emit) {
+  // Level lists hold, per level, per tile variant, the supernodes in level
+  // order (costliest first), each supernode's tiles contiguous.  The
+  // normalisation list is variant-major over all levels (one launch per
+  // variant).
+  const bool cplx = o.dtype == PSELINV_C128;
+  auto build = [&](TaskList& tl, bool variant_major, auto&& var_of, auto&& emit) {
     tl.tasks.clear();
-    tl.per_level.assign(nl, Range{});
+    tl.per_lv.assign((size_t)nl * kNumVar, Range{});
     tl.per_sn.assign(nsn, Range{});
-    for (int32_t l = 0; l < nl; ++l) {
-      tl.per_level[l].begin = (int64_t)tl.tasks.size();
-      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
-        int32_t k = h->level_sn[t];
-        tl.per_sn[k].begin = (int64_t)tl.tasks.size();
-        emit(k, tl.tasks);
-        tl.per_sn[k].end = (int64_t)tl.tasks.size();
+    tl.var.assign(nsn, 0);
+    for (int32_t k = 0; k < nsn; ++k) tl.var[k] = (int8_t)var_of(k);
+    auto add_sn = [&](int32_t k) {
+      tl.per_sn[k].begin = (int64_t)tl.tasks.size();
+      emit(k, 8 << tl.var[k], tl.tasks);
+      tl.per_sn[k].end = (int64_t)tl.tasks.size();
+    };
+    if (variant_major) {
+      for (int v = 0; v < kNumVar; ++v) {
+        tl.whole[v].begin = (int64_t)tl.tasks.size();
+        for (int32_t t = 0; t < nsn; ++t)
+          if (tl.var[h->level_sn[t]] == v) add_sn(h->level_sn[t]);
+        tl.whole[v].end = (int64_t)tl.tasks.size();
       }
-      tl.per_level[l].end = (int64_t)tl.tasks.size();
+      return;
     }
+    for (int32_t l = 0; l < nl; ++l)
+      for (int v = 0; v < kNumVar; ++v) {
+        Range& rg = tl.per_lv[(size_t)l * kNumVar + v];
+        rg.begin = (int64_t)tl.tasks.size();
+        for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t)
+          if (tl.var[h->level_sn[t]] == v) add_sn(h->level_sn[t]);
+        rg.end = (int64_t)tl.tasks.size();
+      }
   };
-  auto rect = [&](int32_t k, std::vector<Task>& out) {  // r x s output tiles
+  auto by_width = [&](int32_t k) { return pick_variant(h->meta[k].s, cplx); };
+  auto by_rows = [&](int32_t) { return cplx ? 2 : 3; };
+  auto rect = [&](int32_t k, int bn, std::vector<Task>& out) {  // r x s output tiles
     const SnMeta& m = h->meta[k];
     for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
-      for (int32_t n0 = 0; n0 < m.s; n0 += kTileN) out.push_back({k, m0, n0, 0});
+      for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, 0});
   };
-  build(h->t_lhat, rect);
-  build(h->t_gemm1, rect);
-  build(h->t_trsm, rect);
-  build(h->t_gemm2, [&](int32_t k, std::vector<Task>& out) {
+  build(h->t_lhat, true, by_width, rect);
+  build(h->t_gemm1, false, by_width, rect);
+  build(h->t_trsm, false, by_width, rect);
+  build(h->t_gemm2, false, by_width, [&](int32_t k, int bn, std::vector<Task>& out) {
     const SnMeta& m = h->meta[k];
     for (int32_t c = 0; c < m.nchunk; ++c)
       for (int32_t m0 = 0; m0 < m.s; m0 += kTileM)
-        for (int32_t n0 = 0; n0 < m.s; n0 += kTileN) out.push_back({k, m0, n0, c});
+        for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, c});
   });
-  build(h->t_schur, [&](int32_t k, std::vector<Task>& out) {
+  build(h->t_schur, false, by_rows, [&](int32_t k, int bn, std::vector<Task>& out) {
     const SnMeta& m = h->meta[k];
     for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
-      for (int32_t n0 = 0; n0 <= m0; n0 += kTileM) out.push_back({k, m0, n0, 0});
+      for (int32_t n0 = 0; n0 < m0 + kTileM && n0 < m.r; n0 += bn) out.push_back({k, m0, n0, 0});
   });
   // level-local offsets of the step-3 partial products
   h->part_max = 0;

@@ -62,7 +62,7 @@ int alloc(pselinv_handle* h, void** dst, int64_t bytes) {
 }
 
 void free_device(pselinv_handle* h) {
-  void** ptrs[] = {&h->d_meta, &h->d_desc, &h->d_relidx, &h->d_valmap, &h->d_tasks, &h->d_levelsn,
+  void** ptrs[] = {&h->d_meta, &h->d_desc, &h->d_relidx, &h->d_valmap, &h->d_diagmask, &h->d_tasks, &h->d_levelsn,
                    &h->d_L,    &h->d_X,    &h->d_D,      &h->d_lhat,   &h->d_linv,  &h->d_part, &h->d_status};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
@@ -91,6 +91,7 @@ int ensure_device(pselinv_handle* h) {
   if ((rc = upload(h, &h->d_desc, h->desc))) return rc;
   if ((rc = upload(h, &h->d_relidx, h->relidx))) return rc;
   if ((rc = upload(h, &h->d_valmap, h->valmap))) return rc;
+  if ((rc = upload(h, &h->d_diagmask, h->diagmask))) return rc;
   if ((rc = upload(h, &h->d_levelsn, h->level_sn))) return rc;
   std::vector<psi::Task> all;
   h->off_lhat = (int64_t)all.size();
@@ -118,6 +119,24 @@ int ensure_device(pselinv_handle* h) {
 
 const psi::Task* tasks_at(const pselinv_handle* h, int64_t base, int64_t off) {
   return (const psi::Task*)h->d_tasks + base + off;
+}
+
+psi::KArgs kargs(pselinv_handle* h) {
+  psi::KArgs a;
+  a.dtype = h->opts.dtype;
+  a.maxw = h->max_width;
+  a.meta = (const psi::SnMeta*)h->d_meta;
+  a.desc = (const psi::ColDesc*)h->d_desc;
+  a.relidx = (const int32_t*)h->d_relidx;
+  a.L = h->d_L;
+  a.D = h->d_D;
+  a.Linv = h->d_linv;
+  a.Lhat = h->d_lhat;
+  a.X = h->d_X;
+  a.part = h->d_part;
+  a.status = (int*)h->d_status;
+  a.sz = sizes(h);
+  return a;
 }
 
 // Optional event bracketing of one kernel class (pselinv_set_timing).
@@ -162,46 +181,62 @@ struct Timer {
 
 // Enqueue one schedule of the selected inversion on stream st.
 int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record) {
-  const psi::Sizes sz = sizes(h);
-  const auto* meta = (const psi::SnMeta*)h->d_meta;
-  const auto* desc = (const psi::ColDesc*)h->d_desc;
-  const auto* rel = (const int32_t*)h->d_relidx;
+  using psi::Kern;
+  const psi::KArgs a = kargs(h);
   const auto* lsn = (const int32_t*)h->d_levelsn;
-  double* X = (double*)h->d_X;
-  double* Lhat = (double*)h->d_lhat;
-  double* part = (double*)h->d_part;
   Timer tm{h, st, record};
   int rc;
-  const int64_t nlhat = (int64_t)h->t_lhat.tasks.size();
-  rc = tm.run(0, 1 + (nlhat > 0), [&] {
-    return psi::launch_normalise(meta, h->nsn, tasks_at(h, h->off_lhat, 0), nlhat, (const double*)h->d_L,
-                                 (const double*)h->d_D, (double*)h->d_linv, Lhat, X, h->max_width, sz, st);
+  // normalisation pass: every supernode at once (Algorithm 3, first loop)
+  int64_t nlhat_launch = 0;
+  for (int v = 0; v < psi::kNumVar; ++v) nlhat_launch += h->t_lhat.whole[v].end > h->t_lhat.whole[v].begin;
+  rc = tm.run(0, 1 + nlhat_launch, [&] {
+    cudaError_t e = psi::launch_per_sn(Kern::NormDiag, a, nullptr, h->nsn, st);
+    for (int v = 0; v < psi::kNumVar && e == cudaSuccess; ++v) {
+      const psi::Range r = h->t_lhat.whole[v];
+      e = psi::launch_tiles(Kern::Lhat, v, a, tasks_at(h, h->off_lhat, r.begin), r.end - r.begin, st);
+    }
+    return e;
   });
   if (rc) return rc;
-  auto step = [&](const int32_t* sns, int nsn_step, psi::Range r1, psi::Range r2) {
-    int e;
-    if ((e = tm.run(1, r1.end > r1.begin, [&] {
-           return psi::launch_gemm1(meta, tasks_at(h, h->off_gemm1, r1.begin), r1.end - r1.begin, desc, rel, Lhat,
-                                    X, sz, st);
+  // one step: the given supernodes, with per-variant task ranges of steps 2 and 3
+  auto step = [&](const int32_t* sns, int nsn_step, const psi::Range* r1, const psi::Range* r2) {
+    int n1 = 0, n2 = 0, e;
+    for (int v = 0; v < psi::kNumVar; ++v) {
+      n1 += r1[v].end > r1[v].begin;
+      n2 += r2[v].end > r2[v].begin;
+    }
+    if ((e = tm.run(1, n1, [&] {
+           cudaError_t x = cudaSuccess;
+           for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
+             x = psi::launch_tiles(Kern::Gemm1, v, a, tasks_at(h, h->off_gemm1, r1[v].begin), r1[v].end - r1[v].begin,
+                                   st);
+           return x;
          })))
       return e;
-    if ((e = tm.run(2, r2.end > r2.begin, [&] {
-           return psi::launch_gemm2(meta, tasks_at(h, h->off_gemm2, r2.begin), r2.end - r2.begin, Lhat, X, part,
-                                    sz, st);
+    if ((e = tm.run(2, n2, [&] {
+           cudaError_t x = cudaSuccess;
+           for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
+             x = psi::launch_tiles(Kern::Gemm2, v, a, tasks_at(h, h->off_gemm2, r2[v].begin), r2[v].end - r2[v].begin,
+                                   st);
+           return x;
          })))
       return e;
-    return tm.run(3, nsn_step > 0, [&] { return psi::launch_diag_final(meta, sns, nsn_step, part, X, sz, st); });
+    return tm.run(3, nsn_step > 0, [&] { return psi::launch_per_sn(Kern::DiagFinal, a, sns, nsn_step, st); });
   };
   if (mode == PSELINV_PLAIN) {
     // one supernode per launch, reverse postorder (descending index)
     std::vector<int32_t> pos(h->nsn);
     for (int32_t t = 0; t < h->nsn; ++t) pos[h->level_sn[t]] = t;
-    for (int32_t k = h->nsn - 1; k >= 0; --k)
-      if ((rc = step(lsn + pos[k], 1, h->t_gemm1.per_sn[k], h->t_gemm2.per_sn[k]))) return rc;
+    for (int32_t k = h->nsn - 1; k >= 0; --k) {
+      psi::Range r1[psi::kNumVar], r2[psi::kNumVar];
+      r1[h->t_gemm1.var[k]] = h->t_gemm1.per_sn[k];
+      r2[h->t_gemm2.var[k]] = h->t_gemm2.per_sn[k];
+      if ((rc = step(lsn + pos[k], 1, r1, r2))) return rc;
+    }
   } else {
     for (int32_t l = 0; l < h->nlevels; ++l)
-      if ((rc = step(lsn + h->level_ptr[l], h->level_ptr[l + 1] - h->level_ptr[l], h->t_gemm1.per_level[l],
-                     h->t_gemm2.per_level[l])))
+      if ((rc = step(lsn + h->level_ptr[l], h->level_ptr[l + 1] - h->level_ptr[l],
+                     &h->t_gemm1.per_lv[(size_t)l * psi::kNumVar], &h->t_gemm2.per_lv[(size_t)l * psi::kNumVar])))
         return rc;
   }
   return PSELINV_OK;
@@ -241,10 +276,6 @@ int pselinv_analyze(int64_t n, const int64_t* h_colptr, const int32_t* h_rowind,
     delete h;
     return set_err(nullptr, PSELINV_ERR_ARG, "dtype must be PSELINV_F64 or PSELINV_C128");
   }
-  if (h->opts.dtype == PSELINV_C128) {
-    delete h;
-    return set_err(nullptr, PSELINV_ERR_ARG, "complex128 values are not supported by this build");
-  }
   if (h->opts.batch < 1 || h->opts.batch > 65535) {
     delete h;
     return set_err(nullptr, PSELINV_ERR_ARG, "batch must be 1..65535");
@@ -268,21 +299,26 @@ int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream) {
   const psi::Sizes sz = sizes(h);
   const int64_t B = h->opts.batch;
   h->factored = h->inverted = false;
-  PSI_CUDA(h, cudaMemsetAsync(h->d_L, 0, sizeof(double) * B * h->panel_total, st));
+  PSI_CUDA(h, cudaMemsetAsync(h->d_L, 0, elem_size(h) * B * h->panel_total, st));
   PSI_CUDA(h, cudaMemsetAsync(h->d_status, 0x7f, sizeof(int), st));
   PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + 1, 0, sizeof(int) * (kStatusWords - 1), st));
-  PSI_CUDA(h, psi::launch_scatter_values((const double*)d_values, (const int64_t*)h->d_valmap, h->nnz_a,
-                                         (double*)h->d_L, sz, st));
-  const auto* meta = (const psi::SnMeta*)h->d_meta;
+  const psi::KArgs a = kargs(h);
+  PSI_CUDA(h, psi::launch_scatter_values(h->opts.dtype, d_values, (const int64_t*)h->d_valmap, h->nnz_a, h->d_L,
+                                         sz, st));
   const auto* lsn = (const int32_t*)h->d_levelsn;
   for (int32_t l = h->nlevels - 1; l >= 0; --l) {
-    const psi::Range rt = h->t_trsm.per_level[l], rs = h->t_schur.per_level[l];
-    PSI_CUDA(h, psi::launch_factor_level(meta, lsn + h->level_ptr[l], h->level_ptr[l + 1] - h->level_ptr[l],
-                                         tasks_at(h, h->off_trsm, rt.begin), rt.end - rt.begin,
-                                         tasks_at(h, h->off_schur, rs.begin), rs.end - rs.begin,
-                                         (const psi::ColDesc*)h->d_desc, (const int32_t*)h->d_relidx,
-                                         (double*)h->d_L, (double*)h->d_D, (double*)h->d_linv,
-                                         (double*)h->d_lhat, h->max_width, sz, (int*)h->d_status, st));
+    const int32_t* sns = lsn + h->level_ptr[l];
+    const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
+    PSI_CUDA(h, psi::launch_per_sn(psi::Kern::FactorDiag, a, sns, nsl, st));
+    for (int v = 0; v < psi::kNumVar; ++v) {
+      const psi::Range r = h->t_trsm.per_lv[(size_t)l * psi::kNumVar + v];
+      PSI_CUDA(h, psi::launch_tiles(psi::Kern::Trsm, v, a, tasks_at(h, h->off_trsm, r.begin), r.end - r.begin, st));
+    }
+    PSI_CUDA(h, psi::launch_per_sn(psi::Kern::CopyBack, a, sns, nsl, st));
+    for (int v = 0; v < psi::kNumVar; ++v) {
+      const psi::Range r = h->t_schur.per_lv[(size_t)l * psi::kNumVar + v];
+      PSI_CUDA(h, psi::launch_tiles(psi::Kern::Schur, v, a, tasks_at(h, h->off_schur, r.begin), r.end - r.begin, st));
+    }
   }
   int status[2];
   PSI_CUDA(h, cudaMemcpyAsync(status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
@@ -352,8 +388,17 @@ int pselinv_get_panels(pselinv_handle* h, int32_t which, void* d_out, void* stre
 int pselinv_get_selected(pselinv_handle* h, void* d_out, void* stream) {
   if (!h || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
   if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
-  PSI_CUDA(h, psi::launch_gather_values((const double*)h->d_X, (const int64_t*)h->d_valmap, h->nnz_a,
-                                        (double*)d_out, sizes(h), (cudaStream_t)stream));
+  PSI_CUDA(h, psi::launch_gather_values(h->opts.dtype, h->d_X, (const int64_t*)h->d_valmap, nullptr, h->nnz_a,
+                                        d_out, sizes(h), (cudaStream_t)stream));
+  return PSELINV_OK;
+}
+
+int pselinv_logdet_grad(pselinv_handle* h, void* d_out, void* stream) {
+  if (!h || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
+  PSI_CUDA(h, psi::launch_gather_values(h->opts.dtype, h->d_X, (const int64_t*)h->d_valmap,
+                                        (const uint8_t*)h->d_diagmask, h->nnz_a, d_out, sizes(h),
+                                        (cudaStream_t)stream));
   return PSELINV_OK;
 }
 
@@ -362,7 +407,7 @@ int pselinv_logdet(pselinv_handle* h, double* h_out, void* stream) {
   if (!h->factored) return set_err(h, PSELINV_ERR_STATE, "no factor yet");
   cudaStream_t st = (cudaStream_t)stream;
   double* dev = (double*)((int*)h->d_status + kStatusWords);
-  PSI_CUDA(h, psi::launch_logdet((const double*)h->d_D, h->n, dev, h->opts.batch, st));
+  PSI_CUDA(h, psi::launch_logdet(h->opts.dtype, h->d_D, h->n, dev, h->opts.batch, st));
   PSI_CUDA(h, cudaMemcpyAsync(h_out, dev, sizeof(double) * 2 * h->opts.batch, cudaMemcpyDeviceToHost, st));
   PSI_CUDA(h, cudaStreamSynchronize(st));
   return PSELINV_OK;

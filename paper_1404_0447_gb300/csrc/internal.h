@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <climits>
 #include <string>
 #include <vector>
 
@@ -52,10 +53,33 @@ constexpr int kChunkRows = 512;  // rows per step-3 partial product
 constexpr int kTileM = 64;       // output tile rows of the grouped GEMMs
 constexpr int kTileN = 64;       // output tile columns
 
+// Tile-width variants of the tile GEMMs: BN = 8 << var.
+constexpr int kNumVar = 4;
+
+// Tile width of an output with `width` columns: the variant with the least
+// padded width ceil(width / BN) * BN, the wider tile on ties; complex tiles
+// stop at BN = 32 (register budget).
+inline int pick_variant(int width, bool cplx) {
+  const int maxv = cplx ? 2 : 3;
+  int best = 0;
+  int64_t best_pad = INT64_MAX;
+  for (int v = 0; v <= maxv; ++v) {
+    const int bn = 8 << v;
+    const int64_t pad = (int64_t)((width + bn - 1) / bn) * bn;
+    if (pad <= best_pad) {
+      best_pad = pad;
+      best = v;
+    }
+  }
+  return best;
+}
+
 struct TaskList {
   std::vector<Task> tasks;
-  std::vector<Range> per_level;  // indexed by level (0 = root level)
-  std::vector<Range> per_sn;     // indexed by supernode
+  std::vector<Range> per_lv;  // [level * kNumVar + var] (level 0 = root level)
+  std::vector<Range> per_sn;  // [supernode]
+  std::vector<int8_t> var;    // [supernode] tile variant used for that supernode
+  Range whole[kNumVar];       // lists built variant-major over all levels
 };
 
 }  // namespace psi
@@ -73,6 +97,7 @@ struct pselinv_handle {
   std::vector<int32_t> rows, relidx, nblk;
   std::vector<int64_t> rowptr, panel_off, relptr;
   std::vector<int64_t> valmap;  // user entry q -> panel offset of (i, j), i >= j internal
+  std::vector<uint8_t> diagmask;  // user entry q is a diagonal entry
   std::vector<psi::SnMeta> meta;
   std::vector<psi::ColDesc> desc;
   int64_t panel_total = 0, lhat_total = 0, linv_total = 0, part_max = 0;
@@ -96,6 +121,7 @@ struct pselinv_handle {
   void* d_desc = nullptr;
   void* d_relidx = nullptr;
   void* d_valmap = nullptr;
+  void* d_diagmask = nullptr;
   void* d_tasks = nullptr;  // all task arrays back to back
   int64_t off_lhat = 0, off_gemm1 = 0, off_gemm2 = 0, off_trsm = 0, off_schur = 0;
   void* d_levelsn = nullptr;

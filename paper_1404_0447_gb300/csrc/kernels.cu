@@ -1,9 +1,11 @@
-// Device kernels of the supernodal LDL^T and the selected inversion.
+// Device kernels of the supernodal LDL^T and the selected inversion,
+// templated on the scalar (double, or complex symmetric Cplx) and on the
+// output tile width BN of the tile GEMMs.
 //
-// Storage (per batch member, offsets in SnMeta): L and X panels are
-// (s + r) x s column-major blocks with ld = s + r whose rows are the
-// supernode's own columns followed by R(K) = C; Lhat_{C,K} is r x s with
-// ld = r; (L_KK)^{-1} is s x s with ld = s; D holds the pivots.
+// Storage (per batch member, offsets in SnMeta, elements of the scalar):
+// L and X panels are (s + r) x s column-major blocks with ld = s + r whose
+// rows are the supernode's own columns followed by R(K) = C; Lhat_{C,K} is
+// r x s with ld = r; (L_KK)^{-1} is s x s with ld = s; D holds the pivots.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -12,135 +14,177 @@
 
 namespace psi {
 
-// --------------------------------------------------------------------------
-// small helpers
-// --------------------------------------------------------------------------
-
 // packed lower-triangular index, column-major: (i, j), i >= j, order s
 __device__ __forceinline__ int pk(int i, int j, int s) { return j * s - (j * (j - 1)) / 2 + (i - j); }
 
-__device__ __forceinline__ bool bad_pivot(double d) { return !(isfinite(d)) || d == 0.0; }
-
-__device__ void report_pivot(int* status, int col, double d) {
+__device__ void report_pivot(int* status, int col, bool zero) {
   atomicMin(&status[0], col);
-  atomicMax(&status[1], d == 0.0 ? 1 : 2);
+  atomicMax(&status[1], zero ? 1 : 2);
 }
 
 // --------------------------------------------------------------------------
 // value scatter / selected-entry gather (HBM-bound, index driven)
 // --------------------------------------------------------------------------
 
-__global__ void k_scatter_values(const double* __restrict__ vals, const int64_t* __restrict__ vmap,
-                                 int64_t nnz, double* __restrict__ L, int64_t panel_total) {
+template <class T>
+__global__ void k_scatter_values(const T* __restrict__ vals, const int64_t* __restrict__ vmap, int64_t nnz,
+                                 T* __restrict__ L, int64_t panel_total) {
   const int b = blockIdx.y;
-  const double* v = vals + (int64_t)b * nnz;
-  double* Lb = L + (int64_t)b * panel_total;
+  const T* v = vals + (int64_t)b * nnz;
+  T* Lb = L + (int64_t)b * panel_total;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x)
     Lb[vmap[q]] = v[q];
 }
 
-__global__ void k_gather_values(const double* __restrict__ X, int64_t panel_total, const int64_t* __restrict__ vmap,
-                                int64_t nnz, double* __restrict__ out) {
+// out[q] = X at the panel position of stored entry q; with a diagonal mask,
+// off-diagonal entries are doubled (gradient with respect to a stored value
+// that stands for both A_ij and A_ji).
+template <class T>
+__global__ void k_gather_values(const T* __restrict__ X, int64_t panel_total, const int64_t* __restrict__ vmap,
+                                const uint8_t* __restrict__ diagmask, int64_t nnz, T* __restrict__ out) {
   const int b = blockIdx.y;
-  const double* Xb = X + (int64_t)b * panel_total;
-  double* o = out + (int64_t)b * nnz;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x)
-    o[q] = Xb[vmap[q]];
+  const T* Xb = X + (int64_t)b * panel_total;
+  T* o = out + (int64_t)b * nnz;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+    const T v = Xb[vmap[q]];
+    o[q] = (diagmask && !diagmask[q]) ? 2.0 * v : v;
+  }
 }
 
 // --------------------------------------------------------------------------
-// factorisation: dense LDL^T of the diagonal block and its inverse
+// diagonal blocks
 // --------------------------------------------------------------------------
 
-// One CTA per supernode of the level.  The s x s diagonal block (lower part,
-// already holding A_KK minus all descendant updates) is factored in shared
-// memory by right-looking LDL^T; L_KK (unit diagonal implied, d_j written on
-// the diagonal slot) goes back to the panel, d to D, and (L_KK)^{-1} to linv.
-__global__ void k_factor_diag(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns, double* __restrict__ L,
-                              double* __restrict__ D, double* __restrict__ Linv, Sizes sz, int* status) {
-  extern __shared__ double sh[];
+// V = (L_KK)^{-1} for the unit lower triangle held packed in Tp (shared
+// memory), written column-major to global memory (ld s, zeros above the
+// diagonal); one column per thread.
+template <class T>
+__device__ void unit_lower_inverse(const T* Tp, int s, T* V) {
+  for (int c = threadIdx.x; c < s; c += blockDim.x) {
+    for (int i = 0; i < c; ++i) V[i + c * s] = Sc<T>::zero();
+    V[c + c * s] = Sc<T>::one();
+    for (int i = c + 1; i < s; ++i) {
+      T acc = Sc<T>::zero();
+      for (int q = c; q < i; ++q) acc += Tp[pk(i, q, s)] * V[q + c * s];
+      V[i + c * s] = -acc;
+    }
+  }
+}
+
+// Factorisation, one CTA per supernode of the level: right-looking LDL^T of
+// the s x s diagonal block (lower part, already holding A_KK minus all
+// descendant updates) in shared memory; L_KK (unit diagonal implied, d_j on
+// the diagonal slot) back to the panel, d to D, (L_KK)^{-1} to linv.
+template <class T>
+__global__ void k_factor_diag(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns, T* __restrict__ L,
+                              T* __restrict__ D, T* __restrict__ Linv, Sizes sz, int* status) {
+  extern __shared__ __align__(16) unsigned char shraw[];
+  T* Tp = reinterpret_cast<T*>(shraw);
   const int k = sns[blockIdx.x];
   const int b = blockIdx.y;
   const SnMeta m = meta[k];
   const int s = m.s, ld = m.s + m.r;
-  double* P = L + b * sz.panel + m.panel;
-  double* T = sh;                         // packed L_KK, s(s+1)/2
-  double* V = sh + s * (s + 1) / 2;       // packed inverse
+  T* P = L + b * sz.panel + m.panel;
   const int nt = blockDim.x, t = threadIdx.x;
   for (int e = t; e < s * s; e += nt) {
     const int i = e % s, j = e / s;
-    if (i >= j) T[pk(i, j, s)] = P[i + (int64_t)j * ld];
+    if (i >= j) Tp[pk(i, j, s)] = P[i + (int64_t)j * ld];
   }
   __syncthreads();
   for (int j = 0; j < s; ++j) {
-    const double d = T[pk(j, j, s)];
-    if (t == 0 && bad_pivot(d)) report_pivot(status, m.f + j, d);
-    for (int i = j + 1 + t; i < s; i += nt) T[pk(i, j, s)] /= d;
+    const T d = Tp[pk(j, j, s)];
+    if (t == 0 && Sc<T>::bad(d)) report_pivot(status, m.f + j, Sc<T>::is_zero(d));
+    for (int i = j + 1 + t; i < s; i += nt) Tp[pk(i, j, s)] = Tp[pk(i, j, s)] / d;
     __syncthreads();
     const int w = s - j - 1;
     for (int e = t; e < w * w; e += nt) {
       const int ii = j + 1 + e % w, kk = j + 1 + e / w;
-      if (ii >= kk) T[pk(ii, kk, s)] -= T[pk(ii, j, s)] * T[pk(kk, j, s)] * d;
+      if (ii >= kk) Tp[pk(ii, kk, s)] -= Tp[pk(ii, j, s)] * Tp[pk(kk, j, s)] * d;
     }
     __syncthreads();
   }
-  // inverse of the unit lower triangle, one column per thread
-  for (int c = t; c < s; c += nt) {
-    V[pk(c, c, s)] = 1.0;
-    for (int i = c + 1; i < s; ++i) {
-      double acc = 0.0;
-      for (int q = c; q < i; ++q) acc += T[pk(i, q, s)] * V[pk(q, c, s)];
-      V[pk(i, c, s)] = -acc;
-    }
+  T* V = Linv + b * sz.linv + m.linv;
+  unit_lower_inverse(Tp, s, V);
+  for (int e = t; e < s * s; e += nt) {
+    const int i = e % s, j = e / s;
+    if (i >= j) P[i + (int64_t)j * ld] = Tp[pk(i, j, s)];
   }
+  for (int j = t; j < s; j += nt) D[b * sz.n + m.f + j] = Tp[pk(j, j, s)];
+}
+
+// Normalisation, diagonal part (all supernodes, one CTA each):
+// (L_KK)^{-1} -> linv and M_K = L_KK^{-T} D_K^{-1} L_KK^{-1} -> the diagonal
+// block of the X panel (Algorithm 1 step 3's first term; U_KK = D_K L_KK^T).
+template <class T>
+__global__ void k_norm_diag(const SnMeta* __restrict__ meta, const T* __restrict__ L, const T* __restrict__ D,
+                            T* __restrict__ Linv, T* __restrict__ X, Sizes sz) {
+  extern __shared__ __align__(16) unsigned char shraw[];
+  T* Tp = reinterpret_cast<T*>(shraw);
+  const int k = blockIdx.x;
+  const int b = blockIdx.y;
+  const SnMeta m = meta[k];
+  const int s = m.s, ld = m.s + m.r;
+  const T* P = L + b * sz.panel + m.panel;
+  const T* d = D + b * sz.n + m.f;
+  T* rd = Tp + s * (s + 1) / 2;  // 1 / d_q
+  const int nt = blockDim.x, t = threadIdx.x;
+  for (int e = t; e < s * s; e += nt) {
+    const int i = e % s, j = e / s;
+    if (i > j) Tp[pk(i, j, s)] = P[i + (int64_t)j * ld];
+  }
+  for (int q = t; q < s; q += nt) rd[q] = Sc<T>::one() / d[q];
   __syncthreads();
-  double* Vi = Linv + b * sz.linv + m.linv;
+  T* V = Linv + b * sz.linv + m.linv;
+  unit_lower_inverse(Tp, s, V);
+  __syncthreads();
+  T* XK = X + b * sz.panel + m.panel;
   for (int e = t; e < s * s; e += nt) {
     const int i = e % s, j = e / s;
     if (i >= j) {
-      P[i + (int64_t)j * ld] = T[pk(i, j, s)];
-      Vi[i + j * s] = V[pk(i, j, s)];
-    } else {
-      Vi[i + j * s] = 0.0;
+      T acc = Sc<T>::zero();
+      for (int q = i; q < s; ++q) acc += V[q + i * s] * rd[q] * V[q + j * s];
+      XK[i + (int64_t)j * ld] = acc;
+      XK[j + (int64_t)i * ld] = acc;
     }
   }
-  for (int j = t; j < s; j += nt) D[b * sz.n + m.f + j] = T[pk(j, j, s)];
 }
 
-// Off-diagonal panel solve: Ltmp_{C,K} = A_{C,K} (L_KK)^{-T} D_K^{-1}
-// (tiles of r x s), written to the scratch buffer, then copied back.
-__global__ void __launch_bounds__(TG_THREADS) k_trsm(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
-                                                     const double* __restrict__ L, const double* __restrict__ D,
-                                                     const double* __restrict__ Linv, double* __restrict__ Ltmp,
-                                                     Sizes sz) {
-  __shared__ TileSmem sm;
-  const Task tk = tasks[blockIdx.x];
+// Step 3 finish: X_KK = (Z + Z^T) / 2 with Z = M_K - sum_c P_c (the
+// symmetrisation at the end of Section 2.1 / Algorithm 3).  One thread per
+// unordered pair {i, j} reads and writes exactly (i, j) and (j, i).
+template <class T>
+__global__ void k_diag_final(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns,
+                             const T* __restrict__ part, T* __restrict__ X, Sizes sz) {
+  const int k = sns[blockIdx.x];
   const int b = blockIdx.y;
-  const SnMeta m = meta[tk.sn];
-  const int s = m.s, r = m.r, ld = s + r;
-  const double* A = L + b * sz.panel + m.panel + s;          // rows below the diagonal block
-  const double* Vi = Linv + b * sz.linv + m.linv;
-  const double* d = D + b * sz.n + m.f;
-  double acc[4][4][2] = {};
-  auto la = [&](int mm, int kk) { const int row = tk.m0 + mm; return row < r ? A[row + (int64_t)kk * ld] : 0.0; };
-  auto lb = [&](int kk, int nn) { const int col = tk.n0 + nn; return col < s ? Vi[col + kk * s] : 0.0; };
-  tile_mma(sm, 0, s, [](int) { return false; }, la, lb, acc);
-  double* out = Ltmp + b * sz.lhat + m.lhat;
-  tile_epilogue(acc, [&](int mm, int nn, double v) {
-    const int row = tk.m0 + mm, col = tk.n0 + nn;
-    if (row < r && col < s) out[row + (int64_t)col * r] = v / d[col];
-  });
+  const SnMeta m = meta[k];
+  const int s = m.s, ld = m.s + m.r;
+  T* XK = X + b * sz.panel + m.panel;
+  const T* pp = part + b * sz.part + m.part;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    if (i < j) continue;
+    T zij = XK[i + (int64_t)j * ld], zji = XK[j + (int64_t)i * ld];
+    for (int c = 0; c < m.nchunk; ++c) {
+      zij -= pp[(int64_t)c * s * s + i + j * s];
+      zji -= pp[(int64_t)c * s * s + j + i * s];
+    }
+    const T x = 0.5 * (zij + zji);
+    XK[i + (int64_t)j * ld] = x;
+    XK[j + (int64_t)i * ld] = x;
+  }
 }
 
-// Copy Ltmp back into the panels of the level's supernodes.
-__global__ void k_copyback(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns, double* __restrict__ L,
-                           const double* __restrict__ Ltmp, Sizes sz) {
+// Copy the factor scratch back into the panels of the level's supernodes.
+template <class T>
+__global__ void k_copyback(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns, T* __restrict__ L,
+                           const T* __restrict__ Ltmp, Sizes sz) {
   const int k = sns[blockIdx.x];
   const int b = blockIdx.y;
   const SnMeta m = meta[k];
   const int s = m.s, r = m.r, ld = s + r;
-  double* P = L + b * sz.panel + m.panel + s;
-  const double* src = Ltmp + b * sz.lhat + m.lhat;
+  T* P = L + b * sz.panel + m.panel + s;
+  const T* src = Ltmp + b * sz.lhat + m.lhat;
   const int64_t tot = (int64_t)r * s;
   for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
     const int64_t i = e % r, j = e / r;
@@ -148,102 +192,110 @@ __global__ void k_copyback(const SnMeta* __restrict__ meta, const int32_t* __res
   }
 }
 
-// Schur-complement update of the ancestors: for the lower tiles of
-// U = L_{C,K} D_K L_{C,K}^T, subtract U[i][k] (i >= k) from the ancestor
-// entry located through the column descriptor of k and the relative index
-// of i.  Several supernodes of one level can hit the same entry: FP64
-// atomics.
-__global__ void __launch_bounds__(TG_THREADS) k_schur(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
-                                                      const ColDesc* __restrict__ desc,
-                                                      const int32_t* __restrict__ relidx, double* __restrict__ L,
-                                                      const double* __restrict__ D, const double* __restrict__ Ltmp,
-                                                      Sizes sz) {
-  __shared__ TileSmem sm;
-  const Task tk = tasks[blockIdx.x];
-  const int b = blockIdx.y;
-  const SnMeta m = meta[tk.sn];
-  const int s = m.s, r = m.r;
-  const double* Lc = Ltmp + b * sz.lhat + m.lhat;
-  const double* d = D + b * sz.n + m.f;
-  double acc[4][4][2] = {};
-  auto la = [&](int mm, int kk) { const int row = tk.m0 + mm; return row < r ? Lc[row + (int64_t)kk * r] * d[kk] : 0.0; };
-  auto lb = [&](int kk, int nn) { const int col = tk.n0 + nn; return col < r ? Lc[col + (int64_t)kk * r] : 0.0; };
-  tile_mma(sm, 0, s, [](int) { return false; }, la, lb, acc);
-  double* Lb = L + b * sz.panel;
-  const ColDesc* dk = desc + m.desc;
-  tile_epilogue(acc, [&](int mm, int nn, double v) {
-    const int i = tk.m0 + mm, kc = tk.n0 + nn;
-    if (i < r && kc <= i) {
-      const ColDesc cd = dk[kc];
-      atomicAdd(&Lb[cd.col + relidx[cd.rel + i]], -v);
-    }
-  });
-}
-
 // --------------------------------------------------------------------------
-// selected inversion
+// tile GEMMs
 // --------------------------------------------------------------------------
 
-// Normalisation, diagonal part (all supernodes, one CTA each):
-// (L_KK)^{-1} -> linv and M_K = L_KK^{-T} D_K^{-1} L_KK^{-1} -> the diagonal
-// block of the X panel (Algorithm 1 step 3's first term; U_KK = D_K L_KK^T).
-__global__ void k_norm_diag(const SnMeta* __restrict__ meta, const double* __restrict__ L, const double* __restrict__ D,
-                            double* __restrict__ Linv, double* __restrict__ X, Sizes sz) {
-  extern __shared__ double sh[];
-  const int k = blockIdx.x;
-  const int b = blockIdx.y;
-  const SnMeta m = meta[k];
-  const int s = m.s, ld = m.s + m.r;
-  const double* P = L + b * sz.panel + m.panel;
-  const double* d = D + b * sz.n + m.f;
-  double* T = sh;
-  double* V = sh + s * (s + 1) / 2;
-  const int nt = blockDim.x, t = threadIdx.x;
-  for (int e = t; e < s * s; e += nt) {
-    const int i = e % s, j = e / s;
-    if (i > j) T[pk(i, j, s)] = P[i + (int64_t)j * ld];
-  }
-  __syncthreads();
-  for (int c = t; c < s; c += nt) {
-    V[pk(c, c, s)] = 1.0;
-    for (int i = c + 1; i < s; ++i) {
-      double acc = 0.0;
-      for (int q = c; q < i; ++q) acc += T[pk(i, q, s)] * V[pk(q, c, s)];
-      V[pk(i, c, s)] = -acc;
-    }
-  }
-  __syncthreads();
-  double* Vi = Linv + b * sz.linv + m.linv;
-  double* XK = X + b * sz.panel + m.panel;
-  for (int e = t; e < s * s; e += nt) {
-    const int i = e % s, j = e / s;
-    Vi[i + j * s] = i >= j ? V[pk(i, j, s)] : 0.0;
-    if (i >= j) {
-      double acc = 0.0;
-      for (int q = i; q < s; ++q) acc += V[pk(q, i, s)] * V[pk(q, j, s)] / d[q];
-      XK[i + (int64_t)j * ld] = acc;
-      XK[j + (int64_t)i * ld] = acc;
-    }
-  }
-}
-
-// Normalisation, off-diagonal part: Lhat_{C,K} = L_{C,K} (L_KK)^{-1}.
-__global__ void __launch_bounds__(TG_THREADS) k_lhat(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
-                                                     const double* __restrict__ L, const double* __restrict__ Linv,
-                                                     double* __restrict__ Lhat, Sizes sz) {
-  __shared__ TileSmem sm;
+// Factorisation panel solve: Ltmp_{C,K} = A_{C,K} (L_KK)^{-T} D_K^{-1}.
+template <class T, int BN>
+__global__ void __launch_bounds__(TG_THREADS) k_trsm(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
+                                                     const T* __restrict__ L, const T* __restrict__ D,
+                                                     const T* __restrict__ Linv, T* __restrict__ Ltmp, Sizes sz) {
+  __shared__ TileSmem<T, BN> sm;
   const Task tk = tasks[blockIdx.x];
   const int b = blockIdx.y;
   const SnMeta m = meta[tk.sn];
   const int s = m.s, r = m.r, ld = s + r;
-  const double* A = L + b * sz.panel + m.panel + s;
-  const double* Vi = Linv + b * sz.linv + m.linv;
-  double acc[4][4][2] = {};
-  auto la = [&](int mm, int kk) { const int row = tk.m0 + mm; return row < r ? A[row + (int64_t)kk * ld] : 0.0; };
-  auto lb = [&](int kk, int nn) { const int col = tk.n0 + nn; return col < s ? Vi[kk + col * s] : 0.0; };
-  tile_mma(sm, 0, s, [](int) { return false; }, la, lb, acc);
-  double* out = Lhat + b * sz.lhat + m.lhat;
-  tile_epilogue(acc, [&](int mm, int nn, double v) {
+  const T* A = L + b * sz.panel + m.panel + s;
+  const T* Vi = Linv + b * sz.linv + m.linv;
+  const T* d = D + b * sz.n + m.f;
+  Acc<T, BN> acc;
+  acc_zero<T, BN>(acc);
+  auto la = [&](int mm, int kk) {
+    const int row = tk.m0 + mm;
+    return row < r ? A[row + (int64_t)kk * ld] : Sc<T>::zero();
+  };
+  auto lb = [&](int kk, int nn) {
+    const int col = tk.n0 + nn;
+    return col < s ? Vi[col + kk * s] : Sc<T>::zero();
+  };
+  tile_mma<T, BN>(sm, 0, s, [](int) { return false; }, la, lb, acc);
+  T* out = Ltmp + b * sz.lhat + m.lhat;
+  tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+    const int row = tk.m0 + mm, col = tk.n0 + nn;
+    if (row < r && col < s) out[row + (int64_t)col * r] = v / d[col];
+  });
+}
+
+// Schur-complement update of the ancestors: lower tiles of
+// U = L_{C,K} D_K L_{C,K}^T; U[i][k] (i >= k) is subtracted from the ancestor
+// entry found through the column descriptor of k and the relative index of i.
+// Several supernodes of one level can hit the same entry: FP64 atomics.
+template <class T, int BN>
+__global__ void __launch_bounds__(TG_THREADS) k_schur(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
+                                                      const ColDesc* __restrict__ desc,
+                                                      const int32_t* __restrict__ relidx, T* __restrict__ L,
+                                                      const T* __restrict__ D, const T* __restrict__ Ltmp, Sizes sz) {
+  __shared__ TileSmem<T, BN> sm;
+  const Task tk = tasks[blockIdx.x];
+  const int b = blockIdx.y;
+  const SnMeta m = meta[tk.sn];
+  const int s = m.s, r = m.r;
+  const T* Lc = Ltmp + b * sz.lhat + m.lhat;
+  const T* d = D + b * sz.n + m.f;
+  Acc<T, BN> acc;
+  acc_zero<T, BN>(acc);
+  auto la = [&](int mm, int kk) {
+    const int row = tk.m0 + mm;
+    return row < r ? Lc[row + (int64_t)kk * r] * d[kk] : Sc<T>::zero();
+  };
+  auto lb = [&](int kk, int nn) {
+    const int col = tk.n0 + nn;
+    return col < r ? Lc[col + (int64_t)kk * r] : Sc<T>::zero();
+  };
+  tile_mma<T, BN>(sm, 0, s, [](int) { return false; }, la, lb, acc);
+  T* Lb = L + b * sz.panel;
+  const ColDesc* dk = desc + m.desc;
+  tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+    const int i = tk.m0 + mm, kc = tk.n0 + nn;
+    if (i < r && kc <= i) {
+      const ColDesc cd = dk[kc];
+      T* dst = &Lb[cd.col + relidx[cd.rel + i]];
+      if constexpr (Sc<T>::P == 1) {
+        atomicAdd(dst, -v);
+      } else {
+        atomicAdd(&reinterpret_cast<double*>(dst)[0], -v.re);
+        atomicAdd(&reinterpret_cast<double*>(dst)[1], -v.im);
+      }
+    }
+  });
+}
+
+// Normalisation, off-diagonal part: Lhat_{C,K} = L_{C,K} (L_KK)^{-1}.
+template <class T, int BN>
+__global__ void __launch_bounds__(TG_THREADS) k_lhat(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
+                                                     const T* __restrict__ L, const T* __restrict__ Linv,
+                                                     T* __restrict__ Lhat, Sizes sz) {
+  __shared__ TileSmem<T, BN> sm;
+  const Task tk = tasks[blockIdx.x];
+  const int b = blockIdx.y;
+  const SnMeta m = meta[tk.sn];
+  const int s = m.s, r = m.r, ld = s + r;
+  const T* A = L + b * sz.panel + m.panel + s;
+  const T* Vi = Linv + b * sz.linv + m.linv;
+  Acc<T, BN> acc;
+  acc_zero<T, BN>(acc);
+  auto la = [&](int mm, int kk) {
+    const int row = tk.m0 + mm;
+    return row < r ? A[row + (int64_t)kk * ld] : Sc<T>::zero();
+  };
+  auto lb = [&](int kk, int nn) {
+    const int col = tk.n0 + nn;
+    return col < s ? Vi[kk + col * s] : Sc<T>::zero();
+  };
+  tile_mma<T, BN>(sm, 0, s, [](int) { return false; }, la, lb, acc);
+  T* out = Lhat + b * sz.lhat + m.lhat;
+  tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
     if (row < r && col < s) out[row + (int64_t)col * r] = v;
   });
@@ -252,104 +304,103 @@ __global__ void __launch_bounds__(TG_THREADS) k_lhat(const SnMeta* __restrict__ 
 // Step 2: X_{C,K} = -X_{C,C} Lhat_{C,K}.  X_{C,C} is read straight from the
 // ancestors' X panels: entry (i, k) with i >= k (rows of C are sorted) sits
 // in column desc[k].col at row relidx[desc[k].rel + i]; entries above the
-// diagonal use the symmetric one.  The result is written into rows s.. of
-// K's own X panel (Algorithm 3 overwrites Lhat by X_{C,K}; here Lhat stays
-// in its own buffer).
+// diagonal use the symmetric one.  The result goes to rows s.. of K's own X
+// panel (Algorithm 3 overwrites Lhat by X_{C,K}; here Lhat stays in its own
+// buffer).
+template <class T, int BN>
 __global__ void __launch_bounds__(TG_THREADS) k_gemm1(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
                                                       const ColDesc* __restrict__ desc,
-                                                      const int32_t* __restrict__ relidx, const double* __restrict__ Lhat,
-                                                      double* __restrict__ X, Sizes sz) {
-  __shared__ TileSmem sm;
+                                                      const int32_t* __restrict__ relidx, const T* __restrict__ Lhat,
+                                                      T* __restrict__ X, Sizes sz) {
+  __shared__ TileSmem<T, BN> sm;
   const Task tk = tasks[blockIdx.x];
   const int b = blockIdx.y;
   const SnMeta m = meta[tk.sn];
   const int s = m.s, r = m.r, ld = s + r;
   const ColDesc* dk = desc + m.desc;
-  const double* Xb = X + b * sz.panel;
-  const double* Lh = Lhat + b * sz.lhat + m.lhat;
-  double acc[4][4][2] = {};
+  const T* Xb = X + b * sz.panel;
+  const T* Lh = Lhat + b * sz.lhat + m.lhat;
+  Acc<T, BN> acc;
+  acc_zero<T, BN>(acc);
   auto la = [&](int mm, int kk) {
     const int i = tk.m0 + mm;
-    if (i >= r) return 0.0;
+    if (i >= r) return Sc<T>::zero();
     const int lo = i < kk ? i : kk, hi = i < kk ? kk : i;
     const ColDesc cd = dk[lo];
     return Xb[cd.col + relidx[cd.rel + hi]];
   };
-  auto lb = [&](int kk, int nn) { const int col = tk.n0 + nn; return col < s ? Lh[kk + (int64_t)col * r] : 0.0; };
-  // where a k-tile lies wholly above the tile's rows the entries come from
-  // the columns of C in the m direction: run the threads along k there so
-  // the panel reads stay contiguous
+  auto lb = [&](int kk, int nn) {
+    const int col = tk.n0 + nn;
+    return col < s ? Lh[kk + (int64_t)col * r] : Sc<T>::zero();
+  };
+  // where a k-tile lies wholly right of the tile's rows the entries come from
+  // the columns of C in the m direction: threads run along k there so the
+  // panel reads stay contiguous
   const int m0 = tk.m0;
-  tile_mma(sm, 0, r, [m0](int kt) { return kt >= m0 + TG_BM; }, la, lb, acc);
-  double* out = X + b * sz.panel + m.panel + s;
-  tile_epilogue(acc, [&](int mm, int nn, double v) {
+  tile_mma<T, BN>(sm, 0, r, [m0](int kt) { return kt >= m0 + TG_BM; }, la, lb, acc);
+  T* out = X + b * sz.panel + m.panel + s;
+  tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
     if (row < r && col < s) out[row + (int64_t)col * ld] = -v;
   });
 }
 
 // Step 3, partial products: P_c = Lhat_{rows c, K}^T X_{rows c, K} over a
-// chunk of kChunkRows rows of C (s x s tiles).
+// chunk of kChunkRows rows of C (plain transpose; s x s output tiles).
+template <class T, int BN>
 __global__ void __launch_bounds__(TG_THREADS) k_gemm2(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
-                                                      const double* __restrict__ Lhat, const double* __restrict__ X,
-                                                      double* __restrict__ part, Sizes sz) {
-  __shared__ TileSmem sm;
+                                                      const T* __restrict__ Lhat, const T* __restrict__ X,
+                                                      T* __restrict__ part, Sizes sz) {
+  __shared__ TileSmem<T, BN> sm;
   const Task tk = tasks[blockIdx.x];
   const int b = blockIdx.y;
   const SnMeta m = meta[tk.sn];
   const int s = m.s, r = m.r, ld = s + r;
-  const double* Lh = Lhat + b * sz.lhat + m.lhat;
-  const double* Y = X + b * sz.panel + m.panel + s;
-  double acc[4][4][2] = {};
-  auto la = [&](int mm, int kk) { const int i = tk.m0 + mm; return i < s ? Lh[kk + (int64_t)i * r] : 0.0; };
-  auto lb = [&](int kk, int nn) { const int col = tk.n0 + nn; return col < s ? Y[kk + (int64_t)col * ld] : 0.0; };
+  const T* Lh = Lhat + b * sz.lhat + m.lhat;
+  const T* Y = X + b * sz.panel + m.panel + s;
+  Acc<T, BN> acc;
+  acc_zero<T, BN>(acc);
+  auto la = [&](int mm, int kk) {
+    const int i = tk.m0 + mm;
+    return i < s ? Lh[kk + (int64_t)i * r] : Sc<T>::zero();
+  };
+  auto lb = [&](int kk, int nn) {
+    const int col = tk.n0 + nn;
+    return col < s ? Y[kk + (int64_t)col * ld] : Sc<T>::zero();
+  };
   const int kb = tk.c * kChunkRows, ke = min(r, kb + kChunkRows);
-  tile_mma(sm, kb, ke, [](int) { return true; }, la, lb, acc);
-  double* out = part + b * sz.part + m.part + (int64_t)tk.c * s * s;
-  tile_epilogue(acc, [&](int mm, int nn, double v) {
+  tile_mma<T, BN>(sm, kb, ke, [](int) { return true; }, la, lb, acc);
+  T* out = part + b * sz.part + m.part + (int64_t)tk.c * s * s;
+  tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
     if (row < s && col < s) out[row + col * s] = v;
   });
 }
 
-// Step 3, finish: X_KK = (Z + Z^T) / 2 with Z = M_K - sum_c P_c (the
-// symmetrisation at the end of Section 2.1 / Algorithm 3).  One thread per
-// unordered pair {i, j} reads and writes exactly (i, j) and (j, i).
-__global__ void k_diag_final(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns,
-                             const double* __restrict__ part, double* __restrict__ X, Sizes sz) {
-  const int k = sns[blockIdx.x];
-  const int b = blockIdx.y;
-  const SnMeta m = meta[k];
-  const int s = m.s, ld = m.s + m.r;
-  double* XK = X + b * sz.panel + m.panel;
-  const double* pp = part + b * sz.part + m.part;
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-    const int i = e % s, j = e / s;
-    if (i < j) continue;
-    double zij = XK[i + (int64_t)j * ld], zji = XK[j + (int64_t)i * ld];
-    for (int c = 0; c < m.nchunk; ++c) {
-      zij -= pp[(int64_t)c * s * s + i + j * s];
-      zji -= pp[(int64_t)c * s * s + j + i * s];
-    }
-    const double x = 0.5 * (zij + zji);
-    XK[i + (int64_t)j * ld] = x;
-    XK[j + (int64_t)i * ld] = x;
-  }
-}
+// --------------------------------------------------------------------------
+// log det
+// --------------------------------------------------------------------------
 
-// log det = sum_j log|d_j| and the count of negative pivots, per batch member.
-__global__ void k_logdet(const double* __restrict__ D, int64_t n, double* __restrict__ out) {
+// Real: (sum log|d_j|, number of negative pivots); complex: sum of principal
+// logs (log|d_j|, arg d_j), per batch member.
+template <class T>
+__global__ void k_logdet(const T* __restrict__ D, int64_t n, double* __restrict__ out) {
   __shared__ double s1[256];
   __shared__ double s2[256];
   const int b = blockIdx.x;
-  double a = 0.0, neg = 0.0;
+  double a = 0.0, c = 0.0;
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-    const double d = D[b * n + j];
-    a += log(fabs(d));
-    neg += d < 0.0 ? 1.0 : 0.0;
+    const T d = D[b * n + j];
+    if constexpr (Sc<T>::P == 1) {
+      a += log(fabs(d));
+      c += d < 0.0 ? 1.0 : 0.0;
+    } else {
+      a += log(hypot(d.re, d.im));
+      c += atan2(d.im, d.re);
+    }
   }
   s1[threadIdx.x] = a;
-  s2[threadIdx.x] = neg;
+  s2[threadIdx.x] = c;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
@@ -374,69 +425,128 @@ static inline unsigned blocks_for(int64_t n, int threads, int cap = 152 * 16) {
   return (unsigned)(b < cap ? b : cap);
 }
 
-cudaError_t launch_scatter_values(const double* vals, const int64_t* vmap, int64_t nnz, double* L, const Sizes& sz,
-                                  cudaStream_t st) {
-  k_scatter_values<<<dim3(blocks_for(nnz, 256), sz.batch), 256, 0, st>>>(vals, vmap, nnz, L, sz.panel);
-  return cudaGetLastError();
-}
-cudaError_t launch_gather_values(const double* X, const int64_t* vmap, int64_t nnz, double* out, const Sizes& sz,
-                                 cudaStream_t st) {
-  k_gather_values<<<dim3(blocks_for(nnz, 256), sz.batch), 256, 0, st>>>(X, sz.panel, vmap, nnz, out);
-  return cudaGetLastError();
+template <class T>
+static size_t diag_smem(int maxw) {
+  return sizeof(T) * ((size_t)maxw * (maxw + 1) / 2 + maxw);
 }
 
-static size_t diag_smem(int maxw) { return sizeof(double) * (size_t)maxw * (maxw + 1); }
+template <class T>
+static cudaError_t setup_t() {
+  cudaError_t e = cudaFuncSetAttribute(k_factor_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)diag_smem<T>(kMaxWidth));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_norm_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)diag_smem<T>(kMaxWidth));
+}
 
 cudaError_t setup_kernels() {
-  const size_t sm = diag_smem(kMaxWidth);
-  cudaError_t e = cudaFuncSetAttribute(k_factor_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = setup_t<double>();
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_norm_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return setup_t<Cplx>();
 }
 
-cudaError_t launch_factor_level(const SnMeta* meta, const int32_t* sns, int nsn_level, const Task* trsm,
-                                int64_t ntrsm, const Task* schur, int64_t nschur, const ColDesc* desc,
-                                const int32_t* relidx, double* L, double* D, double* Linv, double* Ltmp,
-                                int maxw, const Sizes& sz, int* status, cudaStream_t st) {
-  if (nsn_level <= 0) return cudaSuccess;
-  k_factor_diag<<<dim3(nsn_level, sz.batch), 256, diag_smem(maxw), st>>>(meta, sns, L, D, Linv, sz, status);
-  if (ntrsm > 0) {
-    k_trsm<<<dim3((unsigned)ntrsm, sz.batch), TG_THREADS, 0, st>>>(meta, trsm, L, D, Linv, Ltmp, sz);
-    k_copyback<<<dim3(nsn_level, sz.batch), 256, 0, st>>>(meta, sns, L, Ltmp, sz);
-  }
-  if (nschur > 0)
-    k_schur<<<dim3((unsigned)nschur, sz.batch), TG_THREADS, 0, st>>>(meta, schur, desc, relidx, L, D, Ltmp, sz);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_normalise(const SnMeta* meta, int nsn, const Task* lhat_tasks, int64_t nlhat, const double* L,
-                             const double* D, double* Linv, double* Lhat, double* X, int maxw, const Sizes& sz,
+template <class T>
+static cudaError_t scatter_t(const void* vals, const int64_t* vmap, int64_t nnz, void* L, const Sizes& sz,
                              cudaStream_t st) {
-  k_norm_diag<<<dim3(nsn, sz.batch), 256, diag_smem(maxw), st>>>(meta, L, D, Linv, X, sz);
-  if (nlhat > 0) k_lhat<<<dim3((unsigned)nlhat, sz.batch), TG_THREADS, 0, st>>>(meta, lhat_tasks, L, Linv, Lhat, sz);
+  k_scatter_values<T><<<dim3(blocks_for(nnz, 256), sz.batch), 256, 0, st>>>((const T*)vals, vmap, nnz, (T*)L,
+                                                                           sz.panel);
+  return cudaGetLastError();
+}
+cudaError_t launch_scatter_values(int dtype, const void* vals, const int64_t* vmap, int64_t nnz, void* L,
+                                  const Sizes& sz, cudaStream_t st) {
+  return dtype == PSELINV_C128 ? scatter_t<Cplx>(vals, vmap, nnz, L, sz, st)
+                               : scatter_t<double>(vals, vmap, nnz, L, sz, st);
+}
+
+template <class T>
+static cudaError_t gather_t(const void* X, const int64_t* vmap, const uint8_t* mask, int64_t nnz, void* out,
+                            const Sizes& sz, cudaStream_t st) {
+  k_gather_values<T><<<dim3(blocks_for(nnz, 256), sz.batch), 256, 0, st>>>((const T*)X, sz.panel, vmap, mask, nnz,
+                                                                          (T*)out);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_values(int dtype, const void* X, const int64_t* vmap, const uint8_t* diagmask, int64_t nnz,
+                                 void* out, const Sizes& sz, cudaStream_t st) {
+  return dtype == PSELINV_C128 ? gather_t<Cplx>(X, vmap, diagmask, nnz, out, sz, st)
+                               : gather_t<double>(X, vmap, diagmask, nnz, out, sz, st);
+}
+
+// ---- tile-kernel launch for one task range of one variant ----
+
+template <class T, int BN>
+static cudaError_t tiles_tb(Kern k, const KArgs& a, const Task* t, int64_t n, cudaStream_t st) {
+  const dim3 grid((unsigned)n, a.sz.batch);
+  switch (k) {
+    case Kern::Trsm:
+      k_trsm<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.L, (const T*)a.D, (const T*)a.Linv,
+                                                 (T*)a.Lhat, a.sz);
+      break;
+    case Kern::Schur:
+      k_schur<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, a.desc, a.relidx, (T*)a.L, (const T*)a.D,
+                                                  (const T*)a.Lhat, a.sz);
+      break;
+    case Kern::Lhat:
+      k_lhat<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.L, (const T*)a.Linv, (T*)a.Lhat, a.sz);
+      break;
+    case Kern::Gemm1:
+      k_gemm1<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, a.desc, a.relidx, (const T*)a.Lhat, (T*)a.X, a.sz);
+      break;
+    default:
+      k_gemm2<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.Lhat, (const T*)a.X, (T*)a.part, a.sz);
+      break;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm1(const SnMeta* meta, const Task* g1, int64_t ng1, const ColDesc* desc, const int32_t* relidx,
-                         const double* Lhat, double* X, const Sizes& sz, cudaStream_t st) {
-  if (ng1 > 0) k_gemm1<<<dim3((unsigned)ng1, sz.batch), TG_THREADS, 0, st>>>(meta, g1, desc, relidx, Lhat, X, sz);
+template <class T>
+static cudaError_t tiles_t(Kern k, int var, const KArgs& a, const Task* t, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  switch (var) {
+    case 0: return tiles_tb<T, 8>(k, a, t, n, st);
+    case 1: return tiles_tb<T, 16>(k, a, t, n, st);
+    case 2: return tiles_tb<T, 32>(k, a, t, n, st);
+    default:
+      if constexpr (Sc<T>::P == 1) return tiles_tb<T, 64>(k, a, t, n, st);
+      return cudaErrorInvalidValue;  // complex tiles stop at BN = 32 (register budget)
+  }
+}
+
+cudaError_t launch_tiles(Kern k, int var, const KArgs& a, const Task* t, int64_t n, cudaStream_t st) {
+  return a.dtype == PSELINV_C128 ? tiles_t<Cplx>(k, var, a, t, n, st) : tiles_t<double>(k, var, a, t, n, st);
+}
+
+template <class T>
+static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st) {
+  if (nsn <= 0) return cudaSuccess;
+  const dim3 grid(nsn, a.sz.batch);
+  switch (k) {
+    case Kern::FactorDiag:
+      k_factor_diag<T><<<grid, 256, diag_smem<T>(a.maxw), st>>>(a.meta, sns, (T*)a.L, (T*)a.D, (T*)a.Linv, a.sz,
+                                                                a.status);
+      break;
+    case Kern::CopyBack:
+      k_copyback<T><<<grid, 256, 0, st>>>(a.meta, sns, (T*)a.L, (const T*)a.Lhat, a.sz);
+      break;
+    case Kern::NormDiag:  // every supernode: blockIdx.x is the supernode itself
+      k_norm_diag<T><<<grid, 256, diag_smem<T>(a.maxw), st>>>(a.meta, (const T*)a.L, (const T*)a.D, (T*)a.Linv,
+                                                              (T*)a.X, a.sz);
+      break;
+    default:
+      k_diag_final<T><<<grid, 256, 0, st>>>(a.meta, sns, (const T*)a.part, (T*)a.X, a.sz);
+      break;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm2(const SnMeta* meta, const Task* g2, int64_t ng2, const double* Lhat, const double* X,
-                         double* part, const Sizes& sz, cudaStream_t st) {
-  if (ng2 > 0) k_gemm2<<<dim3((unsigned)ng2, sz.batch), TG_THREADS, 0, st>>>(meta, g2, Lhat, X, part, sz);
-  return cudaGetLastError();
+cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st) {
+  return a.dtype == PSELINV_C128 ? per_sn_t<Cplx>(k, a, sns, nsn, st) : per_sn_t<double>(k, a, sns, nsn, st);
 }
 
-cudaError_t launch_diag_final(const SnMeta* meta, const int32_t* sns, int nsn_step, const double* part, double* X,
-                              const Sizes& sz, cudaStream_t st) {
-  if (nsn_step > 0) k_diag_final<<<dim3(nsn_step, sz.batch), 256, 0, st>>>(meta, sns, part, X, sz);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_logdet(const double* D, int64_t n, double* out, int batch, cudaStream_t st) {
-  k_logdet<<<batch, 256, 0, st>>>(D, n, out);
+cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st) {
+  if (dtype == PSELINV_C128)
+    k_logdet<Cplx><<<batch, 256, 0, st>>>((const Cplx*)D, n, out);
+  else
+    k_logdet<double><<<batch, 256, 0, st>>>((const double*)D, n, out);
   return cudaGetLastError();
 }
 

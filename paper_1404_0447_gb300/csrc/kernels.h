@@ -7,7 +7,7 @@
 
 namespace psi {
 
-// Per-batch-member sizes (elements) of every batched array.
+// Per-batch-member sizes (elements of the scalar) of every batched array.
 struct Sizes {
   int64_t panel;  // L and X panels
   int64_t lhat;   // normalised factor / factor scratch
@@ -17,24 +17,37 @@ struct Sizes {
   int batch;
 };
 
+enum class Kern { Trsm, Schur, Lhat, Gemm1, Gemm2, FactorDiag, CopyBack, NormDiag, DiagFinal };
+
+// Everything a kernel may need; device pointers typed by dtype inside.
+struct KArgs {
+  int dtype;  // PSELINV_F64 / PSELINV_C128
+  int maxw;   // widest supernode (shared-memory size of the diagonal kernels)
+  const SnMeta* meta;
+  const ColDesc* desc;
+  const int32_t* relidx;
+  void* L;
+  void* D;
+  void* Linv;
+  void* Lhat;
+  void* X;
+  void* part;
+  int* status;
+  Sizes sz;
+};
+
 cudaError_t setup_kernels();
-cudaError_t launch_scatter_values(const double* vals, const int64_t* vmap, int64_t nnz, double* L, const Sizes& sz,
-                                  cudaStream_t st);
-cudaError_t launch_gather_values(const double* X, const int64_t* vmap, int64_t nnz, double* out, const Sizes& sz,
-                                 cudaStream_t st);
-cudaError_t launch_factor_level(const SnMeta* meta, const int32_t* sns, int nsn_level, const Task* trsm,
-                                int64_t ntrsm, const Task* schur, int64_t nschur, const ColDesc* desc,
-                                const int32_t* relidx, double* L, double* D, double* Linv, double* Ltmp, int maxw,
-                                const Sizes& sz, int* status, cudaStream_t st);
-cudaError_t launch_normalise(const SnMeta* meta, int nsn, const Task* lhat_tasks, int64_t nlhat, const double* L,
-                             const double* D, double* Linv, double* Lhat, double* X, int maxw, const Sizes& sz,
-                             cudaStream_t st);
-cudaError_t launch_gemm1(const SnMeta* meta, const Task* g1, int64_t ng1, const ColDesc* desc, const int32_t* relidx,
-                         const double* Lhat, double* X, const Sizes& sz, cudaStream_t st);
-cudaError_t launch_gemm2(const SnMeta* meta, const Task* g2, int64_t ng2, const double* Lhat, const double* X,
-                         double* part, const Sizes& sz, cudaStream_t st);
-cudaError_t launch_diag_final(const SnMeta* meta, const int32_t* sns, int nsn_step, const double* part, double* X,
-                              const Sizes& sz, cudaStream_t st);
-cudaError_t launch_logdet(const double* D, int64_t n, double* out, int batch, cudaStream_t st);
+cudaError_t launch_scatter_values(int dtype, const void* vals, const int64_t* vmap, int64_t nnz, void* L,
+                                  const Sizes& sz, cudaStream_t st);
+// diagmask == nullptr: plain gather; else off-diagonal entries doubled.
+cudaError_t launch_gather_values(int dtype, const void* X, const int64_t* vmap, const uint8_t* diagmask, int64_t nnz,
+                                 void* out, const Sizes& sz, cudaStream_t st);
+// Tile kernels (Trsm, Schur, Lhat, Gemm1, Gemm2) over n tasks of one tile
+// width variant (BN = 8 << var).
+cudaError_t launch_tiles(Kern k, int var, const KArgs& a, const Task* tasks, int64_t n, cudaStream_t st);
+// Per-supernode kernels (FactorDiag, CopyBack, NormDiag, DiagFinal) over the
+// nsn supernodes listed in sns (NormDiag: supernodes 0..nsn-1, sns unused).
+cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st);
+cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st);
 
 }  // namespace psi

@@ -58,18 +58,20 @@ __global__ void k_static_linv(int s, const double* __restrict__ L, double* __res
 __global__ void __launch_bounds__(psi::TG_THREADS) k_static_m(int s, int tiles_per_dim,
                                                               const double* __restrict__ scratch,
                                                               const double* __restrict__ d, double* __restrict__ M) {
-  __shared__ psi::TileSmem sm;
+  constexpr int BN = 64;
+  __shared__ psi::TileSmem<double, BN> sm;
   const int per_block = tiles_per_dim * tiles_per_dim;
   const int b = blockIdx.x / per_block, t = blockIdx.x % per_block;
-  const int m0 = (t % tiles_per_dim) * psi::TG_BM, n0 = (t / tiles_per_dim) * psi::TG_BN;
+  const int m0 = (t % tiles_per_dim) * psi::TG_BM, n0 = (t / tiles_per_dim) * BN;
   const double* V = scratch + (int64_t)b * s * s;
   const double* db = d + (int64_t)b * s;
-  double acc[4][4][2] = {};
+  psi::Acc<double, BN> acc;
+  psi::acc_zero<double, BN>(acc);
   auto la = [&](int mm, int q) { const int i = m0 + mm; return i < s ? V[q + i * s] / db[q] : 0.0; };
   auto lb = [&](int q, int nn) { const int j = n0 + nn; return j < s ? V[q + j * s] : 0.0; };
-  psi::tile_mma(sm, 0, s, [](int) { return true; }, la, lb, acc);
+  psi::tile_mma<double, BN>(sm, 0, s, [](int) { return true; }, la, lb, acc);
   double* Mb = M + (int64_t)b * s * s;
-  psi::tile_epilogue(acc, [&](int mm, int nn, double v) {
+  psi::tile_epilogue<double, BN>(acc, [&](int mm, int nn, double v) {
     const int i = m0 + mm, j = n0 + nn;
     if (i < s && j < s) Mb[i + j * s] = v;
   });

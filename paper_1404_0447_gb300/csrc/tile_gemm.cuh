@@ -1,56 +1,135 @@
-// FP64 tile GEMM core on the DMMA pipe (mma.sync m8n8k4 .f64; tcgen05 has
-// no f64 kind, so this is the tensor-core path for double precision on
-// sm_103a).  One CTA of 128 threads computes a 64 x 64 output tile as a
-// 2 x 2 grid of warps, each warp 32 x 32 = 4 x 4 fragments of 8 x 8.
+// FP64 tile GEMM core on sm_103a: mma.sync m8n8k4 .f64 (on GB300 these run
+// on the FP64 pipe; tcgen05 has no f64 kind).  One CTA of 128 threads
+// computes a 64 x BN output tile, BN in {8, 16, 32, 64}; complex128
+// operands are split into real and imaginary planes and each complex
+// fragment product takes four real MMAs (complex symmetric matrices: no
+// conjugation anywhere).
 //
 // Operands are fetched element by element through loader functors, so the
 // same core serves dense panels and the index-driven gather of X_{C,C}
-// (relative indices) without a staging copy in global memory.  Global
-// loads for k-tile t+1 are issued into registers before the MMAs of tile t
-// and stored to the other shared-memory buffer afterwards.
+// (relative indices) without a staging copy in global memory.  Global loads
+// for k-tile t+1 are issued into registers before the MMAs of tile t and
+// stored to the other shared-memory buffer afterwards.
 #pragma once
 
 #include <cstdint>
 
 namespace psi {
 
-constexpr int TG_BM = 64, TG_BN = 64, TG_BK = 16, TG_THREADS = 128;
-constexpr int TG_PAD = 4;  // row stride 68 doubles: conflict-free fragment reads
-constexpr int TG_LDA = TG_BM + TG_PAD, TG_LDB = TG_BN + TG_PAD;
-constexpr int TG_AREG = TG_BM * TG_BK / TG_THREADS;  // 8 elements per thread
-constexpr int TG_BREG = TG_BK * TG_BN / TG_THREADS;  // 8 elements per thread
+// ---------------------------------------------------------------------------
+// scalar types
+// ---------------------------------------------------------------------------
 
-struct TileSmem {
-  double a[2][TG_BK][TG_LDA];
-  double b[2][TG_BK][TG_LDB];
+struct Cplx {
+  double re, im;
 };
 
-// D = A(8x4) * B(4x8) + D.  Lane l holds A[l>>2][l&3], B[l&3][l>>2] and
-// D[l>>2][2*(l&3) + {0,1}].
+__host__ __device__ __forceinline__ Cplx operator+(Cplx a, Cplx b) { return {a.re + b.re, a.im + b.im}; }
+__host__ __device__ __forceinline__ Cplx operator-(Cplx a, Cplx b) { return {a.re - b.re, a.im - b.im}; }
+__host__ __device__ __forceinline__ Cplx operator-(Cplx a) { return {-a.re, -a.im}; }
+__host__ __device__ __forceinline__ Cplx operator*(Cplx a, Cplx b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__host__ __device__ __forceinline__ Cplx operator*(double a, Cplx b) { return {a * b.re, a * b.im}; }
+// a / b = a * conj(b) / |b|^2
+__host__ __device__ __forceinline__ Cplx operator/(Cplx a, Cplx b) {
+  const double den = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den};
+}
+__host__ __device__ __forceinline__ Cplx& operator+=(Cplx& a, Cplx b) { return a = a + b; }
+__host__ __device__ __forceinline__ Cplx& operator-=(Cplx& a, Cplx b) { return a = a - b; }
+
+template <class T>
+struct Sc;
+template <>
+struct Sc<double> {
+  static constexpr int P = 1;  // real planes
+  __device__ __forceinline__ static double zero() { return 0.0; }
+  __device__ __forceinline__ static double one() { return 1.0; }
+  __device__ __forceinline__ static double plane(double v, int) { return v; }
+  __device__ __forceinline__ static bool bad(double v) { return !isfinite(v) || v == 0.0; }
+  __device__ __forceinline__ static bool is_zero(double v) { return v == 0.0; }
+};
+template <>
+struct Sc<Cplx> {
+  static constexpr int P = 2;
+  __device__ __forceinline__ static Cplx zero() { return {0.0, 0.0}; }
+  __device__ __forceinline__ static Cplx one() { return {1.0, 0.0}; }
+  __device__ __forceinline__ static double plane(Cplx v, int p) { return p ? v.im : v.re; }
+  __device__ __forceinline__ static bool bad(Cplx v) {
+    return !isfinite(v.re) || !isfinite(v.im) || (v.re == 0.0 && v.im == 0.0);
+  }
+  __device__ __forceinline__ static bool is_zero(Cplx v) { return v.re == 0.0 && v.im == 0.0; }
+};
+
+// ---------------------------------------------------------------------------
+// tile geometry
+// ---------------------------------------------------------------------------
+
+constexpr int TG_BM = 64, TG_BK = 16, TG_THREADS = 128;
+constexpr int TG_LDA = TG_BM + 4;  // row stride = 4 (mod 16) doubles: conflict-free fragment reads
+
+// Warps: BN >= 32 -> 2 x 2 (warp tile 32 x BN/2); BN <= 16 -> 4 x 1 (16 x BN).
+template <int BN>
+struct Geo {
+  static constexpr int WN = BN >= 32 ? 2 : 1;
+  static constexpr int WM = 4 / WN;
+  static constexpr int FM = TG_BM / WM / 8;  // 8-row fragments per warp
+  static constexpr int FN = BN / WN / 8;     // 8-column fragments per warp
+  static constexpr int LDB = BN + 4;         // 4 (mod 16) for every BN
+  static constexpr int BREG = TG_BK * BN / TG_THREADS;
+};
+constexpr int TG_AREG = TG_BM * TG_BK / TG_THREADS;  // 8 A elements per thread per k-tile
+
+template <class T, int BN>
+struct TileSmem {
+  static constexpr int P = Sc<T>::P;
+  double a[2][P][TG_BK][TG_LDA];
+  double b[2][P][TG_BK][Geo<BN>::LDB];
+};
+
+template <class T, int BN>
+using Acc = double[Sc<T>::P][Geo<BN>::FM][Geo<BN>::FN][2];
+
+// D(8x8) += A(8x4) B(4x8).  Lane l holds A[l>>2][l&3], B[l&3][l>>2] and
+// D[l>>2][2(l&3) + {0,1}].
 __device__ __forceinline__ void dmma884(double& d0, double& d1, double a, double b) {
   asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
                : "+d"(d0), "+d"(d1)
                : "d"(a), "d"(b));
 }
 
-// Accumulates acc += A[m0:m0+64, kbeg:kend] * B[kbeg:kend, n0:n0+64].
+template <class T, int BN>
+__device__ __forceinline__ void acc_zero(Acc<T, BN>& acc) {
+  constexpr int P = Sc<T>::P;
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int i = 0; i < Geo<BN>::FM; ++i)
+#pragma unroll
+      for (int j = 0; j < Geo<BN>::FN; ++j) acc[p][i][j][0] = acc[p][i][j][1] = 0.0;
+}
+
+// acc += A[0:64, kbeg:kend] * B[kbeg:kend, 0:BN] of the tile.
 // la(m, k) (m tile-local, k global) and lb(k, n) (n tile-local) return the
-// operand element, or 0 outside the operand.  a_by_k_at(kt) picks, per
-// k-tile starting at kt, the thread mapping of the A loads:
-//   A: if a_by_k, thread t loads k = kt + t % 16, m = t / 16 + 8 j (j < 8);
-//      else        thread t loads m = t % 64,     k = t / 64 + 2 j.
-//   B: thread t loads k = kt + t % 16, n = t / 16 + 8 j.
-// acc[i][j][e] is row wm + 8 i + (lane >> 2), column wn + 8 j + 2 (lane & 3) + e
-// of the tile, with (wm, wn) = 32 * (warp % 2, warp / 2).
-template <class MA, class LA, class LB>
-__device__ __forceinline__ void tile_mma(TileSmem& sm, int kbeg, int kend, const MA& a_by_k_at, const LA& la,
-                                         const LB& lb, double (&acc)[4][4][2]) {
+// operand element (or zero outside the operand); a_by_k_at(kt) picks, per
+// k-tile, the thread mapping of the A loads:
+//   A: a_by_k: thread t loads k = kt + t % 16, m = t / 16 + 8 j (j < 8);
+//      else:   thread t loads m = t % 64,     k = kt + t / 64 + 2 j.
+//   B: thread t loads k = kt + t % 16, n = t / 16 + 8 j (j < BN / 8).
+// acc[p][i][j][e] is plane p of tile element (wm + 8 i + lane / 4,
+// wn + 8 j + 2 (lane % 4) + e), (wm, wn) = the warp's origin.
+template <class T, int BN, class MA, class LA, class LB>
+__device__ __forceinline__ void tile_mma(TileSmem<T, BN>& sm, int kbeg, int kend, const MA& a_by_k_at, const LA& la,
+                                         const LB& lb, Acc<T, BN>& acc) {
+  using G = Geo<BN>;
+  constexpr int P = Sc<T>::P;
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
-  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+  const int wm = (warp % G::WM) * (TG_BM / G::WM), wn = (warp / G::WM) * (BN / G::WN);
   const int g = lane >> 2, q = lane & 3;
-  double ra[TG_AREG], rb[TG_BREG];
-  bool a_by_k = false;  // thread mapping of the A tile held in ra
+  T ra[TG_AREG], rb[G::BREG];
+  bool a_by_k = false;
 
   auto fetch = [&](int kt) {
     a_by_k = a_by_k_at(kt);
@@ -58,31 +137,34 @@ __device__ __forceinline__ void tile_mma(TileSmem& sm, int kbeg, int kend, const
 #pragma unroll
       for (int j = 0; j < TG_AREG; ++j) {
         const int kk = kt + (t & 15), mm = (t >> 4) + 8 * j;
-        ra[j] = kk < kend ? la(mm, kk) : 0.0;
+        ra[j] = kk < kend ? la(mm, kk) : Sc<T>::zero();
       }
     } else {
 #pragma unroll
       for (int j = 0; j < TG_AREG; ++j) {
         const int kk = kt + (t >> 6) + 2 * j, mm = t & 63;
-        ra[j] = kk < kend ? la(mm, kk) : 0.0;
+        ra[j] = kk < kend ? la(mm, kk) : Sc<T>::zero();
       }
     }
 #pragma unroll
-    for (int j = 0; j < TG_BREG; ++j) {
+    for (int j = 0; j < G::BREG; ++j) {
       const int kk = kt + (t & 15), nn = (t >> 4) + 8 * j;
-      rb[j] = kk < kend ? lb(kk, nn) : 0.0;
+      rb[j] = kk < kend ? lb(kk, nn) : Sc<T>::zero();
     }
   };
   auto stash = [&](int buf) {
-    if (a_by_k) {
 #pragma unroll
-      for (int j = 0; j < TG_AREG; ++j) sm.a[buf][t & 15][(t >> 4) + 8 * j] = ra[j];
-    } else {
+    for (int p = 0; p < P; ++p) {
+      if (a_by_k) {
 #pragma unroll
-      for (int j = 0; j < TG_AREG; ++j) sm.a[buf][(t >> 6) + 2 * j][t & 63] = ra[j];
+        for (int j = 0; j < TG_AREG; ++j) sm.a[buf][p][t & 15][(t >> 4) + 8 * j] = Sc<T>::plane(ra[j], p);
+      } else {
+#pragma unroll
+        for (int j = 0; j < TG_AREG; ++j) sm.a[buf][p][(t >> 6) + 2 * j][t & 63] = Sc<T>::plane(ra[j], p);
+      }
+#pragma unroll
+      for (int j = 0; j < G::BREG; ++j) sm.b[buf][p][t & 15][(t >> 4) + 8 * j] = Sc<T>::plane(rb[j], p);
     }
-#pragma unroll
-    for (int j = 0; j < TG_BREG; ++j) sm.b[buf][t & 15][(t >> 4) + 8 * j] = rb[j];
   };
 
   const int nk = (kend - kbeg + TG_BK - 1) / TG_BK;
@@ -95,15 +177,25 @@ __device__ __forceinline__ void tile_mma(TileSmem& sm, int kbeg, int kend, const
     if (it + 1 < nk) fetch(kbeg + (it + 1) * TG_BK);
 #pragma unroll
     for (int ks = 0; ks < TG_BK; ks += 4) {
-      double fa[4], fb[4];
+      double fa[P][G::FM], fb[P][G::FN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) fa[i] = sm.a[buf][ks + q][wm + 8 * i + g];
+      for (int p = 0; p < P; ++p) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) fb[j] = sm.b[buf][ks + q][wn + 8 * j + g];
+        for (int i = 0; i < G::FM; ++i) fa[p][i] = sm.a[buf][p][ks + q][wm + 8 * i + g];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < G::FN; ++j) fb[p][j] = sm.b[buf][p][ks + q][wn + 8 * j + g];
+      }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) dmma884(acc[i][j][0], acc[i][j][1], fa[i], fb[j]);
+      for (int i = 0; i < G::FM; ++i)
+#pragma unroll
+        for (int j = 0; j < G::FN; ++j) {
+          dmma884(acc[0][i][j][0], acc[0][i][j][1], fa[0][i], fb[0][j]);
+          if constexpr (P == 2) {
+            dmma884(acc[0][i][j][0], acc[0][i][j][1], -fa[1][i], fb[1][j]);
+            dmma884(acc[1][i][j][0], acc[1][i][j][1], fa[0][i], fb[1][j]);
+            dmma884(acc[1][i][j][0], acc[1][i][j][1], fa[1][i], fb[0][j]);
+          }
+        }
     }
     if (it + 1 < nk) stash(buf ^ 1);
     __syncthreads();
@@ -111,18 +203,27 @@ __device__ __forceinline__ void tile_mma(TileSmem& sm, int kbeg, int kend, const
 }
 
 // Visit every accumulator with its tile coordinates: f(m, n, value).
-template <class F>
-__device__ __forceinline__ void tile_epilogue(const double (&acc)[4][4][2], const F& f) {
+template <class T, int BN, class F>
+__device__ __forceinline__ void tile_epilogue(const Acc<T, BN>& acc, const F& f) {
+  using G = Geo<BN>;
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
-  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+  const int wm = (warp % G::WM) * (TG_BM / G::WM), wn = (warp / G::WM) * (BN / G::WN);
   const int g = lane >> 2, q = lane & 3;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < G::FM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < G::FN; ++j)
 #pragma unroll
-      for (int e = 0; e < 2; ++e) f(wm + 8 * i + g, wn + 8 * j + 2 * q + e, acc[i][j][e]);
+      for (int e = 0; e < 2; ++e) {
+        T v;
+        if constexpr (Sc<T>::P == 1) {
+          v = acc[0][i][j][e];
+        } else {
+          v = T{acc[0][i][j][e], acc[1][i][j][e]};
+        }
+        f(wm + 8 * i + g, wn + 8 * j + 2 * q + e, v);
+      }
 }
 
 }  // namespace psi

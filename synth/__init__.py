@@ -233,6 +233,18 @@ class GraphLaplacian:
         assert np.all(keys[out] == c * self.n + r)
         return out
 
+    def assemble_torch(self, theta):
+        """Differentiable torch version of ``assemble`` (theta: float64 tensor)."""
+        import torch
+        dev = theta.device
+        idx = lambda a: torch.as_tensor(a, dtype=torch.int64, device=dev)
+        v = torch.zeros(self.rowind.size, dtype=theta.dtype, device=dev)
+        v = v.index_add(0, idx(self.pos_diag), torch.full((self.n,), self.shift, dtype=theta.dtype, device=dev))
+        v = v.index_add(0, idx(self.pos_diag[self.ei]), theta)
+        v = v.index_add(0, idx(self.pos_diag[self.ej]), theta)
+        v = v.index_add(0, idx(self.pos_edge), -theta)
+        return v
+
     def assemble(self, theta=None):
         theta = self.theta if theta is None else np.asarray(theta, np.float64)
         v = np.zeros(self.rowind.size)
