@@ -162,6 +162,22 @@ int pselinv_analyze(int64_t n, const int64_t* h_colptr, const int32_t* h_rowind,
                     const int32_t* h_perm, const pselinv_opts* opts, pselinv_handle** out);
 
 /*
+ * Symbolic analysis of an uneven batch: k independent symmetric matrices,
+ * each with its own pattern and optional ordering, analysed as the one
+ * block-diagonal matrix diag(A_0, ..., A_{k-1}).  Its elimination forest has
+ * one tree per member, so the priority lists of Algorithm 2 (roots at 1)
+ * merge the members level by level and every level runs as one grouped
+ * launch over all members.  Member b's unknowns are n_0 + ... + n_{b-1} + [0, n_b)
+ * and its stored values follow those of members 0..b-1 (values of
+ * pselinv_factor, outputs of pselinv_get_selected / pselinv_logdet_grad /
+ * pselinv_selinv_adjoint).  h_perm may be NULL, or hold NULL entries.
+ * Errors as pselinv_analyze (a member's failure names the member).
+ */
+int pselinv_analyze_batch(int32_t k, const int64_t* h_n, const int64_t* const* h_colptr,
+                          const int32_t* const* h_rowind, const int32_t* const* h_perm, const pselinv_opts* opts,
+                          pselinv_handle** out);
+
+/*
  * Numeric factorisation A = L D L^T on the device (supernodal, level by
  * level from the leaves; no pivoting, Section 4).  Not the optimisation
  * target of this library; it produces the input of the selected inversion.
@@ -220,16 +236,33 @@ int pselinv_logdet_grad(pselinv_handle* h, void* d_out, void* stream);
 int pselinv_logdet(pselinv_handle* h, double* h_out, void* stream);
 
 /*
- * Adjoint of the selected inversion: given G (device, batch x
- * panel_entries, same panel layout as X; only the lower-triangle entries
- * of each panel are read, G symmetric), returns in d_gradA (device,
- * batch x nnz_a, user order) the values of -(X G X) at A's stored
- * positions, i.e. the gradient of <G, X> (bilinear pairing over the full
- * symmetric selected pattern) with respect to each stored entry read as a
- * full-matrix entry.  Requires a prior selinv.  Uses L and D, recomputes
- * Lhat; reverse sweep leaves -> root, then the LDL^T adjoint root -> leaves.
+ * Adjoint of the selected inversion.  For J = <G, X> = sum over the full
+ * symmetric selected pattern of G_ij X_ij (bilinear: no conjugation for
+ * complex symmetric A), returns dJ/d(stored values of A's lower CSC), user
+ * order: -(X G X)_jj on the diagonal and -2 (X G X)_ij off it (a stored
+ * off-diagonal value stands for A_ij and A_ji), the same convention as
+ * pselinv_logdet_grad.
+ *
+ * d_G      device, batch x panel_entries in the X panel layout, read
+ *          according to g_kind:
+ *          PSELINV_G_SYMMETRIC: G symmetric on the selected pattern; only
+ *            the lower triangle of each diagonal block and the rows below
+ *            are read (J as above);
+ *          PSELINV_G_PANEL: d_G holds dJ/d(panel entries of X) for any J
+ *            (every panel entry read; the diagonal block's two triangles are
+ *            separate entries), e.g. the incoming gradient of an autograd
+ *            function whose output is the X panels
+ * d_gradA  device, batch x nnz_a
+ * Requires a prior pselinv_selinv on the same factor (uses X, L, D;
+ * recomputes Lhat and (L_KK)^{-1}).  Reverse sweep leaves -> root of the
+ * recurrence of Algorithm 1 (steps 3, 2, 1 in that order per supernode,
+ * scattering into the ancestors' adjoints through the relative indices),
+ * then the adjoint of the supernodal LDL^T root -> leaves.  Allocates its
+ * work buffers on first use.
  */
-int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, void* d_gradA, void* stream);
+#define PSELINV_G_SYMMETRIC 0
+#define PSELINV_G_PANEL 1
+int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, void* d_gradA, void* stream);
 
 /*
  * Kernel timing of the selected inversion (measurement support, no paper

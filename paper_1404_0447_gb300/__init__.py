@@ -21,8 +21,9 @@ ERRORS = {-1: "ERR_ARG", -2: "ERR_NOT_LOWER", -3: "ERR_ZERO_PIVOT", -4: "ERR_NON
 F64, C128 = 0, 1
 RELAX_NONE, RELAX_AMALG = 0, 1
 PLAIN, LEVEL, GRAPH = 0, 1, 2
+G_SYMMETRIC, G_PANEL = 0, 1
 
-EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_factor", "pselinv_selinv",
+EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_analyze_batch", "pselinv_factor", "pselinv_selinv",
             "pselinv_get_panels", "pselinv_get_selected", "pselinv_logdet_grad", "pselinv_logdet",
             "pselinv_selinv_adjoint",
             "pselinv_set_timing", "pselinv_get_timing", "pselinv_get_info", "pselinv_export_symbolic",
@@ -76,13 +77,14 @@ def load_library():
     L.pselinv_default_opts.argtypes = [ctypes.POINTER(Opts)]
     L.pselinv_default_opts.restype = None
     L.pselinv_analyze.argtypes = [ctypes.c_int64, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
+    L.pselinv_analyze_batch.argtypes = [ctypes.c_int32, vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
     L.pselinv_factor.argtypes = [vp, vp, vp]
     L.pselinv_selinv.argtypes = [vp, ctypes.c_int32, vp]
     L.pselinv_get_panels.argtypes = [vp, ctypes.c_int32, vp, vp]
     L.pselinv_get_selected.argtypes = [vp, vp, vp]
     L.pselinv_logdet.argtypes = [vp, vp, vp]
     L.pselinv_logdet_grad.argtypes = [vp, vp, vp]
-    L.pselinv_selinv_adjoint.argtypes = [vp, vp, vp, vp]
+    L.pselinv_selinv_adjoint.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
     L.pselinv_set_timing.argtypes = [vp, ctypes.c_int32]
     L.pselinv_get_timing.argtypes = [vp, vp, vp]
     L.pselinv_get_info.argtypes = [vp, ctypes.POINTER(Info)]
@@ -126,12 +128,26 @@ class SelInv:
     def __init__(self, n, colptr, rowind, perm=None, **opts):
         self._lib = load_library()
         self.opts = default_opts(**opts)
-        cp = np.ascontiguousarray(colptr, np.int64)
-        ri = np.ascontiguousarray(rowind, np.int32)
-        pp = None if perm is None else np.ascontiguousarray(perm, np.int32)
         h = ctypes.c_void_p()
-        rc = self._lib.pselinv_analyze(int(n), _ptr(cp), _ptr(ri), None if pp is None else _ptr(pp),
-                                       ctypes.byref(self.opts), ctypes.byref(h))
+        if isinstance(n, (list, tuple)):
+            # uneven batch: lists of members -> pselinv_analyze_batch
+            k = len(n)
+            ns = np.ascontiguousarray(n, np.int64)
+            cps = [np.ascontiguousarray(c, np.int64) for c in colptr]
+            ris = [np.ascontiguousarray(r, np.int32) for r in rowind]
+            pps = [None if (perm is None or perm[b] is None) else np.ascontiguousarray(perm[b], np.int32)
+                   for b in range(k)]
+            self._keep = (ns, cps, ris, pps)
+            arr = lambda xs: (ctypes.c_void_p * k)(*[None if x is None else x.ctypes.data for x in xs])
+            rc = self._lib.pselinv_analyze_batch(k, _ptr(ns), arr(cps), arr(ris), arr(pps),
+                                                 ctypes.byref(self.opts), ctypes.byref(h))
+            n = int(ns.sum())
+        else:
+            cp = np.ascontiguousarray(colptr, np.int64)
+            ri = np.ascontiguousarray(rowind, np.int32)
+            pp = None if perm is None else np.ascontiguousarray(perm, np.int32)
+            rc = self._lib.pselinv_analyze(int(n), _ptr(cp), _ptr(ri), None if pp is None else _ptr(pp),
+                                           ctypes.byref(self.opts), ctypes.byref(h))
         if rc != PSELINV_OK:
             raise PselinvError(rc, self._lib.pselinv_last_error(None).decode())
         self._h = h
@@ -213,6 +229,20 @@ class SelInv:
         self._check(self._lib.pselinv_logdet_grad(self._h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out.view(self.opts.batch, nnz)
 
+    def adjoint(self, G, g_kind=G_SYMMETRIC, out=None, stream=None):
+        """pselinv_selinv_adjoint: dJ/d(stored lower values of A) for
+        J = <G, X> (G symmetric on the selected pattern, panel layout) or,
+        with g_kind=G_PANEL, for any J with dJ/d(X panels) = G."""
+        import torch
+        assert G.is_cuda and G.dtype == self.torch_dtype and G.is_contiguous()
+        assert G.numel() == self.opts.batch * self.info["panel_entries"]
+        nnz = self.info["nnz_a"]
+        if out is None:
+            out = torch.empty(self.opts.batch * nnz, dtype=self.torch_dtype, device="cuda")
+        self._check(self._lib.pselinv_selinv_adjoint(self._h, ctypes.c_void_p(G.data_ptr()), int(g_kind),
+                                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out.view(self.opts.batch, nnz)
+
     def set_timing(self, enable=True):
         self._check(self._lib.pselinv_set_timing(self._h, 1 if enable else 0))
 
@@ -272,19 +302,46 @@ def _autograd():
             h.selinv(ctx.mode)
             return h.logdet_grad() * g[:, None], None, None
 
-    return LogDet
+    class SelectedInverse(torch.autograd.Function):
+        """X panels (the selected inverse) of the batch of symmetric matrices
+        with lower-CSC values ``values``; backward = the hand-written adjoint
+        of the selected inversion and of the LDL^T (pselinv_selinv_adjoint)."""
+
+        @staticmethod
+        def forward(ctx, values, handle, mode):
+            handle.factor(values.detach().contiguous())
+            handle.selinv(mode)
+            ctx.handle = handle
+            return handle.panels(0)
+
+        @staticmethod
+        def backward(ctx, g):
+            return ctx.handle.adjoint(g.contiguous(), G_PANEL), None, None
+
+    return LogDet, SelectedInverse
 
 
 _LogDet = None
+_SelInv = None
 
 
 def logdet(values, handle, mode=LEVEL):
     """Differentiable log det of the batch of real symmetric matrices whose
     lower-CSC values are ``values`` ([batch, nnz] or [nnz]) on the pattern
     analysed by ``handle``; returns a [batch] tensor."""
-    global _LogDet
+    global _LogDet, _SelInv
     if _LogDet is None:
-        _LogDet = _autograd()
+        _LogDet, _SelInv = _autograd()
     v = values if values.dim() == 2 else values.unsqueeze(0)
     out = _LogDet.apply(v, handle, mode)
     return out if values.dim() == 2 else out[0]
+
+
+def selected_inverse(values, handle, mode=LEVEL):
+    """Differentiable selected inverse: the X panels ([batch, panel_entries])
+    of the matrices with lower-CSC values ``values`` ([batch, nnz]); the
+    backward pass runs the library's adjoint kernels."""
+    global _LogDet, _SelInv
+    if _SelInv is None:
+        _LogDet, _SelInv = _autograd()
+    return _SelInv.apply(values, handle, mode)

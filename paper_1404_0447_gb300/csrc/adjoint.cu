@@ -1,0 +1,386 @@
+// Adjoint of the selected inversion and of the supernodal LDL^T.
+//
+// J = <G, X> (bilinear, over the full symmetric selected pattern).  Panel
+// variables per supernode K: the full diagonal block X_KK and X_CK = Y.  The
+// forward recurrence (Algorithm 1 in the symmetric form of Eq. 14, with
+// V = (L_KK)^{-1}, E = D_K^{-1}):
+//   M = V^T E V,  Lhat = L_CK V,  Y = -X_CC Lhat,  Z = M - Lhat^T Y,
+//   X_KK = (Z + Z^T) / 2,  X_CK = Y.
+// Reverse sweep, supernodes leaves -> root (levels deepest first):
+//   Zb   = (Xb_KK + Xb_KK^T) / 2                          (= Mbar)
+//   Yb   = Xb_CK - Lhat Zb
+//   Hb   = -X_CC Yb - Y Zb^T                              (Lhat-bar)
+//   ancestors: Xb_CC += -(Yb Lhat^T + Lhat Yb^T) on the stored lower
+//              triangle (diagonal halved), through the relative indices
+//   Lb_CK = Hb V^T
+//   Vb    = L_CK^T Hb + 2 E V Zb,  Db_t = -(V Zb V^T)_tt / d_t^2,
+//   Lb_KK = strict_lower(-V^T Vb V^T).
+// LDL^T adjoint, supernodes root -> leaves (levels top first), with Fb the
+// adjoint of the updated (Schur-complemented) panel values:
+//   T1 = (W + W^T) L_CK,  W = Fb gathered at C x C (stored lower triangle)
+//   Q  = (Lb_CK E - T1) V                                 -> Fb_CK
+//   R  = Q^T L_CK
+//   Db_t += -1/2 sum_i L_CK[i,t] T1[i,t] - sum_j L_KK[j,t] R[j,t]
+//   Lb_KK -= strict_lower(R D)
+//   P = strict_lower(L_KK^T Lb_KK) E + diag(Db),  Ab = V^T P V
+//   Fb_KK (stored lower) = Ab_ij + Ab_ji (i > j), Ab_ii.
+// dJ/d(stored A values) = Fb at the value map.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "kernels.h"
+#include "tile_gemm.cuh"
+
+namespace psi {
+
+enum AdjOp { A_YBAR, A_LHBAR, A_LBAROFF, A_T1, A_Q, A_VPART, A_RPART, A_SYR2K };
+
+template <class T>
+__device__ __forceinline__ void atomic_add_t(T* p, T v) {
+  if constexpr (Sc<T>::P == 1) {
+    atomicAdd(p, v);
+  } else {
+    atomicAdd(&reinterpret_cast<double*>(p)[0], v.re);
+    atomicAdd(&reinterpret_cast<double*>(p)[1], v.im);
+  }
+}
+
+template <class T, int BN, int OP>
+__global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* __restrict__ tasks) {
+  __shared__ TileSmem<T, BN> sm;
+  const Task tk = tasks[blockIdx.x];
+  const int b = blockIdx.y;
+  const Sizes sz = a.k.sz;
+  const SnMeta m = a.k.meta[tk.sn];
+  const int s = m.s, r = m.r, ld = s + r;
+  const T* X = (const T*)a.k.X + b * sz.panel;
+  const T* L = (const T*)a.k.L + b * sz.panel;
+  const T* Lh = (const T*)a.k.Lhat + b * sz.lhat + m.lhat;
+  const T* V = (const T*)a.k.Linv + b * sz.linv + m.linv;
+  const T* d = (const T*)a.k.D + b * sz.n + m.f;
+  T* Xb = (T*)a.Xb + b * sz.panel;
+  T* Lb = (T*)a.Lb + b * sz.panel;
+  const T* Z = (const T*)a.Zb + b * sz.linv + m.linv;
+  T* Yb = (T*)a.Yb + b * sz.lhat + m.lhat;
+  T* Hb = (T*)a.Hb + b * sz.lhat + m.lhat;
+  const ColDesc* dk = a.k.desc + m.desc;
+  const int32_t* rel = a.k.relidx;
+  const T zero = Sc<T>::zero();
+  const int m0 = tk.m0, n0 = tk.n0;
+  auto none = [](int) { return false; };
+  auto by_k = [](int) { return true; };
+  auto upper_by_k = [m0](int kt) { return kt >= m0 + TG_BM; };
+  Acc<T, BN> acc;
+  acc_zero<T, BN>(acc);
+
+  if constexpr (OP == A_YBAR) {  // Yb = Xb_CK - Lhat Zb
+    auto la = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Lh[i + (int64_t)t * r] : zero; };
+    auto lb = [&](int t, int nn) { const int n = n0 + nn; return n < s ? Z[t + n * s] : zero; };
+    tile_mma<T, BN>(sm, 0, s, none, la, lb, acc);
+    const T* XbCK = Xb + m.panel + s;
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int i = m0 + mm, n = n0 + nn;
+      if (i < r && n < s) Yb[i + (int64_t)n * r] = XbCK[i + (int64_t)n * ld] - v;
+    });
+  } else if constexpr (OP == A_LHBAR) {  // Hb = -X_CC Yb - Y Zb^T
+    auto la1 = [&](int mm, int kk) {
+      const int i = m0 + mm;
+      if (i >= r) return zero;
+      const int lo = i < kk ? i : kk, hi = i < kk ? kk : i;
+      const ColDesc cd = dk[lo];
+      return X[cd.col + rel[cd.rel + hi]];
+    };
+    auto lb1 = [&](int kk, int nn) { const int n = n0 + nn; return n < s ? Yb[kk + (int64_t)n * r] : zero; };
+    tile_mma<T, BN>(sm, 0, r, upper_by_k, la1, lb1, acc);
+    const T* Y = X + m.panel + s;
+    auto la2 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Y[i + (int64_t)t * ld] : zero; };
+    auto lb2 = [&](int t, int nn) { const int n = n0 + nn; return n < s ? Z[n + t * s] : zero; };
+    tile_mma<T, BN>(sm, 0, s, none, la2, lb2, acc);
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int i = m0 + mm, n = n0 + nn;
+      if (i < r && n < s) Hb[i + (int64_t)n * r] = -v;
+    });
+  } else if constexpr (OP == A_LBAROFF) {  // Lb_CK = Hb V^T
+    auto la = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Hb[i + (int64_t)t * r] : zero; };
+    auto lb = [&](int t, int nn) { const int n = n0 + nn; return n < s ? V[n + t * s] : zero; };
+    tile_mma<T, BN>(sm, 0, s, none, la, lb, acc);
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int i = m0 + mm, n = n0 + nn;
+      if (i < r && n < s) Lb[m.panel + s + i + (int64_t)n * ld] = v;
+    });
+  } else if constexpr (OP == A_T1) {  // T1 = (W + W^T) L_CK, W gathered from Fb (= Xb)
+    auto la = [&](int mm, int kk) {
+      const int i = m0 + mm;
+      if (i >= r) return zero;
+      const int lo = i < kk ? i : kk, hi = i < kk ? kk : i;
+      const ColDesc cd = dk[lo];
+      const T w = Xb[cd.col + rel[cd.rel + hi]];
+      return i == kk ? 2.0 * w : w;
+    };
+    auto lb = [&](int kk, int nn) { const int n = n0 + nn; return n < s ? L[m.panel + s + kk + (int64_t)n * ld] : zero; };
+    tile_mma<T, BN>(sm, 0, r, upper_by_k, la, lb, acc);
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int i = m0 + mm, n = n0 + nn;
+      if (i < r && n < s) Yb[i + (int64_t)n * r] = v;
+    });
+  } else if constexpr (OP == A_Q) {  // Q = (Lb_CK E - T1) V -> Fb_CK
+    auto la = [&](int mm, int t) {
+      const int i = m0 + mm;
+      return i < r ? Lb[m.panel + s + i + (int64_t)t * ld] / d[t] - Yb[i + (int64_t)t * r] : zero;
+    };
+    auto lb = [&](int t, int nn) { const int n = n0 + nn; return n < s ? V[t + n * s] : zero; };
+    tile_mma<T, BN>(sm, 0, s, none, la, lb, acc);
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int i = m0 + mm, n = n0 + nn;
+      if (i < r && n < s) Xb[m.panel + s + i + (int64_t)n * ld] = v;
+    });
+  } else if constexpr (OP == A_VPART || OP == A_RPART) {
+    // chunk partials of L_CK^T Hb (VPART) or Q^T L_CK with Q = Fb_CK (RPART)
+    const int kb = tk.c * kChunkRows, ke = min(r, kb + kChunkRows);
+    auto la = [&](int mm, int kk) {
+      const int i = m0 + mm;
+      if (i >= s) return zero;
+      return OP == A_VPART ? L[m.panel + s + kk + (int64_t)i * ld] : Xb[m.panel + s + kk + (int64_t)i * ld];
+    };
+    auto lb = [&](int kk, int nn) {
+      const int n = n0 + nn;
+      if (n >= s) return zero;
+      return OP == A_VPART ? Hb[kk + (int64_t)n * r] : L[m.panel + s + kk + (int64_t)n * ld];
+    };
+    tile_mma<T, BN>(sm, kb, ke, by_k, la, lb, acc);
+    T* out = (T*)a.k.part + b * sz.part + m.part + (int64_t)tk.c * s * s;
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int i = m0 + mm, n = n0 + nn;
+      if (i < s && n < s) out[i + n * s] = v;
+    });
+  } else {  // A_SYR2K: ancestors' Xb += -(Yb Lhat^T + Lhat Yb^T), lower, diagonal halved
+    auto la1 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Yb[i + (int64_t)t * r] : zero; };
+    auto lb1 = [&](int t, int nn) { const int n = n0 + nn; return n < r ? Lh[n + (int64_t)t * r] : zero; };
+    tile_mma<T, BN>(sm, 0, s, none, la1, lb1, acc);
+    auto la2 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Lh[i + (int64_t)t * r] : zero; };
+    auto lb2 = [&](int t, int nn) { const int n = n0 + nn; return n < r ? Yb[n + (int64_t)t * r] : zero; };
+    tile_mma<T, BN>(sm, 0, s, none, la2, lb2, acc);
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int i = m0 + mm, kc = n0 + nn;
+      if (i < r && kc <= i) {
+        const ColDesc cd = dk[kc];
+        atomic_add_t(&Xb[cd.col + rel[cd.rel + i]], (i == kc ? -0.5 : -1.0) * v);
+      }
+    });
+  }
+}
+
+// --------------------------------------------------------------------------
+// per-supernode kernels (one CTA each)
+// --------------------------------------------------------------------------
+
+// C = op(A) op(B) for s x s column-major blocks (ld s), by the whole CTA.
+template <class T, bool TA, bool TB>
+__device__ void cta_mm(int s, const T* A, const T* B, T* C) {
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    T acc = Sc<T>::zero();
+    for (int k = 0; k < s; ++k) acc += (TA ? A[k + i * s] : A[i + k * s]) * (TB ? B[j + k * s] : B[k + j * s]);
+    C[e] = acc;
+  }
+}
+
+// Seed of the reverse sweep (all supernodes; blockIdx.x is the supernode).
+// Symmetric G: Xb_KK = G (mirrored from its stored lower triangle) and
+// Xb_CK = 2 G_CK (X_CK stands for both X_CK and X_KC).  Panel gradient:
+// Xb = G entry for entry.
+template <class T>
+__global__ void k_adj_seed(AdjArgs a) {
+  const int k = blockIdx.x, b = blockIdx.y;
+  const Sizes sz = a.k.sz;
+  const SnMeta m = a.k.meta[k];
+  const int s = m.s, r = m.r, ld = s + r;
+  const T* G = (const T*)a.G + b * sz.panel + m.panel;
+  T* Xb = (T*)a.Xb + b * sz.panel + m.panel;
+  const int64_t tot = (int64_t)ld * s;
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int i = (int)(e % ld), j = (int)(e / ld);
+    T v;
+    if (a.g_kind == PSELINV_G_PANEL)
+      v = G[e];
+    else if (i >= s)
+      v = 2.0 * G[e];
+    else
+      v = i >= j ? G[i + (int64_t)j * ld] : G[j + (int64_t)i * ld];
+    Xb[e] = v;
+  }
+}
+
+// Zb = (Xb_KK + Xb_KK^T) / 2 for the supernodes of a level.
+template <class T>
+__global__ void k_adj_zbar(AdjArgs a, const int32_t* __restrict__ sns) {
+  const int k = sns[blockIdx.x], b = blockIdx.y;
+  const Sizes sz = a.k.sz;
+  const SnMeta m = a.k.meta[k];
+  const int s = m.s, ld = s + m.r;
+  const T* Xb = (const T*)a.Xb + b * sz.panel + m.panel;
+  T* Z = (T*)a.Zb + b * sz.linv + m.linv;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    Z[e] = 0.5 * (Xb[i + (int64_t)j * ld] + Xb[j + (int64_t)i * ld]);
+  }
+}
+
+// Diagonal-block adjoints of the reverse sweep: Vb, Db, Lb_KK.
+template <class T>
+__global__ void k_adj_diag_rev(AdjArgs a, const int32_t* __restrict__ sns) {
+  const int k = sns[blockIdx.x], b = blockIdx.y;
+  const Sizes sz = a.k.sz;
+  const SnMeta m = a.k.meta[k];
+  const int s = m.s, ld = s + m.r;
+  const T* V = (const T*)a.k.Linv + b * sz.linv + m.linv;
+  const T* d = (const T*)a.k.D + b * sz.n + m.f;
+  const T* part = (const T*)a.k.part + b * sz.part + m.part;
+  T* Z = (T*)a.Zb + b * sz.linv + m.linv;  // Zb in, Vb out
+  T* W = (T*)a.W1 + b * sz.linv + m.linv;
+  T* Db = (T*)a.Db + b * sz.n + m.f;
+  T* Lb = (T*)a.Lb + b * sz.panel + m.panel;
+  cta_mm<T, false, false>(s, V, Z, W);  // G1 = V Zb
+  __syncthreads();
+  for (int t = threadIdx.x; t < s; t += blockDim.x) {
+    T acc = Sc<T>::zero();
+    for (int j = 0; j < s; ++j) acc += W[t + j * s] * V[t + j * s];
+    Db[t] = -(acc / (d[t] * d[t]));
+  }
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int t = e % s;
+    T vb = 2.0 * W[e] / d[t];
+    for (int c = 0; c < m.nchunk; ++c) vb += part[(int64_t)c * s * s + e];
+    Z[e] = vb;  // Vb (Zb no longer needed: G1 holds V Zb)
+  }
+  __syncthreads();
+  cta_mm<T, false, true>(s, Z, V, W);  // G2 = Vb V^T
+  __syncthreads();
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    if (i <= j) continue;
+    T acc = Sc<T>::zero();
+    for (int q = 0; q < s; ++q) acc += V[q + i * s] * W[q + j * s];
+    Lb[i + (int64_t)j * ld] = -acc;  // strict lower of -V^T Vb V^T
+  }
+}
+
+// Diagonal-block step of the LDL^T adjoint: Db and Lb_KK updates from the
+// panel solve and the Schur update, then Fb_KK.
+template <class T>
+__global__ void k_adj_diag_fac(AdjArgs a, const int32_t* __restrict__ sns) {
+  const int k = sns[blockIdx.x], b = blockIdx.y;
+  const Sizes sz = a.k.sz;
+  const SnMeta m = a.k.meta[k];
+  const int s = m.s, r = m.r, ld = s + r;
+  const T* Lp = (const T*)a.k.L + b * sz.panel + m.panel;
+  const T* V = (const T*)a.k.Linv + b * sz.linv + m.linv;
+  const T* d = (const T*)a.k.D + b * sz.n + m.f;
+  const T* part = (const T*)a.k.part + b * sz.part + m.part;
+  const T* T1 = (const T*)a.Yb + b * sz.lhat + m.lhat;
+  T* Db = (T*)a.Db + b * sz.n + m.f;
+  const T* Lb = (const T*)a.Lb + b * sz.panel + m.panel;
+  T* W = (T*)a.W1 + b * sz.linv + m.linv;
+  T* Pm = (T*)a.Zb + b * sz.linv + m.linv;
+  T* Fb = (T*)a.Xb + b * sz.panel + m.panel;
+  const T zero = Sc<T>::zero();
+  auto R = [&](int i, int j) {
+    T v = zero;
+    for (int c = 0; c < m.nchunk; ++c) v += part[(int64_t)c * s * s + i + j * s];
+    return v;
+  };
+  auto Lkk = [&](int i, int j) { return i == j ? Sc<T>::one() : (i > j ? Lp[i + (int64_t)j * ld] : zero); };
+  for (int t = threadIdx.x; t < s; t += blockDim.x) {
+    T acc = zero, acc2 = zero;
+    for (int i = 0; i < r; ++i) acc += Lp[s + i + (int64_t)t * ld] * T1[i + (int64_t)t * r];
+    for (int j = t; j < s; ++j) acc2 += Lkk(j, t) * R(j, t);
+    Db[t] = Db[t] - 0.5 * acc - acc2;
+  }
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    W[e] = i > j ? Lb[i + (int64_t)j * ld] - R(i, j) * d[j] : zero;  // Lb_KK, strict lower
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    T v = zero;
+    if (i > j) {
+      for (int q = i; q < s; ++q) v += Lkk(q, i) * W[q + j * s];
+      v = v / d[j];
+    } else if (i == j) {
+      v = Db[i];
+    }
+    Pm[e] = v;
+  }
+  __syncthreads();
+  cta_mm<T, false, false>(s, Pm, V, W);  // P V
+  __syncthreads();
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    if (i < j) continue;
+    T aij = zero, aji = zero;
+    for (int q = 0; q < s; ++q) {
+      aij += V[q + i * s] * W[q + j * s];
+      aji += V[q + j * s] * W[q + i * s];
+    }
+    Fb[i + (int64_t)j * ld] = i == j ? aij : aij + aji;
+  }
+}
+
+// --------------------------------------------------------------------------
+// launches
+// --------------------------------------------------------------------------
+
+template <class T, int BN>
+static cudaError_t adj_tile_tb(int op, const AdjArgs& a, const Task* t, int64_t n, cudaStream_t st) {
+  const dim3 grid((unsigned)n, a.k.sz.batch);
+  switch (op) {
+    case A_YBAR: k_adj_tile<T, BN, A_YBAR><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_LHBAR: k_adj_tile<T, BN, A_LHBAR><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_LBAROFF: k_adj_tile<T, BN, A_LBAROFF><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_T1: k_adj_tile<T, BN, A_T1><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_Q: k_adj_tile<T, BN, A_Q><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_VPART: k_adj_tile<T, BN, A_VPART><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_RPART: k_adj_tile<T, BN, A_RPART><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    default: k_adj_tile<T, BN, A_SYR2K><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+  }
+  return cudaGetLastError();
+}
+
+template <class T>
+static cudaError_t adj_tile_t(int op, int var, const AdjArgs& a, const Task* t, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  switch (var) {
+    case 0: return adj_tile_tb<T, 8>(op, a, t, n, st);
+    case 1: return adj_tile_tb<T, 16>(op, a, t, n, st);
+    case 2: return adj_tile_tb<T, 32>(op, a, t, n, st);
+    default:
+      if constexpr (Sc<T>::P == 1) return adj_tile_tb<T, 64>(op, a, t, n, st);
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_adj_tiles(AdjKern k, int var, const AdjArgs& a, const Task* t, int64_t n, cudaStream_t st) {
+  static const int map[] = {A_YBAR, A_LHBAR, A_LBAROFF, A_T1, A_Q, A_VPART, A_RPART, A_SYR2K};
+  const int op = map[(int)k];
+  return a.k.dtype == PSELINV_C128 ? adj_tile_t<Cplx>(op, var, a, t, n, st) : adj_tile_t<double>(op, var, a, t, n, st);
+}
+
+template <class T>
+static cudaError_t adj_sn_t(AdjSn k, const AdjArgs& a, const int32_t* sns, int nsn, cudaStream_t st) {
+  if (nsn <= 0) return cudaSuccess;
+  const dim3 grid(nsn, a.k.sz.batch);
+  switch (k) {
+    case AdjSn::Seed: k_adj_seed<T><<<grid, 256, 0, st>>>(a); break;
+    case AdjSn::Zbar: k_adj_zbar<T><<<grid, 256, 0, st>>>(a, sns); break;
+    case AdjSn::DiagRev: k_adj_diag_rev<T><<<grid, 256, 0, st>>>(a, sns); break;
+    default: k_adj_diag_fac<T><<<grid, 256, 0, st>>>(a, sns); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_per_sn(AdjSn k, const AdjArgs& a, const int32_t* sns, int nsn, cudaStream_t st) {
+  return a.k.dtype == PSELINV_C128 ? adj_sn_t<Cplx>(k, a, sns, nsn, st) : adj_sn_t<double>(k, a, sns, nsn, st);
+}
+
+}  // namespace psi

@@ -63,7 +63,8 @@ int alloc(pselinv_handle* h, void** dst, int64_t bytes) {
 
 void free_device(pselinv_handle* h) {
   void** ptrs[] = {&h->d_meta, &h->d_desc, &h->d_relidx, &h->d_valmap, &h->d_diagmask, &h->d_tasks, &h->d_levelsn,
-                   &h->d_L,    &h->d_X,    &h->d_D,      &h->d_lhat,   &h->d_linv,  &h->d_part, &h->d_status};
+                   &h->d_L,    &h->d_X,    &h->d_D,      &h->d_lhat,   &h->d_linv,  &h->d_part, &h->d_status,
+                   &h->d_xb,   &h->d_lb,   &h->d_db,     &h->d_zb,     &h->d_w1,    &h->d_yb,   &h->d_hb};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -290,6 +291,45 @@ int pselinv_analyze(int64_t n, const int64_t* h_colptr, const int32_t* h_rowind,
   return PSELINV_OK;
 }
 
+int pselinv_analyze_batch(int32_t k, const int64_t* h_n, const int64_t* const* h_colptr,
+                          const int32_t* const* h_rowind, const int32_t* const* h_perm, const pselinv_opts* opts,
+                          pselinv_handle** out) {
+  if (!out) return set_err(nullptr, PSELINV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (k < 1 || !h_n || !h_colptr || !h_rowind) return set_err(nullptr, PSELINV_ERR_ARG, "bad batch arguments");
+  int64_t N = 0, NNZ = 0;
+  for (int32_t b = 0; b < k; ++b) {
+    if (h_n[b] < 1 || !h_colptr[b] || !h_rowind[b])
+      return set_err(nullptr, PSELINV_ERR_ARG, "member " + std::to_string(b) + ": bad size or NULL pattern");
+    N += h_n[b];
+    NNZ += h_colptr[b][h_n[b]];
+  }
+  if (N >= ((int64_t)1 << 31)) return set_err(nullptr, PSELINV_ERR_ARG, "total order too large");
+  std::vector<int64_t> cp(N + 1);
+  std::vector<int32_t> ri(NNZ), perm(N);
+  int64_t c0 = 0, q0 = 0;
+  for (int32_t b = 0; b < k; ++b) {
+    const int64_t nb = h_n[b];
+    const int64_t* bcp = h_colptr[b];
+    if (bcp[0] != 0) return set_err(nullptr, PSELINV_ERR_NOT_LOWER, "member " + std::to_string(b) + ": colptr[0] != 0");
+    for (int64_t j = 0; j < nb; ++j) cp[c0 + j] = q0 + bcp[j];
+    for (int64_t q = 0; q < bcp[nb]; ++q) {
+      const int32_t r = h_rowind[b][q];
+      if (r < 0 || r >= nb) return set_err(nullptr, PSELINV_ERR_NOT_LOWER, "member " + std::to_string(b) + ": row out of range");
+      ri[q0 + q] = (int32_t)(c0 + r);
+    }
+    for (int64_t j = 0; j < nb; ++j) {
+      const int32_t u = (h_perm && h_perm[b]) ? h_perm[b][j] : (int32_t)j;
+      if (u < 0 || u >= nb) return set_err(nullptr, PSELINV_ERR_NOT_LOWER, "member " + std::to_string(b) + ": bad perm");
+      perm[c0 + j] = (int32_t)(c0 + u);
+    }
+    c0 += nb;
+    q0 += bcp[nb];
+  }
+  cp[N] = q0;
+  return pselinv_analyze(N, cp.data(), ri.data(), perm.data(), opts, out);
+}
+
 int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream) {
   if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
   if (!d_values) return set_err(h, PSELINV_ERR_ARG, "values pointer is NULL");
@@ -413,12 +453,83 @@ int pselinv_logdet(pselinv_handle* h, double* h_out, void* stream) {
   return PSELINV_OK;
 }
 
-int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, void* d_gradA, void* stream) {
-  (void)d_G;
-  (void)d_gradA;
-  (void)stream;
+int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, void* d_gradA, void* stream) {
+  using psi::AdjKern;
+  using psi::AdjSn;
   if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
-  return set_err(h, PSELINV_ERR_STATE, "selinv_adjoint is not available in this build");
+  if (!d_G || !d_gradA) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (g_kind != PSELINV_G_SYMMETRIC && g_kind != PSELINV_G_PANEL) return set_err(h, PSELINV_ERR_ARG, "bad g_kind");
+  if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "selinv_adjoint needs a prior pselinv_selinv");
+  const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
+  int rc;
+  if (!h->d_xb) {
+    if ((rc = alloc(h, &h->d_xb, B * h->panel_total * es))) return rc;
+    if ((rc = alloc(h, &h->d_lb, B * h->panel_total * es))) return rc;
+    if ((rc = alloc(h, &h->d_db, B * h->n * es))) return rc;
+    if ((rc = alloc(h, &h->d_zb, B * h->linv_total * es))) return rc;
+    if ((rc = alloc(h, &h->d_w1, B * h->linv_total * es))) return rc;
+    if ((rc = alloc(h, &h->d_yb, B * h->lhat_total * es))) return rc;
+    if ((rc = alloc(h, &h->d_hb, B * h->lhat_total * es))) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  psi::AdjArgs a;
+  a.k = kargs(h);
+  a.G = d_G;
+  a.g_kind = g_kind;
+  a.Xb = h->d_xb;
+  a.Lb = h->d_lb;
+  a.Db = h->d_db;
+  a.Zb = h->d_zb;
+  a.W1 = h->d_w1;
+  a.Yb = h->d_yb;
+  a.Hb = h->d_hb;
+  // recompute (L_KK)^{-1} and Lhat from L (step 1) instead of trusting stored copies
+  {
+    psi::KArgs na = a.k;
+    na.X = nullptr;
+    PSI_CUDA(h, psi::launch_per_sn(psi::Kern::NormDiag, na, nullptr, h->nsn, st));
+    for (int v = 0; v < psi::kNumVar; ++v) {
+      const psi::Range r = h->t_lhat.whole[v];
+      PSI_CUDA(h, psi::launch_tiles(psi::Kern::Lhat, v, na, tasks_at(h, h->off_lhat, r.begin), r.end - r.begin, st));
+    }
+  }
+  PSI_CUDA(h, cudaMemsetAsync(h->d_lb, 0, B * h->panel_total * es, st));
+  PSI_CUDA(h, cudaMemsetAsync(h->d_db, 0, B * h->n * es, st));
+  PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::Seed, a, nullptr, h->nsn, st));
+  const auto* lsn = (const int32_t*)h->d_levelsn;
+  auto tiles = [&](AdjKern k, const psi::TaskList& tl, int64_t off, int32_t l) -> cudaError_t {
+    for (int v = 0; v < psi::kNumVar; ++v) {
+      const psi::Range r = tl.per_lv[(size_t)l * psi::kNumVar + v];
+      cudaError_t e = psi::launch_adj_tiles(k, v, a, tasks_at(h, off, r.begin), r.end - r.begin, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  // reverse sweep of the selected inversion, leaves -> root
+  for (int32_t l = h->nlevels - 1; l >= 0; --l) {
+    const int32_t* sns = lsn + h->level_ptr[l];
+    const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
+    PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::Zbar, a, sns, nsl, st));
+    PSI_CUDA(h, tiles(AdjKern::Ybar, h->t_gemm1, h->off_gemm1, l));
+    PSI_CUDA(h, tiles(AdjKern::Lhbar, h->t_gemm1, h->off_gemm1, l));
+    PSI_CUDA(h, tiles(AdjKern::Syr2k, h->t_schur, h->off_schur, l));
+    PSI_CUDA(h, tiles(AdjKern::LbarOff, h->t_gemm1, h->off_gemm1, l));
+    PSI_CUDA(h, tiles(AdjKern::Vpart, h->t_gemm2, h->off_gemm2, l));
+    PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::DiagRev, a, sns, nsl, st));
+  }
+  // adjoint of the supernodal LDL^T, root -> leaves
+  PSI_CUDA(h, cudaMemsetAsync(h->d_xb, 0, B * h->panel_total * es, st));
+  for (int32_t l = 0; l < h->nlevels; ++l) {
+    const int32_t* sns = lsn + h->level_ptr[l];
+    const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
+    PSI_CUDA(h, tiles(AdjKern::T1, h->t_gemm1, h->off_gemm1, l));
+    PSI_CUDA(h, tiles(AdjKern::Q, h->t_gemm1, h->off_gemm1, l));
+    PSI_CUDA(h, tiles(AdjKern::Rpart, h->t_gemm2, h->off_gemm2, l));
+    PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::DiagFac, a, sns, nsl, st));
+  }
+  PSI_CUDA(h, psi::launch_gather_values(h->opts.dtype, h->d_xb, (const int64_t*)h->d_valmap, nullptr, h->nnz_a,
+                                        d_gradA, sizes(h), st));
+  return PSELINV_OK;
 }
 
 int pselinv_set_timing(pselinv_handle* h, int32_t enable) {

@@ -132,6 +132,14 @@ struct pselinv_handle {
   void* d_linv = nullptr;   // inverses of the diagonal blocks
   void* d_part = nullptr;   // step-3 partial products (level-local)
   void* d_status = nullptr; // device status words
+  // adjoint work buffers (allocated on first pselinv_selinv_adjoint)
+  void* d_xb = nullptr;     // X-bar, then F-bar (panel layout)
+  void* d_lb = nullptr;     // L-bar (panel layout)
+  void* d_db = nullptr;     // D-bar
+  void* d_zb = nullptr;     // s x s per supernode
+  void* d_w1 = nullptr;     // s x s per supernode
+  void* d_yb = nullptr;     // r x s per supernode
+  void* d_hb = nullptr;     // r x s per supernode
   int64_t device_bytes = 0;
   void* graph_exec = nullptr;  // cudaGraphExec_t of the LEVEL schedule
   void* graph_stream = nullptr;

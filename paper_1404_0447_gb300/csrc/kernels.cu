@@ -136,6 +136,7 @@ __global__ void k_norm_diag(const SnMeta* __restrict__ meta, const T* __restrict
   __syncthreads();
   T* V = Linv + b * sz.linv + m.linv;
   unit_lower_inverse(Tp, s, V);
+  if (!X) return;  // inverse only (the adjoint recomputes it)
   __syncthreads();
   T* XK = X + b * sz.panel + m.panel;
   for (int e = t; e < s * s; e += nt) {

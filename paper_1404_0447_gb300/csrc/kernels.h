@@ -50,4 +50,22 @@ cudaError_t launch_tiles(Kern k, int var, const KArgs& a, const Task* tasks, int
 cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st);
 cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st);
 
+// ---- adjoint (adjoint.cu) ----
+struct AdjArgs {
+  KArgs k;
+  const void* G;  // seed, X panel layout
+  int g_kind;     // PSELINV_G_SYMMETRIC / PSELINV_G_PANEL
+  void* Xb;       // adjoint of X panels; later adjoint of the updated factor panels
+  void* Lb;       // adjoint of L (panel layout)
+  void* Db;       // adjoint of D
+  void* Zb;       // s x s per supernode (linv layout): Zbar, then Vbar, then P
+  void* W1;       // s x s per supernode scratch
+  void* Yb;       // r x s per supernode (lhat layout): Ybar, then T1
+  void* Hb;       // r x s per supernode: Lhat-bar
+};
+enum class AdjKern { Ybar, Lhbar, LbarOff, T1, Q, Vpart, Rpart, Syr2k };
+enum class AdjSn { Seed, Zbar, DiagRev, DiagFac };
+cudaError_t launch_adj_tiles(AdjKern k, int var, const AdjArgs& a, const Task* tasks, int64_t n, cudaStream_t st);
+cudaError_t launch_adj_per_sn(AdjSn k, const AdjArgs& a, const int32_t* sns, int nsn, cudaStream_t st);
+
 }  // namespace psi
