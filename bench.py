@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="grid3d_80",
+                    choices=["grid3d_80", "grid2d_31", "graphlap48", "dg_poles", "uneven48"],
+                    help="grid3d_80 is the headline; the others measure the remaining workload families")
+    ap.add_argument("--poles", type=int, default=16, help="dg_poles: number of poles in the batch")
+    ap.add_argument("--split-k-rows", type=int, default=None, help="override the library default")
+    ap.add_argument("--small-cutoff", type=int, default=None, help="override the library default")
     return ap.parse_args()
 
 
@@ -154,6 +160,15 @@ class ClockSampler:
                 if any(r[3].replace('.', '').isdigit() for r in rows) else None}
 
 
+def tuning(args):
+    kw = {}
+    if args.split_k_rows is not None:
+        kw["split_k_rows"] = args.split_k_rows
+    if args.small_cutoff is not None:
+        kw["small_cutoff"] = args.small_cutoff
+    return kw
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -168,7 +183,7 @@ def run_ours(args):
     P.load_library()
 
     prob = synth.config1(args.side)
-    h = P.SelInv(prob.n, prob.colptr, prob.rowind, max_sn_width=128, relax=P.RELAX_AMALG)
+    h = P.SelInv(prob.n, prob.colptr, prob.rowind, max_sn_width=128, relax=P.RELAX_AMALG, **tuning(args))
     info = h.info
     flops = info["flops_selinv"]
     vals = torch.tensor(prob.values, dtype=torch.float64, device=dev)
@@ -289,10 +304,105 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _time(fn, steps, warmup, stream):
+    """Device time per call of fn() on `stream`, after warm-up (CUDA events)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_workload(args):
+    """Secondary workloads (one JSON line each): level / graph / plain selinv
+    times, TFLOP/s (complex counted x4), and for graphlap48 the logdet
+    forward, backward and adjoint times."""
+    import torch
+    import synth
+    import paper_1404_0447_gb300 as P
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    P.load_library()
+    w = args.workload
+    line = {"workload": w, "steps": args.steps, "warmup": args.warmup}
+    if w == "grid2d_31":
+        p = synth.config0()
+        h = P.SelInv(p.n, p.colptr, p.rowind, max_sn_width=128, relax=P.RELAX_NONE, **tuning(args))
+        vals = torch.tensor(p.values, dtype=torch.float64, device=dev)
+        cplx = False
+    elif w == "graphlap48":
+        gl = synth.GraphLaplacian((48, 48, 48))
+        h = P.SelInv(gl.n, gl.colptr, gl.rowind, perm=synth.nd_order(gl.dims), **tuning(args))
+        vals = torch.tensor(gl.assemble(), dtype=torch.float64, device=dev)
+        cplx = False
+    elif w == "dg_poles":
+        n, cp, ri, hv, z = synth.dg_block_matrix((12, 12, 12), 48, 16)
+        z = z[:args.poles]
+        h = P.SelInv(n, cp, ri, perm=synth.block_nd_order((12, 12, 12), 48), dtype=P.C128, batch=len(z),
+                     **tuning(args))
+        vals = torch.tensor(synth.shifted_values(n, cp, ri, hv, z), dtype=torch.complex128, device=dev)
+        cplx = True
+        line["poles"] = len(z)
+    else:
+        mem = [synth.config4_member(s) for s in synth.uneven_batch_specs()]
+        h = P.SelInv([m.n for m in mem], [m.colptr for m in mem], [m.rowind for m in mem], **tuning(args))
+        vals = torch.tensor(np.concatenate([m.values for m in mem]), dtype=torch.float64, device=dev)
+        cplx = False
+    info = h.info
+    flops = info["flops_selinv"] * info["batch"] * (4 if cplx else 1)
+    line.update({k: info[k] for k in ("n", "nnz_l", "nsn", "nlevels", "batch")})
+    line["flops_per_selinv"] = flops
+    t0 = time.perf_counter()
+    with torch.cuda.stream(st):
+        h.factor(vals.view(-1), stream=st)
+    line["factor_ms"] = 1e3 * (time.perf_counter() - t0)
+    for name, mode in (("level", P.LEVEL), ("graph", P.GRAPH), ("plain", P.PLAIN)):
+        if name == "plain" and w == "dg_poles" and args.poles > 4:
+            continue
+        ms = _time(lambda: h.selinv(mode, stream=st), args.steps if name != "plain" else 1,
+                   args.warmup if name != "plain" else 1, st)
+        line[f"{name}_ms"] = ms
+        line[f"{name}_tflops"] = flops / (ms * 1e-3) / 1e12
+        line[f"{name}_frac_of_fp64_peak"] = line[f"{name}_tflops"] / FP64_PEAK_TFLOPS
+    if "plain_ms" in line:
+        line["speedup_level_vs_plain"] = line["plain_ms"] / line["level_ms"]
+    if w == "graphlap48":
+        # differentiable logdet: forward = factor + logdet, backward = selinv + gradient gather
+        g = torch.empty(info["nnz_a"], dtype=torch.float64, device=dev)
+        line["logdet_forward_ms"] = _time(lambda: (h.factor(vals, stream=st), h.logdet(stream=st)), 3, 1, st)
+        line["logdet_backward_ms"] = _time(lambda: (h.selinv(P.LEVEL, stream=st), h.logdet_grad(out=g, stream=st)),
+                                           args.steps, 1, st)
+        G = torch.randn(info["panel_entries"], dtype=torch.float64, device=dev)
+        h.selinv(P.LEVEL, stream=st)
+        line["adjoint_ms"] = _time(lambda: h.adjoint(G, stream=st), 3, 1, st)
+    if w == "uneven48":
+        # the same members one handle at a time (level schedule each)
+        hs = []
+        for m in mem:
+            hm = P.SelInv(m.n, m.colptr, m.rowind)
+            hm.factor(torch.tensor(m.values, dtype=torch.float64, device=dev), stream=st)
+            hs.append(hm)
+        torch.cuda.synchronize()
+        ms = _time(lambda: [hm.selinv(P.LEVEL, stream=st) for hm in hs], 2, 1, st)
+        line["per_member_level_ms"] = ms
+        line["speedup_merged_graph_vs_per_member"] = ms / line["graph_ms"]
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "grid3d_80":
+        run_workload(args)
     else:
         run_ours(args)
 

@@ -75,8 +75,12 @@ typedef struct {
   int32_t batch;          /* B >= 1 matrices sharing the pattern (e.g. poles H - z_l I) */
   int32_t max_sn_width;   /* width cap w_max, 1..128; 0 means 128 */
   int32_t relax;          /* PSELINV_RELAX_NONE or PSELINV_RELAX_AMALG */
-  int32_t small_cutoff;   /* reserved for the small/large path switch; < 0 = automatic */
+  int32_t small_cutoff;   /* supernodes narrower than this use the narrowest padding-minimal tiles,
+                             wider ones prefer 64-column tiles; < 0 = padding-minimal everywhere */
+  int32_t split_k_rows;   /* step 2 of a supernode with |C| = r is split into ceil(r / split_k_rows)
+                             partial products reduced in a fixed order; <= 0 = no split */
   int32_t debug_checks;   /* nonzero: kernels bounds-check every index and report */
+  int32_t reserved;       /* must be 0 */
   int64_t spin_limit_ns;  /* limit for bounded device waits; <= 0 = 1e9 */
 } pselinv_opts;
 
@@ -120,8 +124,8 @@ typedef struct {
   const int32_t* level_sn;  /* [nsn] supernodes of level k (k = 0 is sigma 1), costliest first */
 } pselinv_symbolic;
 
-/* Fill *o with defaults: F64, batch 1, w_max 128, RELAX_AMALG, automatic
-   cutoff, no debug checks, 1 s spin limit. */
+/* Fill *o with defaults: F64, batch 1, w_max 128, RELAX_AMALG, padding-minimal
+   tiles, split_k_rows 1024, no debug checks, 1 s spin limit. */
 void pselinv_default_opts(pselinv_opts* o);
 
 /*
@@ -279,6 +283,19 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
 #define PSELINV_NTIMERS 4
 int pselinv_set_timing(pselinv_handle* h, int32_t enable);
 int pselinv_get_timing(pselinv_handle* h, double* h_ms, int64_t* h_launches);
+
+/*
+ * Autotuner (measurement-driven choice of the schedule; no paper
+ * counterpart beyond Section 3.3's remark that task order matters).  On a
+ * factored handle, times pselinv_selinv (LEVEL schedule, CUDA events on
+ * `stream`, best of two after a warm-up) for each candidate schedule --
+ * first split_k_rows over {0, 512, 1024, 2048, 4096} with the current
+ * small_cutoff, then small_cutoff over {-1, 32, 64} with the best split --
+ * keeps the fastest in the handle, and returns it in h_best[0] =
+ * split_k_rows, h_best[1] = small_cutoff and its time in *h_best_ms.
+ * Overwrites the X panels; drops a captured GRAPH schedule.  Synchronises.
+ */
+int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void* stream);
 
 int pselinv_get_info(const pselinv_handle* h, pselinv_info* info);
 int pselinv_export_symbolic(const pselinv_handle* h, pselinv_symbolic* view);

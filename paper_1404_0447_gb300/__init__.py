@@ -26,7 +26,8 @@ G_SYMMETRIC, G_PANEL = 0, 1
 EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_analyze_batch", "pselinv_factor", "pselinv_selinv",
             "pselinv_get_panels", "pselinv_get_selected", "pselinv_logdet_grad", "pselinv_logdet",
             "pselinv_selinv_adjoint",
-            "pselinv_set_timing", "pselinv_get_timing", "pselinv_get_info", "pselinv_export_symbolic",
+            "pselinv_set_timing", "pselinv_get_timing", "pselinv_autotune", "pselinv_get_info",
+            "pselinv_export_symbolic",
             "pselinv_destroy", "pselinv_last_error", "pselinv_block_inverse_static"]
 
 
@@ -38,8 +39,8 @@ class PselinvError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("batch", ctypes.c_int32), ("max_sn_width", ctypes.c_int32),
-                ("relax", ctypes.c_int32), ("small_cutoff", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
-                ("spin_limit_ns", ctypes.c_int64)]
+                ("relax", ctypes.c_int32), ("small_cutoff", ctypes.c_int32), ("split_k_rows", ctypes.c_int32),
+                ("debug_checks", ctypes.c_int32), ("reserved", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -87,6 +88,7 @@ def load_library():
     L.pselinv_selinv_adjoint.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
     L.pselinv_set_timing.argtypes = [vp, ctypes.c_int32]
     L.pselinv_get_timing.argtypes = [vp, vp, vp]
+    L.pselinv_autotune.argtypes = [vp, vp, vp, vp]
     L.pselinv_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.pselinv_export_symbolic.argtypes = [vp, ctypes.POINTER(Symbolic)]
     L.pselinv_destroy.argtypes = [vp]
@@ -242,6 +244,14 @@ class SelInv:
         self._check(self._lib.pselinv_selinv_adjoint(self._h, ctypes.c_void_p(G.data_ptr()), int(g_kind),
                                                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out.view(self.opts.batch, nnz)
+
+    def autotune(self, stream=None):
+        """pselinv_autotune: returns {"split_k_rows", "small_cutoff", "ms"} and keeps that schedule."""
+        best = np.zeros(2, np.int32)
+        ms = np.zeros(1, np.float64)
+        self._check(self._lib.pselinv_autotune(self._h, _ptr(best), _ptr(ms), _stream_ptr(stream)))
+        self.opts.split_k_rows, self.opts.small_cutoff = int(best[0]), int(best[1])
+        return {"split_k_rows": int(best[0]), "small_cutoff": int(best[1]), "ms": float(ms[0])}
 
     def set_timing(self, enable=True):
         self._check(self._lib.pselinv_set_timing(self._h, 1 if enable else 0))

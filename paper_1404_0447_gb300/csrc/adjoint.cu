@@ -197,18 +197,18 @@ __global__ void k_adj_seed(AdjArgs a) {
   const int s = m.s, r = m.r, ld = s + r;
   const T* G = (const T*)a.G + b * sz.panel + m.panel;
   T* Xb = (T*)a.Xb + b * sz.panel + m.panel;
-  const int64_t tot = (int64_t)ld * s;
-  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int i = (int)(e % ld), j = (int)(e / ld);
-    T v;
-    if (a.g_kind == PSELINV_G_PANEL)
-      v = G[e];
-    else if (i >= s)
-      v = 2.0 * G[e];
-    else
-      v = i >= j ? G[i + (int64_t)j * ld] : G[j + (int64_t)i * ld];
-    Xb[e] = v;
-  }
+  for (int j = 0; j < s; ++j)
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+      const int64_t e = i + (int64_t)j * ld;
+      T v;
+      if (a.g_kind == PSELINV_G_PANEL)
+        v = G[e];
+      else if (i >= s)
+        v = 2.0 * G[e];
+      else
+        v = i >= j ? G[e] : G[j + (int64_t)i * ld];
+      Xb[e] = v;
+    }
 }
 
 // Zb = (Xb_KK + Xb_KK^T) / 2 for the supernodes of a level.

@@ -430,12 +430,35 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
     }
   }
 
+  h->perm = perm;
+  h->parent = parent;
+  return build_schedule(h);
+}
+
+// Schedule of the grouped launches (depends on the tuning options, not on the
+// pattern): step-2 slices of wide C, the task lists and the level-local
+// offsets of the partial-product buffers.
+int build_schedule(pselinv_handle* h) {
+  {
+    const pselinv_opts& o = h->opts;
+    for (SnMeta& m : h->meta) {
+      m.ksplit = 1;
+      m.kchunk = m.r;
+      if (o.split_k_rows > 0 && m.r > o.split_k_rows) {
+        const int32_t parts = (m.r + o.split_k_rows - 1) / o.split_k_rows;
+        m.kchunk = ((m.r + parts - 1) / parts + 15) / 16 * 16;
+        m.ksplit = (m.r + m.kchunk - 1) / m.kchunk;
+      }
+    }
+  }
   // ---- task lists ----
   // Level lists hold, per level, per tile variant, the supernodes in level
   // order (costliest first), each supernode's tiles contiguous.  The
   // normalisation list is variant-major over all levels (one launch per
   // variant).
+  const pselinv_opts& o = h->opts;
   const bool cplx = o.dtype == PSELINV_C128;
+  const int32_t nsn = h->nsn, nl = h->nlevels;
   auto build = [&](TaskList& tl, bool variant_major, auto&& var_of, auto&& emit) {
     tl.tasks.clear();
     tl.per_lv.assign((size_t)nl * kNumVar, Range{});
@@ -465,7 +488,7 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
         rg.end = (int64_t)tl.tasks.size();
       }
   };
-  auto by_width = [&](int32_t k) { return pick_variant(h->meta[k].s, cplx); };
+  auto by_width = [&](int32_t k) { return pick_variant(h->meta[k].s, cplx, o.small_cutoff); };
   auto by_rows = [&](int32_t) { return cplx ? 2 : 3; };
   auto rect = [&](int32_t k, int bn, std::vector<Task>& out) {  // r x s output tiles
     const SnMeta& m = h->meta[k];
@@ -473,7 +496,13 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
       for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, 0});
   };
   build(h->t_lhat, true, by_width, rect);
-  build(h->t_gemm1, false, by_width, rect);
+  build(h->t_rect, false, by_width, rect);
+  build(h->t_gemm1, false, by_width, [&](int32_t k, int bn, std::vector<Task>& out) {  // step 2: + k-parts
+    const SnMeta& m = h->meta[k];
+    for (int32_t c = 0; c < m.ksplit; ++c)
+      for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
+        for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, c});
+  });
   build(h->t_trsm, false, by_width, rect);
   build(h->t_gemm2, false, by_width, [&](int32_t k, int bn, std::vector<Task>& out) {
     const SnMeta& m = h->meta[k];
@@ -488,17 +517,23 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
   });
   // level-local offsets of the step-3 partial products
   h->part_max = 0;
+  h->ypart_max = 0;
+  h->level_split.assign(nl, 0);
   for (int32_t l = 0; l < nl; ++l) {
-    int64_t off = 0;
+    int64_t off = 0, yoff = 0;
     for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
       SnMeta& m = h->meta[h->level_sn[t]];
       m.part = off;
       off += (int64_t)m.nchunk * m.s * m.s;
+      m.ypart = yoff;
+      if (m.ksplit > 1) {
+        yoff += (int64_t)m.ksplit * m.r * m.s;
+        h->level_split[l] = 1;
+      }
     }
     h->part_max = std::max(h->part_max, off);
+    h->ypart_max = std::max(h->ypart_max, yoff);
   }
-  h->perm = perm;
-  h->parent = parent;
   return PSELINV_OK;
 }
 

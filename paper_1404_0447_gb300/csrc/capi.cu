@@ -41,6 +41,7 @@ psi::Sizes sizes(const pselinv_handle* h) {
   s.linv = h->linv_total;
   s.n = h->n;
   s.part = h->part_max;
+  s.ypart = h->ypart_max;
   s.batch = h->opts.batch;
   return s;
 }
@@ -63,7 +64,8 @@ int alloc(pselinv_handle* h, void** dst, int64_t bytes) {
 
 void free_device(pselinv_handle* h) {
   void** ptrs[] = {&h->d_meta, &h->d_desc, &h->d_relidx, &h->d_valmap, &h->d_diagmask, &h->d_tasks, &h->d_levelsn,
-                   &h->d_L,    &h->d_X,    &h->d_D,      &h->d_lhat,   &h->d_linv,  &h->d_part, &h->d_status,
+                   &h->d_L,    &h->d_X,    &h->d_D,      &h->d_lhat,   &h->d_linv,  &h->d_part, &h->d_ypart,
+                   &h->d_status,
                    &h->d_xb,   &h->d_lb,   &h->d_db,     &h->d_zb,     &h->d_w1,    &h->d_yb,   &h->d_hb};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
@@ -80,6 +82,8 @@ void free_device(pselinv_handle* h) {
   h->device_bytes = 0;
 }
 
+int upload_schedule(pselinv_handle* h);
+
 int ensure_device(pselinv_handle* h) {
   if (h->dev_sym) return PSELINV_OK;
   int count = 0;
@@ -88,12 +92,38 @@ int ensure_device(pselinv_handle* h) {
   PSI_CUDA(h, cudaGetDevice(&h->device));
   PSI_CUDA(h, psi::setup_kernels());
   int rc;
-  if ((rc = upload(h, &h->d_meta, h->meta))) return rc;
   if ((rc = upload(h, &h->d_desc, h->desc))) return rc;
   if ((rc = upload(h, &h->d_relidx, h->relidx))) return rc;
   if ((rc = upload(h, &h->d_valmap, h->valmap))) return rc;
   if ((rc = upload(h, &h->d_diagmask, h->diagmask))) return rc;
   if ((rc = upload(h, &h->d_levelsn, h->level_sn))) return rc;
+  if ((rc = upload_schedule(h))) return rc;
+  const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
+  if ((rc = alloc(h, &h->d_L, B * h->panel_total * es))) return rc;
+  if ((rc = alloc(h, &h->d_X, B * h->panel_total * es))) return rc;
+  if ((rc = alloc(h, &h->d_D, B * h->n * es))) return rc;
+  if ((rc = alloc(h, &h->d_lhat, B * h->lhat_total * es))) return rc;
+  if ((rc = alloc(h, &h->d_linv, B * h->linv_total * es))) return rc;
+  if ((rc = alloc(h, &h->d_status, sizeof(int) * kStatusWords + sizeof(double) * 2 * B))) return rc;
+  h->dev_sym = true;
+  return PSELINV_OK;
+}
+
+// Upload the tuning-dependent part (metadata, task lists, partial buffers);
+// called again by the autotuner after build_schedule.
+int upload_schedule(pselinv_handle* h) {
+  int rc;
+  void** old[] = {&h->d_meta, &h->d_tasks, &h->d_part, &h->d_ypart};
+  for (void** p : old)
+    if (*p) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
+  if (h->graph_exec) {
+    cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  if ((rc = upload(h, &h->d_meta, h->meta))) return rc;
   std::vector<psi::Task> all;
   h->off_lhat = (int64_t)all.size();
   all.insert(all.end(), h->t_lhat.tasks.begin(), h->t_lhat.tasks.end());
@@ -105,16 +135,12 @@ int ensure_device(pselinv_handle* h) {
   all.insert(all.end(), h->t_trsm.tasks.begin(), h->t_trsm.tasks.end());
   h->off_schur = (int64_t)all.size();
   all.insert(all.end(), h->t_schur.tasks.begin(), h->t_schur.tasks.end());
+  h->off_rect = (int64_t)all.size();
+  all.insert(all.end(), h->t_rect.tasks.begin(), h->t_rect.tasks.end());
   if ((rc = upload(h, &h->d_tasks, all))) return rc;
   const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
-  if ((rc = alloc(h, &h->d_L, B * h->panel_total * es))) return rc;
-  if ((rc = alloc(h, &h->d_X, B * h->panel_total * es))) return rc;
-  if ((rc = alloc(h, &h->d_D, B * h->n * es))) return rc;
-  if ((rc = alloc(h, &h->d_lhat, B * h->lhat_total * es))) return rc;
-  if ((rc = alloc(h, &h->d_linv, B * h->linv_total * es))) return rc;
   if ((rc = alloc(h, &h->d_part, B * h->part_max * es))) return rc;
-  if ((rc = alloc(h, &h->d_status, sizeof(int) * kStatusWords + sizeof(double) * 2 * B))) return rc;
-  h->dev_sym = true;
+  if ((rc = alloc(h, &h->d_ypart, B * h->ypart_max * es))) return rc;
   return PSELINV_OK;
 }
 
@@ -135,6 +161,7 @@ psi::KArgs kargs(pselinv_handle* h) {
   a.Lhat = h->d_lhat;
   a.X = h->d_X;
   a.part = h->d_part;
+  a.ypart = h->d_ypart;
   a.status = (int*)h->d_status;
   a.sz = sizes(h);
   return a;
@@ -200,8 +227,8 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record) {
   });
   if (rc) return rc;
   // one step: the given supernodes, with per-variant task ranges of steps 2 and 3
-  auto step = [&](const int32_t* sns, int nsn_step, const psi::Range* r1, const psi::Range* r2) {
-    int n1 = 0, n2 = 0, e;
+  auto step = [&](const int32_t* sns, int nsn_step, const psi::Range* r1, const psi::Range* r2, bool split) {
+    int n1 = split ? 1 : 0, n2 = 0, e;
     for (int v = 0; v < psi::kNumVar; ++v) {
       n1 += r1[v].end > r1[v].begin;
       n2 += r2[v].end > r2[v].begin;
@@ -211,6 +238,7 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record) {
            for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
              x = psi::launch_tiles(Kern::Gemm1, v, a, tasks_at(h, h->off_gemm1, r1[v].begin), r1[v].end - r1[v].begin,
                                    st);
+           if (split && x == cudaSuccess) x = psi::launch_per_sn(Kern::Gemm1Reduce, a, sns, nsn_step, st);
            return x;
          })))
       return e;
@@ -232,12 +260,13 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record) {
       psi::Range r1[psi::kNumVar], r2[psi::kNumVar];
       r1[h->t_gemm1.var[k]] = h->t_gemm1.per_sn[k];
       r2[h->t_gemm2.var[k]] = h->t_gemm2.per_sn[k];
-      if ((rc = step(lsn + pos[k], 1, r1, r2))) return rc;
+      if ((rc = step(lsn + pos[k], 1, r1, r2, h->meta[k].ksplit > 1))) return rc;
     }
   } else {
     for (int32_t l = 0; l < h->nlevels; ++l)
       if ((rc = step(lsn + h->level_ptr[l], h->level_ptr[l + 1] - h->level_ptr[l],
-                     &h->t_gemm1.per_lv[(size_t)l * psi::kNumVar], &h->t_gemm2.per_lv[(size_t)l * psi::kNumVar])))
+                     &h->t_gemm1.per_lv[(size_t)l * psi::kNumVar], &h->t_gemm2.per_lv[(size_t)l * psi::kNumVar],
+                     h->level_split[l] != 0)))
         return rc;
   }
   return PSELINV_OK;
@@ -260,7 +289,9 @@ void pselinv_default_opts(pselinv_opts* o) {
   o->max_sn_width = psi::kMaxWidth;
   o->relax = PSELINV_RELAX_AMALG;
   o->small_cutoff = -1;
+  o->split_k_rows = 1024;
   o->debug_checks = 0;
+  o->reserved = 0;
   o->spin_limit_ns = 1000000000LL;
 }
 
@@ -510,10 +541,10 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
     const int32_t* sns = lsn + h->level_ptr[l];
     const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
     PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::Zbar, a, sns, nsl, st));
-    PSI_CUDA(h, tiles(AdjKern::Ybar, h->t_gemm1, h->off_gemm1, l));
-    PSI_CUDA(h, tiles(AdjKern::Lhbar, h->t_gemm1, h->off_gemm1, l));
+    PSI_CUDA(h, tiles(AdjKern::Ybar, h->t_rect, h->off_rect, l));
+    PSI_CUDA(h, tiles(AdjKern::Lhbar, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Syr2k, h->t_schur, h->off_schur, l));
-    PSI_CUDA(h, tiles(AdjKern::LbarOff, h->t_gemm1, h->off_gemm1, l));
+    PSI_CUDA(h, tiles(AdjKern::LbarOff, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Vpart, h->t_gemm2, h->off_gemm2, l));
     PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::DiagRev, a, sns, nsl, st));
   }
@@ -522,8 +553,8 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
   for (int32_t l = 0; l < h->nlevels; ++l) {
     const int32_t* sns = lsn + h->level_ptr[l];
     const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
-    PSI_CUDA(h, tiles(AdjKern::T1, h->t_gemm1, h->off_gemm1, l));
-    PSI_CUDA(h, tiles(AdjKern::Q, h->t_gemm1, h->off_gemm1, l));
+    PSI_CUDA(h, tiles(AdjKern::T1, h->t_rect, h->off_rect, l));
+    PSI_CUDA(h, tiles(AdjKern::Q, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Rpart, h->t_gemm2, h->off_gemm2, l));
     PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::DiagFac, a, sns, nsl, st));
   }
@@ -561,6 +592,70 @@ int pselinv_get_timing(pselinv_handle* h, double* h_ms, int64_t* h_launches) {
   return PSELINV_OK;
 }
 
+int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void* stream) {
+  if (!h || !h_best || !h_best_ms) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (!h->factored) return set_err(h, PSELINV_ERR_STATE, "autotune needs a factored handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  PSI_CUDA(h, cudaEventCreate(&e0));
+  PSI_CUDA(h, cudaEventCreate(&e1));
+  const bool timing = h->timing;
+  h->timing = false;
+  auto measure = [&](int32_t split, int32_t cutoff, double* ms) -> int {
+    h->opts.split_k_rows = split;
+    h->opts.small_cutoff = cutoff;
+    int rc = psi::build_schedule(h);
+    if (!rc) rc = upload_schedule(h);
+    if (!rc) rc = enqueue_selinv(h, PSELINV_LEVEL, st, false);  // warm-up
+    double best = 1e300;
+    for (int rep = 0; rep < 2 && !rc; ++rep) {
+      float t = 0.f;
+      cudaError_t e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) rc = enqueue_selinv(h, PSELINV_LEVEL, st, false);
+      if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (!rc && e != cudaSuccess) rc = cuda_err(h, e, "autotune timing");
+      if (t < best) best = t;
+    }
+    *ms = best;
+    return rc;
+  };
+  int32_t best_split = h->opts.split_k_rows, best_cut = h->opts.small_cutoff;
+  double best_ms = 1e300, ms = 0;
+  int rc = PSELINV_OK;
+  for (int32_t split : {0, 512, 1024, 2048, 4096}) {
+    if ((rc = measure(split, best_cut, &ms))) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_split = split;
+    }
+  }
+  for (int32_t cut : {-1, 32, 64}) {
+    if (rc || cut == best_cut) continue;
+    if ((rc = measure(best_split, cut, &ms))) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_cut = cut;
+    }
+  }
+  if (!rc) {
+    h->opts.split_k_rows = best_split;
+    h->opts.small_cutoff = best_cut;
+    rc = psi::build_schedule(h);
+    if (!rc) rc = upload_schedule(h);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->timing = timing;
+  if (rc) return rc;
+  h_best[0] = best_split;
+  h_best[1] = best_cut;
+  *h_best_ms = best_ms;
+  h->inverted = false;  // X was overwritten by the trial runs
+  return PSELINV_OK;
+}
+
 int pselinv_get_info(const pselinv_handle* h, pselinv_info* info) {
   if (!h || !info) return PSELINV_ERR_ARG;
   info->n = h->n;
@@ -576,7 +671,21 @@ int pselinv_get_info(const pselinv_handle* h, pselinv_info* info) {
   info->flops_selinv = h->flops_selinv;
   info->flops_gemm1 = h->flops_gemm1;
   info->bytes_selinv = h->bytes_selinv;
-  info->device_bytes = h->device_bytes;
+  // device memory held now (the autotuner reallocates the schedule buffers)
+  if (h->dev_sym) {
+    const int64_t B = h->opts.batch, es = (int64_t)elem_size(h), tasks =
+        (int64_t)(h->t_lhat.tasks.size() + h->t_gemm1.tasks.size() + h->t_gemm2.tasks.size() +
+                  h->t_trsm.tasks.size() + h->t_schur.tasks.size() + h->t_rect.tasks.size());
+    int64_t bytes = (int64_t)(sizeof(psi::SnMeta) * h->meta.size() + sizeof(psi::ColDesc) * h->desc.size() +
+                              4 * h->relidx.size() + 8 * h->valmap.size() + h->diagmask.size() +
+                              4 * h->level_sn.size()) +
+                    (int64_t)sizeof(psi::Task) * tasks +
+                    B * es * (2 * h->panel_total + h->n + h->lhat_total + h->linv_total + h->part_max + h->ypart_max);
+    if (h->d_xb) bytes += B * es * (2 * h->panel_total + h->n + 2 * h->linv_total + 2 * h->lhat_total);
+    info->device_bytes = bytes;
+  } else {
+    info->device_bytes = 0;
+  }
   return PSELINV_OK;
 }
 

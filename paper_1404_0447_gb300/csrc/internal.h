@@ -23,6 +23,9 @@ struct SnMeta {
   int64_t linv;    // offset of (L_KK)^{-1} (s x s, ld = s)
   int64_t desc;    // offset of this supernode's r column descriptors
   int64_t part;    // level-local offset of the step-3 partial products (nchunk * s * s)
+  int32_t ksplit;  // step-2 partial products (1 = written directly)
+  int32_t kchunk;  // rows of C per step-2 partial product
+  int64_t ypart;   // level-local offset of the step-2 partial products (ksplit * r * s)
 };
 
 // Where column k of X_{C,C} (k-th row of C) lives: element offset of that
@@ -59,8 +62,9 @@ constexpr int kNumVar = 4;
 // Tile width of an output with `width` columns: the variant with the least
 // padded width ceil(width / BN) * BN, the wider tile on ties; complex tiles
 // stop at BN = 32 (register budget).
-inline int pick_variant(int width, bool cplx) {
+inline int pick_variant(int width, bool cplx, int small_cutoff = -1) {
   const int maxv = cplx ? 2 : 3;
+  if (small_cutoff >= 0 && width >= small_cutoff) return maxv;  // wide supernodes: widest tile
   int best = 0;
   int64_t best_pad = INT64_MAX;
   for (int v = 0; v <= maxv; ++v) {
@@ -100,14 +104,16 @@ struct pselinv_handle {
   std::vector<uint8_t> diagmask;  // user entry q is a diagonal entry
   std::vector<psi::SnMeta> meta;
   std::vector<psi::ColDesc> desc;
-  int64_t panel_total = 0, lhat_total = 0, linv_total = 0, part_max = 0;
+  std::vector<int8_t> level_split;  // level holds a supernode whose step 2 is split
+  int64_t panel_total = 0, lhat_total = 0, linv_total = 0, part_max = 0, ypart_max = 0;
   int64_t nnz_l = 0, max_r = 0;
   int32_t max_width = 0;
   double flops_selinv = 0, flops_gemm1 = 0, bytes_selinv = 0;
 
   // task lists (levels in priority order; supernodes of a level costliest first)
   psi::TaskList t_lhat;   // normalisation tiles (all supernodes)
-  psi::TaskList t_gemm1;  // step 2 tiles
+  psi::TaskList t_gemm1;  // step 2 tiles (with k-slices of split supernodes)
+  psi::TaskList t_rect;   // r x s tiles per level, unsplit (adjoint)
   psi::TaskList t_gemm2;  // step 3 partial-product tiles
   psi::TaskList t_trsm;   // factorisation: off-diagonal panel solve tiles
   psi::TaskList t_schur;  // factorisation: Schur-complement update tiles
@@ -123,7 +129,7 @@ struct pselinv_handle {
   void* d_valmap = nullptr;
   void* d_diagmask = nullptr;
   void* d_tasks = nullptr;  // all task arrays back to back
-  int64_t off_lhat = 0, off_gemm1 = 0, off_gemm2 = 0, off_trsm = 0, off_schur = 0;
+  int64_t off_lhat = 0, off_gemm1 = 0, off_gemm2 = 0, off_trsm = 0, off_schur = 0, off_rect = 0;
   void* d_levelsn = nullptr;
   void* d_L = nullptr;      // L panels (unit diagonal implied; D on the diagonal slots)
   void* d_X = nullptr;      // X panels
@@ -131,6 +137,7 @@ struct pselinv_handle {
   void* d_lhat = nullptr;   // normalised factor / factor scratch
   void* d_linv = nullptr;   // inverses of the diagonal blocks
   void* d_part = nullptr;   // step-3 partial products (level-local)
+  void* d_ypart = nullptr;  // step-2 partial products (level-local)
   void* d_status = nullptr; // device status words
   // adjoint work buffers (allocated on first pselinv_selinv_adjoint)
   void* d_xb = nullptr;     // X-bar, then F-bar (panel layout)
@@ -157,4 +164,7 @@ namespace psi {
 // analyze.cpp
 int analyze(pselinv_handle* h, int64_t n, const int64_t* colptr, const int32_t* rowind,
             const int32_t* perm);
+// Rebuild the tuning-dependent schedule (step-2 slices, task lists,
+// partial-product offsets) from h->opts.
+int build_schedule(pselinv_handle* h);
 }  // namespace psi

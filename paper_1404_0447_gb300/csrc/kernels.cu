@@ -176,7 +176,8 @@ __global__ void k_diag_final(const SnMeta* __restrict__ meta, const int32_t* __r
   }
 }
 
-// Copy the factor scratch back into the panels of the level's supernodes.
+// Copy the factor scratch back into the panels of the level's supernodes
+// (blockIdx.z strides over the columns; threads run down a column).
 template <class T>
 __global__ void k_copyback(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns, T* __restrict__ L,
                            const T* __restrict__ Ltmp, Sizes sz) {
@@ -186,11 +187,8 @@ __global__ void k_copyback(const SnMeta* __restrict__ meta, const int32_t* __res
   const int s = m.s, r = m.r, ld = s + r;
   T* P = L + b * sz.panel + m.panel + s;
   const T* src = Ltmp + b * sz.lhat + m.lhat;
-  const int64_t tot = (int64_t)r * s;
-  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int64_t i = e % r, j = e / r;
-    P[i + j * ld] = src[e];
-  }
+  for (int j = blockIdx.z; j < s; j += gridDim.z)
+    for (int i = threadIdx.x; i < r; i += blockDim.x) P[i + (int64_t)j * ld] = src[i + (int64_t)j * r];
 }
 
 // --------------------------------------------------------------------------
@@ -312,7 +310,7 @@ template <class T, int BN>
 __global__ void __launch_bounds__(TG_THREADS) k_gemm1(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
                                                       const ColDesc* __restrict__ desc,
                                                       const int32_t* __restrict__ relidx, const T* __restrict__ Lhat,
-                                                      T* __restrict__ X, Sizes sz) {
+                                                      T* __restrict__ X, T* __restrict__ ypart, Sizes sz) {
   __shared__ TileSmem<T, BN> sm;
   const Task tk = tasks[blockIdx.x];
   const int b = blockIdx.y;
@@ -337,13 +335,48 @@ __global__ void __launch_bounds__(TG_THREADS) k_gemm1(const SnMeta* __restrict__
   // where a k-tile lies wholly right of the tile's rows the entries come from
   // the columns of C in the m direction: threads run along k there so the
   // panel reads stay contiguous
+  // step 2 of a wide C is split over kchunk-row slices of C (task.c), each
+  // written to its own partial buffer and summed in order by k_gemm1_reduce
   const int m0 = tk.m0;
-  tile_mma<T, BN>(sm, 0, r, [m0](int kt) { return kt >= m0 + TG_BM; }, la, lb, acc);
+  const int kb = tk.c * m.kchunk, ke = min(r, kb + m.kchunk);
+  tile_mma<T, BN>(sm, kb, ke, [m0](int kt) { return kt >= m0 + TG_BM; }, la, lb, acc);
+  if (m.ksplit == 1) {
+    T* out = X + b * sz.panel + m.panel + s;
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int row = tk.m0 + mm, col = tk.n0 + nn;
+      if (row < r && col < s) out[row + (int64_t)col * ld] = -v;
+    });
+  } else {
+    T* out = ypart + b * sz.ypart + m.ypart + (int64_t)tk.c * r * s;
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int row = tk.m0 + mm, col = tk.n0 + nn;
+      if (row < r && col < s) out[row + (int64_t)col * r] = v;
+    });
+  }
+}
+
+// Step 2 finish for split supernodes: X_{C,K} = -(sum of the partial
+// products in slice order); other supernodes of the level exit at once.
+// blockIdx.z strides over the s columns; threads run down a column.
+template <class T>
+__global__ void k_gemm1_reduce(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns,
+                               const T* __restrict__ ypart, T* __restrict__ X, Sizes sz) {
+  const int k = sns[blockIdx.x];
+  const int b = blockIdx.y;
+  const SnMeta m = meta[k];
+  if (m.ksplit == 1) return;
+  const int s = m.s, r = m.r, ld = s + r;
+  const T* yp = ypart + b * sz.ypart + m.ypart;
   T* out = X + b * sz.panel + m.panel + s;
-  tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
-    const int row = tk.m0 + mm, col = tk.n0 + nn;
-    if (row < r && col < s) out[row + (int64_t)col * ld] = -v;
-  });
+  const int64_t rs = (int64_t)r * s;
+  for (int j = blockIdx.z; j < s; j += gridDim.z) {
+    const T* col = yp + (int64_t)j * r;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      T acc = col[i];
+      for (int c = 1; c < m.ksplit; ++c) acc += col[c * rs + i];
+      out[i + (int64_t)j * ld] = -acc;
+    }
+  }
 }
 
 // Step 3, partial products: P_c = Lhat_{rows c, K}^T X_{rows c, K} over a
@@ -490,7 +523,8 @@ static cudaError_t tiles_tb(Kern k, const KArgs& a, const Task* t, int64_t n, cu
       k_lhat<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.L, (const T*)a.Linv, (T*)a.Lhat, a.sz);
       break;
     case Kern::Gemm1:
-      k_gemm1<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, a.desc, a.relidx, (const T*)a.Lhat, (T*)a.X, a.sz);
+      k_gemm1<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, a.desc, a.relidx, (const T*)a.Lhat, (T*)a.X,
+                                                  (T*)a.ypart, a.sz);
       break;
     default:
       k_gemm2<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.Lhat, (const T*)a.X, (T*)a.part, a.sz);
@@ -526,11 +560,14 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
                                                                 a.status);
       break;
     case Kern::CopyBack:
-      k_copyback<T><<<grid, 256, 0, st>>>(a.meta, sns, (T*)a.L, (const T*)a.Lhat, a.sz);
+      k_copyback<T><<<dim3(nsn, a.sz.batch, 16), 256, 0, st>>>(a.meta, sns, (T*)a.L, (const T*)a.Lhat, a.sz);
       break;
     case Kern::NormDiag:  // every supernode: blockIdx.x is the supernode itself
       k_norm_diag<T><<<grid, 256, diag_smem<T>(a.maxw), st>>>(a.meta, (const T*)a.L, (const T*)a.D, (T*)a.Linv,
                                                               (T*)a.X, a.sz);
+      break;
+    case Kern::Gemm1Reduce:
+      k_gemm1_reduce<T><<<dim3(nsn, a.sz.batch, 16), 256, 0, st>>>(a.meta, sns, (const T*)a.ypart, (T*)a.X, a.sz);
       break;
     default:
       k_diag_final<T><<<grid, 256, 0, st>>>(a.meta, sns, (const T*)a.part, (T*)a.X, a.sz);

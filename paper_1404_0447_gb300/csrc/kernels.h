@@ -14,10 +14,11 @@ struct Sizes {
   int64_t linv;   // diagonal-block inverses
   int64_t n;      // pivots
   int64_t part;   // step-3 partial products
+  int64_t ypart;  // step-2 partial products
   int batch;
 };
 
-enum class Kern { Trsm, Schur, Lhat, Gemm1, Gemm2, FactorDiag, CopyBack, NormDiag, DiagFinal };
+enum class Kern { Trsm, Schur, Lhat, Gemm1, Gemm2, FactorDiag, CopyBack, NormDiag, DiagFinal, Gemm1Reduce };
 
 // Everything a kernel may need; device pointers typed by dtype inside.
 struct KArgs {
@@ -32,6 +33,7 @@ struct KArgs {
   void* Lhat;
   void* X;
   void* part;
+  void* ypart;
   int* status;
   Sizes sz;
 };
@@ -45,7 +47,7 @@ cudaError_t launch_gather_values(int dtype, const void* X, const int64_t* vmap, 
 // Tile kernels (Trsm, Schur, Lhat, Gemm1, Gemm2) over n tasks of one tile
 // width variant (BN = 8 << var).
 cudaError_t launch_tiles(Kern k, int var, const KArgs& a, const Task* tasks, int64_t n, cudaStream_t st);
-// Per-supernode kernels (FactorDiag, CopyBack, NormDiag, DiagFinal) over the
+// Per-supernode kernels (FactorDiag, CopyBack, NormDiag, DiagFinal, Gemm1Reduce) over the
 // nsn supernodes listed in sns (NormDiag: supernodes 0..nsn-1, sns unused).
 cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st);
 cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st);

@@ -51,9 +51,9 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-def check_problem(P, n, cp, ri, vals, wmax=128, relax=1, perm=None, modes=(1,)):
+def check_problem(P, n, cp, ri, vals, wmax=128, relax=1, perm=None, modes=(1,), **opts):
     import torch
-    h = P.SelInv(n, cp, ri, perm=perm, max_sn_width=wmax, relax=relax)
+    h = P.SelInv(n, cp, ri, perm=perm, max_sn_width=wmax, relax=relax, **opts)
     h.factor(torch_vals(vals))
     sym, off, Xo, Lo, do = oracle_panels(n, cp, ri, vals, wmax, relax, perm)
     assert np.array_equal(h.symbolic()["panel_off"], off)
@@ -82,6 +82,30 @@ def test_3d_grids_tiles_and_ragged_tails(P, side, wmax, relax):
     assert np.array_equal(outs[0], outs[1])
     if side == 24:
         assert h.info["max_r"] > 512   # several step-3 row chunks, several 64-row tiles
+
+
+@pytest.mark.parametrize("split,cutoff", [(0, -1), (48, -1), (100, 32), (333, 64), (16, 0)])
+def test_split_step2_and_tile_policies(P, split, cutoff):
+    """Step 2 split into slices of `split` rows of C (reduced in order) and the
+    wide-tile policy for supernodes of width >= `cutoff` give the oracle's X."""
+    p = synth.grid_problem((14, 13, 12), 0.01, 0.1, 91)
+    h, outs, sym, Xo = check_problem(P, p.n, p.colptr, p.rowind, p.values, 64, 1, modes=(1, 0, 2),
+                                     split_k_rows=split, small_cutoff=cutoff)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def test_autotune_keeps_a_correct_schedule(P):
+    import torch
+    p = synth.grid_problem((18, 17, 16), 0.01, 0.1, 5)
+    h = P.SelInv(p.n, p.colptr, p.rowind)
+    h.factor(torch_vals(p.values))
+    best = h.autotune()
+    assert best["split_k_rows"] in (0, 512, 1024, 2048, 4096) and best["small_cutoff"] in (-1, 32, 64)
+    assert best["ms"] > 0
+    sym, off, Xo, Lo, do = oracle_panels(p.n, p.colptr, p.rowind, p.values, 128, 1)
+    for mode in (P.GRAPH, P.LEVEL, P.PLAIN):
+        h.selinv(mode)
+        assert rel(h.panels(0)[0].cpu().numpy(), Xo) <= TOL
 
 
 def test_random_pattern_with_permutation(P):
