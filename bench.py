@@ -234,6 +234,10 @@ def run_ours(args):
     h.selinv(P.GRAPH, stream=stream)
     torch.cuda.synchronize()
     ms_graph, _ = timed(P.GRAPH, max(1, args.steps))
+    h.selinv(P.PERSISTENT, stream=stream)
+    h.sync_status(stream=stream)
+    ms_persistent, _ = timed(P.PERSISTENT, max(1, args.steps))
+    h.sync_status(stream=stream)
     ms_plain = None
     if not args.no_plain:
         h.selinv(P.PLAIN, stream=stream)
@@ -290,7 +294,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "n": prob.n, "nnz_a_lower": info["nnz_a"],
                            "nnz_l": info["nnz_l"], "supernodes": info["nsn"], "levels": info["nlevels"],
                            "flops_per_step": flops, "schedule": "level (one grouped launch per kernel per level)",
-                           "batched_ms": ms, "graph_ms": ms_graph, "plain_ms": ms_plain,
+                           "batched_ms": ms, "graph_ms": ms_graph, "persistent_ms": ms_persistent, "plain_ms": ms_plain,
                            "speedup_batched_vs_plain": ms_plain / ms if ms_plain else None,
                            "kernel_ms_per_step": {"normalise": kms[0] / args.steps, "step2_gemm1": kms[1] / args.steps,
                                                   "step3_partials": kms[2] / args.steps,
@@ -364,7 +368,7 @@ def run_workload(args):
     with torch.cuda.stream(st):
         h.factor(vals.view(-1), stream=st)
     line["factor_ms"] = 1e3 * (time.perf_counter() - t0)
-    for name, mode in (("level", P.LEVEL), ("graph", P.GRAPH), ("plain", P.PLAIN)):
+    for name, mode in (("level", P.LEVEL), ("graph", P.GRAPH), ("persistent", P.PERSISTENT), ("plain", P.PLAIN)):
         if name == "plain" and w == "dg_poles" and args.poles > 4:
             continue
         ms = _time(lambda: h.selinv(mode, stream=st), args.steps if name != "plain" else 1,

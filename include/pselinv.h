@@ -67,6 +67,9 @@ extern "C" {
 #define PSELINV_PLAIN 0 /* one supernode per launch, reverse postorder */
 #define PSELINV_LEVEL 1 /* one grouped launch per kernel per level of Algorithm 2 */
 #define PSELINV_GRAPH 2 /* the LEVEL sequence captured once into a CUDA graph and replayed */
+#define PSELINV_PERSISTENT 3 /* one persistent launch per level running all of that level's work from
+                                one task list with bounded dependency waits; captured once into a
+                                CUDA graph and replayed */
 
 typedef struct pselinv_handle pselinv_handle;
 
@@ -211,6 +214,22 @@ int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream);
  * d_out: device, batch x panel_entries elements of the dtype.
  */
 int pselinv_get_panels(pselinv_handle* h, int32_t which, void* d_out, void* stream);
+
+/*
+ * Synchronise `stream` and report device-side failures of earlier enqueued
+ * work on h: PSELINV_ERR_TIMEOUT if a bounded wait of the PERSISTENT
+ * schedule ran out (that call's results are invalid; the flag is cleared and
+ * the handle stays usable).  Returns PSELINV_OK otherwise.
+ */
+int pselinv_sync_status(pselinv_handle* h, void* stream);
+
+/*
+ * Debug switches (failure-detection tests; no paper counterpart).  Bit 1
+ * (value 2): the next PERSISTENT pselinv_selinv arms one dependency wait
+ * that is never satisfied, so it must end by the spin limit with
+ * PSELINV_ERR_TIMEOUT from pselinv_sync_status instead of hanging.
+ */
+int pselinv_set_debug(pselinv_handle* h, int32_t flags);
 
 /*
  * Gather the selected inverse at the positions of A's lower CSC in the

@@ -20,11 +20,11 @@ ERRORS = {-1: "ERR_ARG", -2: "ERR_NOT_LOWER", -3: "ERR_ZERO_PIVOT", -4: "ERR_NON
           -5: "ERR_OOM", -6: "ERR_CUDA", -7: "ERR_TIMEOUT", -8: "ERR_STATE"}
 F64, C128 = 0, 1
 RELAX_NONE, RELAX_AMALG = 0, 1
-PLAIN, LEVEL, GRAPH = 0, 1, 2
+PLAIN, LEVEL, GRAPH, PERSISTENT = 0, 1, 2, 3
 G_SYMMETRIC, G_PANEL = 0, 1
 
 EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_analyze_batch", "pselinv_factor", "pselinv_selinv",
-            "pselinv_get_panels", "pselinv_get_selected", "pselinv_logdet_grad", "pselinv_logdet",
+            "pselinv_get_panels", "pselinv_sync_status", "pselinv_set_debug", "pselinv_get_selected", "pselinv_logdet_grad", "pselinv_logdet",
             "pselinv_selinv_adjoint",
             "pselinv_set_timing", "pselinv_get_timing", "pselinv_autotune", "pselinv_get_info",
             "pselinv_export_symbolic",
@@ -82,6 +82,8 @@ def load_library():
     L.pselinv_factor.argtypes = [vp, vp, vp]
     L.pselinv_selinv.argtypes = [vp, ctypes.c_int32, vp]
     L.pselinv_get_panels.argtypes = [vp, ctypes.c_int32, vp, vp]
+    L.pselinv_sync_status.argtypes = [vp, vp]
+    L.pselinv_set_debug.argtypes = [vp, ctypes.c_int32]
     L.pselinv_get_selected.argtypes = [vp, vp, vp]
     L.pselinv_logdet.argtypes = [vp, vp, vp]
     L.pselinv_logdet_grad.argtypes = [vp, vp, vp]
@@ -206,6 +208,13 @@ class SelInv:
 
     def selinv(self, mode=LEVEL, stream=None):
         self._check(self._lib.pselinv_selinv(self._h, int(mode), _stream_ptr(stream)))
+
+    def sync_status(self, stream=None):
+        """Synchronise and raise PselinvError(ERR_TIMEOUT) if a bounded device wait ran out."""
+        self._check(self._lib.pselinv_sync_status(self._h, _stream_ptr(stream)))
+
+    def set_debug(self, flags):
+        self._check(self._lib.pselinv_set_debug(self._h, int(flags)))
 
     def panels(self, which=0, stream=None):
         import torch

@@ -534,6 +534,32 @@ int build_schedule(pselinv_handle* h) {
     h->part_max = std::max(h->part_max, off);
     h->ypart_max = std::max(h->ypart_max, yoff);
   }
+  // persistent schedule: per level [step-2 tiles][slice reductions][step-3 tiles][finishes]
+  h->plist.clear();
+  h->plevel_ptr.assign(nl + 1, 0);
+  h->pn1.assign(nsn, 0);
+  h->pn2.assign(nsn, 0);
+  for (int32_t k = 0; k < nsn; ++k) {
+    h->pn1[k] = (int32_t)(h->t_gemm1.per_sn[k].end - h->t_gemm1.per_sn[k].begin);
+    h->pn2[k] = (int32_t)(h->t_gemm2.per_sn[k].end - h->t_gemm2.per_sn[k].begin);
+  }
+  for (int32_t l = 0; l < nl; ++l) {
+    h->plevel_ptr[l] = (int64_t)h->plist.size();
+    for (int v = 0; v < kNumVar; ++v) {
+      const Range rg = h->t_gemm1.per_lv[(size_t)l * kNumVar + v];
+      for (int64_t t = rg.begin; t < rg.end; ++t) h->plist.push_back({P_STEP2, (int16_t)v, (int32_t)t});
+    }
+    for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t)
+      if (h->meta[h->level_sn[t]].ksplit > 1)
+        for (int g = 0; g < kReduceGroups; ++g) h->plist.push_back({P_REDUCE, (int16_t)g, h->level_sn[t]});
+    for (int v = 0; v < kNumVar; ++v) {
+      const Range rg = h->t_gemm2.per_lv[(size_t)l * kNumVar + v];
+      for (int64_t t = rg.begin; t < rg.end; ++t) h->plist.push_back({P_STEP3, (int16_t)v, (int32_t)t});
+    }
+    for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t)
+      h->plist.push_back({P_FINISH, 0, h->level_sn[t]});
+  }
+  h->plevel_ptr[nl] = (int64_t)h->plist.size();
   return PSELINV_OK;
 }
 

@@ -2,6 +2,7 @@
 // factorisation and selected-inversion schedules, results and errors.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cstring>
 #include <string>
@@ -66,7 +67,8 @@ void free_device(pselinv_handle* h) {
   void** ptrs[] = {&h->d_meta, &h->d_desc, &h->d_relidx, &h->d_valmap, &h->d_diagmask, &h->d_tasks, &h->d_levelsn,
                    &h->d_L,    &h->d_X,    &h->d_D,      &h->d_lhat,   &h->d_linv,  &h->d_part, &h->d_ypart,
                    &h->d_status,
-                   &h->d_xb,   &h->d_lb,   &h->d_db,     &h->d_zb,     &h->d_w1,    &h->d_yb,   &h->d_hb};
+                   &h->d_xb,   &h->d_lb,   &h->d_db,     &h->d_zb,     &h->d_w1,    &h->d_yb,   &h->d_hb,
+                   &h->d_plist, &h->d_pn,  &h->d_pctr};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -76,13 +78,17 @@ void free_device(pselinv_handle* h) {
   h->ev_used = 0;
   h->ev_spans.clear();
   if (h->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);
+  if (h->pgraph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->pgraph_exec);
   if (h->graph_stream) cudaStreamDestroy((cudaStream_t)h->graph_stream);
-  h->graph_exec = h->graph_stream = nullptr;
+  h->graph_exec = h->pgraph_exec = h->graph_stream = nullptr;
   h->dev_sym = false;
   h->device_bytes = 0;
 }
 
 int upload_schedule(pselinv_handle* h);
+int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record);
+const psi::Task* tasks_at(const pselinv_handle* h, int64_t base, int64_t off);
+psi::KArgs kargs(pselinv_handle* h);
 
 int ensure_device(pselinv_handle* h) {
   if (h->dev_sym) return PSELINV_OK;
@@ -91,6 +97,7 @@ int ensure_device(pselinv_handle* h) {
   if (e != cudaSuccess || count == 0) return set_err(h, PSELINV_ERR_CUDA, "no CUDA device available");
   PSI_CUDA(h, cudaGetDevice(&h->device));
   PSI_CUDA(h, psi::setup_kernels());
+  PSI_CUDA(h, psi::persistent_grid(h->opts.dtype, &h->pgrid));
   int rc;
   if ((rc = upload(h, &h->d_desc, h->desc))) return rc;
   if ((rc = upload(h, &h->d_relidx, h->relidx))) return rc;
@@ -105,6 +112,7 @@ int ensure_device(pselinv_handle* h) {
   if ((rc = alloc(h, &h->d_lhat, B * h->lhat_total * es))) return rc;
   if ((rc = alloc(h, &h->d_linv, B * h->linv_total * es))) return rc;
   if ((rc = alloc(h, &h->d_status, sizeof(int) * kStatusWords + sizeof(double) * 2 * B))) return rc;
+  PSI_CUDA(h, cudaMemset(h->d_status, 0, sizeof(int) * kStatusWords));
   h->dev_sym = true;
   return PSELINV_OK;
 }
@@ -113,16 +121,18 @@ int ensure_device(pselinv_handle* h) {
 // called again by the autotuner after build_schedule.
 int upload_schedule(pselinv_handle* h) {
   int rc;
-  void** old[] = {&h->d_meta, &h->d_tasks, &h->d_part, &h->d_ypart};
+  void** old[] = {&h->d_meta, &h->d_tasks, &h->d_part, &h->d_ypart, &h->d_plist, &h->d_pn, &h->d_pctr};
   for (void** p : old)
     if (*p) {
       cudaFree(*p);
       *p = nullptr;
     }
-  if (h->graph_exec) {
-    cudaGraphExecDestroy((cudaGraphExec_t)h->graph_exec);
-    h->graph_exec = nullptr;
-  }
+  void** graphs[] = {&h->graph_exec, &h->pgraph_exec};
+  for (void** g : graphs)
+    if (*g) {
+      cudaGraphExecDestroy((cudaGraphExec_t)*g);
+      *g = nullptr;
+    }
   if ((rc = upload(h, &h->d_meta, h->meta))) return rc;
   std::vector<psi::Task> all;
   h->off_lhat = (int64_t)all.size();
@@ -141,6 +151,43 @@ int upload_schedule(pselinv_handle* h) {
   const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
   if ((rc = alloc(h, &h->d_part, B * h->part_max * es))) return rc;
   if ((rc = alloc(h, &h->d_ypart, B * h->ypart_max * es))) return rc;
+  if ((rc = upload(h, &h->d_plist, h->plist))) return rc;
+  std::vector<int32_t> pn(h->pn1);
+  pn.insert(pn.end(), h->pn2.begin(), h->pn2.end());
+  if ((rc = upload(h, &h->d_pn, pn))) return rc;
+  if ((rc = alloc(h, &h->d_pctr, (int64_t)sizeof(int) * (3 * B * h->nsn + h->nlevels)))) return rc;
+  return PSELINV_OK;
+}
+
+// Persistent schedule: reset the counters, the normalisation pass, then one
+// persistent launch per level.
+int enqueue_persistent(pselinv_handle* h, cudaStream_t st) {
+  const psi::KArgs a = kargs(h);
+  const int64_t B = h->opts.batch;
+  PSI_CUDA(h, cudaMemsetAsync(h->d_pctr, 0, sizeof(int) * (3 * B * h->nsn + h->nlevels), st));
+  PSI_CUDA(h, psi::launch_per_sn(psi::Kern::NormDiag, a, nullptr, h->nsn, st));
+  for (int v = 0; v < psi::kNumVar; ++v) {
+    const psi::Range r = h->t_lhat.whole[v];
+    PSI_CUDA(h, psi::launch_tiles(psi::Kern::Lhat, v, a, tasks_at(h, h->off_lhat, r.begin), r.end - r.begin, st));
+  }
+  psi::PArgs p;
+  int* ctr = (int*)h->d_pctr;
+  p.g1 = tasks_at(h, h->off_gemm1, 0);
+  p.g2 = tasks_at(h, h->off_gemm2, 0);
+  p.c1 = ctr;
+  p.c2 = ctr + B * h->nsn;
+  p.cr = ctr + 2 * B * h->nsn;
+  p.head = ctr + 3 * B * h->nsn;
+  p.n1 = (const int32_t*)h->d_pn;
+  p.n2 = (const int32_t*)h->d_pn + h->nsn;
+  p.nsn = h->nsn;
+  p.spin_ns = h->opts.spin_limit_ns > 0 ? h->opts.spin_limit_ns : 1000000000LL;
+  const psi::PTask* list = (const psi::PTask*)h->d_plist;
+  for (int32_t l = 0; l < h->nlevels; ++l) {
+    const int64_t b0 = h->plevel_ptr[l], n = h->plevel_ptr[l + 1] - b0;
+    const int grid = (int)std::min<int64_t>(h->pgrid, n * B);
+    PSI_CUDA(h, psi::launch_persistent_level(a, p, list + b0, (int)n, l, grid, st));
+  }
   return PSELINV_OK;
 }
 
@@ -405,18 +452,50 @@ int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream) {
 
 int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream) {
   if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
-  if (mode != PSELINV_PLAIN && mode != PSELINV_LEVEL && mode != PSELINV_GRAPH)
+  if (mode != PSELINV_PLAIN && mode != PSELINV_LEVEL && mode != PSELINV_GRAPH && mode != PSELINV_PERSISTENT)
     return set_err(h, PSELINV_ERR_ARG, "bad selinv mode");
   if (!h->factored) return set_err(h, PSELINV_ERR_STATE, "selinv called before a successful factor");
   cudaStream_t st = (cudaStream_t)stream;
-  if (mode != PSELINV_GRAPH) {
+  if (mode == PSELINV_PERSISTENT) {
+    if (!h->pgraph_exec) {
+      if (!h->graph_stream) {
+        cudaStream_t cs;
+        PSI_CUDA(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        h->graph_stream = cs;
+      }
+      cudaStream_t cs = (cudaStream_t)h->graph_stream;
+      PSI_CUDA(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      int rc = enqueue_persistent(h, cs);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(cs, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_err(h, e, "cudaStreamEndCapture");
+      cudaGraphExec_t ex;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_err(h, e, "cudaGraphInstantiate");
+      h->pgraph_exec = ex;
+    }
+    if (h->debug_flags & 2) {  // arm one never-satisfied wait (status word 3)
+      PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + 3, 1, 1, st));
+      h->debug_flags &= ~2;
+    }
+    PSI_CUDA(h, cudaGraphLaunch((cudaGraphExec_t)h->pgraph_exec, st));
+    h->launches[1] += h->nlevels;
+  } else if (mode != PSELINV_GRAPH) {
     int rc = enqueue_selinv(h, mode, st, h->timing);
     if (rc) return rc;
   } else {
     if (!h->graph_exec) {
-      cudaStream_t cs;
-      PSI_CUDA(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-      h->graph_stream = cs;
+      if (!h->graph_stream) {
+        cudaStream_t ns;
+        PSI_CUDA(h, cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking));
+        h->graph_stream = ns;
+      }
+      cudaStream_t cs = (cudaStream_t)h->graph_stream;
       PSI_CUDA(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       int64_t before[4];
       std::memcpy(before, h->launches, sizeof(before));
@@ -442,6 +521,29 @@ int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream) {
     for (int q = 0; q < 4; ++q) h->launches[q] += h->graph_launches[q];
   }
   h->inverted = true;
+  return PSELINV_OK;
+}
+
+int pselinv_sync_status(pselinv_handle* h, void* stream) {
+  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
+  if (!h->dev_sym) return PSELINV_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int status[kStatusWords];
+  PSI_CUDA(h, cudaMemcpyAsync(status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
+  PSI_CUDA(h, cudaStreamSynchronize(st));
+  if (status[2]) {
+    PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + 2, 0, 2 * sizeof(int), st));
+    PSI_CUDA(h, cudaStreamSynchronize(st));
+    h->inverted = false;
+    return set_err(h, PSELINV_ERR_TIMEOUT,
+                   "a bounded device wait of the persistent schedule ran out; that selinv's results are invalid");
+  }
+  return PSELINV_OK;
+}
+
+int pselinv_set_debug(pselinv_handle* h, int32_t flags) {
+  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
+  h->debug_flags = flags;
   return PSELINV_OK;
 }
 

@@ -46,6 +46,15 @@ struct Task {
   int32_t c;
 };
 
+// One entry of a level's task list in the persistent schedule.
+enum PKind : int16_t { P_STEP2 = 0, P_REDUCE = 1, P_STEP3 = 2, P_FINISH = 3 };
+struct PTask {
+  int16_t kind;  // PKind
+  int16_t var;   // tile variant (STEP2 / STEP3) or column group (REDUCE)
+  int32_t idx;   // index into the step-2 / step-3 task array, or the supernode
+};
+constexpr int kReduceGroups = 8;  // column groups of one slice reduction
+
 // Contiguous task ranges [begin, end) for a level and for a supernode.
 struct Range {
   int64_t begin = 0, end = 0;
@@ -105,6 +114,9 @@ struct pselinv_handle {
   std::vector<psi::SnMeta> meta;
   std::vector<psi::ColDesc> desc;
   std::vector<int8_t> level_split;  // level holds a supernode whose step 2 is split
+  std::vector<psi::PTask> plist;     // persistent schedule: task lists of all levels
+  std::vector<int64_t> plevel_ptr;   // [nlevels+1] offsets into plist
+  std::vector<int32_t> pn1, pn2;     // step-2 / step-3 tiles per supernode
   int64_t panel_total = 0, lhat_total = 0, linv_total = 0, part_max = 0, ypart_max = 0;
   int64_t nnz_l = 0, max_r = 0;
   int32_t max_width = 0;
@@ -148,6 +160,12 @@ struct pselinv_handle {
   void* d_yb = nullptr;     // r x s per supernode
   void* d_hb = nullptr;     // r x s per supernode
   int64_t device_bytes = 0;
+  void* d_plist = nullptr;  // persistent schedule
+  void* d_pn = nullptr;     // pn1 then pn2
+  void* d_pctr = nullptr;   // c1, c2, cr counters, then per-level heads
+  int pgrid = 0;
+  void* pgraph_exec = nullptr;  // cudaGraphExec_t of the PERSISTENT schedule
+  int debug_flags = 0;
   void* graph_exec = nullptr;  // cudaGraphExec_t of the LEVEL schedule
   void* graph_stream = nullptr;
 

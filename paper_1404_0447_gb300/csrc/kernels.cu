@@ -10,6 +10,7 @@
 
 #include "internal.h"
 #include "kernels.h"
+#include "selinv_steps.cuh"
 #include "tile_gemm.cuh"
 
 namespace psi {
@@ -150,30 +151,9 @@ __global__ void k_norm_diag(const SnMeta* __restrict__ meta, const T* __restrict
   }
 }
 
-// Step 3 finish: X_KK = (Z + Z^T) / 2 with Z = M_K - sum_c P_c (the
-// symmetrisation at the end of Section 2.1 / Algorithm 3).  One thread per
-// unordered pair {i, j} reads and writes exactly (i, j) and (j, i).
 template <class T>
-__global__ void k_diag_final(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns,
-                             const T* __restrict__ part, T* __restrict__ X, Sizes sz) {
-  const int k = sns[blockIdx.x];
-  const int b = blockIdx.y;
-  const SnMeta m = meta[k];
-  const int s = m.s, ld = m.s + m.r;
-  T* XK = X + b * sz.panel + m.panel;
-  const T* pp = part + b * sz.part + m.part;
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-    const int i = e % s, j = e / s;
-    if (i < j) continue;
-    T zij = XK[i + (int64_t)j * ld], zji = XK[j + (int64_t)i * ld];
-    for (int c = 0; c < m.nchunk; ++c) {
-      zij -= pp[(int64_t)c * s * s + i + j * s];
-      zji -= pp[(int64_t)c * s * s + j + i * s];
-    }
-    const T x = 0.5 * (zij + zji);
-    XK[i + (int64_t)j * ld] = x;
-    XK[j + (int64_t)i * ld] = x;
-  }
+__global__ void k_diag_final(KArgs a, const int32_t* __restrict__ sns) {
+  step3_finish<T>(a, sns[blockIdx.x], blockIdx.y, false);
 }
 
 // Copy the factor scratch back into the panels of the level's supernodes
@@ -300,115 +280,23 @@ __global__ void __launch_bounds__(TG_THREADS) k_lhat(const SnMeta* __restrict__ 
   });
 }
 
-// Step 2: X_{C,K} = -X_{C,C} Lhat_{C,K}.  X_{C,C} is read straight from the
-// ancestors' X panels: entry (i, k) with i >= k (rows of C are sorted) sits
-// in column desc[k].col at row relidx[desc[k].rel + i]; entries above the
-// diagonal use the symmetric one.  The result goes to rows s.. of K's own X
-// panel (Algorithm 3 overwrites Lhat by X_{C,K}; here Lhat stays in its own
-// buffer).
+// Steps 2 and 3 as grouped per-level kernels (bodies in selinv_steps.cuh).
 template <class T, int BN>
-__global__ void __launch_bounds__(TG_THREADS) k_gemm1(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
-                                                      const ColDesc* __restrict__ desc,
-                                                      const int32_t* __restrict__ relidx, const T* __restrict__ Lhat,
-                                                      T* __restrict__ X, T* __restrict__ ypart, Sizes sz) {
+__global__ void __launch_bounds__(TG_THREADS) k_gemm1(KArgs a, const Task* __restrict__ tasks) {
   __shared__ TileSmem<T, BN> sm;
-  const Task tk = tasks[blockIdx.x];
-  const int b = blockIdx.y;
-  const SnMeta m = meta[tk.sn];
-  const int s = m.s, r = m.r, ld = s + r;
-  const ColDesc* dk = desc + m.desc;
-  const T* Xb = X + b * sz.panel;
-  const T* Lh = Lhat + b * sz.lhat + m.lhat;
-  Acc<T, BN> acc;
-  acc_zero<T, BN>(acc);
-  auto la = [&](int mm, int kk) {
-    const int i = tk.m0 + mm;
-    if (i >= r) return Sc<T>::zero();
-    const int lo = i < kk ? i : kk, hi = i < kk ? kk : i;
-    const ColDesc cd = dk[lo];
-    return Xb[cd.col + relidx[cd.rel + hi]];
-  };
-  auto lb = [&](int kk, int nn) {
-    const int col = tk.n0 + nn;
-    return col < s ? Lh[kk + (int64_t)col * r] : Sc<T>::zero();
-  };
-  // where a k-tile lies wholly right of the tile's rows the entries come from
-  // the columns of C in the m direction: threads run along k there so the
-  // panel reads stay contiguous
-  // step 2 of a wide C is split over kchunk-row slices of C (task.c), each
-  // written to its own partial buffer and summed in order by k_gemm1_reduce
-  const int m0 = tk.m0;
-  const int kb = tk.c * m.kchunk, ke = min(r, kb + m.kchunk);
-  tile_mma<T, BN>(sm, kb, ke, [m0](int kt) { return kt >= m0 + TG_BM; }, la, lb, acc);
-  if (m.ksplit == 1) {
-    T* out = X + b * sz.panel + m.panel + s;
-    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
-      const int row = tk.m0 + mm, col = tk.n0 + nn;
-      if (row < r && col < s) out[row + (int64_t)col * ld] = -v;
-    });
-  } else {
-    T* out = ypart + b * sz.ypart + m.ypart + (int64_t)tk.c * r * s;
-    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
-      const int row = tk.m0 + mm, col = tk.n0 + nn;
-      if (row < r && col < s) out[row + (int64_t)col * r] = v;
-    });
-  }
+  step2_tile<T, BN>(a, tasks[blockIdx.x], blockIdx.y, sm);
 }
 
-// Step 2 finish for split supernodes: X_{C,K} = -(sum of the partial
-// products in slice order); other supernodes of the level exit at once.
-// blockIdx.z strides over the s columns; threads run down a column.
+// blockIdx.z strides over the columns of the split supernodes of the level
 template <class T>
-__global__ void k_gemm1_reduce(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns,
-                               const T* __restrict__ ypart, T* __restrict__ X, Sizes sz) {
-  const int k = sns[blockIdx.x];
-  const int b = blockIdx.y;
-  const SnMeta m = meta[k];
-  if (m.ksplit == 1) return;
-  const int s = m.s, r = m.r, ld = s + r;
-  const T* yp = ypart + b * sz.ypart + m.ypart;
-  T* out = X + b * sz.panel + m.panel + s;
-  const int64_t rs = (int64_t)r * s;
-  for (int j = blockIdx.z; j < s; j += gridDim.z) {
-    const T* col = yp + (int64_t)j * r;
-    for (int i = threadIdx.x; i < r; i += blockDim.x) {
-      T acc = col[i];
-      for (int c = 1; c < m.ksplit; ++c) acc += col[c * rs + i];
-      out[i + (int64_t)j * ld] = -acc;
-    }
-  }
+__global__ void k_gemm1_reduce(KArgs a, const int32_t* __restrict__ sns) {
+  step2_reduce<T>(a, sns[blockIdx.x], blockIdx.y, blockIdx.z, gridDim.z, false);
 }
 
-// Step 3, partial products: P_c = Lhat_{rows c, K}^T X_{rows c, K} over a
-// chunk of kChunkRows rows of C (plain transpose; s x s output tiles).
 template <class T, int BN>
-__global__ void __launch_bounds__(TG_THREADS) k_gemm2(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
-                                                      const T* __restrict__ Lhat, const T* __restrict__ X,
-                                                      T* __restrict__ part, Sizes sz) {
+__global__ void __launch_bounds__(TG_THREADS) k_gemm2(KArgs a, const Task* __restrict__ tasks) {
   __shared__ TileSmem<T, BN> sm;
-  const Task tk = tasks[blockIdx.x];
-  const int b = blockIdx.y;
-  const SnMeta m = meta[tk.sn];
-  const int s = m.s, r = m.r, ld = s + r;
-  const T* Lh = Lhat + b * sz.lhat + m.lhat;
-  const T* Y = X + b * sz.panel + m.panel + s;
-  Acc<T, BN> acc;
-  acc_zero<T, BN>(acc);
-  auto la = [&](int mm, int kk) {
-    const int i = tk.m0 + mm;
-    return i < s ? Lh[kk + (int64_t)i * r] : Sc<T>::zero();
-  };
-  auto lb = [&](int kk, int nn) {
-    const int col = tk.n0 + nn;
-    return col < s ? Y[kk + (int64_t)col * ld] : Sc<T>::zero();
-  };
-  const int kb = tk.c * kChunkRows, ke = min(r, kb + kChunkRows);
-  tile_mma<T, BN>(sm, kb, ke, [](int) { return true; }, la, lb, acc);
-  T* out = part + b * sz.part + m.part + (int64_t)tk.c * s * s;
-  tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
-    const int row = tk.m0 + mm, col = tk.n0 + nn;
-    if (row < s && col < s) out[row + col * s] = v;
-  });
+  step3_tile<T, BN>(a, tasks[blockIdx.x], blockIdx.y, sm, false);
 }
 
 // --------------------------------------------------------------------------
@@ -523,11 +411,10 @@ static cudaError_t tiles_tb(Kern k, const KArgs& a, const Task* t, int64_t n, cu
       k_lhat<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.L, (const T*)a.Linv, (T*)a.Lhat, a.sz);
       break;
     case Kern::Gemm1:
-      k_gemm1<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, a.desc, a.relidx, (const T*)a.Lhat, (T*)a.X,
-                                                  (T*)a.ypart, a.sz);
+      k_gemm1<T, BN><<<grid, TG_THREADS, 0, st>>>(a, t);
       break;
     default:
-      k_gemm2<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.Lhat, (const T*)a.X, (T*)a.part, a.sz);
+      k_gemm2<T, BN><<<grid, TG_THREADS, 0, st>>>(a, t);
       break;
   }
   return cudaGetLastError();
@@ -567,10 +454,10 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
                                                               (T*)a.X, a.sz);
       break;
     case Kern::Gemm1Reduce:
-      k_gemm1_reduce<T><<<dim3(nsn, a.sz.batch, 16), 256, 0, st>>>(a.meta, sns, (const T*)a.ypart, (T*)a.X, a.sz);
+      k_gemm1_reduce<T><<<dim3(nsn, a.sz.batch, 16), 256, 0, st>>>(a, sns);
       break;
     default:
-      k_diag_final<T><<<grid, 256, 0, st>>>(a.meta, sns, (const T*)a.part, (T*)a.X, a.sz);
+      k_diag_final<T><<<grid, 256, 0, st>>>(a, sns);
       break;
   }
   return cudaGetLastError();

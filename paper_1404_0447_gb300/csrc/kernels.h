@@ -52,6 +52,23 @@ cudaError_t launch_tiles(Kern k, int var, const KArgs& a, const Task* tasks, int
 cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st);
 cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st);
 
+// ---- persistent per-level schedule (persistent.cu) ----
+struct PArgs {
+  const Task* g1;       // step-2 task array (t_gemm1)
+  const Task* g2;       // step-3 task array (t_gemm2)
+  int* c1;              // [batch][nsn] finished step-2 tiles
+  int* c2;              // [batch][nsn] finished step-3 tiles
+  int* cr;              // [batch][nsn] finished slice reductions
+  const int32_t* n1;    // [nsn] step-2 tiles per supernode
+  const int32_t* n2;    // [nsn] step-3 tiles per supernode
+  int* head;            // [nlevels] dequeue counters
+  int nsn;
+  long long spin_ns;    // bound of every wait
+};
+cudaError_t launch_persistent_level(const KArgs& a, const PArgs& p, const PTask* list, int ntask, int level,
+                                    int grid, cudaStream_t st);
+cudaError_t persistent_grid(int dtype, int* grid);
+
 // ---- adjoint (adjoint.cu) ----
 struct AdjArgs {
   KArgs k;

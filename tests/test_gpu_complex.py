@@ -37,7 +37,7 @@ def test_pole_batch_matches_oracle(P, elems, nb, wmax):
     n, cp, ri, v, z, hv = poles_problem(elems, nb, 4, seed=31 + nb)
     h = P.SelInv(n, cp, ri, dtype=P.C128, batch=len(z), max_sn_width=wmax, relax=P.RELAX_AMALG)
     h.factor(tvals(v))
-    for mode in (P.LEVEL, P.PLAIN):
+    for mode in (P.LEVEL, P.PLAIN, P.PERSISTENT):
         h.selinv(mode)
         X = h.panels(0).cpu().numpy()
         for l in range(len(z)):

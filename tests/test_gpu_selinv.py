@@ -70,16 +70,17 @@ def check_problem(P, n, cp, ri, vals, wmax=128, relax=1, perm=None, modes=(1,), 
 
 def test_config0_all_schedules_bitwise_equal(P):
     p = synth.config0()
-    h, outs, sym, Xo = check_problem(P, p.n, p.colptr, p.rowind, p.values, 128, 0, modes=(0, 1, 2, 1, 2))
+    h, outs, sym, Xo = check_problem(P, p.n, p.colptr, p.rowind, p.values, 128, 0, modes=(0, 1, 2, 3, 1, 2, 3))
     # the schedules run identical per-supernode arithmetic: bitwise equal
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+    assert np.array_equal(outs[1], outs[3])
 
 
 @pytest.mark.parametrize("side,wmax,relax", [(12, 16, 1), (16, 128, 1), (13, 128, 0), (24, 128, 1)])
 def test_3d_grids_tiles_and_ragged_tails(P, side, wmax, relax):
     p = synth.grid_problem((side, side + 1, side - 1), 0.01, 0.1, 77 + side)
-    h, outs, sym, Xo = check_problem(P, p.n, p.colptr, p.rowind, p.values, wmax, relax, modes=(1, 0))
-    assert np.array_equal(outs[0], outs[1])
+    h, outs, sym, Xo = check_problem(P, p.n, p.colptr, p.rowind, p.values, wmax, relax, modes=(1, 0, 3))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[3])
     if side == 24:
         assert h.info["max_r"] > 512   # several step-3 row chunks, several 64-row tiles
 
@@ -89,9 +90,10 @@ def test_split_step2_and_tile_policies(P, split, cutoff):
     """Step 2 split into slices of `split` rows of C (reduced in order) and the
     wide-tile policy for supernodes of width >= `cutoff` give the oracle's X."""
     p = synth.grid_problem((14, 13, 12), 0.01, 0.1, 91)
-    h, outs, sym, Xo = check_problem(P, p.n, p.colptr, p.rowind, p.values, 64, 1, modes=(1, 0, 2),
+    h, outs, sym, Xo = check_problem(P, p.n, p.colptr, p.rowind, p.values, 64, 1, modes=(1, 0, 2, 3),
                                      split_k_rows=split, small_cutoff=cutoff)
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+    assert np.array_equal(outs[1], outs[3])
 
 
 def test_autotune_keeps_a_correct_schedule(P):
@@ -103,9 +105,34 @@ def test_autotune_keeps_a_correct_schedule(P):
     assert best["split_k_rows"] in (0, 512, 1024, 2048, 4096) and best["small_cutoff"] in (-1, 32, 64)
     assert best["ms"] > 0
     sym, off, Xo, Lo, do = oracle_panels(p.n, p.colptr, p.rowind, p.values, 128, 1)
-    for mode in (P.GRAPH, P.LEVEL, P.PLAIN):
+    for mode in (P.GRAPH, P.LEVEL, P.PLAIN, P.PERSISTENT):
         h.selinv(mode)
         assert rel(h.panels(0)[0].cpu().numpy(), Xo) <= TOL
+
+
+def test_persistent_wait_times_out_and_handle_recovers(P):
+    """Failure detection without a GPU fault: one dependency wait of the
+    persistent schedule is armed with a completion that never comes; the
+    launch must end by the 2 ms spin limit and report ERR_TIMEOUT, and the
+    same handle must then give correct results."""
+    import time
+    import torch
+    p = synth.grid_problem((12, 11, 10), 0.01, 0.1, 3)
+    h = P.SelInv(p.n, p.colptr, p.rowind, spin_limit_ns=2_000_000)
+    h.factor(torch_vals(p.values))
+    h.selinv(P.PERSISTENT)
+    h.sync_status()
+    good = h.panels(0)[0].cpu().numpy()
+    h.set_debug(2)
+    t0 = time.time()
+    h.selinv(P.PERSISTENT)
+    with pytest.raises(P.PselinvError) as e:
+        h.sync_status()
+    assert e.value.code == -7
+    assert time.time() - t0 < 10.0
+    h.selinv(P.PERSISTENT)
+    h.sync_status()
+    assert np.array_equal(h.panels(0)[0].cpu().numpy(), good)
 
 
 def test_random_pattern_with_permutation(P):
@@ -151,7 +178,7 @@ def test_edge_cases(P, kind):
         A = G @ G.T / n + np.eye(n)
         rows, cols = np.tril_indices(n)
         cp, ri, v = synth.lower_csc_from_coo(n, rows, cols, A[rows, cols])
-    check_problem(P, n, cp, ri, v, 128, 1, modes=(1, 0, 2))
+    check_problem(P, n, cp, ri, v, 128, 1, modes=(1, 0, 2, 3))
 
 
 def test_bad_pivots_are_reported_and_handle_recovers(P):

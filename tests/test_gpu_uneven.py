@@ -40,7 +40,7 @@ def test_small_uneven_batch_against_oracle(P):
     h.factor(torch.tensor(vals, dtype=torch.float64, device="cuda"))
     levels = h.info["nlevels"]
     assert levels == max(P.SelInv(m.n, m.colptr, m.rowind, max_sn_width=16).info["nlevels"] for m in mem)
-    for mode in (P.GRAPH, P.PLAIN):
+    for mode in (P.GRAPH, P.PLAIN, P.PERSISTENT):
         h.selinv(mode)
         sel = h.selected()[0].cpu().numpy()
         q0 = 0
