@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(TG_THREADS) k_trsm(const SnMeta* __restrict__ 
     const int col = tk.n0 + nn;
     return col < s ? Vi[col + kk * s] : Sc<T>::zero();
   };
-  tile_mma<T, BN>(sm, 0, s, [](int) { return false; }, la, lb, acc);
+  // (L_KK)^{-T} is upper triangular: output columns < n0 + BN need only k < n0 + BN
+  tile_mma<T, BN>(sm, 0, min(s, tk.n0 + BN), [](int) { return false; }, la, lb, acc);
   T* out = Ltmp + b * sz.lhat + m.lhat;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
@@ -272,7 +273,8 @@ __global__ void __launch_bounds__(TG_THREADS) k_lhat(const SnMeta* __restrict__ 
     const int col = tk.n0 + nn;
     return col < s ? Vi[kk + col * s] : Sc<T>::zero();
   };
-  tile_mma<T, BN>(sm, 0, s, [](int) { return false; }, la, lb, acc);
+  // (L_KK)^{-1} is lower triangular: output columns >= n0 need only k >= n0
+  tile_mma<T, BN>(sm, tk.n0, s, [](int) { return false; }, la, lb, acc);
   T* out = Lhat + b * sz.lhat + m.lhat;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
