@@ -67,6 +67,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device=None):
+    """Max of a per-rank scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(flops_per_rank, world, ms_max):
+    """Throughput of N independent replicas timed by the slowest rank."""
+    return flops_per_rank * world / (ms_max * 1e-3) / 1e12
+
+
 def oracle_sample_tflops(side=CPU_SAMPLE_SIDE):
     """Time the oracle's column selected inversion (its factorisation done
     first, untimed) on the side^3 member of the workload family; return
@@ -225,10 +241,7 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         ms, (kms, kl) = timed(P.LEVEL, args.steps, record=True)
     clocks = clk.summary()
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
 
     # graph-replayed level schedule and the plain one-supernode-per-launch schedule
     h.selinv(P.GRAPH, stream=stream)
@@ -268,7 +281,7 @@ def run_ours(args):
                "h2d_bytes_per_step": int(host_vals.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
                "includes": "pinned H2D of A's values, pselinv_factor, pselinv_selinv, D2H of the X panels"}
 
-    value = flops * world / (ms * 1e-3) / 1e12
+    value = whole_job_tflops(flops, world, ms)
     # roofline of the dominant kernel (step 2, X_{C,K} = -X_{C,C} Lhat): algorithmic
     # flops per launch over its event-timed average launch duration
     g1_launches = max(1, int(kl[1]) // args.steps)

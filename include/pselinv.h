@@ -251,6 +251,24 @@ int pselinv_get_selected(pselinv_handle* h, void* d_out, void* stream);
 int pselinv_logdet_grad(pselinv_handle* h, void* d_out, void* stream);
 
 /*
+ * Pole sum of a batch (the expansion of Section 4.4, Gamma = sum_l w_l
+ * (H - z_l S)^{-1}, on the selected pattern): d_out = sum_b w_b X_b in the
+ * X panel layout (one panel array, dtype of the handle).  h_weights: host,
+ * batch complex weights as (re, im) pairs for C128 handles, batch real
+ * weights for F64 handles.  Requires selinv.  HBM-bound pass over the batch.
+ */
+int pselinv_pole_sum(pselinv_handle* h, const double* h_weights, void* d_out, void* stream);
+
+/*
+ * Trace pairing of Section 4.3, Eq. (16): for every batch member b,
+ * S_b = sum over the nonzeros of A_b (both triangles) of X_ij A_ji, so that
+ * E_b = |1 - S_b / n|.  d_values: the batch's values of A (as passed to
+ * pselinv_factor).  h_out: host, batch x 2 doubles (re, im; im = 0 for F64).
+ * Requires selinv.  Synchronises the stream.
+ */
+int pselinv_trace_sum(pselinv_handle* h, const void* d_values, double* h_out, void* stream);
+
+/*
  * log det A = sum_j log d_j (Section 2.1's LDL^T).  h_out (host) receives
  * per batch member two doubles: F64 -> (sum log|d_j|, number of negative
  * pivots); C128 -> (real, imaginary) of the sum of principal logs.

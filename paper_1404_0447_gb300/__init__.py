@@ -24,7 +24,7 @@ PLAIN, LEVEL, GRAPH, PERSISTENT = 0, 1, 2, 3
 G_SYMMETRIC, G_PANEL = 0, 1
 
 EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_analyze_batch", "pselinv_factor", "pselinv_selinv",
-            "pselinv_get_panels", "pselinv_sync_status", "pselinv_set_debug", "pselinv_get_selected", "pselinv_logdet_grad", "pselinv_logdet",
+            "pselinv_get_panels", "pselinv_pole_sum", "pselinv_trace_sum", "pselinv_sync_status", "pselinv_set_debug", "pselinv_get_selected", "pselinv_logdet_grad", "pselinv_logdet",
             "pselinv_selinv_adjoint",
             "pselinv_set_timing", "pselinv_get_timing", "pselinv_autotune", "pselinv_get_info",
             "pselinv_export_symbolic",
@@ -83,6 +83,8 @@ def load_library():
     L.pselinv_selinv.argtypes = [vp, ctypes.c_int32, vp]
     L.pselinv_get_panels.argtypes = [vp, ctypes.c_int32, vp, vp]
     L.pselinv_sync_status.argtypes = [vp, vp]
+    L.pselinv_pole_sum.argtypes = [vp, vp, vp, vp]
+    L.pselinv_trace_sum.argtypes = [vp, vp, vp, vp]
     L.pselinv_set_debug.argtypes = [vp, ctypes.c_int32]
     L.pselinv_get_selected.argtypes = [vp, vp, vp]
     L.pselinv_logdet.argtypes = [vp, vp, vp]
@@ -208,6 +210,25 @@ class SelInv:
 
     def selinv(self, mode=LEVEL, stream=None):
         self._check(self._lib.pselinv_selinv(self._h, int(mode), _stream_ptr(stream)))
+
+    def pole_sum(self, weights, out=None, stream=None):
+        """pselinv_pole_sum: sum_b w_b X_b over the batch (X panel layout)."""
+        import torch
+        w = np.ascontiguousarray(weights, np.complex128 if self.opts.dtype == C128 else np.float64)
+        assert w.size == self.opts.batch
+        if out is None:
+            out = torch.empty(self.info["panel_entries"], dtype=self.torch_dtype, device="cuda")
+        self._check(self._lib.pselinv_pole_sum(self._h, ctypes.c_void_p(w.ctypes.data),
+                                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def trace_error(self, values, stream=None):
+        """E_b = |1 - (1/n) sum_{A_ij != 0} X_ij A_ji| per batch member (Eq. 16), from pselinv_trace_sum."""
+        out = np.zeros(2 * self.opts.batch, np.float64)
+        self._check(self._lib.pselinv_trace_sum(self._h, ctypes.c_void_p(values.data_ptr()), _ptr(out),
+                                                _stream_ptr(stream)))
+        s = out[0::2] + 1j * out[1::2]
+        return np.abs(1.0 - s / self.n)
 
     def sync_status(self, stream=None):
         """Synchronise and raise PselinvError(ERR_TIMEOUT) if a bounded device wait ran out."""

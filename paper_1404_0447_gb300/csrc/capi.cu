@@ -111,7 +111,7 @@ int ensure_device(pselinv_handle* h) {
   if ((rc = alloc(h, &h->d_D, B * h->n * es))) return rc;
   if ((rc = alloc(h, &h->d_lhat, B * h->lhat_total * es))) return rc;
   if ((rc = alloc(h, &h->d_linv, B * h->linv_total * es))) return rc;
-  if ((rc = alloc(h, &h->d_status, sizeof(int) * kStatusWords + sizeof(double) * 2 * B))) return rc;
+  if ((rc = alloc(h, &h->d_status, sizeof(int) * kStatusWords + sizeof(double) * 6 * B))) return rc;
   PSI_CUDA(h, cudaMemset(h->d_status, 0, sizeof(int) * kStatusWords));
   h->dev_sym = true;
   return PSELINV_OK;
@@ -572,6 +572,37 @@ int pselinv_logdet_grad(pselinv_handle* h, void* d_out, void* stream) {
   PSI_CUDA(h, psi::launch_gather_values(h->opts.dtype, h->d_X, (const int64_t*)h->d_valmap,
                                         (const uint8_t*)h->d_diagmask, h->nnz_a, d_out, sizes(h),
                                         (cudaStream_t)stream));
+  return PSELINV_OK;
+}
+
+int pselinv_pole_sum(pselinv_handle* h, const double* h_weights, void* d_out, void* stream) {
+  if (!h || !h_weights || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int B = h->opts.batch;
+  double* w = (double*)((int*)h->d_status + kStatusWords) + 2 * B;
+  const size_t wbytes = sizeof(double) * (h->opts.dtype == PSELINV_C128 ? 2 : 1) * B;
+  PSI_CUDA(h, cudaMemcpyAsync(w, h_weights, wbytes, cudaMemcpyHostToDevice, st));
+  PSI_CUDA(h, psi::launch_pole_sum(h->opts.dtype, h->d_X, h->panel_total, B, w, d_out, st));
+  return PSELINV_OK;
+}
+
+int pselinv_trace_sum(pselinv_handle* h, const void* d_values, double* h_out, void* stream) {
+  if (!h || !d_values || !h_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int B = h->opts.batch;
+  double* dev = (double*)((int*)h->d_status + kStatusWords) + 4 * B;
+  PSI_CUDA(h, psi::launch_trace_sum(h->opts.dtype, h->d_X, h->panel_total, (const int64_t*)h->d_valmap,
+                                    (const uint8_t*)h->d_diagmask, d_values, h->nnz_a, B, dev, st));
+  const bool cz = h->opts.dtype == PSELINV_C128;
+  std::vector<double> tmp((cz ? 2 : 1) * B);
+  PSI_CUDA(h, cudaMemcpyAsync(tmp.data(), dev, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost, st));
+  PSI_CUDA(h, cudaStreamSynchronize(st));
+  for (int b = 0; b < B; ++b) {
+    h_out[2 * b] = tmp[(cz ? 2 : 1) * b];
+    h_out[2 * b + 1] = cz ? tmp[2 * b + 1] : 0.0;
+  }
   return PSELINV_OK;
 }
 

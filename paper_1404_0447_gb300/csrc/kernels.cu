@@ -340,6 +340,68 @@ __global__ void k_logdet(const T* __restrict__ D, int64_t n, double* __restrict_
 }
 
 // --------------------------------------------------------------------------
+// pole sum and trace pairing
+// --------------------------------------------------------------------------
+
+// out[e] = sum_b w_b X_b[e]  (grid-stride, HBM-bound)
+template <class T>
+__global__ void k_pole_sum(const T* __restrict__ X, int64_t panel_total, int batch, const T* __restrict__ w,
+                           T* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < panel_total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    T acc = Sc<T>::zero();
+    for (int b = 0; b < batch; ++b) acc += w[b] * X[(int64_t)b * panel_total + e];
+    out[e] = acc;
+  }
+}
+
+// S_b = sum_q m_q X(q) A_q with m_q = 1 on the diagonal, 2 off it; one CTA
+// per batch member, fixed reduction order (deterministic).
+template <class T>
+__global__ void k_trace_sum(const T* __restrict__ X, int64_t panel_total, const int64_t* __restrict__ vmap,
+                            const uint8_t* __restrict__ diagmask, const T* __restrict__ vals, int64_t nnz,
+                            T* __restrict__ out) {
+  __shared__ T red[1024];
+  const int b = blockIdx.x;
+  const T* Xb = X + (int64_t)b * panel_total;
+  const T* v = vals + (int64_t)b * nnz;
+  T acc = Sc<T>::zero();
+  for (int64_t q = threadIdx.x; q < nnz; q += blockDim.x) {
+    const T t = Xb[vmap[q]] * v[q];
+    acc += diagmask[q] ? t : 2.0 * t;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[b] = red[0];
+}
+
+cudaError_t launch_pole_sum(int dtype, const void* X, int64_t panel_total, int batch, const void* w, void* out,
+                            cudaStream_t st) {
+  const unsigned grid = 152 * 8;
+  if (dtype == PSELINV_C128)
+    k_pole_sum<Cplx><<<grid, 256, 0, st>>>((const Cplx*)X, panel_total, batch, (const Cplx*)w, (Cplx*)out);
+  else
+    k_pole_sum<double><<<grid, 256, 0, st>>>((const double*)X, panel_total, batch, (const double*)w, (double*)out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_sum(int dtype, const void* X, int64_t panel_total, const int64_t* vmap,
+                             const uint8_t* diagmask, const void* vals, int64_t nnz, int batch, void* out,
+                             cudaStream_t st) {
+  if (dtype == PSELINV_C128)
+    k_trace_sum<Cplx><<<batch, 1024, 0, st>>>((const Cplx*)X, panel_total, vmap, diagmask, (const Cplx*)vals, nnz,
+                                              (Cplx*)out);
+  else
+    k_trace_sum<double><<<batch, 1024, 0, st>>>((const double*)X, panel_total, vmap, diagmask, (const double*)vals,
+                                                nnz, (double*)out);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
 // launch wrappers
 // --------------------------------------------------------------------------
 

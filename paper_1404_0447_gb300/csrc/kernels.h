@@ -51,6 +51,11 @@ cudaError_t launch_tiles(Kern k, int var, const KArgs& a, const Task* tasks, int
 // nsn supernodes listed in sns (NormDiag: supernodes 0..nsn-1, sns unused).
 cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st);
 cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st);
+cudaError_t launch_pole_sum(int dtype, const void* X, int64_t panel_total, int batch, const void* w, void* out,
+                            cudaStream_t st);
+cudaError_t launch_trace_sum(int dtype, const void* X, int64_t panel_total, const int64_t* vmap,
+                             const uint8_t* diagmask, const void* vals, int64_t nnz, int batch, void* out,
+                             cudaStream_t st);
 
 // ---- persistent per-level schedule (persistent.cu) ----
 struct PArgs {

@@ -84,6 +84,27 @@ def test_complex_logdet_and_selected_entries(P):
         assert abs(oracle.logdet(d)[1] - ld[l, 1]) < 1e-9
 
 
+def test_pole_sum_and_trace_error_per_pole(P):
+    """Gamma = sum_l w_l X_l (the pole expansion of Section 4.4) and E(z_l)
+    of Eq. (16) per pole, against the panels and the oracle's E."""
+    import torch
+    n, cp, ri, v, z, hv = poles_problem((4, 3, 3), 8, 5, seed=17)
+    h = P.SelInv(n, cp, ri, dtype=P.C128, batch=5, max_sn_width=32)
+    vt = tvals(v)
+    h.factor(vt)
+    h.selinv(P.LEVEL)
+    w = np.random.default_rng(2).normal(size=5) + 1j * np.random.default_rng(3).normal(size=5)
+    G = h.pole_sum(w).cpu().numpy()
+    X = h.panels(0).cpu().numpy()
+    want = (w[:, None] * X).sum(0)
+    assert np.max(np.abs(G - want)) <= 1e-13 * np.max(np.abs(want))
+    E = h.trace_error(vt)
+    sel = h.selected().cpu().numpy()
+    for l in range(5):
+        assert abs(E[l] - oracle.trace_error(n, cp, ri, v[l], sel[l])) < 1e-13
+        assert E[l] < 1e-12
+
+
 @pytest.mark.slow
 def test_full_size_dg_two_poles_trace_identity_and_batch_equivalence(P):
     """The 12^3-element, 48-dof DG-like matrix (n = 82,944) with its first two
