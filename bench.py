@@ -33,6 +33,11 @@ METRIC = "selinv ms & FP64 TFLOP/s (frac of peak), batched vs plain, err<=1e-10"
 # float64) and mma.sync m8n8k4 f64 throughput both ~1.10 TFLOP/s; see
 # profiles/fp64_peak_gb300.md.
 FP64_PEAK_TFLOPS = 1.10
+# DRAM bytes per step-2 launch (all k_gemm1 widths and slice reductions) at
+# the full 80^3 workload with the default schedule, from one-pass ncu
+# counters: profiles/k_gemm1_traffic_grid3d_80.md.  Set to None whenever
+# those kernels change until they are measured again.
+STEP2_TRAFFIC_BYTES_PER_LAUNCH = 458.27e6
 WORKLOAD = ("grid3d_80: 80^3 7-point Laplacian, n=512000, diag 6+U(0.01,0.1), geometric nested "
             "dissection, relaxed supernodes of width <= 128, FP64")
 # Oracle sample for the CPU baseline: the same grid family at a size the
@@ -288,11 +293,22 @@ def run_ours(args):
     g1_ms_launch = kms[1] / args.steps / g1_launches
     g1_flops_launch = info["flops_gemm1"] / g1_launches
     achieved = g1_flops_launch / (g1_ms_launch * 1e-3) / 1e12
-    roofline = {"bound": "tensor", "kernel": "k_gemm1 (step 2, FP64 DMMA m8n8k4)", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "measured cuBLAS DGEMM / DMMA throughput on this pool's GB300 (FP64 has no entry "
-                               "in MEASURED_PEAKS.json)",
-                "traffic": None, "launches_per_step": g1_launches,
+    sym = h.symbolic()
+    sw = np.diff(sym["sn_start"]).astype(float)
+    rr = np.diff(sym["rowptr"]).astype(float)
+    rel = np.diff(sym["relptr"]).astype(float)
+    g1_alg_bytes = float(np.sum(8 * rr * (rr + 1) / 2 + 16 * rr * sw + 4 * rel))
+    default_schedule = args.split_k_rows is None and args.small_cutoff is None and args.side == 80
+    roofline = {"bound": "tensor",
+                "kernel": "step 2: k_gemm1 (all tile widths, FP64 mma.sync m8n8k4, which runs on the FP64 pipe "
+                          "of sm_103a) + slice reductions",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "measured cuBLAS DGEMM / mma.sync f64 throughput on this pool's GB300 (FP64 has no "
+                               "entry in MEASURED_PEAKS.json)",
+                "traffic": STEP2_TRAFFIC_BYTES_PER_LAUNCH if default_schedule else None,
+                "traffic_unit": "DRAM bytes per launch (ncu, one pass, full workload)",
+                "algorithmic_bytes_per_launch": g1_alg_bytes / g1_launches,
+                "launches_per_step": g1_launches,
                 "whole_step_frac": value / world / FP64_PEAK_TFLOPS}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
