@@ -37,7 +37,7 @@ FP64_PEAK_TFLOPS = 1.10
 # the full 80^3 workload with the default schedule, from one-pass ncu
 # counters: profiles/k_gemm1_traffic_grid3d_80.md.  Set to None whenever
 # those kernels change until they are measured again.
-STEP2_TRAFFIC_BYTES_PER_LAUNCH = 458.27e6
+STEP2_TRAFFIC_BYTES_PER_LAUNCH = 446.09e6
 WORKLOAD = ("grid3d_80: 80^3 7-point Laplacian, n=512000, diag 6+U(0.01,0.1), geometric nested "
             "dissection, relaxed supernodes of width <= 128, FP64")
 # Oracle sample for the CPU baseline: the same grid family at a size the
@@ -269,22 +269,32 @@ def run_ours(args):
         host_out = torch.empty(info["panel_entries"], dtype=torch.float64).pin_memory()
         dev_vals = torch.empty_like(vals)
         xbuf = torch.empty(info["panel_entries"], dtype=torch.float64, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         for it in range(2):
             barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with torch.cuda.stream(stream):
+                ev[0].record(stream)
                 dev_vals.copy_(host_vals, non_blocking=True)
+                ev[1].record(stream)
                 h.factor(dev_vals, stream=stream)
+                ev[2].record(stream)
                 h.selinv(P.LEVEL, stream=stream)
+                ev[3].record(stream)
                 h._check(h._lib.pselinv_get_panels(h._h, 0, P.ctypes.c_void_p(xbuf.data_ptr()),
                                                    P._stream_ptr(stream)))
                 host_out.copy_(xbuf, non_blocking=True)
+                ev[4].record(stream)
             stream.synchronize()
             t_e2e = time.perf_counter() - t0
-        e2e = {"value": flops / t_e2e / 1e12 * world, "unit": "TFLOP/s", "ms_per_step": 1e3 * t_e2e,
+        phases = {name: ev[i].elapsed_time(ev[i + 1])
+                  for i, name in enumerate(("h2d_ms", "factor_ms", "selinv_ms", "d2h_ms"))}
+        e2e = {"value": whole_job_tflops(flops, world, max_over_ranks(1e3 * t_e2e, dev)), "unit": "TFLOP/s",
+               "ms_per_step": 1e3 * t_e2e,
                "h2d_bytes_per_step": int(host_vals.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
-               "includes": "pinned H2D of A's values, pselinv_factor, pselinv_selinv, D2H of the X panels"}
+               "includes": "pinned H2D of A's values, pselinv_factor, pselinv_selinv, D2H of the X panels",
+               "phases": phases}
 
     value = whole_job_tflops(flops, world, ms)
     # roofline of the dominant kernel (step 2, X_{C,K} = -X_{C,C} Lhat): algorithmic

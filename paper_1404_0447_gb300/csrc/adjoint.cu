@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
     });
   } else if constexpr (OP == A_VPART || OP == A_RPART) {
     // chunk partials of L_CK^T Hb (VPART) or Q^T L_CK with Q = Fb_CK (RPART)
-    const int kb = tk.c * kChunkRows, ke = min(r, kb + kChunkRows);
+    const int kb = tk.c * m.kchunk3, ke = min(r, kb + m.kchunk3);
     auto la = [&](int mm, int kk) {
       const int i = m0 + mm;
       if (i >= s) return zero;

@@ -308,7 +308,6 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
     m.f = ss[k];
     m.s = ss[k + 1] - ss[k];
     m.r = (int32_t)(h->rowptr[k + 1] - h->rowptr[k]);
-    m.nchunk = (m.r + kChunkRows - 1) / kChunkRows;
     m.panel = h->panel_off[k];
     h->panel_off[k + 1] = h->panel_off[k] + (int64_t)(m.s + m.r) * m.s;
     m.lhat = lhat;
@@ -440,14 +439,47 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
 // offsets of the partial-product buffers.
 int build_schedule(pselinv_handle* h) {
   {
+    // Step-2 slices: at most split_k_rows rows of C each; in a level whose
+    // tiles cannot fill the GPU (fewer than kTargetTiles) the slices shrink,
+    // down to kMinSlice2 rows, until it can.  Step-3 row chunks likewise from
+    // kChunkRows down to kMinChunk3.  Slice sizes are multiples of 16.
     const pselinv_opts& o = h->opts;
-    for (SnMeta& m : h->meta) {
-      m.ksplit = 1;
-      m.kchunk = m.r;
-      if (o.split_k_rows > 0 && m.r > o.split_k_rows) {
-        const int32_t parts = (m.r + o.split_k_rows - 1) / o.split_k_rows;
-        m.kchunk = ((m.r + parts - 1) / parts + 15) / 16 * 16;
-        m.ksplit = (m.r + m.kchunk - 1) / m.kchunk;
+    const bool cplx = o.dtype == PSELINV_C128;
+    auto slices = [](int32_t r, int32_t rows, int32_t* chunk) {
+      const int32_t parts = (r + rows - 1) / rows;
+      *chunk = ((r + parts - 1) / parts + 15) / 16 * 16;
+      return (r + *chunk - 1) / *chunk;
+    };
+    for (int32_t l = 0; l < h->nlevels; ++l) {
+      int64_t t2 = 0, t3 = 0;
+      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+        SnMeta& m = h->meta[h->level_sn[t]];
+        const int bn = 8 << pick_variant(m.s, cplx, o.small_cutoff);
+        const int64_t mt = (m.r + kTileM - 1) / kTileM, nt = (m.s + bn - 1) / bn, st = (m.s + kTileM - 1) / kTileM;
+        m.ksplit = 1;
+        m.kchunk = m.r;
+        if (o.split_k_rows > 0 && m.r > o.split_k_rows) m.ksplit = slices(m.r, o.split_k_rows, &m.kchunk);
+        m.nchunk = m.r > 0 ? slices(m.r, kChunkRows, &m.kchunk3) : 0;
+        if (m.r == 0) m.kchunk3 = kChunkRows;
+        t2 += mt * nt * m.ksplit;
+        t3 += (int64_t)m.nchunk * st * nt;
+      }
+      if (o.split_k_rows > 0 && t2 > 0 && t2 < kTargetTiles) {
+        const int64_t f = (kTargetTiles + t2 - 1) / t2;
+        for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+          SnMeta& m = h->meta[h->level_sn[t]];
+          const int32_t rows = std::max<int32_t>(kMinSlice2, (int32_t)((m.r + m.ksplit * f - 1) / (m.ksplit * f)));
+          if (m.r > rows) m.ksplit = slices(m.r, rows, &m.kchunk);
+        }
+      }
+      if (t3 > 0 && t3 < kTargetTiles) {
+        const int64_t f = (kTargetTiles + t3 - 1) / t3;
+        for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+          SnMeta& m = h->meta[h->level_sn[t]];
+          if (m.r == 0) continue;
+          const int32_t rows = std::max<int32_t>(kMinChunk3, (int32_t)((m.r + m.nchunk * f - 1) / (m.nchunk * f)));
+          m.nchunk = slices(m.r, rows, &m.kchunk3);
+        }
       }
     }
   }
@@ -557,7 +589,7 @@ int build_schedule(pselinv_handle* h) {
       for (int64_t t = rg.begin; t < rg.end; ++t) h->plist.push_back({P_STEP3, (int16_t)v, (int32_t)t});
     }
     for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t)
-      h->plist.push_back({P_FINISH, 0, h->level_sn[t]});
+      for (int q = 0; q < kFinishParts; ++q) h->plist.push_back({P_FINISH, (int16_t)q, h->level_sn[t]});
   }
   h->plevel_ptr[nl] = (int64_t)h->plist.size();
   return PSELINV_OK;

@@ -26,6 +26,8 @@ struct SnMeta {
   int32_t ksplit;  // step-2 partial products (1 = written directly)
   int32_t kchunk;  // rows of C per step-2 partial product
   int64_t ypart;   // level-local offset of the step-2 partial products (ksplit * r * s)
+  int32_t kchunk3; // rows of C per step-3 partial product (nchunk = ceil(r / kchunk3))
+  int32_t pad_;
 };
 
 // Where column k of X_{C,C} (k-th row of C) lives: element offset of that
@@ -54,6 +56,7 @@ struct PTask {
   int32_t idx;   // index into the step-2 / step-3 task array, or the supernode
 };
 constexpr int kReduceGroups = 8;  // column groups of one slice reduction
+constexpr int kFinishParts = 8;   // CTAs (or persistent tasks) sharing one step-3 finish
 
 // Contiguous task ranges [begin, end) for a level and for a supernode.
 struct Range {
@@ -61,7 +64,10 @@ struct Range {
 };
 
 constexpr int kMaxWidth = 128;   // widest supernode the kernels accept
-constexpr int kChunkRows = 512;  // rows per step-3 partial product
+constexpr int kChunkRows = 512;  // rows per step-3 partial product (before the per-level boost)
+constexpr int kTargetTiles = 4 * 152;  // tiles a level should offer the GPU (4 per SM)
+constexpr int kMinSlice2 = 256;   // smallest step-2 slice the per-level boost makes
+constexpr int kMinChunk3 = 64;    // smallest step-3 chunk the per-level boost makes
 constexpr int kTileM = 64;       // output tile rows of the grouped GEMMs
 constexpr int kTileN = 64;       // output tile columns
 

@@ -153,7 +153,7 @@ __global__ void k_norm_diag(const SnMeta* __restrict__ meta, const T* __restrict
 
 template <class T>
 __global__ void k_diag_final(KArgs a, const int32_t* __restrict__ sns) {
-  step3_finish<T>(a, sns[blockIdx.x], blockIdx.y, false);
+  step3_finish<T>(a, sns[blockIdx.x], blockIdx.y, blockIdx.z, gridDim.z, false);
 }
 
 // Copy the factor scratch back into the panels of the level's supernodes
@@ -521,7 +521,7 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
       k_gemm1_reduce<T><<<dim3(nsn, a.sz.batch, 16), 256, 0, st>>>(a, sns);
       break;
     default:
-      k_diag_final<T><<<grid, 256, 0, st>>>(a, sns);
+      k_diag_final<T><<<dim3(nsn, a.sz.batch, kFinishParts), 256, 0, st>>>(a, sns);
       break;
   }
   return cudaGetLastError();

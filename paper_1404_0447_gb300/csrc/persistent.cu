@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_persistent_level(KArgs a, PArgs 
           target = p.n2[k] + 1;
         }
         if (ctr && !cta_wait(ctr, target, p.spin_ns, status)) break;
-        step3_finish<T>(a, k, b, true);
+        step3_finish<T>(a, k, b, pt.var, kFinishParts, true);
         break;
       }
     }

@@ -98,7 +98,7 @@ __device__ __forceinline__ void step2_reduce(const KArgs& a, int k, int b, int c
 }
 
 // Step 3 partial product tile: P_c = Lhat_{rows c, K}^T X_{rows c, K} over a
-// chunk of kChunkRows rows of C (plain transpose; s x s output tiles).
+// chunk of kchunk3 rows of C (plain transpose; s x s output tiles).
 template <class T, int BN>
 __device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b, TileSmem<T, BN>& sm, bool cg) {
   const Sizes& sz = a.sz;
@@ -116,7 +116,7 @@ __device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b
     const int col = tk.n0 + nn;
     return col < s ? ld_maybe_cg(Y + kk + (int64_t)col * ld, cg) : Sc<T>::zero();
   };
-  const int kb = tk.c * kChunkRows, ke = min(r, kb + kChunkRows);
+  const int kb = tk.c * m.kchunk3, ke = min(r, kb + m.kchunk3);
   tile_mma<T, BN>(sm, kb, ke, [](int) { return true; }, la, lb, acc);
   T* out = (T*)a.part + b * sz.part + m.part + (int64_t)tk.c * s * s;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
@@ -129,13 +129,14 @@ __device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b
 // symmetrisation at the end of Section 2.1 / Algorithm 3).  One thread per
 // unordered pair {i, j} reads and writes exactly (i, j) and (j, i).
 template <class T>
-__device__ __forceinline__ void step3_finish(const KArgs& a, int k, int b, bool cg) {
+__device__ __forceinline__ void step3_finish(const KArgs& a, int k, int b, int part, int nparts, bool cg) {
   const Sizes& sz = a.sz;
   const SnMeta m = a.meta[k];
   const int s = m.s, ld = m.s + m.r;
   T* XK = (T*)a.X + b * sz.panel + m.panel;
   const T* pp = (const T*)a.part + b * sz.part + m.part;
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+  // the CTAs part = 0..nparts-1 share the pairs of one supernode
+  for (int e = threadIdx.x + part * blockDim.x; e < s * s; e += nparts * blockDim.x) {
     const int i = e % s, j = e / s;
     if (i < j) continue;
     T zij = XK[i + (int64_t)j * ld], zji = XK[j + (int64_t)i * ld];
