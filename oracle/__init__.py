@@ -80,6 +80,12 @@ def lib():
             f.argtypes = [ctypes.c_int32, i64p, i32p, vp, vp, vp, vp]
             f = getattr(L, f"orc_solve_{sfx}")
             f.argtypes = [ctypes.c_int32, i64p, i32p, vp, vp, vp]
+            f = getattr(L, f"orc_ldu_{sfx}")
+            f.argtypes = [ctypes.c_int32, i64p, i32p, vp, vp, i64p, i32p, vp, vp, vp]
+            f = getattr(L, f"orc_selinv_lu_{sfx}")
+            f.argtypes = [ctypes.c_int32, i64p, i32p, vp, vp, vp, vp, vp, vp]
+            f = getattr(L, f"orc_solve_lu_{sfx}")
+            f.argtypes = [ctypes.c_int32, i64p, i32p, vp, vp, vp, vp]
         L.orc_logdet_d.argtypes = [ctypes.c_int32, f64p, f64p]
         L.orc_logdet_z.argtypes = [ctypes.c_int32, c128p, f64p]
         _lib = L
@@ -252,6 +258,50 @@ def solve(n, lcolptr, lrowind, lvals, d, b):
     return x
 
 
+def ldu(n, colptr, rowind, lower, upper, lcolptr, lrowind):
+    """Pivot-free A = L D U' (non-symmetric values on a symmetric pattern).
+    Returns (lv, uv, d): L_ij and U'_ji at the L positions (i, j), and D."""
+    cz = _cplx(lower) or _cplx(upper)
+    dt = np.complex128 if cz else np.float64
+    lv = np.zeros(len(lrowind), dt)
+    uv = np.zeros(len(lrowind), dt)
+    d = np.zeros(n, dt)
+    f = lib().orc_ldu_z if cz else lib().orc_ldu_d
+    st = f(n, _i64(colptr), _i32(rowind), np.ascontiguousarray(lower, dt), np.ascontiguousarray(upper, dt),
+           _i64(lcolptr), _i32(lrowind), lv, uv, d)
+    if st == -(n + 1):
+        raise ValueError("A has entries outside the given L pattern")
+    if st < 0:
+        raise ZeroDivisionError(f"zero or non-finite pivot at column {-st - 1}")
+    return lv, uv, d
+
+
+def selinv_lu(n, lcolptr, lrowind, lv, uv, d):
+    """Non-symmetric column selected inversion: X_ij (xv) and X_ji (xu) at
+    the L positions (i, j), and the diagonal xd."""
+    cz = _cplx(lv) or _cplx(uv)
+    dt = np.complex128 if cz else np.float64
+    xv = np.zeros(len(lrowind), dt)
+    xu = np.zeros(len(lrowind), dt)
+    xd = np.zeros(n, dt)
+    f = lib().orc_selinv_lu_z if cz else lib().orc_selinv_lu_d
+    st = f(n, _i64(lcolptr), _i32(lrowind), np.ascontiguousarray(lv, dt), np.ascontiguousarray(uv, dt),
+           np.ascontiguousarray(d, dt), xv, xu, xd)
+    if st < 0:
+        raise ValueError(f"pattern not elimination-closed at column {-st - 1}")
+    return xv, xu, xd
+
+
+def solve_lu(n, lcolptr, lrowind, lv, uv, d, b):
+    cz = _cplx(lv) or _cplx(b)
+    dt = np.complex128 if cz else np.float64
+    x = np.array(b, dtype=dt, copy=True, order="C")
+    f = lib().orc_solve_lu_z if cz else lib().orc_solve_lu_d
+    f(n, _i64(lcolptr), _i32(lrowind), np.ascontiguousarray(lv, dt), np.ascontiguousarray(uv, dt),
+      np.ascontiguousarray(d, dt), x)
+    return x
+
+
 def logdet(d):
     """Real: (sum log|d_j|, number of negative pivots).  Complex: sum of
     principal logs as (real, imaginary) -- not wrapped to (-pi, pi]."""
@@ -286,28 +336,60 @@ def selected_inverse(n, colptr, rowind, values, wmax=0, relax=0, pattern="supern
     return sym, lv, d, xv, xd, lcp, lri
 
 
+def selected_inverse_lu(n, colptr, rowind, lower, upper, wmax=0, relax=0, pattern="supernodal"):
+    """Non-symmetric counterpart of ``selected_inverse``: returns
+    (sym, lv, uv, d, xv, xu, xd, lcp, lri)."""
+    sym = analyse(n, colptr, rowind, wmax, relax)
+    cp, ri = sym["colptr"], sym["rowind"]
+    lo, up = lower, upper
+    if not np.array_equal(sym["post"], np.arange(n)):
+        from synth import permute_lower_unsym
+        _, _, lo, up, _, _ = permute_lower_unsym(n, colptr, rowind, lower, upper, sym["post"])
+    if pattern == "supernodal":
+        lcp, lri = supernodal_pattern(n, sym["sn_start"], sym["rcount"], sym["rrows"])
+    else:
+        lcp, lri = sym["lcolptr"], sym["lrowind"]
+    lv, uv, d = ldu(n, cp, ri, lo, up, lcp, lri)
+    xv, xu, xd = selinv_lu(n, lcp, lri, lv, uv, d)
+    return sym, lv, uv, d, xv, xu, xd, lcp, lri
+
+
+def panels_from_columns_lu(n, sn_start, rcount, rrows, lcp, xv, xu, xd):
+    """Panels of a non-symmetric X: (offsets, XL, XU) where XL holds X_ij at
+    panel position (i, j) (full diagonal block) and XU holds X_ji there."""
+    off, XL = _panels(n, sn_start, rcount, lcp, xv, xu, xd)
+    _, XU = _panels(n, sn_start, rcount, lcp, xu, xv, xd)
+    return off, XL, XU
+
+
 def panels_from_columns(n, sn_start, rcount, rrows, lcp, xv, xd):
     """Lay a column-form X on the supernodal pattern out as the panels the
     GPU library stores: per supernode K an (s+r) x s column-major block whose
     rows are cols(K) then R(K); the diagonal block is filled on both sides of
     the diagonal (X is symmetric).  Returns (panel offsets int64[nsn+1],
     flat values)."""
+    return _panels(n, sn_start, rcount, lcp, xv, xv, xd)
+
+
+def _panels(n, sn_start, rcount, lcp, below, above, xd):
+    """Panel layout of column-form values: column j of K holds ``below``
+    (struct(j) rows: j+1..last(K), then R(K)) under the diagonal; the
+    diagonal block's part above the diagonal takes ``above`` mirrored."""
     nsn = len(sn_start) - 1
     s = np.diff(sn_start).astype(np.int64)
     r = np.asarray(rcount, np.int64)
     sizes = (s + r) * s
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    out = np.zeros(int(off[-1]), dtype=xv.dtype)
+    out = np.zeros(int(off[-1]), dtype=np.result_type(below, above, xd))
     for k in range(nsn):
         f, sk, rk = int(sn_start[k]), int(s[k]), int(r[k])
         ld = sk + rk
-        P = np.zeros((sk, ld), dtype=xv.dtype)         # P[col, row]: column-major panel
+        P = np.zeros((sk, ld), dtype=out.dtype)        # P[col, row]: column-major panel
         for b in range(sk):
             j = f + b
             P[b, b] = xd[j]
-            col = xv[lcp[j]:lcp[j + 1]]                  # rows j+1..last(K), then R(K)
-            P[b, b + 1:] = col
-            P[b + 1:sk, b] = col[:sk - b - 1]            # mirror inside the diagonal block
+            P[b, b + 1:] = below[lcp[j]:lcp[j + 1]]
+            P[b + 1:sk, b] = above[lcp[j]:lcp[j] + sk - b - 1]   # (row b, col b+c) = mirror
         out[off[k]:off[k + 1]] = P.ravel()
     return off, out
 
@@ -323,6 +405,60 @@ def dense_from_lower(n, colptr, rowind, values):
     A[rowind, cols] = values
     A[cols, rowind] = values
     return A
+
+
+def dense_from_lower_lu(n, colptr, rowind, lower, upper):
+    """Dense A from A_ij (``lower``) and A_ji (``upper``) on a lower pattern."""
+    dt = np.complex128 if (_cplx(lower) or _cplx(upper)) else np.float64
+    A = np.zeros((n, n), dt)
+    cols = np.repeat(np.arange(n), np.diff(colptr))
+    A[cols, rowind] = upper
+    A[rowind, cols] = lower          # the diagonal takes ``lower``
+    return A
+
+
+def convdiff_inverse_entries(dims, beta, shift, pairs):
+    """Entries of A^{-1} for the constant-coefficient upwind
+    convection-diffusion operator A = sum_a (I x .. x T_a x .. x I) + shift I
+    with T_a = tridiag(-(1 + b_a), 2, -(1 - b_a)) of order m_a, |b_a| < 1.
+
+    With rho_a = sqrt((1 + b_a) / (1 - b_a)) and S = diag(rho^{p_a}) per
+    axis, S^{-1} T_a S = tridiag(-t_a, 2, -t_a), t_a = sqrt(1 - b_a^2), whose
+    eigenpairs are 2 - 2 t_a cos(k pi/(m+1)) and sine vectors.  Hence
+
+      (A^{-1})_pq = prod_a rho_a^(p_a - q_a) *
+        sum_k prod_a (2/(m_a+1)) sin(k_a p_a pi/(m_a+1)) sin(k_a q_a pi/(m_a+1))
+              / (shift + sum_a (2 - 2 t_a cos(k_a pi/(m_a+1)))),
+
+    the mode sum added with math.fsum; p, q natural indices (x fastest).
+    """
+    dims = [int(m) for m in dims]
+    beta = [float(b) for b in beta][:len(dims)]
+    ks = [np.arange(1, m + 1) for m in dims]
+    tau = [math.sqrt(1.0 - b * b) for b in beta]
+    rho = [math.sqrt((1.0 + b) / (1.0 - b)) for b in beta]
+    lam = [2.0 - 2.0 * t * np.cos(k * np.pi / (m + 1)) for k, m, t in zip(ks, dims, tau)]
+    grids = np.meshgrid(*lam[::-1], indexing="ij")
+    denom = shift + sum(grids)
+    out = np.empty(len(pairs))
+    for t, (p, q) in enumerate(pairs):
+        pc, qc = [], []
+        pp, qq = int(p), int(q)
+        for m in dims:
+            pc.append(pp % m + 1); pp //= m
+            qc.append(qq % m + 1); qq //= m
+        fac = []
+        for a, m in enumerate(dims):
+            fac.append((2.0 / (m + 1)) * np.sin(ks[a] * pc[a] * np.pi / (m + 1))
+                       * np.sin(ks[a] * qc[a] * np.pi / (m + 1)))
+        num = fac[-1]
+        for a in range(len(dims) - 2, -1, -1):
+            num = np.multiply.outer(num, fac[a])
+        scale = 1.0
+        for a in range(len(dims)):
+            scale *= rho[a] ** (pc[a] - qc[a])
+        out[t] = scale * math.fsum((num / denom).ravel())
+    return out
 
 
 def dense_inverse(n, colptr, rowind, values):

@@ -130,3 +130,144 @@ int ORC_SFX(orc_solve)(int32_t n, const int64_t* lcp, const int32_t* lri, const 
   }
   return 0;
 }
+
+/*
+ * Non-symmetric A with a symmetric pattern: left-looking pivot-free
+ * A = L D U' with L unit lower, U' unit upper and D diagonal -- the LU
+ * factorisation Algorithm 1 takes as input, with U = D U' (so the pivots
+ * of U are D and U_KK^{-1} L_KK^{-1} = U'_KK^{-1} D_K^{-1} L_KK^{-1}).
+ * Input: av = A_ij and au = A_ji at every stored lower position (i, j),
+ * i >= j, of the same CSC pattern (au's diagonal entries are not read).
+ * Output on the L pattern: lv = L_ij and uv = U'_ji (the upper factor held
+ * transposed, at the position of L_ij), plus d.
+ *
+ *   for j = 0..n-1:
+ *     w(i) = A_ij, v(i) = A_ji                        (i in {j} U struct(j))
+ *     for every k < j with j in struct(k):
+ *       w(i) -= L_ik d_k U'_kj,  v(i) -= L_jk d_k U'_ki  (i in {j} U struct(k), i >= j)
+ *     d_j = w(j);  L_ij = w(i) / d_j;  U'_ji = v(i) / d_j   (i in struct(j))
+ *
+ * Returns 0, -(j+1) for a zero or non-finite pivot, -(n+1) for an entry
+ * outside the pattern.
+ */
+int ORC_SFX(orc_ldu)(int32_t n, const int64_t* cp, const int32_t* ri, const ORC_T* av, const ORC_T* au,
+                     const int64_t* lcp, const int32_t* lri, ORC_T* lv, ORC_T* uv, ORC_T* d) {
+  int64_t nnzl = lcp[n];
+  int64_t* rp = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  for (int64_t p = 0; p < nnzl; ++p) rp[lri[p] + 1]++;
+  for (int32_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+  int32_t* rk = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnzl > 0 ? nnzl : 1));
+  int64_t* rpos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnzl > 0 ? nnzl : 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int32_t i = 0; i < n; ++i) fill[i] = rp[i];
+  for (int32_t k = 0; k < n; ++k)
+    for (int64_t p = lcp[k]; p < lcp[k + 1]; ++p) {
+      rk[fill[lri[p]]] = k;
+      rpos[fill[lri[p]]++] = p;
+    }
+  ORC_T* w = (ORC_T*)calloc((size_t)(n > 0 ? n : 1), sizeof(ORC_T));
+  ORC_T* v = (ORC_T*)calloc((size_t)(n > 0 ? n : 1), sizeof(ORC_T));
+  char* in = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  int status = 0;
+  for (int32_t j = 0; j < n && status == 0; ++j) {
+    in[j] = 1;
+    for (int64_t p = lcp[j]; p < lcp[j + 1]; ++p) in[lri[p]] = 1;
+    for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
+      if (!in[ri[p]]) { status = -(n + 1); break; }
+      w[ri[p]] = av[p];
+      if (ri[p] != j) v[ri[p]] = au[p];
+    }
+    if (status) break;
+    for (int64_t q = rp[j]; q < rp[j + 1]; ++q) {
+      int32_t k = rk[q];
+      int64_t pj = rpos[q];                   /* position of (j, k) in column k */
+      ORC_T fl = uv[pj] * d[k];               /* d_k U'_kj */
+      ORC_T fu = lv[pj] * d[k];               /* L_jk d_k */
+      w[j] -= lv[pj] * fl;                    /* i = j: L_jk d_k U'_kj */
+      for (int64_t p = pj + 1; p < lcp[k + 1]; ++p) {
+        w[lri[p]] -= lv[p] * fl;
+        v[lri[p]] -= uv[p] * fu;
+      }
+    }
+    d[j] = w[j];
+    w[j] = 0;
+    in[j] = 0;
+    if (ORC_ISBAD(d[j])) status = -(j + 1);
+    for (int64_t p = lcp[j]; p < lcp[j + 1]; ++p) {
+      lv[p] = w[lri[p]] / d[j];
+      uv[p] = v[lri[p]] / d[j];
+      w[lri[p]] = 0;
+      v[lri[p]] = 0;
+      in[lri[p]] = 0;
+    }
+  }
+  free(rp); free(rk); free(rpos); free(fill); free(w); free(v); free(in);
+  return status;
+}
+
+/*
+ * Non-symmetric selected inversion, column form of Algorithm 1 (one-column
+ * supernodes: Lhat = L and Uhat = U' because L_jj = U'_jj = 1, and
+ * U_jj^{-1} L_jj^{-1} = 1/d_j).  For j = n-1 down to 0 with C = struct(j):
+ *
+ *   X_ij = - sum_{k in C} X_ik L_kj            (i in C)    step 2
+ *   X_jj = 1/d_j - sum_{k in C} U'_jk X_kj                 step 3
+ *   X_ji = - sum_{k in C} U'_jk X_ki           (i in C)    step 4
+ *
+ * X is held as xv (X_ij at the L position (i, j), i > j), xu (X_ji at the
+ * same position) and xd.  For a, b in C with a > b, X_ab is xv and X_ba is
+ * xu at the position of a in struct(b), found by the same merge walk as the
+ * symmetric form.  Returns 0, or -(j+1) if the walk for column j fails.
+ */
+int ORC_SFX(orc_selinv_lu)(int32_t n, const int64_t* lcp, const int32_t* lri, const ORC_T* lv, const ORC_T* uv,
+                           const ORC_T* d, ORC_T* xv, ORC_T* xu, ORC_T* xd) {
+  ORC_T* y = (ORC_T*)calloc((size_t)(n > 0 ? n : 1), sizeof(ORC_T));   /* sum_k X_{C[a],k} L_kj */
+  ORC_T* z = (ORC_T*)calloc((size_t)(n > 0 ? n : 1), sizeof(ORC_T));   /* sum_k U'_jk X_{k,C[a]} */
+  int status = 0;
+  for (int32_t j = n - 1; j >= 0 && status == 0; --j) {
+    int64_t p0 = lcp[j], r = lcp[j + 1] - lcp[j];
+    const int32_t* C = lri + p0;
+    const ORC_T* Lj = lv + p0;                /* L_{C[a], j} */
+    const ORC_T* Uj = uv + p0;                /* U'_{j, C[a]} */
+    for (int64_t a = 0; a < r; ++a) y[a] = z[a] = 0;
+    for (int64_t b = 0; b < r && status == 0; ++b) {
+      int32_t k = C[b];
+      y[b] += xd[k] * Lj[b];                  /* X_kk L_kj */
+      z[b] += Uj[b] * xd[k];                  /* U'_jk X_kk */
+      int64_t q = lcp[k], qend = lcp[k + 1];
+      for (int64_t a = b + 1; a < r; ++a) {   /* C[a] > k */
+        while (q < qend && lri[q] != C[a]) ++q;
+        if (q == qend) { status = -(j + 1); break; }
+        ORC_T xlo = xv[q];                    /* X_{C[a], k} */
+        ORC_T xup = xu[q];                    /* X_{k, C[a]} */
+        y[a] += xlo * Lj[b];
+        y[b] += xup * Lj[a];
+        z[a] += Uj[b] * xup;
+        z[b] += Uj[a] * xlo;
+      }
+    }
+    ORC_T acc = 0;
+    for (int64_t a = 0; a < r; ++a) {
+      xv[p0 + a] = -y[a];
+      xu[p0 + a] = -z[a];
+      acc += Uj[a] * xv[p0 + a];
+    }
+    xd[j] = 1.0 / d[j] - acc;
+  }
+  free(y); free(z);
+  return status;
+}
+
+/* Solve A x = b with A = L D U' (in place): L w = b, w /= d, U' x = w. */
+int ORC_SFX(orc_solve_lu)(int32_t n, const int64_t* lcp, const int32_t* lri, const ORC_T* lv, const ORC_T* uv,
+                          const ORC_T* d, ORC_T* b) {
+  for (int32_t j = 0; j < n; ++j)
+    for (int64_t p = lcp[j]; p < lcp[j + 1]; ++p) b[lri[p]] -= lv[p] * b[j];
+  for (int32_t j = 0; j < n; ++j) b[j] /= d[j];
+  for (int32_t j = n - 1; j >= 0; --j) {
+    ORC_T acc = b[j];
+    for (int64_t p = lcp[j]; p < lcp[j + 1]; ++p) acc -= uv[p] * b[lri[p]];
+    b[j] = acc;
+  }
+  return 0;
+}

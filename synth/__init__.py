@@ -78,6 +78,33 @@ def permute_lower(n, colptr, rowind, values, perm):
     return newcolptr, lo[order].astype(np.int32), np.ascontiguousarray(newvals), order
 
 
+def permute_lower_unsym(n, colptr, rowind, lower, upper, perm):
+    """``permute_lower`` for a non-symmetric matrix with a symmetric pattern,
+    held as ``lower`` (A_ij) and ``upper`` (A_ji) at the stored lower
+    positions (i, j), i >= j.  An entry whose two indices swap order under
+    the permutation lands transposed, so its two values trade places.
+    Returns (colptr, rowind, lower, upper, src, flip) with ``flip[q]`` true
+    where output position ``q`` was transposed."""
+    perm = np.asarray(perm, dtype=np.int64)
+    inv = np.empty(n, dtype=np.int64)
+    inv[perm] = np.arange(n, dtype=np.int64)
+    cols = np.repeat(np.arange(n, dtype=np.int64), np.diff(colptr))
+    flip_in = inv[np.asarray(rowind, dtype=np.int64)] < inv[cols]
+    cp, ri, _, src = permute_lower(n, colptr, rowind, np.zeros(len(rowind)), perm)
+    flip = flip_in[src]
+    lo, up = np.asarray(lower), np.asarray(upper)
+    new_lo = np.where(flip, up[..., src], lo[..., src])
+    new_up = np.where(flip, lo[..., src], up[..., src])
+    return cp, ri, np.ascontiguousarray(new_lo), np.ascontiguousarray(new_up), src, flip
+
+
+def to_scipy_full_unsym(n, colptr, rowind, lower, upper):
+    """Full scipy CSC matrix from the lower/upper value pair on a lower pattern."""
+    lo = sp.csc_matrix((lower, rowind, colptr), shape=(n, n))
+    up = sp.csc_matrix((upper, rowind, colptr), shape=(n, n))
+    return (lo + up.T - sp.diags(up.diagonal())).tocsc()
+
+
 def to_scipy_full(n, colptr, rowind, values):
     """Full symmetric scipy CSC matrix from the lower CSC (plain transpose)."""
     lower = sp.csc_matrix((values, rowind, colptr), shape=(n, n))
@@ -186,6 +213,51 @@ def grid_laplacian(dims, shift_lo, shift_hi, seed, shift_const=None):
     vals = np.concatenate([2.0 * d + s, -np.ones(ei.size)])
     colptr, rowind, values = lower_csc_from_coo(n, rows, cols, vals)
     return n, colptr, rowind, values
+
+
+def convdiff_grid(dims, seed, beta=0.5, shift_lo=0.01, shift_hi=0.1, beta_const=None, shift_const=None):
+    """Upwind convection-diffusion on a Dirichlet box grid: a non-symmetric
+    matrix with the symmetric 2D/3D nearest-neighbour pattern.
+
+    Along an edge (i, j), i < j, the lower entry is A_ji = -(1 + b_e) and the
+    upper entry A_ij = -(1 - b_e).  Random form: b_e ~ U(-beta, beta) drawn
+    per edge in ``grid_edges`` order, then s_i ~ U(shift_lo, shift_hi) per
+    node; the diagonal is sum over the node's edges of (1 + |b_e|) plus s_i,
+    so A is strictly diagonally dominant by rows and by columns (no pivoting
+    needed).  Constant form (``beta_const`` = one b per axis, x y z, and
+    ``shift_const``): b_e = b_axis and the diagonal is 2 d + shift_const,
+    a Kronecker sum of Toeplitz tridiagonals with a closed-form inverse.
+    Returns (n, colptr, rowind, lower, upper) in natural order.
+    """
+    dims = tuple(int(m) for m in dims)
+    d = sum(1 for m in dims if m > 1)
+    n = int(np.prod(dims))
+    ei, ej = grid_edges(dims)
+    if beta_const is None:
+        g = rng_for(seed)
+        b = g.uniform(-beta, beta, size=ei.size)
+        s = g.uniform(shift_lo, shift_hi, size=n)
+        diag = s.copy()
+        np.add.at(diag, ei, 1.0 + np.abs(b))
+        np.add.at(diag, ej, 1.0 + np.abs(b))
+    else:
+        bc = np.asarray(beta_const, dtype=np.float64)
+        b = bc[_edge_axes(dims, ei, ej)]
+        diag = np.full(n, 2.0 * d + float(shift_const if shift_const is not None else 0.0))
+    rows = np.concatenate([np.arange(n), ej])
+    cols = np.concatenate([np.arange(n), ei])
+    colptr, rowind, lower = lower_csc_from_coo(n, rows, cols, np.concatenate([diag, -(1.0 + b)]))
+    _, _, upper = lower_csc_from_coo(n, rows, cols, np.concatenate([diag, -(1.0 - b)]))
+    return n, colptr, rowind, lower, upper
+
+
+def _edge_axes(dims, ei, ej):
+    """Axis (0 = x, 1 = y, 2 = z) of every grid edge."""
+    dd = tuple(int(m) for m in dims) + (1,) * (3 - len(dims))
+    mx, my, _ = dd
+    xi, yi, zi = ei % mx, (ei // mx) % my, ei // (mx * my)
+    xj, yj, zj = ej % mx, (ej // mx) % my, ej // (mx * my)
+    return np.where(xi != xj, 0, np.where(yi != yj, 1, 2)).astype(np.int64)
 
 
 def laplacian_1d(n):
@@ -381,3 +453,32 @@ def config3(elems=(12, 12, 12), nb=48, npoles=16):
 def config4_member(spec):
     dims, seed = spec
     return grid_problem(dims, 0.1, 1.0, seed, None, f"grid{'x'.join(map(str, dims))}")
+
+
+class UnsymProblem:
+    """One non-symmetric matrix with a symmetric pattern, in ND order:
+    ``values`` holds A_ij and ``values_up`` A_ji at the stored lower
+    positions; ``flip`` marks entries the ordering transposed."""
+
+    def __init__(self, name, n, colptr, rowind, lower, upper, perm, dims=None, extra=None):
+        self.name = name
+        self.n = n
+        self.perm = perm
+        (self.colptr, self.rowind, self.values, self.values_up, self.src,
+         self.flip) = permute_lower_unsym(n, colptr, rowind, lower, upper, perm)
+        self.dims = dims
+        self.extra = extra or {}
+
+    @property
+    def nnz(self):
+        return int(self.rowind.size)
+
+
+def convdiff_problem(side=80, beta_const=None, shift_const=None, dims=None):
+    """Upwind convection-diffusion on a side^3 grid (or ``dims``), random
+    per-edge convection b_e ~ U(-0.5, 0.5) unless ``beta_const`` is given;
+    same ND ordering as the symmetric grid workloads."""
+    dims = tuple(dims) if dims is not None else (side, side, side)
+    n, cp, ri, lo, up = convdiff_grid(dims, BASE_SEED + 5, beta_const=beta_const, shift_const=shift_const)
+    return UnsymProblem(f"convdiff{'x'.join(map(str, dims))}", n, cp, ri, lo, up, nd_order(dims),
+                        dims=dims, extra={"beta_const": beta_const, "shift_const": shift_const})
