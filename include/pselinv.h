@@ -211,9 +211,11 @@ int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream);
 /*
  * Copy panels to caller memory: which = 0 for X (after selinv), 1 for L
  * (after factor; unit diagonal not stored, D on the diagonal positions).
- * d_out: device, batch x panel_entries elements of the dtype.
+ * out: batch x panel_entries elements of the dtype, in device memory or in
+ * host memory the CUDA runtime can address (pinned host memory gives an
+ * asynchronous copy on `stream`; pageable host memory a synchronous one).
  */
-int pselinv_get_panels(pselinv_handle* h, int32_t which, void* d_out, void* stream);
+int pselinv_get_panels(pselinv_handle* h, int32_t which, void* out, void* stream);
 
 /*
  * Synchronise `stream` and report device-side failures of earlier enqueued

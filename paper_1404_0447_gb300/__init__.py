@@ -237,9 +237,13 @@ class SelInv:
     def set_debug(self, flags):
         self._check(self._lib.pselinv_set_debug(self._h, int(flags)))
 
-    def panels(self, which=0, stream=None):
+    def panels(self, which=0, out=None, stream=None):
+        """X (which=0) or L (which=1) panels as a [batch, panel_entries] tensor;
+        ``out`` may be a CUDA tensor or a (pinned) CPU tensor."""
         import torch
-        out = torch.empty(self.opts.batch * self.info["panel_entries"], dtype=self.torch_dtype, device="cuda")
+        if out is None:
+            out = torch.empty(self.opts.batch * self.info["panel_entries"], dtype=self.torch_dtype, device="cuda")
+        assert out.numel() == self.opts.batch * self.info["panel_entries"] and out.dtype == self.torch_dtype
         self._check(self._lib.pselinv_get_panels(self._h, int(which), ctypes.c_void_p(out.data_ptr()),
                                                  _stream_ptr(stream)))
         return out.view(self.opts.batch, -1)

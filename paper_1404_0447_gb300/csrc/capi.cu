@@ -548,13 +548,13 @@ int pselinv_set_debug(pselinv_handle* h, int32_t flags) {
 }
 
 int pselinv_get_panels(pselinv_handle* h, int32_t which, void* d_out, void* stream) {
+  // d_out may be device or host memory: cudaMemcpyDefault resolves it (UVA)
   if (!h || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
   if (which != 0 && which != 1) return set_err(h, PSELINV_ERR_ARG, "which must be 0 (X) or 1 (L)");
   if (which == 0 && !h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
   if (which == 1 && !h->factored) return set_err(h, PSELINV_ERR_STATE, "no factor yet");
   const size_t bytes = elem_size(h) * (size_t)h->opts.batch * (size_t)h->panel_total;
-  PSI_CUDA(h, cudaMemcpyAsync(d_out, which == 0 ? h->d_X : h->d_L, bytes, cudaMemcpyDeviceToDevice,
-                              (cudaStream_t)stream));
+  PSI_CUDA(h, cudaMemcpyAsync(d_out, which == 0 ? h->d_X : h->d_L, bytes, cudaMemcpyDefault, (cudaStream_t)stream));
   return PSELINV_OK;
 }
 

@@ -221,6 +221,18 @@ def test_logdet_and_selected_entries(P):
     assert abs(ld[0] - want) <= 1e-12 * abs(want) and ld[1] == 0
 
 
+def test_panels_into_pinned_host_memory(P):
+    import torch
+    p = synth.config0()
+    h = P.SelInv(p.n, p.colptr, p.rowind)
+    h.factor(torch_vals(p.values))
+    h.selinv(P.LEVEL)
+    host = torch.empty(h.info["panel_entries"], dtype=torch.float64).pin_memory()
+    h.panels(0, out=host)
+    torch.cuda.synchronize()
+    assert torch.equal(host, h.panels(0)[0].cpu())
+
+
 def test_runs_are_bitwise_deterministic(P):
     import torch
     p = synth.config1(side=20)
