@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="grid3d_80",
-                    choices=["grid3d_80", "grid2d_31", "graphlap48", "dg_poles", "uneven48"],
+                    choices=["grid3d_80", "grid2d_31", "graphlap48", "dg_poles", "uneven48", "convdiff80"],
                     help="grid3d_80 is the headline; the others measure the remaining workload families")
     ap.add_argument("--poles", type=int, default=16, help="dg_poles: number of poles in the batch")
     ap.add_argument("--split-k-rows", type=int, default=None, help="override the library default")
@@ -391,6 +391,13 @@ def run_workload(args):
         vals = torch.tensor(synth.shifted_values(n, cp, ri, hv, z), dtype=torch.complex128, device=dev)
         cplx = True
         line["poles"] = len(z)
+    elif w == "convdiff80":
+        # non-symmetric: 80^3 upwind convection-diffusion, A = L D U', Algorithm 1 with step 4
+        p = synth.convdiff_problem(80)
+        h = P.SelInv(p.n, p.colptr, p.rowind, unsym=1, **tuning(args))
+        vals = torch.tensor(p.values, dtype=torch.float64, device=dev)
+        vals_up = torch.tensor(p.values_up, dtype=torch.float64, device=dev)
+        cplx = False
     else:
         mem = [synth.config4_member(s) for s in synth.uneven_batch_specs()]
         h = P.SelInv([m.n for m in mem], [m.colptr for m in mem], [m.rowind for m in mem], **tuning(args))
@@ -400,13 +407,17 @@ def run_workload(args):
     flops = info["flops_selinv"] * info["batch"] * (4 if cplx else 1)
     line.update({k: info[k] for k in ("n", "nnz_l", "nsn", "nlevels", "batch")})
     line["flops_per_selinv"] = flops
-    t0 = time.perf_counter()
+    unsym = w == "convdiff80"
+    factor = ((lambda: h.factor_unsym(vals, vals_up, stream=st)) if unsym
+              else (lambda: h.factor(vals.view(-1), stream=st)))
     with torch.cuda.stream(st):
-        h.factor(vals.view(-1), stream=st)
-    line["factor_ms"] = 1e3 * (time.perf_counter() - t0)
+        factor()
+        line["factor_ms"] = _time(factor, 1, 0, st)
     for name, mode in (("level", P.LEVEL), ("graph", P.GRAPH), ("persistent", P.PERSISTENT), ("plain", P.PLAIN)):
         if w == "dg_poles" and args.poles > 4 and name != "level":
             continue  # ~150 s per selinv at 16 poles: the level schedule only
+        if unsym and mode == P.PERSISTENT:
+            continue  # the persistent schedule is for symmetric handles
         ms = _time(lambda: h.selinv(mode, stream=st), args.steps if name != "plain" else 1,
                    args.warmup if name != "plain" else 1, st)
         line[f"{name}_ms"] = ms
@@ -421,6 +432,16 @@ def run_workload(args):
         line["pole_sum_ms"] = _time(lambda: h.pole_sum(wts, out=gam, stream=st), 3, 1, st)
         line["pole_sum_GBps"] = (info["batch"] + 1) * info["panel_entries"] * 16 / (line["pole_sum_ms"] * 1e-3) / 1e9
         line["trace_E_per_pole"] = [float(e) for e in h.trace_error(vals.view(-1), stream=st)]
+    if unsym:
+        # kernel classes of one level-schedule selinv: steps 2 and 4 are class 1
+        h.set_timing(True)
+        h.selinv(P.LEVEL, stream=st)
+        kms, kl = h.get_timing()
+        h.set_timing(False)
+        line["kernel_ms"] = {"normalise": kms[0], "step2_step4": kms[1], "step3_partials": kms[2],
+                             "step3_finish": kms[3]}
+        line["step2_step4_tflops"] = info["flops_gemm1"] / (kms[1] * 1e-3) / 1e12
+        line["step2_step4_frac_of_fp64_peak"] = line["step2_step4_tflops"] / FP64_PEAK_TFLOPS
     if w == "graphlap48":
         # differentiable logdet: forward = factor + logdet, backward = selinv + gradient gather
         g = torch.empty(info["nnz_a"], dtype=torch.float64, device=dev)

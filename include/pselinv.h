@@ -19,6 +19,19 @@
  * supernodes taken level by level in the priority order of Algorithm 2.
  * Complex matrices are complex symmetric: all transposes are plain.
  *
+ * Non-symmetric matrices with a symmetric pattern (opts.unsym = 1) use
+ * Algorithm 1 in its general form on the pivot-free A = L D U' (L unit
+ * lower, U' unit upper, U = D U'):
+ *
+ *   step 1  Lhat_{C,K} = L_{C,K} (L_{K,K})^{-1},  Uhat_{K,C} = (U'_{K,K})^{-1} U'_{K,C}
+ *   step 2  X_{C,K} = - X_{C,C} Lhat_{C,K}
+ *   step 3  X_{K,K} = U'_{K,K}^{-1} D_K^{-1} L_{K,K}^{-1} - Uhat_{K,C} X_{C,K}   (no symmetrisation)
+ *   step 4  X_{K,C} = - Uhat_{K,C} X_{C,C}
+ *
+ * The upper factor and the upper triangle of X are stored transposed in
+ * panels of the lower layout ("U panels", "XU panels"): panel position
+ * (i, j), i >= j, holds U'_{j,i} and X_{j,i}.
+ *
  * Conventions for every entry point:
  *  - Status: 0 = PSELINV_OK, < 0 = error (PSELINV_ERR_*).  After an error,
  *    pselinv_last_error(handle) returns a message (and, for a bad pivot,
@@ -83,7 +96,10 @@ typedef struct {
   int32_t split_k_rows;   /* step 2 of a supernode with |C| = r is split into ceil(r / split_k_rows)
                              partial products reduced in a fixed order; <= 0 = no split */
   int32_t debug_checks;   /* nonzero: kernels bounds-check every index and report */
-  int32_t reserved;       /* must be 0 */
+  int32_t unsym;          /* 0: symmetric A = L D L^T.  1: non-symmetric A with a symmetric pattern,
+                             A = L D U' (pselinv_factor_unsym; Algorithm 1 with step 4); complex
+                             non-symmetric handles cap w_max at 112 (shared-memory budget of the
+                             diagonal-block factorisation) */
   int64_t spin_limit_ns;  /* limit for bounded device waits; <= 0 = 1e9 */
 } pselinv_opts;
 
@@ -99,8 +115,9 @@ typedef struct {
   int32_t max_width;      /* widest supernode */
   int32_t batch;
   int64_t max_r;          /* largest |C| */
-  double flops_selinv;    /* sum_K 2 r^2 s + 3 r s^2 + 2/3 s^3 (real flops per matrix; x4 for complex) */
-  double flops_gemm1;     /* sum_K 2 r^2 s */
+  double flops_selinv;    /* sum_K 2 r^2 s + 3 r s^2 + 2/3 s^3 (real flops per matrix; x4 for complex);
+                             non-symmetric: sum_K 4 r^2 s + 4 r s^2 + 4/3 s^3 */
+  double flops_gemm1;     /* sum_K 2 r^2 s (non-symmetric: 4 r^2 s, steps 2 and 4) */
   double bytes_selinv;    /* algorithmic HBM bytes of one selinv (per matrix) */
   int64_t device_bytes;   /* device memory the handle holds (after factor) */
 } pselinv_info;
@@ -198,19 +215,40 @@ int pselinv_analyze_batch(int32_t k, const int64_t* h_n, const int64_t* const* h
 int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream);
 
 /*
+ * Numeric factorisation of a non-symmetric A with a symmetric pattern
+ * (handle analysed with opts.unsym = 1): A = L D U', supernodal, level by
+ * level from the leaves, no pivoting.  Per supernode K: the diagonal block
+ * A_KK = L_KK D_K U'_KK by Gaussian elimination, L_{C,K} = A_{C,K}
+ * U'_KK^{-1} D_K^{-1}, U'_{K,C} = D_K^{-1} L_KK^{-1} A_{K,C}, and the Schur
+ * update A_{C,C} -= L_{C,K} D_K U'_{K,C} into the ancestors (both triangles).
+ *
+ * d_lower  device, batch x nnz_a: A_ij at every stored lower position (i, j),
+ *          i >= j, of the pattern given to pselinv_analyze (user order)
+ * d_upper  device, batch x nnz_a: A_ji at the same positions (the entries
+ *          at diagonal positions are not read)
+ * Errors as pselinv_factor; ERR_STATE on a symmetric handle.
+ */
+int pselinv_factor_unsym(pselinv_handle* h, const void* d_lower, const void* d_upper, void* stream);
+
+/*
  * Selected inversion (Algorithm 3's normalisation pass, then steps 2-3 of
  * Algorithm 1 for every supernode, top-down in the priority order of
  * Algorithm 2).  The result stays in the handle's X panels (same layout as
  * the L panels: per supernode an (s + r) x s column-major block, rows = the
  * supernode's columns then R(K); the s x s diagonal block is full and
- * symmetric).  mode: PSELINV_PLAIN, PSELINV_LEVEL or PSELINV_GRAPH.
+ * symmetric).  mode: PSELINV_PLAIN, PSELINV_LEVEL, PSELINV_GRAPH or
+ * PSELINV_PERSISTENT.  Non-symmetric handles: steps 2, 3 and 4 per level
+ * (the diagonal block is full and not symmetric; the upper triangle goes to
+ * the XU panels); PLAIN, LEVEL and GRAPH only (ERR_ARG for PERSISTENT).
  * Enqueues work only; no host synchronisation.  ERR_STATE before factor.
  */
 int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream);
 
 /*
  * Copy panels to caller memory: which = 0 for X (after selinv), 1 for L
- * (after factor; unit diagonal not stored, D on the diagonal positions).
+ * (after factor; unit diagonal not stored, D on the diagonal positions);
+ * non-symmetric handles also 2 for the XU panels (X_{j,i} at position
+ * (i, j)) and 3 for the U panels (U'_{j,i} at (i, j), diagonal slots unused).
  * out: batch x panel_entries elements of the dtype, in device memory or in
  * host memory the CUDA runtime can address (pinned host memory gives an
  * asynchronous copy on `stream`; pageable host memory a synchronous one).
@@ -243,12 +281,21 @@ int pselinv_set_debug(pselinv_handle* h, int32_t flags);
 int pselinv_get_selected(pselinv_handle* h, void* d_out, void* stream);
 
 /*
+ * Non-symmetric handles: the upper triangle of the selected inverse at the
+ * stored lower positions, d_out[b * nnz_a + q] = (A_b^{-1})_{j,i} for the
+ * q-th stored entry (i, j) (the diagonal repeats pselinv_get_selected's).
+ * ERR_STATE on a symmetric handle.
+ */
+int pselinv_get_selected_upper(pselinv_handle* h, void* d_out, void* stream);
+
+/*
  * Gradient of log det A with respect to the stored values of A's lower CSC
  * in the user's order: d log det A = tr(A^{-1} dA), and a stored
  * off-diagonal value stands for both A_ij and A_ji, so
  * d_out[b * nnz_a + q] = X_jj for a diagonal entry and 2 X_ij for an
  * off-diagonal one (X = A_b^{-1} from the last pselinv_selinv; plain
  * transpose for complex symmetric A).  Device pointer, batch x nnz_a.
+ * Symmetric handles only (ERR_STATE otherwise).
  */
 int pselinv_logdet_grad(pselinv_handle* h, void* d_out, void* stream);
 
@@ -258,6 +305,7 @@ int pselinv_logdet_grad(pselinv_handle* h, void* d_out, void* stream);
  * X panel layout (one panel array, dtype of the handle).  h_weights: host,
  * batch complex weights as (re, im) pairs for C128 handles, batch real
  * weights for F64 handles.  Requires selinv.  HBM-bound pass over the batch.
+ * Symmetric handles only (ERR_STATE otherwise).
  */
 int pselinv_pole_sum(pselinv_handle* h, const double* h_weights, void* d_out, void* stream);
 
@@ -266,12 +314,13 @@ int pselinv_pole_sum(pselinv_handle* h, const double* h_weights, void* d_out, vo
  * S_b = sum over the nonzeros of A_b (both triangles) of X_ij A_ji, so that
  * E_b = |1 - S_b / n|.  d_values: the batch's values of A (as passed to
  * pselinv_factor).  h_out: host, batch x 2 doubles (re, im; im = 0 for F64).
- * Requires selinv.  Synchronises the stream.
+ * Requires selinv.  Synchronises the stream.  Symmetric handles only.
  */
 int pselinv_trace_sum(pselinv_handle* h, const void* d_values, double* h_out, void* stream);
 
 /*
- * log det A = sum_j log d_j (Section 2.1's LDL^T).  h_out (host) receives
+ * log det A = sum_j log d_j (Section 2.1's LDL^T, or the pivots of
+ * A = L D U' for non-symmetric handles).  h_out (host) receives
  * per batch member two doubles: F64 -> (sum log|d_j|, number of negative
  * pivots); C128 -> (real, imaginary) of the sum of principal logs.
  * Synchronises the stream.
@@ -301,7 +350,7 @@ int pselinv_logdet(pselinv_handle* h, double* h_out, void* stream);
  * recurrence of Algorithm 1 (steps 3, 2, 1 in that order per supernode,
  * scattering into the ancestors' adjoints through the relative indices),
  * then the adjoint of the supernodal LDL^T root -> leaves.  Allocates its
- * work buffers on first use.
+ * work buffers on first use.  Symmetric handles only (ERR_STATE otherwise).
  */
 #define PSELINV_G_SYMMETRIC 0
 #define PSELINV_G_PANEL 1

@@ -23,8 +23,10 @@ RELAX_NONE, RELAX_AMALG = 0, 1
 PLAIN, LEVEL, GRAPH, PERSISTENT = 0, 1, 2, 3
 G_SYMMETRIC, G_PANEL = 0, 1
 
-EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_analyze_batch", "pselinv_factor", "pselinv_selinv",
-            "pselinv_get_panels", "pselinv_pole_sum", "pselinv_trace_sum", "pselinv_sync_status", "pselinv_set_debug", "pselinv_get_selected", "pselinv_logdet_grad", "pselinv_logdet",
+EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_analyze_batch", "pselinv_factor",
+            "pselinv_factor_unsym", "pselinv_selinv", "pselinv_get_panels", "pselinv_pole_sum", "pselinv_trace_sum",
+            "pselinv_sync_status", "pselinv_set_debug", "pselinv_get_selected", "pselinv_get_selected_upper",
+            "pselinv_logdet_grad", "pselinv_logdet",
             "pselinv_selinv_adjoint",
             "pselinv_set_timing", "pselinv_get_timing", "pselinv_autotune", "pselinv_get_info",
             "pselinv_export_symbolic",
@@ -40,7 +42,7 @@ class PselinvError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("batch", ctypes.c_int32), ("max_sn_width", ctypes.c_int32),
                 ("relax", ctypes.c_int32), ("small_cutoff", ctypes.c_int32), ("split_k_rows", ctypes.c_int32),
-                ("debug_checks", ctypes.c_int32), ("reserved", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64)]
+                ("debug_checks", ctypes.c_int32), ("unsym", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -80,6 +82,7 @@ def load_library():
     L.pselinv_analyze.argtypes = [ctypes.c_int64, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
     L.pselinv_analyze_batch.argtypes = [ctypes.c_int32, vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
     L.pselinv_factor.argtypes = [vp, vp, vp]
+    L.pselinv_factor_unsym.argtypes = [vp, vp, vp, vp]
     L.pselinv_selinv.argtypes = [vp, ctypes.c_int32, vp]
     L.pselinv_get_panels.argtypes = [vp, ctypes.c_int32, vp, vp]
     L.pselinv_sync_status.argtypes = [vp, vp]
@@ -87,6 +90,7 @@ def load_library():
     L.pselinv_trace_sum.argtypes = [vp, vp, vp, vp]
     L.pselinv_set_debug.argtypes = [vp, ctypes.c_int32]
     L.pselinv_get_selected.argtypes = [vp, vp, vp]
+    L.pselinv_get_selected_upper.argtypes = [vp, vp, vp]
     L.pselinv_logdet.argtypes = [vp, vp, vp]
     L.pselinv_logdet_grad.argtypes = [vp, vp, vp]
     L.pselinv_selinv_adjoint.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
@@ -128,7 +132,9 @@ class SelInv:
     ``SelInv(n, colptr, rowind, perm=None, **opts)`` runs pselinv_analyze on
     host numpy arrays.  ``factor(values)`` takes a CUDA tensor of
     batch x nnz values (user order), ``selinv(mode)`` enqueues the selected
-    inversion, ``panels()`` / ``selected()`` return CUDA tensors.
+    inversion, ``panels()`` / ``selected()`` return CUDA tensors.  With
+    ``unsym=1`` the matrix is non-symmetric with a symmetric pattern:
+    ``factor_unsym(lower, upper)`` and ``selected_upper()``.
     """
 
     def __init__(self, n, colptr, rowind, perm=None, **opts):
@@ -208,6 +214,15 @@ class SelInv:
         assert values.numel() == self.opts.batch * self.info["nnz_a"]
         self._check(self._lib.pselinv_factor(self._h, ctypes.c_void_p(values.data_ptr()), _stream_ptr(stream)))
 
+    def factor_unsym(self, lower, upper, stream=None):
+        """pselinv_factor_unsym: A_ij (``lower``) and A_ji (``upper``) at the
+        stored lower positions, CUDA tensors of batch x nnz values."""
+        for v in (lower, upper):
+            assert v.is_cuda and v.dtype == self.torch_dtype and v.is_contiguous()
+            assert v.numel() == self.opts.batch * self.info["nnz_a"]
+        self._check(self._lib.pselinv_factor_unsym(self._h, ctypes.c_void_p(lower.data_ptr()),
+                                                   ctypes.c_void_p(upper.data_ptr()), _stream_ptr(stream)))
+
     def selinv(self, mode=LEVEL, stream=None):
         self._check(self._lib.pselinv_selinv(self._h, int(mode), _stream_ptr(stream)))
 
@@ -238,8 +253,9 @@ class SelInv:
         self._check(self._lib.pselinv_set_debug(self._h, int(flags)))
 
     def panels(self, which=0, out=None, stream=None):
-        """X (which=0) or L (which=1) panels as a [batch, panel_entries] tensor;
-        ``out`` may be a CUDA tensor or a (pinned) CPU tensor."""
+        """X (which=0) or L (which=1) panels -- non-symmetric handles also XU (2)
+        and U (3) -- as a [batch, panel_entries] tensor; ``out`` may be a CUDA
+        tensor or a (pinned) CPU tensor."""
         import torch
         if out is None:
             out = torch.empty(self.opts.batch * self.info["panel_entries"], dtype=self.torch_dtype, device="cuda")
@@ -254,6 +270,16 @@ class SelInv:
         if out is None:
             out = torch.empty(self.opts.batch * nnz, dtype=self.torch_dtype, device="cuda")
         self._check(self._lib.pselinv_get_selected(self._h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out.view(self.opts.batch, nnz)
+
+    def selected_upper(self, out=None, stream=None):
+        """Non-symmetric handles: X_ji at the stored lower positions (i, j)."""
+        import torch
+        nnz = self.info["nnz_a"]
+        if out is None:
+            out = torch.empty(self.opts.batch * nnz, dtype=self.torch_dtype, device="cuda")
+        self._check(self._lib.pselinv_get_selected_upper(self._h, ctypes.c_void_p(out.data_ptr()),
+                                                         _stream_ptr(stream)))
         return out.view(self.opts.batch, nnz)
 
     def logdet_grad(self, out=None, stream=None):

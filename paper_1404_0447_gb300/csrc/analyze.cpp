@@ -31,6 +31,7 @@ struct Pattern {
   std::vector<int64_t> cp;
   std::vector<int32_t> ri;
   std::vector<int64_t> src;
+  std::vector<uint8_t> flip;  // entry transposed by the ordering
 };
 
 Pattern permute_pattern(int64_t n, const int64_t* cp, const int32_t* ri,
@@ -46,6 +47,7 @@ Pattern permute_pattern(int64_t n, const int64_t* cp, const int32_t* ri,
   for (int64_t j = 0; j < n; ++j) P.cp[j + 1] += P.cp[j];
   P.ri.resize(nnz);
   P.src.resize(nnz);
+  P.flip.resize(nnz);
   std::vector<int64_t> next(P.cp.begin(), P.cp.end() - 1);
   for (int64_t j = 0; j < n; ++j)
     for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
@@ -53,20 +55,24 @@ Pattern permute_pattern(int64_t n, const int64_t* cp, const int32_t* ri,
       int64_t q = next[std::min(a, b)]++;
       P.ri[q] = std::max(a, b);
       P.src[q] = p;
+      P.flip[q] = a < b;  // the ordering moved this entry above the diagonal
     }
   // sort every column by row (columns are short; insertion sort on pairs)
   for (int64_t j = 0; j < n; ++j) {
     for (int64_t p = P.cp[j] + 1; p < P.cp[j + 1]; ++p) {
       int32_t r = P.ri[p];
       int64_t s = P.src[p];
+      uint8_t f = P.flip[p];
       int64_t q = p - 1;
       while (q >= P.cp[j] && P.ri[q] > r) {
         P.ri[q + 1] = P.ri[q];
         P.src[q + 1] = P.src[q];
+        P.flip[q + 1] = P.flip[q];
         --q;
       }
       P.ri[q + 1] = r;
       P.src[q + 1] = s;
+      P.flip[q + 1] = f;
     }
   }
   return P;
@@ -161,8 +167,10 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
         return fail(h, PSELINV_ERR_NOT_LOWER, "rows not increasing / out of range in column " + std::to_string(j));
   }
   const pselinv_opts& o = h->opts;
-  const int wcap = o.max_sn_width == 0 ? kMaxWidth : o.max_sn_width;
+  int wcap = o.max_sn_width == 0 ? kMaxWidth : o.max_sn_width;
   if (wcap < 1 || wcap > kMaxWidth) return fail(h, PSELINV_ERR_ARG, "max_sn_width must be 0..128");
+  if (o.unsym != 0 && o.unsym != 1) return fail(h, PSELINV_ERR_ARG, "unsym must be 0 or 1");
+  if (o.unsym && o.dtype == PSELINV_C128) wcap = std::min(wcap, kMaxWidthLUComplex);
   if (o.relax != PSELINV_RELAX_NONE && o.relax != PSELINV_RELAX_AMALG)
     return fail(h, PSELINV_ERR_ARG, "bad relax mode");
 
@@ -317,8 +325,8 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
     m.desc = h->rowptr[k];
     const double s = m.s, r = m.r;
     cost[k] = sn_flops(s, r);
-    h->flops_selinv += cost[k];
-    h->flops_gemm1 += 2 * r * r * s;
+    h->flops_selinv += o.unsym ? 4 * r * r * s + 4 * r * s * s + 4.0 / 3.0 * s * s * s : cost[k];
+    h->flops_gemm1 += (o.unsym ? 4 : 2) * r * r * s;
     h->nnz_l += (int64_t)m.s * (m.s + 1) / 2 + (int64_t)m.s * m.r;
     h->max_r = std::max<int64_t>(h->max_r, m.r);
     h->max_width = std::max(h->max_width, m.s);
@@ -404,12 +412,15 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
   }
   for (int32_t k = 0; k < nsn; ++k) {
     const double s = h->meta[k].s, r = h->meta[k].r;
-    h->bytes_selinv += 8.0 * (r * (r + 1) / 2 + 2 * (s + r) * s) + 4.0 * (h->relptr[k + 1] - h->relptr[k]);
+    const double idx = 4.0 * (h->relptr[k + 1] - h->relptr[k]);
+    h->bytes_selinv += o.unsym ? 8.0 * (r * r + 4 * (s + r) * s) + 2 * idx
+                               : 8.0 * (r * (r + 1) / 2 + 2 * (s + r) * s) + idx;
   }
 
   // ---- value map: A's stored entries -> panel offsets ----
   h->valmap.assign(h->nnz_a, -1);
   h->diagmask.assign(h->nnz_a, 0);
+  if (o.unsym) h->flipmap.assign(h->nnz_a, 0);
   for (int64_t j = 0; j < n; ++j) h->diagmask[cp[j]] = 1;  // diagonal first in every column
   for (int64_t j = 0; j < n; ++j) {
     const SnMeta& m = h->meta[col2sn[j]];
@@ -426,6 +437,7 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
         pos = m.s + (it - R);
       }
       h->valmap[P.src[p]] = m.panel + (j - m.f) * (int64_t)ld + pos;
+      if (o.unsym) h->flipmap[P.src[p]] = P.flip[p];
     }
   }
 

@@ -66,7 +66,7 @@ int alloc(pselinv_handle* h, void** dst, int64_t bytes) {
 void free_device(pselinv_handle* h) {
   void** ptrs[] = {&h->d_meta, &h->d_desc, &h->d_relidx, &h->d_valmap, &h->d_diagmask, &h->d_tasks, &h->d_levelsn,
                    &h->d_L,    &h->d_X,    &h->d_D,      &h->d_lhat,   &h->d_linv,  &h->d_part, &h->d_ypart,
-                   &h->d_status,
+                   &h->d_status, &h->d_flipmap, &h->d_U, &h->d_XU, &h->d_uhat, &h->d_uinv,
                    &h->d_xb,   &h->d_lb,   &h->d_db,     &h->d_zb,     &h->d_w1,    &h->d_yb,   &h->d_hb,
                    &h->d_plist, &h->d_pn,  &h->d_pctr};
   for (void** p : ptrs) {
@@ -89,6 +89,8 @@ int upload_schedule(pselinv_handle* h);
 int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record);
 const psi::Task* tasks_at(const pselinv_handle* h, int64_t base, int64_t off);
 psi::KArgs kargs(pselinv_handle* h);
+psi::KArgs kargs_uside(pselinv_handle* h);
+psi::KArgs kargs_step4(pselinv_handle* h);
 
 int ensure_device(pselinv_handle* h) {
   if (h->dev_sym) return PSELINV_OK;
@@ -112,6 +114,13 @@ int ensure_device(pselinv_handle* h) {
   if ((rc = alloc(h, &h->d_lhat, B * h->lhat_total * es))) return rc;
   if ((rc = alloc(h, &h->d_linv, B * h->linv_total * es))) return rc;
   if ((rc = alloc(h, &h->d_status, sizeof(int) * kStatusWords + sizeof(double) * 6 * B))) return rc;
+  if (h->opts.unsym) {
+    if ((rc = upload(h, &h->d_flipmap, h->flipmap))) return rc;
+    if ((rc = alloc(h, &h->d_U, B * h->panel_total * es))) return rc;
+    if ((rc = alloc(h, &h->d_XU, B * h->panel_total * es))) return rc;
+    if ((rc = alloc(h, &h->d_uhat, B * h->lhat_total * es))) return rc;
+    if ((rc = alloc(h, &h->d_uinv, B * h->linv_total * es))) return rc;
+  }
   PSI_CUDA(h, cudaMemset(h->d_status, 0, sizeof(int) * kStatusWords));
   h->dev_sym = true;
   return PSELINV_OK;
@@ -211,6 +220,30 @@ psi::KArgs kargs(pselinv_handle* h) {
   a.ypart = h->d_ypart;
   a.status = (int*)h->d_status;
   a.sz = sizes(h);
+  a.U = h->d_U;
+  a.Uinv = h->d_uinv;
+  a.Uhat = nullptr;
+  a.XU = h->d_XU;
+  a.strict = 0;
+  return a;
+}
+
+// Non-symmetric handles: the same kernels run on the U side through swapped
+// pointers.  Step 1 of the U side: Uhat^T = (U panel rows C) (U'_KK^T)^{-1}.
+psi::KArgs kargs_uside(pselinv_handle* h) {
+  psi::KArgs a = kargs(h);
+  a.L = h->d_U;
+  a.Linv = h->d_uinv;
+  a.Lhat = h->d_uhat;
+  return a;
+}
+
+// Step 4 as step 2 on the transposes: X and XU trade places, Uhat^T replaces Lhat.
+psi::KArgs kargs_step4(pselinv_handle* h) {
+  psi::KArgs a = kargs(h);
+  a.X = h->d_XU;
+  a.XU = h->d_X;
+  a.Lhat = h->d_uhat;
   return a;
 }
 
@@ -264,12 +297,19 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record) {
   // normalisation pass: every supernode at once (Algorithm 3, first loop)
   int64_t nlhat_launch = 0;
   for (int v = 0; v < psi::kNumVar; ++v) nlhat_launch += h->t_lhat.whole[v].end > h->t_lhat.whole[v].begin;
-  rc = tm.run(0, 1 + nlhat_launch, [&] {
-    cudaError_t e = psi::launch_per_sn(Kern::NormDiag, a, nullptr, h->nsn, st);
-    for (int v = 0; v < psi::kNumVar && e == cudaSuccess; ++v) {
-      const psi::Range r = h->t_lhat.whole[v];
-      e = psi::launch_tiles(Kern::Lhat, v, a, tasks_at(h, h->off_lhat, r.begin), r.end - r.begin, st);
-    }
+  const bool unsym = h->opts.unsym != 0;
+  const psi::KArgs au = unsym ? kargs_uside(h) : a;   // U side of step 1
+  const psi::KArgs a4 = unsym ? kargs_step4(h) : a;   // step 4
+  psi::KArgs a3 = a;                                  // step 3: Uhat_{K,C} X_{C,K}
+  if (unsym) a3.Lhat = h->d_uhat;
+  rc = tm.run(0, (1 + nlhat_launch) * (unsym ? 2 : 1) - (unsym ? 1 : 0), [&] {
+    cudaError_t e = psi::launch_per_sn(unsym ? Kern::NormDiagLU : Kern::NormDiag, a, nullptr, h->nsn, st);
+    for (int side = 0; side < (unsym ? 2 : 1); ++side)
+      for (int v = 0; v < psi::kNumVar && e == cudaSuccess; ++v) {
+        const psi::Range r = h->t_lhat.whole[v];
+        e = psi::launch_tiles(Kern::Lhat, v, side ? au : a, tasks_at(h, h->off_lhat, r.begin), r.end - r.begin,
+                              st);
+      }
     return e;
   });
   if (rc) return rc;
@@ -280,24 +320,30 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record) {
       n1 += r1[v].end > r1[v].begin;
       n2 += r2[v].end > r2[v].begin;
     }
-    if ((e = tm.run(1, n1, [&] {
-           cudaError_t x = cudaSuccess;
-           for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
-             x = psi::launch_tiles(Kern::Gemm1, v, a, tasks_at(h, h->off_gemm1, r1[v].begin), r1[v].end - r1[v].begin,
-                                   st);
-           if (split && x == cudaSuccess) x = psi::launch_per_sn(Kern::Gemm1Reduce, a, sns, nsn_step, st);
-           return x;
-         })))
-      return e;
+    // step 2 (ka = a), or step 4 (ka = a4) of a non-symmetric handle
+    auto gemm1 = [&](const psi::KArgs& ka) {
+      return tm.run(1, n1, [&] {
+        cudaError_t x = cudaSuccess;
+        for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
+          x = psi::launch_tiles(Kern::Gemm1, v, ka, tasks_at(h, h->off_gemm1, r1[v].begin), r1[v].end - r1[v].begin,
+                                st);
+        if (split && x == cudaSuccess) x = psi::launch_per_sn(Kern::Gemm1Reduce, ka, sns, nsn_step, st);
+        return x;
+      });
+    };
+    if ((e = gemm1(a))) return e;
     if ((e = tm.run(2, n2, [&] {
            cudaError_t x = cudaSuccess;
            for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
-             x = psi::launch_tiles(Kern::Gemm2, v, a, tasks_at(h, h->off_gemm2, r2[v].begin), r2[v].end - r2[v].begin,
-                                   st);
+             x = psi::launch_tiles(Kern::Gemm2, v, a3, tasks_at(h, h->off_gemm2, r2[v].begin),
+                                   r2[v].end - r2[v].begin, st);
            return x;
          })))
       return e;
-    return tm.run(3, nsn_step > 0, [&] { return psi::launch_per_sn(Kern::DiagFinal, a, sns, nsn_step, st); });
+    if ((e = tm.run(3, nsn_step > 0, [&] { return psi::launch_per_sn(Kern::DiagFinal, a, sns, nsn_step, st); })))
+      return e;
+    // step 4 reuses the step-2 partial-product buffer after step 2's reduction
+    return unsym ? gemm1(a4) : PSELINV_OK;
   };
   if (mode == PSELINV_PLAIN) {
     // one supernode per launch, reverse postorder (descending index)
@@ -338,7 +384,7 @@ void pselinv_default_opts(pselinv_opts* o) {
   o->small_cutoff = -1;
   o->split_k_rows = 1024;
   o->debug_checks = 0;
-  o->reserved = 0;
+  o->unsym = 0;
   o->spin_limit_ns = 1000000000LL;
 }
 
@@ -408,35 +454,65 @@ int pselinv_analyze_batch(int32_t k, const int64_t* h_n, const int64_t* const* h
   return pselinv_analyze(N, cp.data(), ri.data(), perm.data(), opts, out);
 }
 
-int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream) {
-  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
-  if (!d_values) return set_err(h, PSELINV_ERR_ARG, "values pointer is NULL");
-  int rc = ensure_device(h);
-  if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+// Supernodal factorisation, level by level from the leaves.  Symmetric:
+// A = L D L^T.  Non-symmetric (d_upper set): A = L D U', the U side running
+// the same panel-solve, copy and Schur kernels through swapped pointers.
+int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cudaStream_t st) {
   const psi::Sizes sz = sizes(h);
   const int64_t B = h->opts.batch;
+  const bool unsym = d_upper != nullptr;
   h->factored = h->inverted = false;
   PSI_CUDA(h, cudaMemsetAsync(h->d_L, 0, elem_size(h) * B * h->panel_total, st));
+  if (unsym) PSI_CUDA(h, cudaMemsetAsync(h->d_U, 0, elem_size(h) * B * h->panel_total, st));
   PSI_CUDA(h, cudaMemsetAsync(h->d_status, 0x7f, sizeof(int), st));
   PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + 1, 0, sizeof(int) * (kStatusWords - 1), st));
-  const psi::KArgs a = kargs(h);
-  PSI_CUDA(h, psi::launch_scatter_values(h->opts.dtype, d_values, (const int64_t*)h->d_valmap, h->nnz_a, h->d_L,
-                                         sz, st));
+  psi::KArgs a = kargs(h);
+  a.XU = nullptr;
+  if (unsym)
+    PSI_CUDA(h, psi::launch_scatter_values_lu(h->opts.dtype, d_lower, d_upper, (const int64_t*)h->d_valmap,
+                                              (const uint8_t*)h->d_flipmap, h->nnz_a, h->d_L, h->d_U, sz, st));
+  else
+    PSI_CUDA(h, psi::launch_scatter_values(h->opts.dtype, d_lower, (const int64_t*)h->d_valmap, h->nnz_a, h->d_L,
+                                           sz, st));
+  // L side: L_{C,K} = A_{C,K} (L_KK^{-T} or U'_KK^{-1}) D^{-1} into lhat, copied to the L panels
+  psi::KArgs al = a;
+  if (unsym) al.Linv = h->d_uinv;
+  // U side: U'_{K,C}^T = A_{K,C}^T L_KK^{-T} D^{-1} into uhat, copied to the U panels
+  psi::KArgs au = a;
+  au.L = h->d_U;
+  au.Lhat = h->d_uhat;
+  // Schur: L_{C,K} D U'_{K,C} into the L panels, and its strict upper part (transposed) into the U panels
+  psi::KArgs sl = a, su = a;
+  if (unsym) {
+    sl.Uhat = h->d_uhat;
+    su.L = h->d_U;
+    su.Lhat = h->d_uhat;
+    su.Uhat = h->d_lhat;
+    su.strict = 1;
+  }
   const auto* lsn = (const int32_t*)h->d_levelsn;
   for (int32_t l = h->nlevels - 1; l >= 0; --l) {
     const int32_t* sns = lsn + h->level_ptr[l];
     const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
-    PSI_CUDA(h, psi::launch_per_sn(psi::Kern::FactorDiag, a, sns, nsl, st));
-    for (int v = 0; v < psi::kNumVar; ++v) {
-      const psi::Range r = h->t_trsm.per_lv[(size_t)l * psi::kNumVar + v];
-      PSI_CUDA(h, psi::launch_tiles(psi::Kern::Trsm, v, a, tasks_at(h, h->off_trsm, r.begin), r.end - r.begin, st));
+    PSI_CUDA(h, psi::launch_per_sn(unsym ? psi::Kern::FactorDiagLU : psi::Kern::FactorDiag, a, sns, nsl, st));
+    for (int side = 0; side < (unsym ? 2 : 1); ++side) {
+      const psi::KArgs& ka = side ? au : al;
+      for (int v = 0; v < psi::kNumVar; ++v) {
+        const psi::Range r = h->t_trsm.per_lv[(size_t)l * psi::kNumVar + v];
+        PSI_CUDA(h, psi::launch_tiles(psi::Kern::Trsm, v, ka, tasks_at(h, h->off_trsm, r.begin), r.end - r.begin,
+                                      st));
+      }
+      PSI_CUDA(h, psi::launch_per_sn(psi::Kern::CopyBack, ka, sns, nsl, st));
     }
-    PSI_CUDA(h, psi::launch_per_sn(psi::Kern::CopyBack, a, sns, nsl, st));
-    for (int v = 0; v < psi::kNumVar; ++v) {
-      const psi::Range r = h->t_schur.per_lv[(size_t)l * psi::kNumVar + v];
-      PSI_CUDA(h, psi::launch_tiles(psi::Kern::Schur, v, a, tasks_at(h, h->off_schur, r.begin), r.end - r.begin, st));
-    }
+    for (int side = 0; side < (unsym ? 2 : 1); ++side)
+      for (int v = 0; v < psi::kNumVar; ++v) {
+        const psi::Range r = h->t_schur.per_lv[(size_t)l * psi::kNumVar + v];
+        PSI_CUDA(h, psi::launch_tiles(psi::Kern::Schur, v, side ? su : sl, tasks_at(h, h->off_schur, r.begin),
+                                      r.end - r.begin, st));
+      }
   }
   int status[2];
   PSI_CUDA(h, cudaMemcpyAsync(status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
@@ -449,12 +525,35 @@ int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream) {
   h->factored = true;
   return PSELINV_OK;
 }
+}  // namespace
+
+extern "C" {
+
+int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream) {
+  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
+  if (!d_values) return set_err(h, PSELINV_ERR_ARG, "values pointer is NULL");
+  if (h->opts.unsym) return set_err(h, PSELINV_ERR_STATE, "non-symmetric handle: use pselinv_factor_unsym");
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  return factor_impl(h, d_values, nullptr, (cudaStream_t)stream);
+}
+
+int pselinv_factor_unsym(pselinv_handle* h, const void* d_lower, const void* d_upper, void* stream) {
+  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
+  if (!d_lower || !d_upper) return set_err(h, PSELINV_ERR_ARG, "values pointer is NULL");
+  if (!h->opts.unsym) return set_err(h, PSELINV_ERR_STATE, "symmetric handle: use pselinv_factor");
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  return factor_impl(h, d_lower, d_upper, (cudaStream_t)stream);
+}
 
 int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream) {
   if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
   if (mode != PSELINV_PLAIN && mode != PSELINV_LEVEL && mode != PSELINV_GRAPH && mode != PSELINV_PERSISTENT)
     return set_err(h, PSELINV_ERR_ARG, "bad selinv mode");
   if (!h->factored) return set_err(h, PSELINV_ERR_STATE, "selinv called before a successful factor");
+  if (mode == PSELINV_PERSISTENT && h->opts.unsym)
+    return set_err(h, PSELINV_ERR_ARG, "the PERSISTENT schedule is for symmetric handles");
   cudaStream_t st = (cudaStream_t)stream;
   if (mode == PSELINV_PERSISTENT) {
     if (!h->pgraph_exec) {
@@ -550,24 +649,43 @@ int pselinv_set_debug(pselinv_handle* h, int32_t flags) {
 int pselinv_get_panels(pselinv_handle* h, int32_t which, void* d_out, void* stream) {
   // d_out may be device or host memory: cudaMemcpyDefault resolves it (UVA)
   if (!h || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
-  if (which != 0 && which != 1) return set_err(h, PSELINV_ERR_ARG, "which must be 0 (X) or 1 (L)");
-  if (which == 0 && !h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
-  if (which == 1 && !h->factored) return set_err(h, PSELINV_ERR_STATE, "no factor yet");
+  const int nwhich = h->opts.unsym ? 4 : 2;
+  if (which < 0 || which >= nwhich)
+    return set_err(h, PSELINV_ERR_ARG, "which must be 0 (X), 1 (L), or for non-symmetric handles 2 (XU), 3 (U)");
+  if ((which == 0 || which == 2) && !h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
+  if ((which == 1 || which == 3) && !h->factored) return set_err(h, PSELINV_ERR_STATE, "no factor yet");
   const size_t bytes = elem_size(h) * (size_t)h->opts.batch * (size_t)h->panel_total;
-  PSI_CUDA(h, cudaMemcpyAsync(d_out, which == 0 ? h->d_X : h->d_L, bytes, cudaMemcpyDefault, (cudaStream_t)stream));
+  const void* src[4] = {h->d_X, h->d_L, h->d_XU, h->d_U};
+  PSI_CUDA(h, cudaMemcpyAsync(d_out, src[which], bytes, cudaMemcpyDefault, (cudaStream_t)stream));
   return PSELINV_OK;
 }
 
 int pselinv_get_selected(pselinv_handle* h, void* d_out, void* stream) {
   if (!h || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
   if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
-  PSI_CUDA(h, psi::launch_gather_values(h->opts.dtype, h->d_X, (const int64_t*)h->d_valmap, nullptr, h->nnz_a,
-                                        d_out, sizes(h), (cudaStream_t)stream));
+  if (h->opts.unsym)
+    PSI_CUDA(h, psi::launch_gather_values_lu(h->opts.dtype, h->d_X, h->d_XU, (const int64_t*)h->d_valmap,
+                                             (const uint8_t*)h->d_flipmap, h->nnz_a, 0, d_out, sizes(h),
+                                             (cudaStream_t)stream));
+  else
+    PSI_CUDA(h, psi::launch_gather_values(h->opts.dtype, h->d_X, (const int64_t*)h->d_valmap, nullptr, h->nnz_a,
+                                          d_out, sizes(h), (cudaStream_t)stream));
+  return PSELINV_OK;
+}
+
+int pselinv_get_selected_upper(pselinv_handle* h, void* d_out, void* stream) {
+  if (!h || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (!h->opts.unsym) return set_err(h, PSELINV_ERR_STATE, "symmetric handle: use pselinv_get_selected");
+  if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
+  PSI_CUDA(h, psi::launch_gather_values_lu(h->opts.dtype, h->d_X, h->d_XU, (const int64_t*)h->d_valmap,
+                                           (const uint8_t*)h->d_flipmap, h->nnz_a, 1, d_out, sizes(h),
+                                           (cudaStream_t)stream));
   return PSELINV_OK;
 }
 
 int pselinv_logdet_grad(pselinv_handle* h, void* d_out, void* stream) {
   if (!h || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (h->opts.unsym) return set_err(h, PSELINV_ERR_STATE, "symmetric handles only");
   if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
   PSI_CUDA(h, psi::launch_gather_values(h->opts.dtype, h->d_X, (const int64_t*)h->d_valmap,
                                         (const uint8_t*)h->d_diagmask, h->nnz_a, d_out, sizes(h),
@@ -577,6 +695,7 @@ int pselinv_logdet_grad(pselinv_handle* h, void* d_out, void* stream) {
 
 int pselinv_pole_sum(pselinv_handle* h, const double* h_weights, void* d_out, void* stream) {
   if (!h || !h_weights || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (h->opts.unsym) return set_err(h, PSELINV_ERR_STATE, "symmetric handles only");
   if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
   cudaStream_t st = (cudaStream_t)stream;
   const int B = h->opts.batch;
@@ -589,6 +708,7 @@ int pselinv_pole_sum(pselinv_handle* h, const double* h_weights, void* d_out, vo
 
 int pselinv_trace_sum(pselinv_handle* h, const void* d_values, double* h_out, void* stream) {
   if (!h || !d_values || !h_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (h->opts.unsym) return set_err(h, PSELINV_ERR_STATE, "symmetric handles only");
   if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "no selected inverse yet");
   cudaStream_t st = (cudaStream_t)stream;
   const int B = h->opts.batch;
@@ -623,6 +743,7 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
   if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
   if (!d_G || !d_gradA) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
   if (g_kind != PSELINV_G_SYMMETRIC && g_kind != PSELINV_G_PANEL) return set_err(h, PSELINV_ERR_ARG, "bad g_kind");
+  if (h->opts.unsym) return set_err(h, PSELINV_ERR_STATE, "symmetric handles only");
   if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "selinv_adjoint needs a prior pselinv_selinv");
   const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
   int rc;
@@ -815,6 +936,7 @@ int pselinv_get_info(const pselinv_handle* h, pselinv_info* info) {
                     (int64_t)sizeof(psi::Task) * tasks +
                     B * es * (2 * h->panel_total + h->n + h->lhat_total + h->linv_total + h->part_max + h->ypart_max);
     if (h->d_xb) bytes += B * es * (2 * h->panel_total + h->n + 2 * h->linv_total + 2 * h->lhat_total);
+    if (h->opts.unsym) bytes += h->flipmap.size() + B * es * (2 * h->panel_total + h->lhat_total + h->linv_total);
     info->device_bytes = bytes;
   } else {
     info->device_bytes = 0;

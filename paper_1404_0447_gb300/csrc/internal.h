@@ -64,6 +64,7 @@ struct Range {
 };
 
 constexpr int kMaxWidth = 128;   // widest supernode the kernels accept
+constexpr int kMaxWidthLUComplex = 112;  // complex non-symmetric: two packed triangles in shared memory
 constexpr int kChunkRows = 512;  // rows per step-3 partial product (before the per-level boost)
 constexpr int kTargetTiles = 4 * 152;  // tiles a level should offer the GPU (4 per SM)
 constexpr int kMinSlice2 = 256;   // smallest step-2 slice the per-level boost makes
@@ -117,6 +118,7 @@ struct pselinv_handle {
   std::vector<int64_t> rowptr, panel_off, relptr;
   std::vector<int64_t> valmap;  // user entry q -> panel offset of (i, j), i >= j internal
   std::vector<uint8_t> diagmask;  // user entry q is a diagonal entry
+  std::vector<uint8_t> flipmap;   // non-symmetric: user entry q lies above the diagonal internally
   std::vector<psi::SnMeta> meta;
   std::vector<psi::ColDesc> desc;
   std::vector<int8_t> level_split;  // level holds a supernode whose step 2 is split
@@ -146,6 +148,7 @@ struct pselinv_handle {
   void* d_relidx = nullptr;
   void* d_valmap = nullptr;
   void* d_diagmask = nullptr;
+  void* d_flipmap = nullptr;
   void* d_tasks = nullptr;  // all task arrays back to back
   int64_t off_lhat = 0, off_gemm1 = 0, off_gemm2 = 0, off_trsm = 0, off_schur = 0, off_rect = 0;
   void* d_levelsn = nullptr;
@@ -157,6 +160,11 @@ struct pselinv_handle {
   void* d_part = nullptr;   // step-3 partial products (level-local)
   void* d_ypart = nullptr;  // step-2 partial products (level-local)
   void* d_status = nullptr; // device status words
+  // non-symmetric handles
+  void* d_U = nullptr;      // U panels (U'_{j,i} at position (i, j))
+  void* d_XU = nullptr;     // XU panels (X_{j,i} at position (i, j))
+  void* d_uhat = nullptr;   // Uhat^T / factor scratch of the U side
+  void* d_uinv = nullptr;   // (U'_KK^T)^{-1}
   // adjoint work buffers (allocated on first pselinv_selinv_adjoint)
   void* d_xb = nullptr;     // X-bar, then F-bar (panel layout)
   void* d_lb = nullptr;     // L-bar (panel layout)

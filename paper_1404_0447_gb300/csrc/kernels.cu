@@ -37,6 +37,40 @@ __global__ void k_scatter_values(const T* __restrict__ vals, const int64_t* __re
     Lb[vmap[q]] = v[q];
 }
 
+// Non-symmetric values: entry q's pair (A_ij, A_ji) goes to the L and U
+// panels at its position, or to the U and L panels where the ordering
+// transposed it.
+template <class T>
+__global__ void k_scatter_values_lu(const T* __restrict__ lo, const T* __restrict__ up,
+                                    const int64_t* __restrict__ vmap, const uint8_t* __restrict__ flip,
+                                    int64_t nnz, T* __restrict__ L, T* __restrict__ U, int64_t panel_total) {
+  const int b = blockIdx.y;
+  const T* vl = lo + (int64_t)b * nnz;
+  const T* vu = up + (int64_t)b * nnz;
+  T* Lb = L + (int64_t)b * panel_total;
+  T* Ub = U + (int64_t)b * panel_total;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = vmap[q];
+    const bool f = flip[q] != 0;
+    Lb[p] = f ? vu[q] : vl[q];
+    Ub[p] = f ? vl[q] : vu[q];
+  }
+}
+
+// Non-symmetric gather: X_ij (upper = 0) or X_ji (upper = 1) for the stored
+// entry q at (i, j), from the XL or XU panel depending on the flip.
+template <class T>
+__global__ void k_gather_values_lu(const T* __restrict__ XL, const T* __restrict__ XU, int64_t panel_total,
+                                   const int64_t* __restrict__ vmap, const uint8_t* __restrict__ flip, int64_t nnz,
+                                   int upper, T* __restrict__ out) {
+  const int b = blockIdx.y;
+  const T* Xl = XL + (int64_t)b * panel_total;
+  const T* Xu = XU + (int64_t)b * panel_total;
+  T* o = out + (int64_t)b * nnz;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x)
+    o[q] = ((flip[q] != 0) != (upper != 0)) ? Xu[vmap[q]] : Xl[vmap[q]];
+}
+
 // out[q] = X at the panel position of stored entry q; with a diagonal mask,
 // off-diagonal entries are doubled (gradient with respect to a stored value
 // that stands for both A_ij and A_ji).
@@ -111,6 +145,103 @@ __global__ void k_factor_diag(const SnMeta* __restrict__ meta, const int32_t* __
     if (i >= j) P[i + (int64_t)j * ld] = Tp[pk(i, j, s)];
   }
   for (int j = t; j < s; j += nt) D[b * sz.n + m.f + j] = Tp[pk(j, j, s)];
+}
+
+// Factorisation of a non-symmetric diagonal block, one CTA per supernode of
+// the level: A_KK = L_KK D_K U'_KK by pivot-free Gaussian elimination in
+// shared memory on two packed triangles, Tl (lower part and diagonal, from
+// the L panel) and Tu (Tu(i, j) = A_ji for i > j, from the U panel).  For
+// column j: d = Tl(j, j); L_ij = Tl(i, j) / d and U'_ji = Tu(i, j) / d; then
+// A_ik -= L_ij d U'_jk for i, k > j, on whichever triangle holds (i, k).
+// Back to the panels (L_KK with D on the diagonal, U'_KK^T), D, and the unit
+// lower inverses (L_KK)^{-1} -> linv, (U'_KK^T)^{-1} -> uinv.  On symmetric
+// input every operation matches k_factor_diag's.
+template <class T>
+__global__ void k_factor_diag_lu(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns, T* __restrict__ L,
+                                 T* __restrict__ U, T* __restrict__ D, T* __restrict__ Linv, T* __restrict__ Uinv,
+                                 Sizes sz, int* status) {
+  extern __shared__ __align__(16) unsigned char shraw[];
+  const int k = sns[blockIdx.x];
+  const int b = blockIdx.y;
+  const SnMeta m = meta[k];
+  const int s = m.s, ld = m.s + m.r;
+  T* Tl = reinterpret_cast<T*>(shraw);
+  T* Tu = Tl + s * (s + 1) / 2;
+  T* P = L + b * sz.panel + m.panel;
+  T* Q = U + b * sz.panel + m.panel;
+  const int nt = blockDim.x, t = threadIdx.x;
+  for (int e = t; e < s * s; e += nt) {
+    const int i = e % s, j = e / s;
+    if (i >= j) {
+      Tl[pk(i, j, s)] = P[i + (int64_t)j * ld];
+      Tu[pk(i, j, s)] = i > j ? Q[i + (int64_t)j * ld] : Sc<T>::zero();
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < s; ++j) {
+    const T d = Tl[pk(j, j, s)];
+    if (t == 0 && Sc<T>::bad(d)) report_pivot(status, m.f + j, Sc<T>::is_zero(d));
+    for (int i = j + 1 + t; i < s; i += nt) {
+      Tl[pk(i, j, s)] = Tl[pk(i, j, s)] / d;
+      Tu[pk(i, j, s)] = Tu[pk(i, j, s)] / d;
+    }
+    __syncthreads();
+    const int w = s - j - 1;
+    for (int e = t; e < w * w; e += nt) {
+      const int ii = j + 1 + e % w, kk = j + 1 + e / w;
+      if (ii >= kk) Tl[pk(ii, kk, s)] -= Tl[pk(ii, j, s)] * Tu[pk(kk, j, s)] * d;      // A_{ii,kk}
+      if (ii > kk) Tu[pk(ii, kk, s)] -= Tu[pk(ii, j, s)] * Tl[pk(kk, j, s)] * d;       // A_{kk,ii}
+    }
+    __syncthreads();
+  }
+  unit_lower_inverse(Tl, s, Linv + b * sz.linv + m.linv);
+  unit_lower_inverse(Tu, s, Uinv + b * sz.linv + m.linv);
+  for (int e = t; e < s * s; e += nt) {
+    const int i = e % s, j = e / s;
+    if (i >= j) P[i + (int64_t)j * ld] = Tl[pk(i, j, s)];
+    if (i > j) Q[i + (int64_t)j * ld] = Tu[pk(i, j, s)];
+  }
+  for (int j = t; j < s; j += nt) D[b * sz.n + m.f + j] = Tl[pk(j, j, s)];
+}
+
+// Normalisation of a non-symmetric diagonal block (all supernodes, one CTA
+// each): Vl = (L_KK)^{-1} -> linv, Vu = (U'_KK^T)^{-1} -> uinv, and the
+// first term of step 3, U_KK^{-1} L_KK^{-1} = U'_KK^{-1} D_K^{-1} L_KK^{-1}
+// = Vu^T D_K^{-1} Vl, to the full diagonal block of the X panel.
+template <class T>
+__global__ void k_norm_diag_lu(const SnMeta* __restrict__ meta, const T* __restrict__ L, const T* __restrict__ U,
+                               const T* __restrict__ D, T* __restrict__ Linv, T* __restrict__ Uinv,
+                               T* __restrict__ X, Sizes sz) {
+  extern __shared__ __align__(16) unsigned char shraw[];
+  T* Tp = reinterpret_cast<T*>(shraw);
+  const int k = blockIdx.x;
+  const int b = blockIdx.y;
+  const SnMeta m = meta[k];
+  const int s = m.s, ld = m.s + m.r;
+  const T* d = D + b * sz.n + m.f;
+  T* rd = Tp + s * (s + 1) / 2;
+  const int nt = blockDim.x, t = threadIdx.x;
+  T* Vl = Linv + b * sz.linv + m.linv;
+  T* Vu = Uinv + b * sz.linv + m.linv;
+  for (int side = 0; side < 2; ++side) {
+    const T* P = (side == 0 ? L : U) + b * sz.panel + m.panel;
+    for (int e = t; e < s * s; e += nt) {
+      const int i = e % s, j = e / s;
+      if (i > j) Tp[pk(i, j, s)] = P[i + (int64_t)j * ld];
+    }
+    __syncthreads();
+    unit_lower_inverse(Tp, s, side == 0 ? Vl : Vu);
+    __syncthreads();
+  }
+  for (int q = t; q < s; q += nt) rd[q] = Sc<T>::one() / d[q];
+  __syncthreads();
+  T* XK = X + b * sz.panel + m.panel;
+  for (int e = t; e < s * s; e += nt) {
+    const int i = e % s, j = e / s;
+    T acc = Sc<T>::zero();
+    for (int q = i > j ? i : j; q < s; ++q) acc += Vu[q + i * s] * rd[q] * Vl[q + j * s];
+    XK[i + (int64_t)j * ld] = acc;
+  }
 }
 
 // Normalisation, diagonal part (all supernodes, one CTA each):
@@ -211,17 +342,23 @@ __global__ void __launch_bounds__(TG_THREADS) k_trsm(const SnMeta* __restrict__ 
 // U = L_{C,K} D_K L_{C,K}^T; U[i][k] (i >= k) is subtracted from the ancestor
 // entry found through the column descriptor of k and the relative index of i.
 // Several supernodes of one level can hit the same entry: FP64 atomics.
+// Non-symmetric factor: Ltmp2 is the second operand (U'_{K,C}^T), giving
+// L_{C,K} D_K U'_{K,C} into the L panels and, called again with the operands
+// swapped and `strict`, (U'_{K,C}^T D_K L_{C,K}^T) below the diagonal into the
+// U panels.
 template <class T, int BN>
 __global__ void __launch_bounds__(TG_THREADS) k_schur(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
                                                       const ColDesc* __restrict__ desc,
                                                       const int32_t* __restrict__ relidx, T* __restrict__ L,
-                                                      const T* __restrict__ D, const T* __restrict__ Ltmp, Sizes sz) {
+                                                      const T* __restrict__ D, const T* __restrict__ Ltmp,
+                                                      const T* __restrict__ Ltmp2, int strict, Sizes sz) {
   __shared__ TileSmem<T, BN> sm;
   const Task tk = tasks[blockIdx.x];
   const int b = blockIdx.y;
   const SnMeta m = meta[tk.sn];
   const int s = m.s, r = m.r;
   const T* Lc = Ltmp + b * sz.lhat + m.lhat;
+  const T* Lc2 = Ltmp2 + b * sz.lhat + m.lhat;
   const T* d = D + b * sz.n + m.f;
   Acc<T, BN> acc;
   acc_zero<T, BN>(acc);
@@ -231,14 +368,14 @@ __global__ void __launch_bounds__(TG_THREADS) k_schur(const SnMeta* __restrict__
   };
   auto lb = [&](int kk, int nn) {
     const int col = tk.n0 + nn;
-    return col < r ? Lc[col + (int64_t)kk * r] : Sc<T>::zero();
+    return col < r ? Lc2[col + (int64_t)kk * r] : Sc<T>::zero();
   };
   tile_mma<T, BN>(sm, 0, s, [](int) { return false; }, la, lb, acc);
   T* Lb = L + b * sz.panel;
   const ColDesc* dk = desc + m.desc;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int i = tk.m0 + mm, kc = tk.n0 + nn;
-    if (i < r && kc <= i) {
+    if (i < r && kc + strict <= i) {
       const ColDesc cd = dk[kc];
       T* dst = &Lb[cd.col + relidx[cd.rel + i]];
       if constexpr (Sc<T>::P == 1) {
@@ -283,10 +420,10 @@ __global__ void __launch_bounds__(TG_THREADS) k_lhat(const SnMeta* __restrict__ 
 }
 
 // Steps 2 and 3 as grouped per-level kernels (bodies in selinv_steps.cuh).
-template <class T, int BN>
+template <class T, int BN, bool UNSYM>
 __global__ void __launch_bounds__(TG_THREADS) k_gemm1(KArgs a, const Task* __restrict__ tasks) {
   __shared__ TileSmem<T, BN> sm;
-  step2_tile<T, BN>(a, tasks[blockIdx.x], blockIdx.y, sm);
+  step2_tile<T, BN, UNSYM>(a, tasks[blockIdx.x], blockIdx.y, sm);
 }
 
 // blockIdx.z strides over the columns of the split supernodes of the level
@@ -416,13 +553,26 @@ static size_t diag_smem(int maxw) {
   return sizeof(T) * ((size_t)maxw * (maxw + 1) / 2 + maxw);
 }
 
+// two packed triangles of the non-symmetric diagonal factorisation
+template <class T>
+static size_t diag_smem_lu(int maxw) {
+  return sizeof(T) * (size_t)maxw * (maxw + 1);
+}
+
 template <class T>
 static cudaError_t setup_t() {
   cudaError_t e = cudaFuncSetAttribute(k_factor_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)diag_smem<T>(kMaxWidth));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_norm_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)diag_smem<T>(kMaxWidth));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_norm_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)diag_smem<T>(kMaxWidth));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_norm_diag_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)diag_smem<T>(kMaxWidth));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_factor_diag_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)diag_smem_lu<T>(Sc<T>::P == 1 ? kMaxWidth : kMaxWidthLUComplex));
+  return e;
 }
 
 cudaError_t setup_kernels() {
@@ -442,6 +592,34 @@ cudaError_t launch_scatter_values(int dtype, const void* vals, const int64_t* vm
                                   const Sizes& sz, cudaStream_t st) {
   return dtype == PSELINV_C128 ? scatter_t<Cplx>(vals, vmap, nnz, L, sz, st)
                                : scatter_t<double>(vals, vmap, nnz, L, sz, st);
+}
+
+template <class T>
+static cudaError_t scatter_lu_t(const void* lo, const void* up, const int64_t* vmap, const uint8_t* flip, int64_t nnz,
+                                void* L, void* U, const Sizes& sz, cudaStream_t st) {
+  k_scatter_values_lu<T><<<dim3(blocks_for(nnz, 256), sz.batch), 256, 0, st>>>(
+      (const T*)lo, (const T*)up, vmap, flip, nnz, (T*)L, (T*)U, sz.panel);
+  return cudaGetLastError();
+}
+cudaError_t launch_scatter_values_lu(int dtype, const void* lower, const void* upper, const int64_t* vmap,
+                                     const uint8_t* flip, int64_t nnz, void* L, void* U, const Sizes& sz,
+                                     cudaStream_t st) {
+  return dtype == PSELINV_C128 ? scatter_lu_t<Cplx>(lower, upper, vmap, flip, nnz, L, U, sz, st)
+                               : scatter_lu_t<double>(lower, upper, vmap, flip, nnz, L, U, sz, st);
+}
+
+template <class T>
+static cudaError_t gather_lu_t(const void* XL, const void* XU, const int64_t* vmap, const uint8_t* flip, int64_t nnz,
+                               int upper, void* out, const Sizes& sz, cudaStream_t st) {
+  k_gather_values_lu<T><<<dim3(blocks_for(nnz, 256), sz.batch), 256, 0, st>>>(
+      (const T*)XL, (const T*)XU, sz.panel, vmap, flip, nnz, upper, (T*)out);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_values_lu(int dtype, const void* XL, const void* XU, const int64_t* vmap,
+                                    const uint8_t* flip, int64_t nnz, int upper, void* out, const Sizes& sz,
+                                    cudaStream_t st) {
+  return dtype == PSELINV_C128 ? gather_lu_t<Cplx>(XL, XU, vmap, flip, nnz, upper, out, sz, st)
+                               : gather_lu_t<double>(XL, XU, vmap, flip, nnz, upper, out, sz, st);
 }
 
 template <class T>
@@ -469,13 +647,17 @@ static cudaError_t tiles_tb(Kern k, const KArgs& a, const Task* t, int64_t n, cu
       break;
     case Kern::Schur:
       k_schur<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, a.desc, a.relidx, (T*)a.L, (const T*)a.D,
-                                                  (const T*)a.Lhat, a.sz);
+                                                  (const T*)a.Lhat, (const T*)(a.Uhat ? a.Uhat : a.Lhat),
+                                                  a.strict, a.sz);
       break;
     case Kern::Lhat:
       k_lhat<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.L, (const T*)a.Linv, (T*)a.Lhat, a.sz);
       break;
     case Kern::Gemm1:
-      k_gemm1<T, BN><<<grid, TG_THREADS, 0, st>>>(a, t);
+      if (a.XU)
+        k_gemm1<T, BN, true><<<grid, TG_THREADS, 0, st>>>(a, t);
+      else
+        k_gemm1<T, BN, false><<<grid, TG_THREADS, 0, st>>>(a, t);
       break;
     default:
       k_gemm2<T, BN><<<grid, TG_THREADS, 0, st>>>(a, t);
@@ -519,6 +701,15 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
       break;
     case Kern::Gemm1Reduce:
       k_gemm1_reduce<T><<<dim3(nsn, a.sz.batch, 16), 256, 0, st>>>(a, sns);
+      break;
+    case Kern::FactorDiagLU:
+      k_factor_diag_lu<T><<<grid, 256, diag_smem_lu<T>(a.maxw), st>>>(a.meta, sns, (T*)a.L, (T*)a.U, (T*)a.D,
+                                                                      (T*)a.Linv, (T*)a.Uinv, a.sz, a.status);
+      break;
+    case Kern::NormDiagLU:
+      k_norm_diag_lu<T><<<grid, 256, diag_smem<T>(a.maxw), st>>>(a.meta, (const T*)a.L, (const T*)a.U,
+                                                                 (const T*)a.D, (T*)a.Linv, (T*)a.Uinv,
+                                                                 (T*)a.X, a.sz);
       break;
     default:
       k_diag_final<T><<<dim3(nsn, a.sz.batch, kFinishParts), 256, 0, st>>>(a, sns);

@@ -18,7 +18,10 @@ struct Sizes {
   int batch;
 };
 
-enum class Kern { Trsm, Schur, Lhat, Gemm1, Gemm2, FactorDiag, CopyBack, NormDiag, DiagFinal, Gemm1Reduce };
+enum class Kern {
+  Trsm, Schur, Lhat, Gemm1, Gemm2, FactorDiag, CopyBack, NormDiag, DiagFinal, Gemm1Reduce,
+  FactorDiagLU, NormDiagLU  // non-symmetric diagonal blocks
+};
 
 // Everything a kernel may need; device pointers typed by dtype inside.
 struct KArgs {
@@ -36,11 +39,27 @@ struct KArgs {
   void* ypart;
   int* status;
   Sizes sz;
+  // non-symmetric handles (nullptr / 0 for symmetric ones)
+  void* U;     // U panels: U'_{j,i} at panel position (i, j)
+  void* Uinv;  // (U'_KK^T)^{-1}, linv layout
+  void* Uhat;  // Uhat_{K,C}^T, lhat layout; Schur: second operand (nullptr = Lhat)
+  void* XU;    // XU panels: X_{j,i} at panel position (i, j); step 2 reads X_{C,C} above the
+               // diagonal from here, step 3 finish writes X_KK^T here
+  int strict;  // Schur: skip the diagonal entries of the updated blocks
 };
 
 cudaError_t setup_kernels();
 cudaError_t launch_scatter_values(int dtype, const void* vals, const int64_t* vmap, int64_t nnz, void* L,
                                   const Sizes& sz, cudaStream_t st);
+// Non-symmetric values: lower (A_ij) to the L panels, upper (A_ji) to the U
+// panels, swapped where flip[q] (the ordering transposed entry q).
+cudaError_t launch_scatter_values_lu(int dtype, const void* lower, const void* upper, const int64_t* vmap,
+                                     const uint8_t* flip, int64_t nnz, void* L, void* U, const Sizes& sz,
+                                     cudaStream_t st);
+// Non-symmetric gather: X_ij (upper = 0) or X_ji (upper = 1) at stored entry q.
+cudaError_t launch_gather_values_lu(int dtype, const void* XL, const void* XU, const int64_t* vmap,
+                                    const uint8_t* flip, int64_t nnz, int upper, void* out, const Sizes& sz,
+                                    cudaStream_t st);
 // diagmask == nullptr: plain gather; else off-diagonal entries doubled.
 cudaError_t launch_gather_values(int dtype, const void* X, const int64_t* vmap, const uint8_t* diagmask, int64_t nnz,
                                  void* out, const Sizes& sz, cudaStream_t st);

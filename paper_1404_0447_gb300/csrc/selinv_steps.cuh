@@ -33,7 +33,13 @@ __device__ __forceinline__ T ld_maybe_cg(const T* p, bool cg) {
 // diagonal use the symmetric one.  Unsplit supernodes write rows s.. of K's
 // own X panel (Algorithm 3 overwrites Lhat by X_{C,K}; here Lhat stays in its
 // own buffer); split ones write their slice's partial product.
-template <class T, int BN>
+//
+// UNSYM (non-symmetric A): entry (i, k) with i < k is X_{C[i],C[k]}, read
+// from the XU panels at the same position.  Step 4 of Algorithm 1 in
+// transposed form, X_{K,C}^T = -X_{C,C}^T Uhat_{K,C}^T, is this same tile
+// with X and XU swapped and Uhat^T in place of Lhat: it then writes the XU
+// panel rows.
+template <class T, int BN, bool UNSYM = false>
 __device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b, TileSmem<T, BN>& sm) {
   const Sizes& sz = a.sz;
   const SnMeta m = a.meta[tk.sn];
@@ -41,6 +47,7 @@ __device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b
   const ColDesc* dk = a.desc + m.desc;
   const int32_t* relidx = a.relidx;
   const T* Xb = (const T*)a.X + b * sz.panel;
+  const T* XUb = UNSYM ? (const T*)a.XU + b * sz.panel : Xb;
   const T* Lh = (const T*)a.Lhat + b * sz.lhat + m.lhat;
   Acc<T, BN> acc;
   acc_zero<T, BN>(acc);
@@ -49,6 +56,7 @@ __device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b
     if (i >= r) return Sc<T>::zero();
     const int lo = i < kk ? i : kk, hi = i < kk ? kk : i;
     const ColDesc cd = dk[lo];
+    if constexpr (UNSYM) return (i < kk ? XUb : Xb)[cd.col + relidx[cd.rel + hi]];
     return Xb[cd.col + relidx[cd.rel + hi]];
   };
   auto lb = [&](int kk, int nn) {
@@ -128,6 +136,8 @@ __device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b
 // Step 3 finish: X_KK = (Z + Z^T) / 2 with Z = M_K - sum_c P_c (the
 // symmetrisation at the end of Section 2.1 / Algorithm 3).  One thread per
 // unordered pair {i, j} reads and writes exactly (i, j) and (j, i).
+// Non-symmetric handles (a.XU set): X_KK = Z as it is, and Z^T goes to the
+// diagonal block of the XU panel.
 template <class T>
 __device__ __forceinline__ void step3_finish(const KArgs& a, int k, int b, int part, int nparts, bool cg) {
   const Sizes& sz = a.sz;
@@ -135,6 +145,17 @@ __device__ __forceinline__ void step3_finish(const KArgs& a, int k, int b, int p
   const int s = m.s, ld = m.s + m.r;
   T* XK = (T*)a.X + b * sz.panel + m.panel;
   const T* pp = (const T*)a.part + b * sz.part + m.part;
+  if (a.XU) {
+    T* XUK = (T*)a.XU + b * sz.panel + m.panel;
+    for (int e = threadIdx.x + part * blockDim.x; e < s * s; e += nparts * blockDim.x) {
+      const int i = e % s, j = e / s;
+      T z = XK[i + (int64_t)j * ld];
+      for (int c = 0; c < m.nchunk; ++c) z -= ld_maybe_cg(pp + (int64_t)c * s * s + i + j * s, cg);
+      XK[i + (int64_t)j * ld] = z;
+      XUK[j + (int64_t)i * ld] = z;
+    }
+    return;
+  }
   // the CTAs part = 0..nparts-1 share the pairs of one supernode
   for (int e = threadIdx.x + part * blockDim.x; e < s * s; e += nparts * blockDim.x) {
     const int i = e % s, j = e / s;
