@@ -245,6 +245,25 @@ int pselinv_factor_unsym(pselinv_handle* h, const void* d_lower, const void* d_u
 int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream);
 
 /*
+ * Selected inversion with the result streamed to host memory: the LEVEL
+ * schedule of pselinv_selinv, and on an internal copy stream the X panels of
+ * every level copied to h_x as soon as that level of Algorithm 2 has
+ * finished (its supernodes' panels are final then), so the device-to-host
+ * transfer overlaps the rest of the sweep; the deepest levels, whose many
+ * small supernodes are scattered through the panel array, are copied after
+ * the last level.  The paper keeps X distributed and has no counterpart.
+ *
+ * h_x   host, batch x panel_entries elements (the layout of
+ *       pselinv_get_panels(which = 0)); pinned memory gives the overlap,
+ *       pageable memory works but serialises the copies with the sweep
+ * h_xu  non-symmetric handles: the XU panels likewise (NULL = not copied);
+ *       must be NULL on symmetric handles
+ * When `stream` completes, both the device panels and the host copies are
+ * complete.  Enqueues work only.  ERR_STATE before factor.
+ */
+int pselinv_selinv_to_host(pselinv_handle* h, void* h_x, void* h_xu, void* stream);
+
+/*
  * Copy panels to caller memory: which = 0 for X (after selinv), 1 for L
  * (after factor; unit diagonal not stored, D on the diagonal positions);
  * non-symmetric handles also 2 for the XU panels (X_{j,i} at position

@@ -24,7 +24,7 @@ PLAIN, LEVEL, GRAPH, PERSISTENT = 0, 1, 2, 3
 G_SYMMETRIC, G_PANEL = 0, 1
 
 EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_analyze_batch", "pselinv_factor",
-            "pselinv_factor_unsym", "pselinv_selinv", "pselinv_get_panels", "pselinv_pole_sum", "pselinv_trace_sum",
+            "pselinv_factor_unsym", "pselinv_selinv", "pselinv_selinv_to_host", "pselinv_get_panels", "pselinv_pole_sum", "pselinv_trace_sum",
             "pselinv_sync_status", "pselinv_set_debug", "pselinv_get_selected", "pselinv_get_selected_upper",
             "pselinv_logdet_grad", "pselinv_logdet",
             "pselinv_selinv_adjoint",
@@ -84,6 +84,7 @@ def load_library():
     L.pselinv_factor.argtypes = [vp, vp, vp]
     L.pselinv_factor_unsym.argtypes = [vp, vp, vp, vp]
     L.pselinv_selinv.argtypes = [vp, ctypes.c_int32, vp]
+    L.pselinv_selinv_to_host.argtypes = [vp, vp, vp, vp]
     L.pselinv_get_panels.argtypes = [vp, ctypes.c_int32, vp, vp]
     L.pselinv_sync_status.argtypes = [vp, vp]
     L.pselinv_pole_sum.argtypes = [vp, vp, vp, vp]
@@ -225,6 +226,19 @@ class SelInv:
 
     def selinv(self, mode=LEVEL, stream=None):
         self._check(self._lib.pselinv_selinv(self._h, int(mode), _stream_ptr(stream)))
+
+    def selinv_to_host(self, out, out_u=None, stream=None):
+        """pselinv_selinv_to_host: LEVEL selinv with the X panels (and XU for
+        non-symmetric handles) copied level by level into pinned CPU tensors
+        of batch x panel_entries elements while the sweep runs."""
+        n = self.opts.batch * self.info["panel_entries"]
+        for o in (out, out_u):
+            assert o is None or (o.device.type == "cpu" and o.numel() == n and o.dtype == self.torch_dtype
+                                 and o.is_contiguous())
+        self._check(self._lib.pselinv_selinv_to_host(
+            self._h, ctypes.c_void_p(out.data_ptr()), None if out_u is None else ctypes.c_void_p(out_u.data_ptr()),
+            _stream_ptr(stream)))
+        return out.view(self.opts.batch, -1)
 
     def pole_sum(self, weights, out=None, stream=None):
         """pselinv_pole_sum: sum_b w_b X_b over the batch (X panel layout)."""

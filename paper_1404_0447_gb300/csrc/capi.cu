@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <functional>
 #include <string>
 
 #include "internal.h"
@@ -81,12 +82,17 @@ void free_device(pselinv_handle* h) {
   if (h->pgraph_exec) cudaGraphExecDestroy((cudaGraphExec_t)h->pgraph_exec);
   if (h->graph_stream) cudaStreamDestroy((cudaStream_t)h->graph_stream);
   h->graph_exec = h->pgraph_exec = h->graph_stream = nullptr;
+  for (void* e : h->xfer_ev) cudaEventDestroy((cudaEvent_t)e);
+  h->xfer_ev.clear();
+  if (h->xfer_stream) cudaStreamDestroy((cudaStream_t)h->xfer_stream);
+  h->xfer_stream = nullptr;
   h->dev_sym = false;
   h->device_bytes = 0;
 }
 
 int upload_schedule(pselinv_handle* h);
-int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record);
+int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
+                   const std::function<int(int32_t)>* after_level = nullptr);
 const psi::Task* tasks_at(const pselinv_handle* h, int64_t base, int64_t off);
 psi::KArgs kargs(pselinv_handle* h);
 psi::KArgs kargs_uside(pselinv_handle* h);
@@ -288,7 +294,8 @@ struct Timer {
 };
 
 // Enqueue one schedule of the selected inversion on stream st.
-int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record) {
+int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
+                   const std::function<int(int32_t)>* after_level) {
   using psi::Kern;
   const psi::KArgs a = kargs(h);
   const auto* lsn = (const int32_t*)h->d_levelsn;
@@ -356,13 +363,67 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record) {
       if ((rc = step(lsn + pos[k], 1, r1, r2, h->meta[k].ksplit > 1))) return rc;
     }
   } else {
-    for (int32_t l = 0; l < h->nlevels; ++l)
+    for (int32_t l = 0; l < h->nlevels; ++l) {
       if ((rc = step(lsn + h->level_ptr[l], h->level_ptr[l + 1] - h->level_ptr[l],
                      &h->t_gemm1.per_lv[(size_t)l * psi::kNumVar], &h->t_gemm2.per_lv[(size_t)l * psi::kNumVar],
                      h->level_split[l] != 0)))
         return rc;
+      if (after_level && (rc = (*after_level)(l))) return rc;
+    }
   }
   return PSELINV_OK;
+}
+
+// Copy plan of pselinv_selinv_to_host.  The panels of a level's supernodes
+// are final once that level's step 3 (and step 4) have run.  Levels whose
+// supernodes form at most kXferRuns runs of adjacent panels are copied right
+// after the level; the rest (the deep levels with thousands of scattered
+// small supernodes) are copied after the last level as runs merged across
+// gaps of already-copied panels shorter than kXferGap elements.
+void build_xfer_plan(pselinv_handle* h) {
+  constexpr int64_t kXferRuns = 1024, kXferGap = 1 << 17;
+  h->xfer_off.clear();
+  h->xfer_len.clear();
+  h->xfer_ptr.assign(1, 0);
+  std::vector<uint8_t> done(h->nsn, 0);
+  std::vector<int32_t> s;
+  for (int32_t l = 0; l < h->nlevels; ++l) {
+    s.assign(h->level_sn.begin() + h->level_ptr[l], h->level_sn.begin() + h->level_ptr[l + 1]);
+    std::sort(s.begin(), s.end());
+    int64_t runs = s.empty() ? 0 : 1;
+    for (size_t q = 1; q < s.size(); ++q) runs += s[q] != s[q - 1] + 1;
+    if (runs <= kXferRuns) {
+      for (size_t q = 0; q < s.size();) {
+        size_t e = q + 1;
+        while (e < s.size() && s[e] == s[e - 1] + 1) ++e;
+        h->xfer_off.push_back(h->panel_off[s[q]]);
+        h->xfer_len.push_back(h->panel_off[s[e - 1] + 1] - h->panel_off[s[q]]);
+        for (size_t t = q; t < e; ++t) done[s[t]] = 1;
+        q = e;
+      }
+    }
+    h->xfer_ptr.push_back((int32_t)h->xfer_off.size());
+  }
+  int64_t b = -1, e = -1;  // current tail range [b, e) in elements
+  for (int32_t k = 0; k < h->nsn; ++k) {
+    if (done[k]) continue;
+    const int64_t kb = h->panel_off[k], ke = h->panel_off[k + 1];
+    if (b >= 0 && kb - e < kXferGap) {
+      e = ke;
+    } else {
+      if (b >= 0) {
+        h->xfer_off.push_back(b);
+        h->xfer_len.push_back(e - b);
+      }
+      b = kb;
+      e = ke;
+    }
+  }
+  if (b >= 0) {
+    h->xfer_off.push_back(b);
+    h->xfer_len.push_back(e - b);
+  }
+  h->xfer_ptr.push_back((int32_t)h->xfer_off.size());
 }
 
 }  // namespace
@@ -619,6 +680,59 @@ int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream) {
     PSI_CUDA(h, cudaGraphLaunch((cudaGraphExec_t)h->graph_exec, st));
     for (int q = 0; q < 4; ++q) h->launches[q] += h->graph_launches[q];
   }
+  h->inverted = true;
+  return PSELINV_OK;
+}
+
+int pselinv_selinv_to_host(pselinv_handle* h, void* h_x, void* h_xu, void* stream) {
+  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
+  if (!h_x) return set_err(h, PSELINV_ERR_ARG, "h_x is NULL");
+  if (h_xu && !h->opts.unsym) return set_err(h, PSELINV_ERR_ARG, "h_xu is for non-symmetric handles");
+  if (!h->factored) return set_err(h, PSELINV_ERR_STATE, "selinv called before a successful factor");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->xfer_ev.empty()) {
+    build_xfer_plan(h);
+    cudaStream_t cs;
+    PSI_CUDA(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    h->xfer_stream = cs;
+    for (int32_t l = 0; l <= h->nlevels; ++l) {
+      cudaEvent_t ev;
+      PSI_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      h->xfer_ev.push_back((void*)ev);
+    }
+  }
+  cudaStream_t cs = (cudaStream_t)h->xfer_stream;
+  const size_t es = elem_size(h), pitch = es * (size_t)h->panel_total;
+  const int B = h->opts.batch;
+  auto copy_ranges = [&](int32_t q0, int32_t q1) -> int {
+    for (int32_t q = q0; q < q1; ++q)
+      for (int side = 0; side < (h_xu ? 2 : 1); ++side) {
+        const size_t o = es * (size_t)h->xfer_off[q];
+        char* dst = (char*)(side ? h_xu : h_x) + o;
+        const char* src = (const char*)(side ? h->d_XU : h->d_X) + o;
+        PSI_CUDA(h, cudaMemcpy2DAsync(dst, pitch, src, pitch, es * (size_t)h->xfer_len[q], B, cudaMemcpyDefault,
+                                      cs));
+      }
+    return PSELINV_OK;
+  };
+  // the copy stream must not start before the work already queued on st
+  PSI_CUDA(h, cudaEventRecord((cudaEvent_t)h->xfer_ev[h->nlevels], st));
+  PSI_CUDA(h, cudaStreamWaitEvent(cs, (cudaEvent_t)h->xfer_ev[h->nlevels], 0));
+  const std::function<int(int32_t)> after = [&](int32_t l) -> int {
+    if (h->xfer_ptr[l + 1] == h->xfer_ptr[l]) return PSELINV_OK;
+    PSI_CUDA(h, cudaEventRecord((cudaEvent_t)h->xfer_ev[l], st));
+    PSI_CUDA(h, cudaStreamWaitEvent(cs, (cudaEvent_t)h->xfer_ev[l], 0));
+    return copy_ranges(h->xfer_ptr[l], h->xfer_ptr[l + 1]);
+  };
+  int rc = enqueue_selinv(h, PSELINV_LEVEL, st, h->timing, &after);
+  if (rc) return rc;
+  // tail: after the last level
+  PSI_CUDA(h, cudaEventRecord((cudaEvent_t)h->xfer_ev[h->nlevels], st));
+  PSI_CUDA(h, cudaStreamWaitEvent(cs, (cudaEvent_t)h->xfer_ev[h->nlevels], 0));
+  if ((rc = copy_ranges(h->xfer_ptr[h->nlevels], h->xfer_ptr[h->nlevels + 1]))) return rc;
+  // st completes after every copy
+  PSI_CUDA(h, cudaEventRecord((cudaEvent_t)h->xfer_ev[h->nlevels], cs));
+  PSI_CUDA(h, cudaStreamWaitEvent(st, (cudaEvent_t)h->xfer_ev[h->nlevels], 0));
   h->inverted = true;
   return PSELINV_OK;
 }

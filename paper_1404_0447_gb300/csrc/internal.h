@@ -182,6 +182,11 @@ struct pselinv_handle {
   int debug_flags = 0;
   void* graph_exec = nullptr;  // cudaGraphExec_t of the LEVEL schedule
   void* graph_stream = nullptr;
+  // pselinv_selinv_to_host: per-level copy plan of finished X panels
+  std::vector<int64_t> xfer_off, xfer_len;  // element ranges of one panel array
+  std::vector<int32_t> xfer_ptr;            // [nlevels + 2]: level l's ranges, then the tail
+  void* xfer_stream = nullptr;              // copy stream (cudaStream_t)
+  std::vector<void*> xfer_ev;               // [nlevels + 1] cudaEvent_t
 
   // optional kernel timing (pselinv_set_timing)
   bool timing = false;

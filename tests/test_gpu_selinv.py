@@ -233,6 +233,42 @@ def test_panels_into_pinned_host_memory(P):
     assert torch.equal(host, h.panels(0)[0].cpu())
 
 
+@pytest.mark.parametrize("case", ["grid48", "poles", "unsym"])
+def test_selinv_to_host_matches_device_panels(P, case):
+    """pselinv_selinv_to_host: the level-by-level host copies (including the
+    deferred tail of levels with more than 1024 runs of panels, which 48^3
+    has) reproduce the device panels bit for bit and cover every entry."""
+    import torch
+    if case == "grid48":
+        p = synth.config1(side=48)
+        h = P.SelInv(p.n, p.colptr, p.rowind)
+        h.factor(torch_vals(p.values))
+    elif case == "poles":
+        p = synth.grid_problem((14, 13, 12), 0.01, 0.1, 4)
+        z = np.array([0.3 + 0.2j, -0.1 + 0.05j])
+        vals = np.stack([p.values.astype(np.complex128) for _ in z])
+        diag = np.asarray(p.colptr[:-1])
+        vals[:, diag] -= z[:, None]
+        h = P.SelInv(p.n, p.colptr, p.rowind, dtype=P.C128, batch=2)
+        h.factor(torch.tensor(vals, device="cuda").view(-1))
+    else:
+        p = synth.convdiff_problem(dims=(20, 18, 16))
+        h = P.SelInv(p.n, p.colptr, p.rowind, unsym=1)
+        h.factor_unsym(torch_vals(p.values), torch_vals(p.values_up))
+    n = h.opts.batch * h.info["panel_entries"]
+    out = torch.full((n,), float("nan"), dtype=h.torch_dtype).pin_memory()
+    out_u = torch.full((n,), float("nan"), dtype=h.torch_dtype).pin_memory() if case == "unsym" else None
+    for _ in range(2):
+        h.selinv_to_host(out, out_u)
+        torch.cuda.synchronize()
+        assert torch.equal(out, h.panels(0).view(-1).cpu())
+        if out_u is not None:
+            assert torch.equal(out_u, h.panels(2).view(-1).cpu())
+        out.fill_(float("nan"))
+        if out_u is not None:
+            out_u.fill_(float("nan"))
+
+
 def test_runs_are_bitwise_deterministic(P):
     import torch
     p = synth.config1(side=20)
