@@ -522,3 +522,192 @@ def dense_adjoint(Ainv, G):
     """d<G, P_S(A^{-1})>/dA = -(A^{-1} G A^{-1}) (bilinear pairing, plain
     transpose), as a dense matrix; callers restrict it to A's pattern."""
     return -(Ainv @ G @ Ainv)
+
+
+# --------------------------------------------------------------------------
+# symmetric indefinite: Bunch-Kaufman pivots inside supernodes
+# --------------------------------------------------------------------------
+
+BK_ALPHA = (1.0 + math.sqrt(17.0)) / 8.0
+
+
+def _cabs1(x):
+    """|re| + |im| (the magnitude Bunch-Kaufman compares for complex data)."""
+    return np.abs(np.real(x)) + np.abs(np.imag(x))
+
+
+def bk_block(W):
+    """Bunch-Kaufman factorisation of one dense symmetric block (Bunch and
+    Kaufman 1977, in the lower-triangle form of LAPACK's xSYTF2), with every
+    interchange applied to the whole block so that
+
+        W[p][:, p] = L D L^T,   L unit lower triangular, D block diagonal
+        with 1x1 and 2x2 blocks (L is zero beside each 2x2 block).
+
+    Column k of the reduced block: a = |W_kk|, colmax = max_{i>k} |W_ik| at
+    imax.  a >= alpha colmax: 1x1 pivot.  Otherwise, with rowmax the largest
+    off-diagonal magnitude in row/column imax of the reduced block:
+    a rowmax >= alpha colmax^2 ->
+    1x1; |W_imax,imax| >= alpha rowmax -> 1x1 after swapping k and imax;
+    else 2x2 on (k, k+1) after swapping k+1 and imax.  alpha = (1+sqrt 17)/8.
+    Returns (p, L, d, e, ptype): p[t] = original index at pivot position t;
+    d the diagonal of D; e[t] = D[t+1, t] at the first column of a 2x2 block
+    (0 elsewhere); ptype[t] = 0 (1x1), 1 (first of a 2x2), 2 (second).
+    Raises ZeroDivisionError(k) when the reduced column k is entirely zero.
+    """
+    W = np.array(W, dtype=np.result_type(W, np.float64), copy=True)
+    s = W.shape[0]
+    p = np.arange(s)
+    d = np.zeros(s, W.dtype)
+    e = np.zeros(s, W.dtype)
+    ptype = np.zeros(s, np.int8)
+    k = 0
+    while k < s:
+        absakk = _cabs1(W[k, k])
+        if k + 1 < s:
+            col = _cabs1(W[k + 1:, k])
+            imax = k + 1 + int(np.argmax(col))
+            colmax = float(col.max())
+        else:
+            imax, colmax = k, 0.0
+        if max(absakk, colmax) == 0.0 or not np.isfinite(absakk) or not np.isfinite(colmax):
+            raise ZeroDivisionError(k)
+        kstep, kp = 1, k
+        if absakk < BK_ALPHA * colmax:
+            rowmax = float(_cabs1(W[imax, k:imax]).max())
+            if imax + 1 < s:
+                rowmax = max(rowmax, float(_cabs1(W[imax + 1:, imax]).max()))
+            if absakk * rowmax >= BK_ALPHA * colmax * colmax:
+                kp = k
+            elif _cabs1(W[imax, imax]) >= BK_ALPHA * rowmax:
+                kp = imax
+            else:
+                kp, kstep = imax, 2
+        kk = k + kstep - 1
+        if kp != kk:                      # symmetric interchange of kk and kp
+            W[[kk, kp], :] = W[[kp, kk], :]
+            W[:, [kk, kp]] = W[:, [kp, kk]]
+            p[[kk, kp]] = p[[kp, kk]]
+        if kstep == 1:
+            dk = W[k, k]
+            col = W[k + 1:, k].copy()
+            W[k + 1:, k + 1:] -= np.outer(col, col) / dk
+            W[k + 1:, k] = col / dk
+            d[k] = dk
+        else:
+            D2 = W[k:k + 2, k:k + 2].copy()
+            det = D2[0, 0] * D2[1, 1] - D2[1, 0] * D2[1, 0]
+            if det == 0 or not np.isfinite(det):
+                raise ZeroDivisionError(k)
+            Wc = W[k + 2:, k:k + 2].copy()
+            Lc = Wc @ np.linalg.inv(D2)
+            W[k + 2:, k + 2:] -= Lc @ Wc.T
+            W[k + 2:, k:k + 2] = Lc
+            W[k + 1, k] = 0
+            d[k], d[k + 1], e[k] = D2[0, 0], D2[1, 1], D2[1, 0]
+            ptype[k], ptype[k + 1] = 1, 2
+        k += kstep
+    L = np.tril(W, -1) + np.eye(s, dtype=W.dtype)
+    return p, L, d, e, ptype
+
+
+def block_d(d, e, ptype):
+    """Dense D from its diagonal, 2x2 off-diagonals and pivot types."""
+    D = np.diag(np.asarray(d))
+    for t in np.nonzero(np.asarray(ptype) == 1)[0]:
+        D[t + 1, t] = D[t, t + 1] = e[t]
+    return D
+
+
+def selected_inverse_bk(n, colptr, rowind, values, wmax=0, relax=0):
+    """Supernodal LDL^T with Bunch-Kaufman pivoting restricted to each
+    supernode's diagonal block (interchanges only among a supernode's own
+    columns, so the supernodal structure is unchanged), then Algorithm 1 on
+    the pivoted factor.  Dense n x n working storage: small n only.
+
+    Factor, supernodes in column order (right-looking, Section 2.1 with the
+    2x2 blocks of D allowed): W = S_KK -> bk_block -> p_K, L_KK, D_K;
+    L_CK = S_{C, K p_K} L_KK^{-T} D_K^{-1}; S_CC -= L_CK D_K L_CK^T.
+    Selected inversion, supernodes in reverse order: V = L_KK^{-1},
+    Lhat = L_CK V, Y = -X_CC Lhat, Z = V^T D_K^{-1} V - Lhat^T Y,
+    X_KK = (Z + Z^T)/2 -- all in K's pivot order -- stored back at K's
+    original columns (X_{C, K p_K} = Y, X_{K p_K, K p_K} = X_KK).
+
+    Returns (sym, X, fac): X dense in the analysis order (entries on the
+    supernodal pattern), fac = per-supernode dict list with p (local pivot
+    order), L_KK, L_CK, d, e, ptype."""
+    sym = analyse(n, colptr, rowind, wmax, relax)
+    cp, ri = sym["colptr"], sym["rowind"]
+    vals = values
+    if not np.array_equal(sym["post"], np.arange(n)):
+        from synth import permute_lower
+        _, _, vals, _ = permute_lower(n, colptr, rowind, values, sym["post"])
+    S = dense_from_lower(n, cp, ri, vals)
+    sn = sym["sn_start"]
+    roff = np.concatenate([[0], np.cumsum(sym["rcount"])]).astype(np.int64)
+    fac = []
+    for K in range(len(sn) - 1):
+        f, l = int(sn[K]), int(sn[K + 1])
+        C = sym["rrows"][roff[K]:roff[K + 1]].astype(np.int64)
+        try:
+            p, Lkk, d, e, pt = bk_block(S[f:l, f:l])
+        except ZeroDivisionError as z:
+            raise ZeroDivisionError(f"zero pivot block at column {f + z.args[0]}")
+        cols = f + p
+        D = block_d(d, e, pt)
+        LC = np.linalg.solve(D.T, np.linalg.solve(Lkk, S[np.ix_(C, cols)].T)).T if len(C) else \
+            np.zeros((0, l - f), S.dtype)
+        if len(C):
+            S[np.ix_(C, C)] -= LC @ D @ LC.T
+        fac.append(dict(p=p, L_KK=Lkk, L_CK=LC, d=d, e=e, ptype=pt, C=C))
+    X = np.zeros((n, n), S.dtype)
+    for K in reversed(range(len(sn) - 1)):
+        F = fac[K]
+        f = int(sn[K])
+        cols = f + F["p"]
+        C = F["C"]
+        V = np.linalg.inv(F["L_KK"])
+        M = V.T @ np.linalg.inv(block_d(F["d"], F["e"], F["ptype"])) @ V
+        if len(C):
+            Lhat = F["L_CK"] @ V
+            Y = -X[np.ix_(C, C)] @ Lhat
+            Z = M - Lhat.T @ Y
+            X[np.ix_(C, cols)] = Y
+            X[np.ix_(cols, C)] = Y.T
+        else:
+            Z = M
+        X[np.ix_(cols, cols)] = 0.5 * (Z + Z.T)
+    return sym, X, fac
+
+
+def panels_from_dense(sym, X):
+    """The library's panel layout of a dense X (rows cols(K) then R(K),
+    columns cols(K) in original order)."""
+    sn = sym["sn_start"]
+    roff = np.concatenate([[0], np.cumsum(sym["rcount"])]).astype(np.int64)
+    out = []
+    for K in range(len(sn) - 1):
+        f, l = int(sn[K]), int(sn[K + 1])
+        rows = np.concatenate([np.arange(f, l), sym["rrows"][roff[K]:roff[K + 1]]])
+        out.append(X[np.ix_(rows, np.arange(f, l))].ravel(order="F"))
+    return np.concatenate(out) if out else np.zeros(0, X.dtype)
+
+
+def logdet_bk(fac):
+    """log det A from the pivoted factor: sum of log|d| over 1x1 blocks and
+    log|det| over 2x2 blocks; real: (value, number of negative determinants),
+    complex: (re, im) of the sum of principal logs."""
+    re, im = 0.0, 0.0
+    for F in fac:
+        d, e, pt = F["d"], F["e"], F["ptype"]
+        for t in range(len(d)):
+            if pt[t] == 2:
+                continue
+            v = d[t] * d[t + 1] - e[t] * e[t] if pt[t] == 1 else d[t]
+            if np.iscomplexobj(v):
+                re += math.log(abs(v))
+                im += float(np.angle(v))
+            else:
+                re += math.log(abs(v))
+                im += 1.0 if v < 0 else 0.0
+    return np.array([re, im])
