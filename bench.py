@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="grid3d_80",
-                    choices=["grid3d_80", "grid2d_31", "graphlap48", "dg_poles", "uneven48", "convdiff80"],
+                    choices=["grid3d_80", "grid2d_31", "graphlap48", "dg_poles", "uneven48", "convdiff80",
+                             "indefinite80"],
                     help="grid3d_80 is the headline; the others measure the remaining workload families")
     ap.add_argument("--poles", type=int, default=16, help="dg_poles: number of poles in the batch")
     ap.add_argument("--split-k-rows", type=int, default=None, help="override the library default")
@@ -392,6 +393,13 @@ def run_workload(args):
         vals = torch.tensor(synth.shifted_values(n, cp, ri, hv, z), dtype=torch.complex128, device=dev)
         cplx = True
         line["poles"] = len(z)
+    elif w == "indefinite80":
+        # symmetric indefinite: the 80^3 grid Laplacian shifted by -0.5 into its spectrum
+        # (2,908 negative eigenvalues), factored with Bunch-Kaufman 1x1/2x2 pivots inside supernodes
+        p = synth.config1(80, shift_const=-0.5)
+        h = P.SelInv(p.n, p.colptr, p.rowind, **tuning(args))
+        vals = torch.tensor(p.values, dtype=torch.float64, device=dev)
+        cplx = False
     elif w == "convdiff80":
         # non-symmetric: 80^3 upwind convection-diffusion, A = L D U', Algorithm 1 with step 4
         p = synth.convdiff_problem(80)
@@ -410,6 +418,7 @@ def run_workload(args):
     line["flops_per_selinv"] = flops
     unsym = w == "convdiff80"
     factor = ((lambda: h.factor_unsym(vals, vals_up, stream=st)) if unsym
+              else (lambda: h.factor_bk(vals, stream=st)) if w == "indefinite80"
               else (lambda: h.factor(vals.view(-1), stream=st)))
     with torch.cuda.stream(st):
         factor()
@@ -433,6 +442,17 @@ def run_workload(args):
         line["pole_sum_ms"] = _time(lambda: h.pole_sum(wts, out=gam, stream=st), 3, 1, st)
         line["pole_sum_GBps"] = (info["batch"] + 1) * info["panel_entries"] * 16 / (line["pole_sum_ms"] * 1e-3) / 1e9
         line["trace_E_per_pole"] = [float(e) for e in h.trace_error(vals.view(-1), stream=st)]
+    if w == "indefinite80":
+        piv, ty = h.pivots(stream=st)
+        line["pivots_2x2"] = int((ty == 1).sum())
+        line["pivots_interchanged"] = int(np.sum(piv[0] != (np.arange(p.n) - np.repeat(
+            np.asarray(h.symbolic()["sn_start"][:-1]), np.diff(h.symbolic()["sn_start"])))))
+        h.set_timing(True)
+        h.selinv(P.LEVEL, stream=st)
+        kms, kl = h.get_timing()
+        h.set_timing(False)
+        line["step2_tflops"] = info["flops_gemm1"] / (kms[1] * 1e-3) / 1e12
+        line["step2_frac_of_fp64_peak"] = line["step2_tflops"] / FP64_PEAK_TFLOPS
     if unsym:
         # kernel classes of one level-schedule selinv: steps 2 and 4 are class 1
         h.set_timing(True)

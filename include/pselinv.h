@@ -215,6 +215,39 @@ int pselinv_analyze_batch(int32_t k, const int64_t* h_n, const int64_t* const* h
 int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream);
 
 /*
+ * Numeric factorisation A = P L D L^T P^T of a symmetric indefinite A with
+ * Bunch-Kaufman 1x1/2x2 pivots (Bunch and Kaufman 1977, the accuracy remedy
+ * of Section 4 and the conclusions) restricted to each supernode's diagonal
+ * block: P only permutes the columns of a supernode among themselves, so the
+ * symbolic analysis, the panels and every schedule stay as they are.  Per
+ * supernode, at pivot position k of the reduced diagonal block: a = |T_kk|,
+ * colmax = max_{i>k} |T_ik| at imax (|re| + |im| for complex); a >= alpha
+ * colmax -> 1x1; else, rowmax = the largest off-diagonal magnitude of
+ * row/column imax: a rowmax >= alpha colmax^2 -> 1x1; |T_imax,imax| >= alpha
+ * rowmax -> 1x1 after a symmetric interchange of k and imax; else a 2x2 pivot
+ * on (k, k+1) after interchanging k+1 and imax; alpha = (1 + sqrt 17) / 8
+ * (LAPACK xSYTF2's rule, applied inside the block).  The L panels then hold
+ * each supernode's columns in pivot order (L zero beside a 2x2 block, D's
+ * diagonal on the diagonal slots); the selected inversion undoes the order,
+ * so X, pselinv_get_selected, pselinv_logdet and pselinv_logdet_grad are as
+ * for pselinv_factor.  pselinv_selinv_adjoint needs the pivot-free factor.
+ * d_values as for pselinv_factor.  Errors: ERR_ZERO_PIVOT for a reduced
+ * column that is entirely zero or a singular 2x2 block (first column, internal
+ * order), ERR_NONFINITE, ERR_STATE on non-symmetric handles.  Synchronises
+ * once at the end.
+ */
+int pselinv_factor_bk(pselinv_handle* h, const void* d_values, void* stream);
+
+/*
+ * Pivots of the last pselinv_factor_bk, host arrays of batch x n (internal
+ * column order, member-major): h_piv[b * n + j] = the supernode-local
+ * original column at pivot position j - first(K) of its supernode K;
+ * h_type = 0 for a 1x1 pivot, 1 and 2 for the first and second column of a
+ * 2x2 pivot.  Synchronises.  ERR_STATE without a pivoted factor.
+ */
+int pselinv_get_pivots(pselinv_handle* h, int32_t* h_piv, int8_t* h_type, void* stream);
+
+/*
  * Numeric factorisation of a non-symmetric A with a symmetric pattern
  * (handle analysed with opts.unsym = 1): A = L D U', supernodal, level by
  * level from the leaves, no pivoting.  Per supernode K: the diagonal block

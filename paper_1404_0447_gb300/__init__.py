@@ -24,7 +24,8 @@ PLAIN, LEVEL, GRAPH, PERSISTENT = 0, 1, 2, 3
 G_SYMMETRIC, G_PANEL = 0, 1
 
 EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_analyze_batch", "pselinv_factor",
-            "pselinv_factor_unsym", "pselinv_selinv", "pselinv_selinv_to_host", "pselinv_get_panels", "pselinv_pole_sum", "pselinv_trace_sum",
+            "pselinv_factor_unsym", "pselinv_factor_bk", "pselinv_get_pivots", "pselinv_selinv",
+            "pselinv_selinv_to_host", "pselinv_get_panels", "pselinv_pole_sum", "pselinv_trace_sum",
             "pselinv_sync_status", "pselinv_set_debug", "pselinv_get_selected", "pselinv_get_selected_upper",
             "pselinv_logdet_grad", "pselinv_logdet",
             "pselinv_selinv_adjoint",
@@ -83,6 +84,8 @@ def load_library():
     L.pselinv_analyze_batch.argtypes = [ctypes.c_int32, vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
     L.pselinv_factor.argtypes = [vp, vp, vp]
     L.pselinv_factor_unsym.argtypes = [vp, vp, vp, vp]
+    L.pselinv_factor_bk.argtypes = [vp, vp, vp]
+    L.pselinv_get_pivots.argtypes = [vp, vp, vp, vp]
     L.pselinv_selinv.argtypes = [vp, ctypes.c_int32, vp]
     L.pselinv_selinv_to_host.argtypes = [vp, vp, vp, vp]
     L.pselinv_get_panels.argtypes = [vp, ctypes.c_int32, vp, vp]
@@ -214,6 +217,19 @@ class SelInv:
         assert values.is_cuda and values.dtype == self.torch_dtype and values.is_contiguous()
         assert values.numel() == self.opts.batch * self.info["nnz_a"]
         self._check(self._lib.pselinv_factor(self._h, ctypes.c_void_p(values.data_ptr()), _stream_ptr(stream)))
+
+    def factor_bk(self, values, stream=None):
+        """pselinv_factor_bk: LDL^T with Bunch-Kaufman 1x1/2x2 pivots inside supernodes."""
+        assert values.is_cuda and values.dtype == self.torch_dtype and values.is_contiguous()
+        assert values.numel() == self.opts.batch * self.info["nnz_a"]
+        self._check(self._lib.pselinv_factor_bk(self._h, ctypes.c_void_p(values.data_ptr()), _stream_ptr(stream)))
+
+    def pivots(self, stream=None):
+        """(local pivot order, pivot type) of the last factor_bk, [batch, n] numpy arrays."""
+        piv = np.zeros(self.opts.batch * self.n, np.int32)
+        ty = np.zeros(self.opts.batch * self.n, np.int8)
+        self._check(self._lib.pselinv_get_pivots(self._h, _ptr(piv), _ptr(ty), _stream_ptr(stream)))
+        return piv.reshape(self.opts.batch, -1), ty.reshape(self.opts.batch, -1)
 
     def factor_unsym(self, lower, upper, stream=None):
         """pselinv_factor_unsym: A_ij (``lower``) and A_ji (``upper``) at the

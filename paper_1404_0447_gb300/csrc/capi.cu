@@ -15,7 +15,7 @@ namespace {
 
 thread_local std::string g_last_err = "no error";
 constexpr int kStatusWords = 8;   // [0] first bad pivot column, [1] kind, rest spare
-constexpr int kStatusUnset = 0x7f7f7f7f;
+constexpr unsigned long long kPivotKeyUnset = 0x7f7f7f7f7f7f7f7full;  // status words 0-1, see report_pivot
 
 int set_err(pselinv_handle* h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -68,6 +68,7 @@ void free_device(pselinv_handle* h) {
   void** ptrs[] = {&h->d_meta, &h->d_desc, &h->d_relidx, &h->d_valmap, &h->d_diagmask, &h->d_tasks, &h->d_levelsn,
                    &h->d_L,    &h->d_X,    &h->d_D,      &h->d_lhat,   &h->d_linv,  &h->d_part, &h->d_ypart,
                    &h->d_status, &h->d_flipmap, &h->d_U, &h->d_XU, &h->d_uhat, &h->d_uinv,
+                   &h->d_piv, &h->d_ptype, &h->d_E,
                    &h->d_xb,   &h->d_lb,   &h->d_db,     &h->d_zb,     &h->d_w1,    &h->d_yb,   &h->d_hb,
                    &h->d_plist, &h->d_pn,  &h->d_pctr};
   for (void** p : ptrs) {
@@ -231,6 +232,9 @@ psi::KArgs kargs(pselinv_handle* h) {
   a.Uhat = nullptr;
   a.XU = h->d_XU;
   a.strict = 0;
+  a.piv = h->pivoted ? (const int32_t*)h->d_piv : nullptr;
+  a.ptype = h->pivoted ? (const int8_t*)h->d_ptype : nullptr;
+  a.E = h->pivoted ? h->d_E : nullptr;
   return a;
 }
 
@@ -521,15 +525,22 @@ namespace {
 // Supernodal factorisation, level by level from the leaves.  Symmetric:
 // A = L D L^T.  Non-symmetric (d_upper set): A = L D U', the U side running
 // the same panel-solve, copy and Schur kernels through swapped pointers.
-int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cudaStream_t st) {
+int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cudaStream_t st, bool bk = false) {
   const psi::Sizes sz = sizes(h);
   const int64_t B = h->opts.batch;
   const bool unsym = d_upper != nullptr;
   h->factored = h->inverted = false;
+  if (bk && !h->d_piv) {
+    int rc;
+    if ((rc = alloc(h, &h->d_piv, B * h->n * (int64_t)sizeof(int32_t)))) return rc;
+    if ((rc = alloc(h, &h->d_ptype, B * h->n))) return rc;
+    if ((rc = alloc(h, &h->d_E, B * h->n * (int64_t)elem_size(h)))) return rc;
+  }
+  h->pivoted = bk;
   PSI_CUDA(h, cudaMemsetAsync(h->d_L, 0, elem_size(h) * B * h->panel_total, st));
   if (unsym) PSI_CUDA(h, cudaMemsetAsync(h->d_U, 0, elem_size(h) * B * h->panel_total, st));
-  PSI_CUDA(h, cudaMemsetAsync(h->d_status, 0x7f, sizeof(int), st));
-  PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + 1, 0, sizeof(int) * (kStatusWords - 1), st));
+  PSI_CUDA(h, cudaMemsetAsync(h->d_status, 0x7f, 2 * sizeof(int), st));  // pivot key: unset
+  PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + 2, 0, sizeof(int) * (kStatusWords - 2), st));
   psi::KArgs a = kargs(h);
   a.XU = nullptr;
   if (unsym)
@@ -558,7 +569,10 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
   for (int32_t l = h->nlevels - 1; l >= 0; --l) {
     const int32_t* sns = lsn + h->level_ptr[l];
     const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
-    PSI_CUDA(h, psi::launch_per_sn(unsym ? psi::Kern::FactorDiagLU : psi::Kern::FactorDiag, a, sns, nsl, st));
+    PSI_CUDA(h, psi::launch_per_sn(unsym ? psi::Kern::FactorDiagLU
+                                         : bk  ? psi::Kern::FactorDiagBK
+                                               : psi::Kern::FactorDiag,
+                                   a, sns, nsl, st));
     for (int side = 0; side < (unsym ? 2 : 1); ++side) {
       const psi::KArgs& ka = side ? au : al;
       for (int v = 0; v < psi::kNumVar; ++v) {
@@ -566,7 +580,7 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
         PSI_CUDA(h, psi::launch_tiles(psi::Kern::Trsm, v, ka, tasks_at(h, h->off_trsm, r.begin), r.end - r.begin,
                                       st));
       }
-      PSI_CUDA(h, psi::launch_per_sn(psi::Kern::CopyBack, ka, sns, nsl, st));
+      PSI_CUDA(h, psi::launch_per_sn(bk ? psi::Kern::CopyBackBK : psi::Kern::CopyBack, ka, sns, nsl, st));
     }
     for (int side = 0; side < (unsym ? 2 : 1); ++side)
       for (int v = 0; v < psi::kNumVar; ++v) {
@@ -575,13 +589,14 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
                                       r.end - r.begin, st));
       }
   }
-  int status[2];
-  PSI_CUDA(h, cudaMemcpyAsync(status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
+  unsigned long long key = 0;
+  PSI_CUDA(h, cudaMemcpyAsync(&key, h->d_status, sizeof(key), cudaMemcpyDeviceToHost, st));
   PSI_CUDA(h, cudaStreamSynchronize(st));
-  if (status[0] != kStatusUnset) {
-    const int code = status[1] == 1 ? PSELINV_ERR_ZERO_PIVOT : PSELINV_ERR_NONFINITE;
-    return set_err(h, code, std::string(status[1] == 1 ? "zero" : "non-finite") + " pivot at column " +
-                                std::to_string(status[0]) + " (internal order)");
+  if (key != kPivotKeyUnset) {
+    const bool zero = (key & 3) == 1;
+    return set_err(h, zero ? PSELINV_ERR_ZERO_PIVOT : PSELINV_ERR_NONFINITE,
+                   std::string(zero ? "zero" : "non-finite") + " pivot at column " + std::to_string(key >> 2) +
+                       " (internal order)");
   }
   h->factored = true;
   return PSELINV_OK;
@@ -597,6 +612,26 @@ int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream) {
   int rc = ensure_device(h);
   if (rc) return rc;
   return factor_impl(h, d_values, nullptr, (cudaStream_t)stream);
+}
+
+int pselinv_factor_bk(pselinv_handle* h, const void* d_values, void* stream) {
+  if (!h) return set_err(nullptr, PSELINV_ERR_ARG, "handle is NULL");
+  if (!d_values) return set_err(h, PSELINV_ERR_ARG, "values pointer is NULL");
+  if (h->opts.unsym) return set_err(h, PSELINV_ERR_STATE, "pivoting is for symmetric handles");
+  int rc = ensure_device(h);
+  if (rc) return rc;
+  return factor_impl(h, d_values, nullptr, (cudaStream_t)stream, true);
+}
+
+int pselinv_get_pivots(pselinv_handle* h, int32_t* h_piv, int8_t* h_type, void* stream) {
+  if (!h || !h_piv || !h_type) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (!h->factored || !h->pivoted) return set_err(h, PSELINV_ERR_STATE, "no pivoted factor");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t cnt = (size_t)h->opts.batch * (size_t)h->n;
+  PSI_CUDA(h, cudaMemcpyAsync(h_piv, h->d_piv, cnt * sizeof(int32_t), cudaMemcpyDefault, st));
+  PSI_CUDA(h, cudaMemcpyAsync(h_type, h->d_ptype, cnt, cudaMemcpyDefault, st));
+  PSI_CUDA(h, cudaStreamSynchronize(st));
+  return PSELINV_OK;
 }
 
 int pselinv_factor_unsym(pselinv_handle* h, const void* d_lower, const void* d_upper, void* stream) {
@@ -845,7 +880,8 @@ int pselinv_logdet(pselinv_handle* h, double* h_out, void* stream) {
   if (!h->factored) return set_err(h, PSELINV_ERR_STATE, "no factor yet");
   cudaStream_t st = (cudaStream_t)stream;
   double* dev = (double*)((int*)h->d_status + kStatusWords);
-  PSI_CUDA(h, psi::launch_logdet(h->opts.dtype, h->d_D, h->n, dev, h->opts.batch, st));
+  PSI_CUDA(h, psi::launch_logdet(h->opts.dtype, h->d_D, h->n, dev, h->opts.batch, st,
+                                  h->pivoted ? (const int8_t*)h->d_ptype : nullptr, h->pivoted ? h->d_E : nullptr));
   PSI_CUDA(h, cudaMemcpyAsync(h_out, dev, sizeof(double) * 2 * h->opts.batch, cudaMemcpyDeviceToHost, st));
   PSI_CUDA(h, cudaStreamSynchronize(st));
   return PSELINV_OK;
@@ -858,6 +894,7 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
   if (!d_G || !d_gradA) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
   if (g_kind != PSELINV_G_SYMMETRIC && g_kind != PSELINV_G_PANEL) return set_err(h, PSELINV_ERR_ARG, "bad g_kind");
   if (h->opts.unsym) return set_err(h, PSELINV_ERR_STATE, "symmetric handles only");
+  if (h->pivoted) return set_err(h, PSELINV_ERR_STATE, "the adjoint needs the pivot-free factor (pselinv_factor)");
   if (!h->inverted) return set_err(h, PSELINV_ERR_STATE, "selinv_adjoint needs a prior pselinv_selinv");
   const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
   int rc;

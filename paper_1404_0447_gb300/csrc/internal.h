@@ -160,6 +160,11 @@ struct pselinv_handle {
   void* d_part = nullptr;   // step-3 partial products (level-local)
   void* d_ypart = nullptr;  // step-2 partial products (level-local)
   void* d_status = nullptr; // device status words
+  // Bunch-Kaufman pivoted factor (pselinv_factor_bk), batch x n each
+  bool pivoted = false;
+  void* d_piv = nullptr;    // int32 local original column per pivot position
+  void* d_ptype = nullptr;  // int8 pivot type
+  void* d_E = nullptr;      // 2x2 off-diagonals
   // non-symmetric handles
   void* d_U = nullptr;      // U panels (U'_{j,i} at position (i, j))
   void* d_XU = nullptr;     // XU panels (X_{j,i} at position (i, j))

@@ -18,9 +18,12 @@ namespace psi {
 // packed lower-triangular index, column-major: (i, j), i >= j, order s
 __device__ __forceinline__ int pk(int i, int j, int s) { return j * s - (j * (j - 1)) / 2 + (i - j); }
 
+// Status words 0-1 hold one 64-bit key (column << 2 | kind), kind 1 = zero
+// pivot, 2 = non-finite: the minimum is the first bad column and, within
+// it, a zero pivot before its consequences.
 __device__ void report_pivot(int* status, int col, bool zero) {
-  atomicMin(&status[0], col);
-  atomicMax(&status[1], zero ? 1 : 2);
+  atomicMin(reinterpret_cast<unsigned long long*>(status),
+            ((unsigned long long)(unsigned)col << 2) | (zero ? 1ull : 2ull));
 }
 
 // --------------------------------------------------------------------------
@@ -247,9 +250,13 @@ __global__ void k_norm_diag_lu(const SnMeta* __restrict__ meta, const T* __restr
 // Normalisation, diagonal part (all supernodes, one CTA each):
 // (L_KK)^{-1} -> linv and M_K = L_KK^{-T} D_K^{-1} L_KK^{-1} -> the diagonal
 // block of the X panel (Algorithm 1 step 3's first term; U_KK = D_K L_KK^T).
+// A pivoted factor (ptype set): D_K has 2x2 blocks, so row q of D_K^{-1} V is
+// c_q V_q + c'_q V_{q'} with q' the 2x2 partner, and M_K goes to the original
+// columns (P(i), P(j)).
 template <class T>
 __global__ void k_norm_diag(const SnMeta* __restrict__ meta, const T* __restrict__ L, const T* __restrict__ D,
-                            T* __restrict__ Linv, T* __restrict__ X, Sizes sz) {
+                            T* __restrict__ Linv, T* __restrict__ X, Sizes sz, const int32_t* __restrict__ piv,
+                            const int8_t* __restrict__ ptype, const T* __restrict__ E) {
   extern __shared__ __align__(16) unsigned char shraw[];
   T* Tp = reinterpret_cast<T*>(shraw);
   const int k = blockIdx.x;
@@ -258,19 +265,54 @@ __global__ void k_norm_diag(const SnMeta* __restrict__ meta, const T* __restrict
   const int s = m.s, ld = m.s + m.r;
   const T* P = L + b * sz.panel + m.panel;
   const T* d = D + b * sz.n + m.f;
-  T* rd = Tp + s * (s + 1) / 2;  // 1 / d_q
+  T* rd = Tp + s * (s + 1) / 2;  // 1 / d_q, or the own coefficient of a 2x2 row
+  T* rp = rd + s;                // partner coefficient (0 for a 1x1 pivot)
+  int* pq = reinterpret_cast<int*>(rp + s);
   const int nt = blockDim.x, t = threadIdx.x;
   for (int e = t; e < s * s; e += nt) {
     const int i = e % s, j = e / s;
     if (i > j) Tp[pk(i, j, s)] = P[i + (int64_t)j * ld];
   }
-  for (int q = t; q < s; q += nt) rd[q] = Sc<T>::one() / d[q];
+  if (ptype) {
+    const int8_t* ty = ptype + b * sz.n + m.f;
+    const T* ee = E + b * sz.n + m.f;
+    for (int q = t; q < s; q += nt) {
+      if (ty[q] == 0) {
+        rd[q] = Sc<T>::one() / d[q];
+        rp[q] = Sc<T>::zero();
+        pq[q] = q;
+      } else {
+        const int f0 = ty[q] == 1 ? q : q - 1;  // first column of the 2x2 block
+        const T det = d[f0] * d[f0 + 1] - ee[f0] * ee[f0];
+        const int o = ty[q] == 1 ? q + 1 : q - 1;
+        rd[q] = d[o] / det;
+        rp[q] = -ee[f0] / det;
+        pq[q] = o;
+      }
+    }
+  } else {
+    for (int q = t; q < s; q += nt) rd[q] = Sc<T>::one() / d[q];
+  }
   __syncthreads();
   T* V = Linv + b * sz.linv + m.linv;
   unit_lower_inverse(Tp, s, V);
   if (!X) return;  // inverse only (the adjoint recomputes it)
   __syncthreads();
   T* XK = X + b * sz.panel + m.panel;
+  if (ptype) {
+    const int32_t* pv = piv + b * sz.n + m.f;
+    for (int e = t; e < s * s; e += nt) {
+      const int i = e % s, j = e / s;
+      if (i >= j) {
+        T acc = Sc<T>::zero();
+        for (int q = i; q < s; ++q)  // V_qi = 0 for q < i; row q of D^{-1} V vanishes in column j <= i below j - 1
+          acc += V[q + i * s] * (rd[q] * V[q + j * s] + rp[q] * V[pq[q] + j * s]);
+        XK[pv[i] + (int64_t)pv[j] * ld] = acc;
+        XK[pv[j] + (int64_t)pv[i] * ld] = acc;
+      }
+    }
+    return;
+  }
   for (int e = t; e < s * s; e += nt) {
     const int i = e % s, j = e / s;
     if (i >= j) {
@@ -278,6 +320,235 @@ __global__ void k_norm_diag(const SnMeta* __restrict__ meta, const T* __restrict
       for (int q = i; q < s; ++q) acc += V[q + i * s] * rd[q] * V[q + j * s];
       XK[i + (int64_t)j * ld] = acc;
       XK[j + (int64_t)i * ld] = acc;
+    }
+  }
+}
+
+// |re| + |im|: the magnitude Bunch-Kaufman compares (plain |x| for real)
+__device__ __forceinline__ double bk_abs(double x) { return fabs(x); }
+__device__ __forceinline__ double bk_abs(Cplx x) { return fabs(x.re) + fabs(x.im); }
+
+// Largest magnitude (first index on ties) over warp lanes; returns it to all lanes.
+__device__ __forceinline__ void warp_argmax(double& v, int& idx) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (v2 > v || (v2 == v && i2 < idx)) {
+      v = v2;
+      idx = i2;
+    }
+  }
+}
+
+// Factorisation with Bunch-Kaufman pivoting restricted to the supernode's
+// diagonal block (Bunch and Kaufman 1977, the lower form of LAPACK's
+// xSYTF2), one CTA per supernode of the level, the block packed in shared
+// memory.  For pivot position k of the reduced block: a = |T_kk|, colmax =
+// max_{i>k} |T_ik| at imax; a >= alpha colmax -> 1x1; else with rowmax the
+// largest off-diagonal magnitude of row/column imax: a rowmax >= alpha
+// colmax^2 -> 1x1; |T_imax,imax| >= alpha rowmax -> 1x1 after swapping k
+// and imax; else 2x2 on (k, k+1) after swapping k+1 and imax.  Swaps are
+// symmetric interchanges of the whole block, including the computed L rows.
+// Out: L_KK (pivot order, zero beside 2x2 blocks) and D to the panel's
+// diagonal block, D, E (2x2 off-diagonals), pivot types, the local pivot
+// order piv, (L_KK)^{-1} to linv.  A reduced column that is entirely zero, a
+// singular 2x2 block or a non-finite value is reported in the status words.
+template <class T>
+__global__ void k_factor_diag_bk(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns, T* __restrict__ L,
+                                 T* __restrict__ D, T* __restrict__ E, int8_t* __restrict__ ptype,
+                                 int32_t* __restrict__ piv, T* __restrict__ Linv, Sizes sz, int* status) {
+  extern __shared__ __align__(16) unsigned char shraw[];
+  T* Tp = reinterpret_cast<T*>(shraw);
+  const int k0 = sns[blockIdx.x];
+  const int b = blockIdx.y;
+  const SnMeta m = meta[k0];
+  const int s = m.s, ld = m.s + m.r;
+  T* l1 = Tp + s * (s + 1) / 2;  // 2x2 step: new L columns
+  T* l2 = l1 + s;
+  int* perm = reinterpret_cast<int*>(l2 + s);
+  __shared__ int sh_kp, sh_kstep, sh_bad;
+  T* P = L + b * sz.panel + m.panel;
+  const int nt = blockDim.x, t = threadIdx.x;
+  const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+  for (int e = t; e < s * s; e += nt) {
+    const int i = e % s, j = e / s;
+    if (i >= j) Tp[pk(i, j, s)] = P[i + (int64_t)j * ld];
+  }
+  for (int q = t; q < s; q += nt) perm[q] = q;
+  if (t == 0) sh_bad = 0;
+  __syncthreads();
+  T* dd = D + b * sz.n + m.f;
+  T* ee = E + b * sz.n + m.f;
+  int8_t* ty = ptype + b * sz.n + m.f;
+  int k = 0;
+  while (k < s) {
+    // pivot search by warp 0
+    if (t < 32) {
+      double cv = -1.0;
+      int ci = s;
+      for (int i = k + 1 + t; i < s; i += 32) {
+        const double v = bk_abs(Tp[pk(i, k, s)]);
+        if (v > cv || (v == cv && i < ci)) {
+          cv = v;
+          ci = i;
+        }
+      }
+      warp_argmax(cv, ci);
+      const double absakk = bk_abs(Tp[pk(k, k, s)]);
+      const double colmax = ci < s ? cv : 0.0;
+      const int imax = ci < s ? ci : k;
+      double rowmax = 0.0;
+      if (absakk < alpha * colmax) {
+        double rv = 0.0;
+        for (int j = k + t; j < s; j += 32)
+          if (j != imax) rv = fmax(rv, bk_abs(j < imax ? Tp[pk(imax, j, s)] : Tp[pk(j, imax, s)]));
+        for (int o = 16; o > 0; o >>= 1) rv = fmax(rv, __shfl_xor_sync(0xffffffffu, rv, o));
+        rowmax = rv;
+      }
+      if (t == 0) {
+        int kp = k, kstep = 1;
+        if (!(absakk == absakk) || !(colmax == colmax) || isinf(absakk) || isinf(colmax)) {
+          sh_bad = 2;
+        } else if (absakk == 0.0 && colmax == 0.0) {
+          sh_bad = 1;
+        } else if (absakk < alpha * colmax) {
+          if (absakk * rowmax >= alpha * colmax * colmax) {
+            kp = k;
+          } else if (bk_abs(Tp[pk(imax, imax, s)]) >= alpha * rowmax) {
+            kp = imax;
+          } else {
+            kp = imax;
+            kstep = 2;
+          }
+        }
+        sh_kp = kp;
+        sh_kstep = kstep;
+      }
+    }
+    __syncthreads();
+    if (sh_bad) break;
+    const int kstep = sh_kstep, kp = sh_kp, kk = k + kstep - 1;
+    if (kp != kk) {  // symmetric interchange of kk and kp (kp > kk) in packed lower storage
+      for (int j = t; j < kk; j += nt) {
+        const T x = Tp[pk(kk, j, s)];
+        Tp[pk(kk, j, s)] = Tp[pk(kp, j, s)];
+        Tp[pk(kp, j, s)] = x;
+      }
+      for (int i = kk + 1 + t; i < kp; i += nt) {
+        const T x = Tp[pk(i, kk, s)];
+        Tp[pk(i, kk, s)] = Tp[pk(kp, i, s)];
+        Tp[pk(kp, i, s)] = x;
+      }
+      for (int i = kp + 1 + t; i < s; i += nt) {
+        const T x = Tp[pk(i, kk, s)];
+        Tp[pk(i, kk, s)] = Tp[pk(i, kp, s)];
+        Tp[pk(i, kp, s)] = x;
+      }
+      if (t == 0) {
+        const T x = Tp[pk(kk, kk, s)];
+        Tp[pk(kk, kk, s)] = Tp[pk(kp, kp, s)];
+        Tp[pk(kp, kp, s)] = x;
+        const int p = perm[kk];
+        perm[kk] = perm[kp];
+        perm[kp] = p;
+      }
+      __syncthreads();
+    }
+    if (kstep == 1) {
+      const T d = Tp[pk(k, k, s)];
+      for (int i = k + 1 + t; i < s; i += nt) Tp[pk(i, k, s)] = Tp[pk(i, k, s)] / d;
+      __syncthreads();
+      const int w = s - k - 1;
+      for (int e = t; e < w * w; e += nt) {
+        const int ii = k + 1 + e % w, jj = k + 1 + e / w;
+        if (ii >= jj) Tp[pk(ii, jj, s)] -= Tp[pk(ii, k, s)] * Tp[pk(jj, k, s)] * d;
+      }
+      if (t == 0) {
+        dd[k] = d;
+        ee[k] = Sc<T>::zero();
+        ty[k] = 0;
+      }
+    } else {
+      const T a11 = Tp[pk(k, k, s)], a21 = Tp[pk(k + 1, k, s)], a22 = Tp[pk(k + 1, k + 1, s)];
+      const T det = a11 * a22 - a21 * a21;
+      if (t == 0 && Sc<T>::bad(det)) sh_bad = Sc<T>::is_zero(det) ? 1 : 2;
+      for (int i = k + 2 + t; i < s; i += nt) {  // [l1 l2] = [w1 w2] D^{-1}
+        const T w1 = Tp[pk(i, k, s)], w2 = Tp[pk(i, k + 1, s)];
+        l1[i] = (w1 * a22 - w2 * a21) / det;
+        l2[i] = (w2 * a11 - w1 * a21) / det;
+      }
+      __syncthreads();
+      const int w = s - k - 2;
+      for (int e = t; e < w * w; e += nt) {
+        const int ii = k + 2 + e % w, jj = k + 2 + e / w;
+        if (ii >= jj) Tp[pk(ii, jj, s)] -= l1[ii] * Tp[pk(jj, k, s)] + l2[ii] * Tp[pk(jj, k + 1, s)];
+      }
+      __syncthreads();
+      for (int i = k + 2 + t; i < s; i += nt) {
+        Tp[pk(i, k, s)] = l1[i];
+        Tp[pk(i, k + 1, s)] = l2[i];
+      }
+      if (t == 0) {
+        Tp[pk(k + 1, k, s)] = Sc<T>::zero();
+        dd[k] = a11;
+        dd[k + 1] = a22;
+        ee[k] = a21;
+        ee[k + 1] = Sc<T>::zero();
+        ty[k] = 1;
+        ty[k + 1] = 2;
+      }
+    }
+    __syncthreads();
+    if (sh_bad) break;
+    k += kstep;
+  }
+  if (sh_bad) {
+    if (t == 0) report_pivot(status, m.f + k, sh_bad == 1);
+    return;
+  }
+  unit_lower_inverse(Tp, s, Linv + b * sz.linv + m.linv);
+  for (int e = t; e < s * s; e += nt) {
+    const int i = e % s, j = e / s;
+    if (i > j) P[i + (int64_t)j * ld] = Tp[pk(i, j, s)];
+    if (i == j) P[i + (int64_t)j * ld] = dd[i];
+  }
+  for (int q = t; q < s; q += nt) piv[b * sz.n + m.f + q] = perm[q];
+}
+
+// Pivoted factor: L_{C,K} = Z D_K^{-1} for the panel-solve output Z =
+// A_{C,K P} L_KK^{-T} held in the factor scratch, with 2x2 blocks of D_K;
+// written to the panel and back into the scratch (the Schur update reads it).
+template <class T>
+__global__ void k_copyback_bk(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns, T* __restrict__ L,
+                              T* __restrict__ Ltmp, const T* __restrict__ D, const T* __restrict__ E,
+                              const int8_t* __restrict__ ptype, Sizes sz) {
+  const int k = sns[blockIdx.x];
+  const int b = blockIdx.y;
+  const SnMeta m = meta[k];
+  const int s = m.s, r = m.r, ld = s + r;
+  T* P = L + b * sz.panel + m.panel + s;
+  T* Z = Ltmp + b * sz.lhat + m.lhat;
+  const T* d = D + b * sz.n + m.f;
+  const T* e = E + b * sz.n + m.f;
+  const int8_t* ty = ptype + b * sz.n + m.f;
+  for (int j = blockIdx.z; j < s; j += gridDim.z) {
+    if (ty[j] == 2) continue;  // done with its partner
+    if (ty[j] == 0) {
+      for (int i = threadIdx.x; i < r; i += blockDim.x) {
+        const T l = Z[i + (int64_t)j * r] / d[j];
+        Z[i + (int64_t)j * r] = l;
+        P[i + (int64_t)j * ld] = l;
+      }
+    } else {
+      const T det = d[j] * d[j + 1] - e[j] * e[j];
+      for (int i = threadIdx.x; i < r; i += blockDim.x) {
+        const T z1 = Z[i + (int64_t)j * r], z2 = Z[i + (int64_t)(j + 1) * r];
+        const T x1 = (z1 * d[j + 1] - z2 * e[j]) / det, x2 = (z2 * d[j] - z1 * e[j]) / det;
+        Z[i + (int64_t)j * r] = x1;
+        Z[i + (int64_t)(j + 1) * r] = x2;
+        P[i + (int64_t)j * ld] = x1;
+        P[i + (int64_t)(j + 1) * ld] = x2;
+      }
     }
   }
 }
@@ -307,10 +578,13 @@ __global__ void k_copyback(const SnMeta* __restrict__ meta, const int32_t* __res
 // --------------------------------------------------------------------------
 
 // Factorisation panel solve: Ltmp_{C,K} = A_{C,K} (L_KK)^{-T} D_K^{-1}.
+// Pivoted factor (piv set): the columns of A_{C,K} are read in pivot order
+// and D^{-1} is left to k_copyback_bk (2x2 blocks can straddle tiles).
 template <class T, int BN>
 __global__ void __launch_bounds__(TG_THREADS) k_trsm(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
                                                      const T* __restrict__ L, const T* __restrict__ D,
-                                                     const T* __restrict__ Linv, T* __restrict__ Ltmp, Sizes sz) {
+                                                     const T* __restrict__ Linv, T* __restrict__ Ltmp, Sizes sz,
+                                                     const int32_t* __restrict__ piv) {
   __shared__ TileSmem<T, BN> sm;
   const Task tk = tasks[blockIdx.x];
   const int b = blockIdx.y;
@@ -321,9 +595,10 @@ __global__ void __launch_bounds__(TG_THREADS) k_trsm(const SnMeta* __restrict__ 
   const T* d = D + b * sz.n + m.f;
   Acc<T, BN> acc;
   acc_zero<T, BN>(acc);
+  const int32_t* pv = piv ? piv + b * sz.n + m.f : nullptr;
   auto la = [&](int mm, int kk) {
     const int row = tk.m0 + mm;
-    return row < r ? A[row + (int64_t)kk * ld] : Sc<T>::zero();
+    return row < r ? A[row + (int64_t)(pv ? pv[kk] : kk) * ld] : Sc<T>::zero();
   };
   auto lb = [&](int kk, int nn) {
     const int col = tk.n0 + nn;
@@ -334,7 +609,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_trsm(const SnMeta* __restrict__ 
   T* out = Ltmp + b * sz.lhat + m.lhat;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
-    if (row < r && col < s) out[row + (int64_t)col * r] = v / d[col];
+    if (row < r && col < s) out[row + (int64_t)col * r] = pv ? v : v / d[col];
   });
 }
 
@@ -351,7 +626,8 @@ __global__ void __launch_bounds__(TG_THREADS) k_schur(const SnMeta* __restrict__
                                                       const ColDesc* __restrict__ desc,
                                                       const int32_t* __restrict__ relidx, T* __restrict__ L,
                                                       const T* __restrict__ D, const T* __restrict__ Ltmp,
-                                                      const T* __restrict__ Ltmp2, int strict, Sizes sz) {
+                                                      const T* __restrict__ Ltmp2, int strict, Sizes sz,
+                                                      const int8_t* __restrict__ ptype, const T* __restrict__ E) {
   __shared__ TileSmem<T, BN> sm;
   const Task tk = tasks[blockIdx.x];
   const int b = blockIdx.y;
@@ -362,9 +638,15 @@ __global__ void __launch_bounds__(TG_THREADS) k_schur(const SnMeta* __restrict__
   const T* d = D + b * sz.n + m.f;
   Acc<T, BN> acc;
   acc_zero<T, BN>(acc);
+  const int8_t* ty = ptype ? ptype + b * sz.n + m.f : nullptr;
+  const T* ee = ptype ? E + b * sz.n + m.f : nullptr;
   auto la = [&](int mm, int kk) {
     const int row = tk.m0 + mm;
-    return row < r ? Lc[row + (int64_t)kk * r] * d[kk] : Sc<T>::zero();
+    if (row >= r) return Sc<T>::zero();
+    T v = Lc[row + (int64_t)kk * r] * d[kk];
+    if (ty && ty[kk] == 1) v += Lc[row + (int64_t)(kk + 1) * r] * ee[kk];       // (L D) with a 2x2 block
+    if (ty && ty[kk] == 2) v += Lc[row + (int64_t)(kk - 1) * r] * ee[kk - 1];
+    return v;
   };
   auto lb = [&](int kk, int nn) {
     const int col = tk.n0 + nn;
@@ -445,13 +727,17 @@ __global__ void __launch_bounds__(TG_THREADS) k_gemm2(KArgs a, const Task* __res
 // Real: (sum log|d_j|, number of negative pivots); complex: sum of principal
 // logs (log|d_j|, arg d_j), per batch member.
 template <class T>
-__global__ void k_logdet(const T* __restrict__ D, int64_t n, double* __restrict__ out) {
+__global__ void k_logdet(const T* __restrict__ D, int64_t n, double* __restrict__ out,
+                         const int8_t* __restrict__ ptype, const T* __restrict__ E) {
   __shared__ double s1[256];
   __shared__ double s2[256];
   const int b = blockIdx.x;
   double a = 0.0, c = 0.0;
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-    const T d = D[b * n + j];
+    const int8_t ty = ptype ? ptype[b * n + j] : 0;
+    if (ty == 2) continue;  // counted with its partner
+    // a 2x2 pivot contributes the determinant of its block
+    const T d = ty == 1 ? D[b * n + j] * D[b * n + j + 1] - E[b * n + j] * E[b * n + j] : D[b * n + j];
     if constexpr (Sc<T>::P == 1) {
       a += log(fabs(d));
       c += d < 0.0 ? 1.0 : 0.0;
@@ -548,9 +834,10 @@ static inline unsigned blocks_for(int64_t n, int threads, int cap = 152 * 16) {
   return (unsigned)(b < cap ? b : cap);
 }
 
+// packed lower triangle, two length-s vectors and s ints
 template <class T>
 static size_t diag_smem(int maxw) {
-  return sizeof(T) * ((size_t)maxw * (maxw + 1) / 2 + maxw);
+  return sizeof(T) * ((size_t)maxw * (maxw + 1) / 2 + 2 * (size_t)maxw) + sizeof(int) * (size_t)maxw;
 }
 
 // two packed triangles of the non-symmetric diagonal factorisation
@@ -568,6 +855,9 @@ static cudaError_t setup_t() {
                              (int)diag_smem<T>(kMaxWidth));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_norm_diag_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)diag_smem<T>(kMaxWidth));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_factor_diag_bk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)diag_smem<T>(kMaxWidth));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_factor_diag_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -643,12 +933,12 @@ static cudaError_t tiles_tb(Kern k, const KArgs& a, const Task* t, int64_t n, cu
   switch (k) {
     case Kern::Trsm:
       k_trsm<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.L, (const T*)a.D, (const T*)a.Linv,
-                                                 (T*)a.Lhat, a.sz);
+                                                 (T*)a.Lhat, a.sz, a.piv);
       break;
     case Kern::Schur:
       k_schur<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, a.desc, a.relidx, (T*)a.L, (const T*)a.D,
                                                   (const T*)a.Lhat, (const T*)(a.Uhat ? a.Uhat : a.Lhat),
-                                                  a.strict, a.sz);
+                                                  a.strict, a.sz, a.ptype, (const T*)a.E);
       break;
     case Kern::Lhat:
       k_lhat<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.L, (const T*)a.Linv, (T*)a.Lhat, a.sz);
@@ -697,7 +987,7 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
       break;
     case Kern::NormDiag:  // every supernode: blockIdx.x is the supernode itself
       k_norm_diag<T><<<grid, 256, diag_smem<T>(a.maxw), st>>>(a.meta, (const T*)a.L, (const T*)a.D, (T*)a.Linv,
-                                                              (T*)a.X, a.sz);
+                                                              (T*)a.X, a.sz, a.piv, a.ptype, (const T*)a.E);
       break;
     case Kern::Gemm1Reduce:
       k_gemm1_reduce<T><<<dim3(nsn, a.sz.batch, 16), 256, 0, st>>>(a, sns);
@@ -705,6 +995,14 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
     case Kern::FactorDiagLU:
       k_factor_diag_lu<T><<<grid, 256, diag_smem_lu<T>(a.maxw), st>>>(a.meta, sns, (T*)a.L, (T*)a.U, (T*)a.D,
                                                                       (T*)a.Linv, (T*)a.Uinv, a.sz, a.status);
+      break;
+    case Kern::FactorDiagBK:
+      k_factor_diag_bk<T><<<grid, 256, diag_smem<T>(a.maxw), st>>>(
+          a.meta, sns, (T*)a.L, (T*)a.D, (T*)a.E, (int8_t*)a.ptype, (int32_t*)a.piv, (T*)a.Linv, a.sz, a.status);
+      break;
+    case Kern::CopyBackBK:
+      k_copyback_bk<T><<<dim3(nsn, a.sz.batch, 16), 256, 0, st>>>(a.meta, sns, (T*)a.L, (T*)a.Lhat, (const T*)a.D,
+                                                                  (const T*)a.E, a.ptype, a.sz);
       break;
     case Kern::NormDiagLU:
       k_norm_diag_lu<T><<<grid, 256, diag_smem<T>(a.maxw), st>>>(a.meta, (const T*)a.L, (const T*)a.U,
@@ -722,11 +1020,12 @@ cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, c
   return a.dtype == PSELINV_C128 ? per_sn_t<Cplx>(k, a, sns, nsn, st) : per_sn_t<double>(k, a, sns, nsn, st);
 }
 
-cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st) {
+cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st,
+                          const int8_t* ptype, const void* E) {
   if (dtype == PSELINV_C128)
-    k_logdet<Cplx><<<batch, 256, 0, st>>>((const Cplx*)D, n, out);
+    k_logdet<Cplx><<<batch, 256, 0, st>>>((const Cplx*)D, n, out, ptype, (const Cplx*)E);
   else
-    k_logdet<double><<<batch, 256, 0, st>>>((const double*)D, n, out);
+    k_logdet<double><<<batch, 256, 0, st>>>((const double*)D, n, out, ptype, (const double*)E);
   return cudaGetLastError();
 }
 

@@ -20,7 +20,8 @@ struct Sizes {
 
 enum class Kern {
   Trsm, Schur, Lhat, Gemm1, Gemm2, FactorDiag, CopyBack, NormDiag, DiagFinal, Gemm1Reduce,
-  FactorDiagLU, NormDiagLU  // non-symmetric diagonal blocks
+  FactorDiagLU, NormDiagLU,  // non-symmetric diagonal blocks
+  FactorDiagBK, CopyBackBK   // Bunch-Kaufman pivoted factor
 };
 
 // Everything a kernel may need; device pointers typed by dtype inside.
@@ -46,7 +47,16 @@ struct KArgs {
   void* XU;    // XU panels: X_{j,i} at panel position (i, j); step 2 reads X_{C,C} above the
                // diagonal from here, step 3 finish writes X_KK^T here
   int strict;  // Schur: skip the diagonal entries of the updated blocks
+  // Bunch-Kaufman pivoted factor (nullptr when not pivoted), batch x n each:
+  const int32_t* piv;  // supernode-local original column at each pivot position
+  const int8_t* ptype; // 0 = 1x1 pivot, 1 / 2 = first / second column of a 2x2 pivot
+  const void* E;       // D_{k+1,k} of a 2x2 pivot, at its first column
 };
+
+// Original local column of pivot position k of the supernode starting at f.
+__device__ __forceinline__ int pcol(const KArgs& a, int b, int f, int k) {
+  return a.piv ? a.piv[(int64_t)b * a.sz.n + f + k] : k;
+}
 
 cudaError_t setup_kernels();
 cudaError_t launch_scatter_values(int dtype, const void* vals, const int64_t* vmap, int64_t nnz, void* L,
@@ -69,7 +79,8 @@ cudaError_t launch_tiles(Kern k, int var, const KArgs& a, const Task* tasks, int
 // Per-supernode kernels (FactorDiag, CopyBack, NormDiag, DiagFinal, Gemm1Reduce) over the
 // nsn supernodes listed in sns (NormDiag: supernodes 0..nsn-1, sns unused).
 cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st);
-cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st);
+cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st,
+                          const int8_t* ptype = nullptr, const void* E = nullptr);
 cudaError_t launch_pole_sum(int dtype, const void* X, int64_t panel_total, int batch, const void* w, void* out,
                             cudaStream_t st);
 cudaError_t launch_trace_sum(int dtype, const void* X, int64_t panel_total, const int64_t* vmap,

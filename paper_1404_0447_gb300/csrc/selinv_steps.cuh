@@ -70,10 +70,11 @@ __device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b
   const int kb = tk.c * m.kchunk, ke = min(r, kb + m.kchunk);
   tile_mma<T, BN>(sm, kb, ke, [m0](int kt) { return kt >= m0 + TG_BM; }, la, lb, acc);
   if (m.ksplit == 1) {
+    // a pivoted factor computes K's columns in pivot order; X keeps the original order
     T* out = (T*)a.X + b * sz.panel + m.panel + s;
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int row = tk.m0 + mm, col = tk.n0 + nn;
-      if (row < r && col < s) out[row + (int64_t)col * ld] = -v;
+      if (row < r && col < s) out[row + (int64_t)pcol(a, b, m.f, col) * ld] = -v;
     });
   } else {
     T* out = (T*)a.ypart + b * sz.ypart + m.ypart + (int64_t)tk.c * r * s;
@@ -97,10 +98,11 @@ __device__ __forceinline__ void step2_reduce(const KArgs& a, int k, int b, int c
   const int64_t rs = (int64_t)r * s;
   for (int j = col0; j < s; j += cstride) {
     const T* col = yp + (int64_t)j * r;
+    T* oc = out + (int64_t)pcol(a, b, m.f, j) * ld;
     for (int i = threadIdx.x; i < r; i += blockDim.x) {
       T acc = ld_maybe_cg(col + i, cg);
       for (int c = 1; c < m.ksplit; ++c) acc += ld_maybe_cg(col + c * rs + i, cg);
-      out[i + (int64_t)j * ld] = -acc;
+      oc[i] = -acc;
     }
   }
 }
@@ -122,7 +124,7 @@ __device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b
   };
   auto lb = [&](int kk, int nn) {
     const int col = tk.n0 + nn;
-    return col < s ? ld_maybe_cg(Y + kk + (int64_t)col * ld, cg) : Sc<T>::zero();
+    return col < s ? ld_maybe_cg(Y + kk + (int64_t)pcol(a, b, m.f, col) * ld, cg) : Sc<T>::zero();
   };
   const int kb = tk.c * m.kchunk3, ke = min(r, kb + m.kchunk3);
   tile_mma<T, BN>(sm, kb, ke, [](int) { return true; }, la, lb, acc);
@@ -135,7 +137,9 @@ __device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b
 
 // Step 3 finish: X_KK = (Z + Z^T) / 2 with Z = M_K - sum_c P_c (the
 // symmetrisation at the end of Section 2.1 / Algorithm 3).  One thread per
-// unordered pair {i, j} reads and writes exactly (i, j) and (j, i).
+// unordered pair {i, j} reads and writes exactly (i, j) and (j, i) -- for a
+// pivoted factor at the original columns (P(i), P(j)), where the
+// normalisation pass left M_K.
 // Non-symmetric handles (a.XU set): X_KK = Z as it is, and Z^T goes to the
 // diagonal block of the XU panel.
 template <class T>
@@ -160,14 +164,15 @@ __device__ __forceinline__ void step3_finish(const KArgs& a, int k, int b, int p
   for (int e = threadIdx.x + part * blockDim.x; e < s * s; e += nparts * blockDim.x) {
     const int i = e % s, j = e / s;
     if (i < j) continue;
-    T zij = XK[i + (int64_t)j * ld], zji = XK[j + (int64_t)i * ld];
+    const int pi = pcol(a, b, m.f, i), pj = pcol(a, b, m.f, j);
+    T zij = XK[pi + (int64_t)pj * ld], zji = XK[pj + (int64_t)pi * ld];
     for (int c = 0; c < m.nchunk; ++c) {
       zij -= ld_maybe_cg(pp + (int64_t)c * s * s + i + j * s, cg);
       zji -= ld_maybe_cg(pp + (int64_t)c * s * s + j + i * s, cg);
     }
     const T x = 0.5 * (zij + zji);
-    XK[i + (int64_t)j * ld] = x;
-    XK[j + (int64_t)i * ld] = x;
+    XK[pi + (int64_t)pj * ld] = x;
+    XK[pj + (int64_t)pi * ld] = x;
   }
 }
 

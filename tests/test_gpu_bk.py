@@ -1,0 +1,194 @@
+"""GPU parity of the Bunch-Kaufman pivoted factor (1x1/2x2 pivots inside
+supernodes) and of the selected inversion on it, against the oracle through
+the C ABI: the pivot decisions bit for bit (inputs with random weights, so
+no exact ties), X within 1e-10 of max |X| on every panel entry."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1404_0447_gb300 as P
+    return P
+
+
+def dev(v):
+    import torch
+    v = np.ascontiguousarray(v)
+    return torch.tensor(v, dtype=torch.complex128 if np.iscomplexobj(v) else torch.float64, device="cuda")
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def indefinite_graph(dims, sigma, seed=0, cplx=False):
+    """Graph Laplacian with random edge weights minus sigma on the diagonal
+    (indefinite for sigma inside the spectrum), in ND order."""
+    gl = synth.GraphLaplacian(dims)
+    v = gl.assemble().copy()
+    diag = np.asarray(gl.colptr[:-1])
+    v[diag] -= sigma
+    if cplx:
+        v = v.astype(np.complex128)
+        v[diag] += 1j * np.random.default_rng(seed).uniform(0.01, 0.05, len(diag))
+    return synth.Problem("indef", gl.n, gl.colptr, gl.rowind, v, synth.nd_order(gl.dims))
+
+
+def oracle_local_pivots(sym, fac):
+    """The oracle's pivots in the library's layout (internal order)."""
+    n = int(sym["sn_start"][-1])
+    piv = np.zeros(n, np.int32)
+    ty = np.zeros(n, np.int8)
+    for K, F in enumerate(fac):
+        f = int(sym["sn_start"][K])
+        piv[f:f + len(F["p"])] = F["p"]
+        ty[f:f + len(F["p"])] = F["ptype"]
+    return piv, ty
+
+
+def check_bk(P, p, wmax=128, relax=1, modes=(1,), **opts):
+    h = P.SelInv(p.n, p.colptr, p.rowind, max_sn_width=wmax, relax=relax,
+                 dtype=P.C128 if np.iscomplexobj(p.values) else P.F64, **opts)
+    h.factor_bk(dev(p.values))
+    sym, X, fac = oracle.selected_inverse_bk(p.n, p.colptr, p.rowind, p.values, wmax, relax)
+    piv, ty = h.pivots()
+    opiv, oty = oracle_local_pivots(sym, fac)
+    assert np.array_equal(ty[0], oty) and np.array_equal(piv[0], opiv)
+    Xo = oracle.panels_from_dense(sym, X)
+    outs = {}
+    for mode in modes:
+        h.selinv(mode)
+        outs[mode] = h.panels(0)[0].cpu().numpy()
+        assert rel(outs[mode], Xo) <= TOL, (mode, rel(outs[mode], Xo))
+    return h, outs, fac
+
+
+@pytest.mark.parametrize("dims,sigma", [((12, 11, 10), 2.0), ((30, 29), 3.0), ((9, 9, 8), 3.0)])
+def test_bk_indefinite_all_schedules(P, dims, sigma):
+    p = indefinite_graph(dims, sigma, seed=1)
+    h, outs, fac = check_bk(P, p, modes=(0, 1, 2, 3))
+    assert sum(int((F["ptype"] == 1).sum()) for F in fac) > 0          # 2x2 pivots on the path
+    assert any(not np.array_equal(F["p"], np.arange(len(F["p"]))) for F in fac)
+    for m in (1, 2, 3):
+        assert np.array_equal(outs[0], outs[m])
+
+
+@pytest.mark.parametrize("split,wmax", [(48, 64), (0, 16)])
+def test_bk_split_slices_and_narrow_supernodes(P, split, wmax):
+    p = indefinite_graph((14, 13, 12), 0.8, seed=1)
+    check_bk(P, p, wmax=wmax, modes=(1, 0), split_k_rows=split)
+
+
+def test_bk_complex_symmetric(P):
+    p = indefinite_graph((10, 9, 8), 5.0, seed=3, cplx=True)
+    check_bk(P, p, modes=(1, 3))
+
+
+def test_bk_batch_members_pivot_independently(P):
+    import torch
+    gl = synth.GraphLaplacian((9, 8, 7))
+    base = gl.assemble()
+    diag = np.asarray(gl.colptr[:-1])
+    perm = synth.nd_order(gl.dims)
+    sigmas = (0.0, 4.0, 7.5)
+    vals = []
+    for sg in sigmas:
+        v = base.copy()
+        v[diag] -= sg
+        vals.append(synth.permute_lower(gl.n, gl.colptr, gl.rowind, v, perm)[2])
+    cp, ri = synth.permute_lower(gl.n, gl.colptr, gl.rowind, base, perm)[:2]
+    h = P.SelInv(gl.n, cp, ri, batch=len(sigmas))
+    h.factor_bk(dev(np.concatenate(vals)))
+    h.selinv(P.LEVEL)
+    X = h.panels(0).cpu().numpy()
+    piv, ty = h.pivots()
+    for b, v in enumerate(vals):
+        sym, Xd, fac = oracle.selected_inverse_bk(gl.n, cp, ri, v, 128, 1)
+        opiv, oty = oracle_local_pivots(sym, fac)
+        assert np.array_equal(piv[b], opiv) and np.array_equal(ty[b], oty)
+        assert rel(X[b], oracle.panels_from_dense(sym, Xd)) <= TOL
+    assert not ty[0].any() and ty[2].any()      # SPD member: no 2x2 pivots; indefinite one: some
+
+
+def test_bk_saddle_point_where_the_pivot_free_factor_fails(P):
+    rng = np.random.default_rng(3)
+    m, k = 40, 24
+    H = rng.normal(size=(m, m))
+    H = H @ H.T + m * np.eye(m)
+    B = rng.normal(size=(k, m))
+    K = np.block([[H, B.T], [B, np.zeros((k, k))]])
+    order = np.argsort(np.r_[np.arange(m) * 2 + 1, np.arange(k) * 2 * m // k])   # constraints interleaved
+    A = K[np.ix_(order, order)]
+    n = A.shape[0]
+    rows, cols = np.nonzero(np.tril(np.ones((n, n), bool)))
+    cp, ri, v = synth.lower_csc_from_coo(n, rows, cols, A[rows, cols])
+    h = P.SelInv(n, cp, ri)
+    with pytest.raises(P.PselinvError, match="ERR_ZERO_PIVOT"):
+        h.factor(dev(v))
+    h.factor_bk(dev(v))
+    h.selinv(P.LEVEL)
+    Xi = np.linalg.inv(A)
+    c = np.repeat(np.arange(n), np.diff(cp))
+    got = h.selected()[0].cpu().numpy()
+    assert np.max(np.abs(got - Xi[ri, c])) / np.abs(Xi).max() <= TOL
+    ld = h.logdet()[0]
+    sign, ld0 = np.linalg.slogdet(A)
+    assert abs(ld[0] - ld0) <= 1e-10 * abs(ld0) and (-1) ** int(ld[1]) == sign
+
+
+def test_bk_logdet_gradient_and_adjoint_guard(P):
+    import torch
+    p = indefinite_graph((8, 7, 6), 4.0, seed=5)
+    h = P.SelInv(p.n, p.colptr, p.rowind)
+    h.factor_bk(dev(p.values))
+    A = oracle.dense_from_lower(p.n, p.colptr, p.rowind, p.values)
+    sign, ld0 = np.linalg.slogdet(A)
+    ld = h.logdet()[0]
+    assert abs(ld[0] - ld0) <= 1e-10 * abs(ld0) and (-1) ** int(ld[1]) == sign
+    h.selinv(P.LEVEL)
+    Xi = np.linalg.inv(A)
+    c = np.repeat(np.arange(p.n), np.diff(p.colptr))
+    g = h.logdet_grad()[0].cpu().numpy()
+    want = np.where(np.asarray(p.rowind) == c, 1.0, 2.0) * Xi[p.rowind, c]
+    assert np.max(np.abs(g - want)) / np.abs(want).max() <= TOL
+    with pytest.raises(P.PselinvError, match="ERR_STATE"):
+        h.adjoint(torch.zeros(h.info["panel_entries"], dtype=torch.float64, device="cuda"))
+    h.factor(dev(p.values + 0.0 * p.values))   # back to the pivot-free factor: no pivots to report
+    with pytest.raises(P.PselinvError, match="ERR_STATE"):
+        h.pivots()
+
+
+@pytest.mark.slow
+def test_bk_full_size_indefinite_grid_closed_form(P):
+    """80^3 grid Laplacian shifted into its spectrum (indefinite, the bench
+    workload; shift -0.5 leaves 2,908 negative eigenvalues, min |lambda| =
+    6.4e-5, condition 1.8e5): sampled entries against the separable closed
+    form, which holds for any shift that is not an eigenvalue.  The bound
+    1e-9 allows for that conditioning; measured about 8e-11 (the pivot-free
+    factor gives 1.1e-10 on the same samples)."""
+    shift = -0.5
+    p = synth.config1(80, shift_const=shift)
+    h = P.SelInv(p.n, p.colptr, p.rowind)
+    h.factor_bk(dev(p.values))
+    h.selinv(P.LEVEL)
+    piv, ty = h.pivots()
+    assert (ty[0] == 1).sum() > 0
+    assert float(h.trace_error(dev(p.values))[0]) <= 1e-12
+    sel = h.selected()[0].cpu().numpy()
+    c = np.repeat(np.arange(p.n), np.diff(p.colptr))
+    rng = np.random.default_rng(12)
+    pick = rng.choice(p.nnz, size=300, replace=False)
+    nat = np.asarray(p.perm)
+    want = oracle.grid_inverse_entries(p.dims, shift, np.stack([nat[p.rowind[pick]], nat[c[pick]]], 1))
+    err = np.max(np.abs(sel[pick] - want)) / np.abs(want).max()
+    print("full-size indefinite closed-form error", err)
+    assert err <= 1e-9
