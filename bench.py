@@ -37,7 +37,7 @@ FP64_PEAK_TFLOPS = 1.10
 # the full 80^3 workload with the default schedule, from one-pass ncu
 # counters: profiles/k_gemm1_traffic_grid3d_80.md.  Set to None whenever
 # those kernels change until they are measured again.
-STEP2_TRAFFIC_BYTES_PER_LAUNCH = 449.84e6
+STEP2_TRAFFIC_BYTES_PER_LAUNCH = 460.55e6
 WORKLOAD = ("grid3d_80: 80^3 7-point Laplacian, n=512000, diag 6+U(0.01,0.1), geometric nested "
             "dissection, relaxed supernodes of width <= 128, FP64")
 # Oracle sample for the CPU baseline: the same grid family at a size the
@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--poles", type=int, default=16, help="dg_poles: number of poles in the batch")
     ap.add_argument("--split-k-rows", type=int, default=None, help="override the library default")
     ap.add_argument("--small-cutoff", type=int, default=None, help="override the library default")
+    ap.add_argument("--level-tiles", type=int, default=None, help="override the library default")
+    ap.add_argument("--min-slice-rows", type=int, default=None, help="override the library default")
     return ap.parse_args()
 
 
@@ -188,6 +190,10 @@ def tuning(args):
         kw["split_k_rows"] = args.split_k_rows
     if args.small_cutoff is not None:
         kw["small_cutoff"] = args.small_cutoff
+    if args.level_tiles is not None:
+        kw["level_tiles"] = args.level_tiles
+    if args.min_slice_rows is not None:
+        kw["min_slice_rows"] = args.min_slice_rows
     return kw
 
 
@@ -307,7 +313,8 @@ def run_ours(args):
     rr = np.diff(sym["rowptr"]).astype(float)
     rel = np.diff(sym["relptr"]).astype(float)
     g1_alg_bytes = float(np.sum(8 * rr * (rr + 1) / 2 + 16 * rr * sw + 4 * rel))
-    default_schedule = args.split_k_rows is None and args.small_cutoff is None and args.side == 80
+    default_schedule = (args.split_k_rows is None and args.small_cutoff is None and args.level_tiles is None
+                        and args.min_slice_rows is None and args.side == 80)
     roofline = {"bound": "tensor",
                 "kernel": "step 2: k_gemm1 (all tile widths, FP64 mma.sync m8n8k4, which runs on the FP64 pipe "
                           "of sm_103a) + slice reductions",
@@ -428,6 +435,8 @@ def run_workload(args):
             continue  # ~150 s per selinv at 16 poles: the level schedule only
         if unsym and mode == P.PERSISTENT:
             continue  # the persistent schedule is for symmetric handles
+        if args.no_plain and mode == P.PLAIN:
+            continue
         ms = _time(lambda: h.selinv(mode, stream=st), args.steps if name != "plain" else 1,
                    args.warmup if name != "plain" else 1, st)
         line[f"{name}_ms"] = ms
@@ -447,22 +456,17 @@ def run_workload(args):
         line["pivots_2x2"] = int((ty == 1).sum())
         line["pivots_interchanged"] = int(np.sum(piv[0] != (np.arange(p.n) - np.repeat(
             np.asarray(h.symbolic()["sn_start"][:-1]), np.diff(h.symbolic()["sn_start"])))))
+    if not (w == "dg_poles" and args.poles > 4):
+        # kernel classes of one level-schedule selinv (class 1 = step 2, and step 4 when non-symmetric)
         h.set_timing(True)
         h.selinv(P.LEVEL, stream=st)
         kms, kl = h.get_timing()
         h.set_timing(False)
-        line["step2_tflops"] = info["flops_gemm1"] / (kms[1] * 1e-3) / 1e12
-        line["step2_frac_of_fp64_peak"] = line["step2_tflops"] / FP64_PEAK_TFLOPS
-    if unsym:
-        # kernel classes of one level-schedule selinv: steps 2 and 4 are class 1
-        h.set_timing(True)
-        h.selinv(P.LEVEL, stream=st)
-        kms, kl = h.get_timing()
-        h.set_timing(False)
-        line["kernel_ms"] = {"normalise": kms[0], "step2_step4": kms[1], "step3_partials": kms[2],
-                             "step3_finish": kms[3]}
-        line["step2_step4_tflops"] = info["flops_gemm1"] / (kms[1] * 1e-3) / 1e12
-        line["step2_step4_frac_of_fp64_peak"] = line["step2_step4_tflops"] / FP64_PEAK_TFLOPS
+        s2 = "step2_step4" if unsym else "step2"
+        line["kernel_ms"] = {"normalise": kms[0], s2: kms[1], "step3_partials": kms[2], "step3_finish": kms[3]}
+        line["kernel_launches"] = [int(x) for x in kl]
+        line[f"{s2}_tflops"] = info["flops_gemm1"] * info["batch"] * (4 if cplx else 1) / (kms[1] * 1e-3) / 1e12
+        line[f"{s2}_frac_of_fp64_peak"] = line[f"{s2}_tflops"] / FP64_PEAK_TFLOPS
     if w == "graphlap48":
         # differentiable logdet: forward = factor + logdet, backward = selinv + gradient gather
         g = torch.empty(info["nnz_a"], dtype=torch.float64, device=dev)

@@ -101,6 +101,9 @@ typedef struct {
                              non-symmetric handles cap w_max at 112 (shared-memory budget of the
                              diagonal-block factorisation) */
   int64_t spin_limit_ns;  /* limit for bounded device waits; <= 0 = 1e9 */
+  int32_t level_tiles;    /* a level whose step-2 (step-3) tiles number fewer than this gets its slices
+                             (row chunks) of C shrunk until it has about this many; 0 = 16 per SM (2432) */
+  int32_t min_slice_rows; /* smallest step-2 slice that shrinking makes; 0 = 128 (step-3 chunks: a quarter) */
 } pselinv_opts;
 
 /* Sizes and work counts of an analysed handle. */
@@ -145,7 +148,8 @@ typedef struct {
 } pselinv_symbolic;
 
 /* Fill *o with defaults: F64, batch 1, w_max 128, RELAX_AMALG, padding-minimal
-   tiles, split_k_rows 1024, no debug checks, 1 s spin limit. */
+   tiles, split_k_rows 1024, no debug checks, 1 s spin limit, level_tiles and
+   min_slice_rows 0 (2432 and 128). */
 void pselinv_default_opts(pselinv_opts* o);
 
 /*
@@ -430,9 +434,11 @@ int pselinv_get_timing(pselinv_handle* h, double* h_ms, int64_t* h_launches);
  * factored handle, times pselinv_selinv (LEVEL schedule, CUDA events on
  * `stream`, best of two after a warm-up) for each candidate schedule --
  * first split_k_rows over {0, 512, 1024, 2048, 4096} with the current
- * small_cutoff, then small_cutoff over {-1, 32, 64} with the best split --
- * keeps the fastest in the handle, and returns it in h_best[0] =
- * split_k_rows, h_best[1] = small_cutoff and its time in *h_best_ms.
+ * small_cutoff, then small_cutoff over {-1, 32, 64} with the best split,
+ * then level_tiles over {608, 1216, 2432} -- keeps the fastest in the
+ * handle, and returns it in h_best[0] = split_k_rows, h_best[1] =
+ * small_cutoff, h_best[2] = level_tiles (h_best holds 3 entries) and its
+ * time in *h_best_ms.
  * Overwrites the X panels; drops a captured GRAPH schedule.  Synchronises.
  */
 int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void* stream);

@@ -43,7 +43,8 @@ class PselinvError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("batch", ctypes.c_int32), ("max_sn_width", ctypes.c_int32),
                 ("relax", ctypes.c_int32), ("small_cutoff", ctypes.c_int32), ("split_k_rows", ctypes.c_int32),
-                ("debug_checks", ctypes.c_int32), ("unsym", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64)]
+                ("debug_checks", ctypes.c_int32), ("unsym", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64),
+                ("level_tiles", ctypes.c_int32), ("min_slice_rows", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -336,12 +337,15 @@ class SelInv:
         return out.view(self.opts.batch, nnz)
 
     def autotune(self, stream=None):
-        """pselinv_autotune: returns {"split_k_rows", "small_cutoff", "ms"} and keeps that schedule."""
-        best = np.zeros(2, np.int32)
+        """pselinv_autotune: returns {"split_k_rows", "small_cutoff", "level_tiles", "ms"} and keeps
+        that schedule."""
+        best = np.zeros(3, np.int32)
         ms = np.zeros(1, np.float64)
         self._check(self._lib.pselinv_autotune(self._h, _ptr(best), _ptr(ms), _stream_ptr(stream)))
-        self.opts.split_k_rows, self.opts.small_cutoff = int(best[0]), int(best[1])
-        return {"split_k_rows": int(best[0]), "small_cutoff": int(best[1]), "ms": float(ms[0])}
+        self.opts.split_k_rows, self.opts.small_cutoff, self.opts.level_tiles = (int(best[0]), int(best[1]),
+                                                                                  int(best[2]))
+        return {"split_k_rows": int(best[0]), "small_cutoff": int(best[1]), "level_tiles": int(best[2]),
+                "ms": float(ms[0])}
 
     def set_timing(self, enable=True):
         self._check(self._lib.pselinv_set_timing(self._h, 1 if enable else 0))

@@ -452,11 +452,16 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
 int build_schedule(pselinv_handle* h) {
   {
     // Step-2 slices: at most split_k_rows rows of C each; in a level whose
-    // tiles cannot fill the GPU (fewer than kTargetTiles) the slices shrink,
-    // down to kMinSlice2 rows, until it can.  Step-3 row chunks likewise from
-    // kChunkRows down to kMinChunk3.  Slice sizes are multiples of 16.
+    // tiles cannot fill the GPU (fewer than opts.level_tiles, default
+    // kTargetTiles) the slices shrink, down to opts.min_slice_rows (default
+    // kMinSlice2) rows, until it can.  Step-3 row chunks likewise from
+    // kChunkRows down to a quarter of that minimum.  Slice sizes are
+    // multiples of 16.
     const pselinv_opts& o = h->opts;
     const bool cplx = o.dtype == PSELINV_C128;
+    const int64_t target = o.level_tiles > 0 ? o.level_tiles : kTargetTiles;
+    const int32_t min2 = o.min_slice_rows > 0 ? o.min_slice_rows : kMinSlice2;
+    const int32_t min3 = std::max<int32_t>(16, min2 / 4);
     auto slices = [](int32_t r, int32_t rows, int32_t* chunk) {
       const int32_t parts = (r + rows - 1) / rows;
       *chunk = ((r + parts - 1) / parts + 15) / 16 * 16;
@@ -476,20 +481,20 @@ int build_schedule(pselinv_handle* h) {
         t2 += mt * nt * m.ksplit;
         t3 += (int64_t)m.nchunk * st * nt;
       }
-      if (o.split_k_rows > 0 && t2 > 0 && t2 < kTargetTiles) {
-        const int64_t f = (kTargetTiles + t2 - 1) / t2;
+      if (o.split_k_rows > 0 && t2 > 0 && t2 < target) {
+        const int64_t f = (target + t2 - 1) / t2;
         for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
           SnMeta& m = h->meta[h->level_sn[t]];
-          const int32_t rows = std::max<int32_t>(kMinSlice2, (int32_t)((m.r + m.ksplit * f - 1) / (m.ksplit * f)));
+          const int32_t rows = std::max<int32_t>(min2, (int32_t)((m.r + m.ksplit * f - 1) / (m.ksplit * f)));
           if (m.r > rows) m.ksplit = slices(m.r, rows, &m.kchunk);
         }
       }
-      if (t3 > 0 && t3 < kTargetTiles) {
-        const int64_t f = (kTargetTiles + t3 - 1) / t3;
+      if (t3 > 0 && t3 < target) {
+        const int64_t f = (target + t3 - 1) / t3;
         for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
           SnMeta& m = h->meta[h->level_sn[t]];
           if (m.r == 0) continue;
-          const int32_t rows = std::max<int32_t>(kMinChunk3, (int32_t)((m.r + m.nchunk * f - 1) / (m.nchunk * f)));
+          const int32_t rows = std::max<int32_t>(min3, (int32_t)((m.r + m.nchunk * f - 1) / (m.nchunk * f)));
           m.nchunk = slices(m.r, rows, &m.kchunk3);
         }
       }

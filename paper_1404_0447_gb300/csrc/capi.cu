@@ -1044,9 +1044,21 @@ int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void
       best_cut = cut;
     }
   }
+  // third coordinate: the per-level tile target of the slice shrinking
+  int32_t best_tiles = h->opts.level_tiles;
+  for (int32_t tiles : {4 * 152, 8 * 152, 16 * 152}) {
+    if (rc || tiles == (best_tiles > 0 ? best_tiles : psi::kTargetTiles)) continue;
+    h->opts.level_tiles = tiles;
+    if ((rc = measure(best_split, best_cut, &ms))) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_tiles = tiles;
+    }
+  }
   if (!rc) {
     h->opts.split_k_rows = best_split;
     h->opts.small_cutoff = best_cut;
+    h->opts.level_tiles = best_tiles;
     rc = psi::build_schedule(h);
     if (!rc) rc = upload_schedule(h);
   }
@@ -1056,6 +1068,7 @@ int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void
   if (rc) return rc;
   h_best[0] = best_split;
   h_best[1] = best_cut;
+  h_best[2] = best_tiles > 0 ? best_tiles : psi::kTargetTiles;
   *h_best_ms = best_ms;
   h->inverted = false;  // X was overwritten by the trial runs
   return PSELINV_OK;

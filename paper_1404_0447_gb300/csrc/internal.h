@@ -66,9 +66,8 @@ struct Range {
 constexpr int kMaxWidth = 128;   // widest supernode the kernels accept
 constexpr int kMaxWidthLUComplex = 112;  // complex non-symmetric: two packed triangles in shared memory
 constexpr int kChunkRows = 512;  // rows per step-3 partial product (before the per-level boost)
-constexpr int kTargetTiles = 4 * 152;  // tiles a level should offer the GPU (4 per SM)
-constexpr int kMinSlice2 = 256;   // smallest step-2 slice the per-level boost makes
-constexpr int kMinChunk3 = 64;    // smallest step-3 chunk the per-level boost makes
+constexpr int kTargetTiles = 16 * 152;  // tiles a level should offer the GPU (16 per SM)
+constexpr int kMinSlice2 = 128;   // smallest step-2 slice the per-level boost makes
 constexpr int kTileM = 64;       // output tile rows of the grouped GEMMs
 constexpr int kTileN = 64;       // output tile columns
 
