@@ -80,9 +80,9 @@ extern "C" {
 #define PSELINV_PLAIN 0 /* one supernode per launch, reverse postorder */
 #define PSELINV_LEVEL 1 /* one grouped launch per kernel per level of Algorithm 2 */
 #define PSELINV_GRAPH 2 /* the LEVEL sequence captured once into a CUDA graph and replayed */
-#define PSELINV_PERSISTENT 3 /* one persistent launch per level running all of that level's work from
-                                one task list with bounded dependency waits; captured once into a
-                                CUDA graph and replayed */
+#define PSELINV_PERSISTENT 3 /* one persistent launch for the whole sweep running every level's work
+                                from one task list with bounded dependency waits and no barrier
+                                between levels; captured once into a CUDA graph and replayed */
 
 typedef struct pselinv_handle pselinv_handle;
 

@@ -546,19 +546,26 @@ int build_schedule(pselinv_handle* h) {
   };
   build(h->t_lhat, true, by_width, rect);
   build(h->t_rect, false, by_width, rect);
-  build(h->t_gemm1, false, by_width, [&](int32_t k, int bn, std::vector<Task>& out) {  // step 2: + k-parts
+  auto step2_tiles = [&](int32_t k, int bn, std::vector<Task>& out) {  // step 2: + k-parts
     const SnMeta& m = h->meta[k];
     for (int32_t c = 0; c < m.ksplit; ++c)
       for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
         for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, c});
-  });
-  build(h->t_trsm, false, by_width, rect);
-  build(h->t_gemm2, false, by_width, [&](int32_t k, int bn, std::vector<Task>& out) {
+  };
+  auto step3_tiles = [&](int32_t k, int bn, std::vector<Task>& out) {
     const SnMeta& m = h->meta[k];
     for (int32_t c = 0; c < m.nchunk; ++c)
       for (int32_t m0 = 0; m0 < m.s; m0 += kTileM)
         for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, c});
-  });
+  };
+  build(h->t_gemm1, false, by_width, step2_tiles);
+  build(h->t_trsm, false, by_width, rect);
+  build(h->t_gemm2, false, by_width, step3_tiles);
+  // the persistent kernel holds one shared-memory tile for every task kind,
+  // so its lists stop at 64 x 16 tiles (register budget: more CTAs per SM)
+  auto by_width_narrow = [&](int32_t k) { return std::min(by_width(k), kPersistentMaxVar); };
+  build(h->t_pgemm1, false, by_width_narrow, step2_tiles);
+  build(h->t_pgemm2, false, by_width_narrow, step3_tiles);
   build(h->t_schur, false, by_rows, [&](int32_t k, int bn, std::vector<Task>& out) {
     const SnMeta& m = h->meta[k];
     for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
@@ -589,20 +596,20 @@ int build_schedule(pselinv_handle* h) {
   h->pn1.assign(nsn, 0);
   h->pn2.assign(nsn, 0);
   for (int32_t k = 0; k < nsn; ++k) {
-    h->pn1[k] = (int32_t)(h->t_gemm1.per_sn[k].end - h->t_gemm1.per_sn[k].begin);
-    h->pn2[k] = (int32_t)(h->t_gemm2.per_sn[k].end - h->t_gemm2.per_sn[k].begin);
+    h->pn1[k] = (int32_t)(h->t_pgemm1.per_sn[k].end - h->t_pgemm1.per_sn[k].begin);
+    h->pn2[k] = (int32_t)(h->t_pgemm2.per_sn[k].end - h->t_pgemm2.per_sn[k].begin);
   }
   for (int32_t l = 0; l < nl; ++l) {
     h->plevel_ptr[l] = (int64_t)h->plist.size();
     for (int v = 0; v < kNumVar; ++v) {
-      const Range rg = h->t_gemm1.per_lv[(size_t)l * kNumVar + v];
+      const Range rg = h->t_pgemm1.per_lv[(size_t)l * kNumVar + v];
       for (int64_t t = rg.begin; t < rg.end; ++t) h->plist.push_back({P_STEP2, (int16_t)v, (int32_t)t});
     }
     for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t)
       if (h->meta[h->level_sn[t]].ksplit > 1)
         for (int g = 0; g < kReduceGroups; ++g) h->plist.push_back({P_REDUCE, (int16_t)g, h->level_sn[t]});
     for (int v = 0; v < kNumVar; ++v) {
-      const Range rg = h->t_gemm2.per_lv[(size_t)l * kNumVar + v];
+      const Range rg = h->t_pgemm2.per_lv[(size_t)l * kNumVar + v];
       for (int64_t t = rg.begin; t < rg.end; ++t) h->plist.push_back({P_STEP3, (int16_t)v, (int32_t)t});
     }
     for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t)

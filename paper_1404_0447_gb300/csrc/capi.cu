@@ -68,7 +68,7 @@ void free_device(pselinv_handle* h) {
   void** ptrs[] = {&h->d_meta, &h->d_desc, &h->d_relidx, &h->d_valmap, &h->d_diagmask, &h->d_tasks, &h->d_levelsn,
                    &h->d_L,    &h->d_X,    &h->d_D,      &h->d_lhat,   &h->d_linv,  &h->d_part, &h->d_ypart,
                    &h->d_status, &h->d_flipmap, &h->d_U, &h->d_XU, &h->d_uhat, &h->d_uinv,
-                   &h->d_piv, &h->d_ptype, &h->d_E,
+                   &h->d_piv, &h->d_ptype, &h->d_E, &h->d_snlevel, &h->d_yring, &h->d_pring,
                    &h->d_xb,   &h->d_lb,   &h->d_db,     &h->d_zb,     &h->d_w1,    &h->d_yb,   &h->d_hb,
                    &h->d_plist, &h->d_pn,  &h->d_pctr};
   for (void** p : ptrs) {
@@ -113,6 +113,15 @@ int ensure_device(pselinv_handle* h) {
   if ((rc = upload(h, &h->d_valmap, h->valmap))) return rc;
   if ((rc = upload(h, &h->d_diagmask, h->diagmask))) return rc;
   if ((rc = upload(h, &h->d_levelsn, h->level_sn))) return rc;
+  {
+    // level of every supernode, supernodal parents, level offsets (persistent schedule)
+    std::vector<int32_t> v(2 * (size_t)h->nsn + h->nlevels + 1);
+    for (int32_t l = 0; l < h->nlevels; ++l)
+      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) v[h->level_sn[t]] = l;
+    std::copy(h->sn_parent.begin(), h->sn_parent.end(), v.begin() + h->nsn);
+    std::copy(h->level_ptr.begin(), h->level_ptr.end(), v.begin() + 2 * (size_t)h->nsn);
+    if ((rc = upload(h, &h->d_snlevel, v))) return rc;
+  }
   if ((rc = upload_schedule(h))) return rc;
   const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
   if ((rc = alloc(h, &h->d_L, B * h->panel_total * es))) return rc;
@@ -137,7 +146,8 @@ int ensure_device(pselinv_handle* h) {
 // called again by the autotuner after build_schedule.
 int upload_schedule(pselinv_handle* h) {
   int rc;
-  void** old[] = {&h->d_meta, &h->d_tasks, &h->d_part, &h->d_ypart, &h->d_plist, &h->d_pn, &h->d_pctr};
+  void** old[] = {&h->d_meta, &h->d_tasks, &h->d_part, &h->d_ypart, &h->d_plist, &h->d_pn, &h->d_pctr,
+                   &h->d_yring, &h->d_pring};
   for (void** p : old)
     if (*p) {
       cudaFree(*p);
@@ -163,6 +173,10 @@ int upload_schedule(pselinv_handle* h) {
   all.insert(all.end(), h->t_schur.tasks.begin(), h->t_schur.tasks.end());
   h->off_rect = (int64_t)all.size();
   all.insert(all.end(), h->t_rect.tasks.begin(), h->t_rect.tasks.end());
+  h->off_pgemm1 = (int64_t)all.size();
+  all.insert(all.end(), h->t_pgemm1.tasks.begin(), h->t_pgemm1.tasks.end());
+  h->off_pgemm2 = (int64_t)all.size();
+  all.insert(all.end(), h->t_pgemm2.tasks.begin(), h->t_pgemm2.tasks.end());
   if ((rc = upload(h, &h->d_tasks, all))) return rc;
   const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
   if ((rc = alloc(h, &h->d_part, B * h->part_max * es))) return rc;
@@ -171,16 +185,27 @@ int upload_schedule(pselinv_handle* h) {
   std::vector<int32_t> pn(h->pn1);
   pn.insert(pn.end(), h->pn2.begin(), h->pn2.end());
   if ((rc = upload(h, &h->d_pn, pn))) return rc;
-  if ((rc = alloc(h, &h->d_pctr, (int64_t)sizeof(int) * (3 * B * h->nsn + h->nlevels)))) return rc;
+  if ((rc = alloc(h, &h->d_pctr, (int64_t)sizeof(int) * (4 * B * h->nsn + h->nlevels + 1)))) return rc;
+  return PSELINV_OK;
+}
+
+// Ring of kRing level slots for the persistent schedule's partial products
+// (allocated before its graph is captured; dropped with the schedule).
+int ensure_ring(pselinv_handle* h) {
+  if (h->d_yring) return PSELINV_OK;
+  const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
+  int rc;
+  if ((rc = alloc(h, &h->d_yring, B * psi::kRing * h->ypart_max * es))) return rc;
+  if ((rc = alloc(h, &h->d_pring, B * psi::kRing * h->part_max * es))) return rc;
   return PSELINV_OK;
 }
 
 // Persistent schedule: reset the counters, the normalisation pass, then one
-// persistent launch per level.
+// persistent launch over every level.
 int enqueue_persistent(pselinv_handle* h, cudaStream_t st) {
-  const psi::KArgs a = kargs(h);
+  psi::KArgs a = kargs(h);
   const int64_t B = h->opts.batch;
-  PSI_CUDA(h, cudaMemsetAsync(h->d_pctr, 0, sizeof(int) * (3 * B * h->nsn + h->nlevels), st));
+  PSI_CUDA(h, cudaMemsetAsync(h->d_pctr, 0, sizeof(int) * (4 * B * h->nsn + h->nlevels + 1), st));
   PSI_CUDA(h, psi::launch_per_sn(psi::Kern::NormDiag, a, nullptr, h->nsn, st));
   for (int v = 0; v < psi::kNumVar; ++v) {
     const psi::Range r = h->t_lhat.whole[v];
@@ -188,22 +213,31 @@ int enqueue_persistent(pselinv_handle* h, cudaStream_t st) {
   }
   psi::PArgs p;
   int* ctr = (int*)h->d_pctr;
-  p.g1 = tasks_at(h, h->off_gemm1, 0);
-  p.g2 = tasks_at(h, h->off_gemm2, 0);
+  p.g1 = tasks_at(h, h->off_pgemm1, 0);
+  p.g2 = tasks_at(h, h->off_pgemm2, 0);
   p.c1 = ctr;
   p.c2 = ctr + B * h->nsn;
   p.cr = ctr + 2 * B * h->nsn;
-  p.head = ctr + 3 * B * h->nsn;
+  p.cf = ctr + 3 * B * h->nsn;
+  p.lvl = ctr + 4 * B * h->nsn;
+  p.head = p.lvl + h->nlevels;
   p.n1 = (const int32_t*)h->d_pn;
   p.n2 = (const int32_t*)h->d_pn + h->nsn;
+  p.snlevel = (const int32_t*)h->d_snlevel;
+  p.snparent = p.snlevel + h->nsn;
+  p.level_ptr = p.snparent + h->nsn;
   p.nsn = h->nsn;
+  p.yslot = h->ypart_max;
+  p.pslot = h->part_max;
   p.spin_ns = h->opts.spin_limit_ns > 0 ? h->opts.spin_limit_ns : 1000000000LL;
-  const psi::PTask* list = (const psi::PTask*)h->d_plist;
-  for (int32_t l = 0; l < h->nlevels; ++l) {
-    const int64_t b0 = h->plevel_ptr[l], n = h->plevel_ptr[l + 1] - b0;
-    const int grid = (int)std::min<int64_t>(h->pgrid, n * B);
-    PSI_CUDA(h, psi::launch_persistent_level(a, p, list + b0, (int)n, l, grid, st));
-  }
+  // partial products in the ring: member stride kRing slots
+  a.ypart = h->d_yring;
+  a.part = h->d_pring;
+  a.sz.ypart = psi::kRing * h->ypart_max;
+  a.sz.part = psi::kRing * h->part_max;
+  const int64_t n = h->plevel_ptr[h->nlevels];
+  const int grid = (int)std::min<int64_t>(h->pgrid, n * B);
+  PSI_CUDA(h, psi::launch_persistent(a, p, (const psi::PTask*)h->d_plist, n, grid, st));
   return PSELINV_OK;
 }
 
@@ -652,6 +686,8 @@ int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream) {
     return set_err(h, PSELINV_ERR_ARG, "the PERSISTENT schedule is for symmetric handles");
   cudaStream_t st = (cudaStream_t)stream;
   if (mode == PSELINV_PERSISTENT) {
+    int rrc = ensure_ring(h);
+    if (rrc) return rrc;
     if (!h->pgraph_exec) {
       if (!h->graph_stream) {
         cudaStream_t cs;
@@ -1093,7 +1129,8 @@ int pselinv_get_info(const pselinv_handle* h, pselinv_info* info) {
   if (h->dev_sym) {
     const int64_t B = h->opts.batch, es = (int64_t)elem_size(h), tasks =
         (int64_t)(h->t_lhat.tasks.size() + h->t_gemm1.tasks.size() + h->t_gemm2.tasks.size() +
-                  h->t_trsm.tasks.size() + h->t_schur.tasks.size() + h->t_rect.tasks.size());
+                  h->t_trsm.tasks.size() + h->t_schur.tasks.size() + h->t_rect.tasks.size() +
+                  h->t_pgemm1.tasks.size() + h->t_pgemm2.tasks.size());
     int64_t bytes = (int64_t)(sizeof(psi::SnMeta) * h->meta.size() + sizeof(psi::ColDesc) * h->desc.size() +
                               4 * h->relidx.size() + 8 * h->valmap.size() + h->diagmask.size() +
                               4 * h->level_sn.size()) +
@@ -1101,6 +1138,8 @@ int pselinv_get_info(const pselinv_handle* h, pselinv_info* info) {
                     B * es * (2 * h->panel_total + h->n + h->lhat_total + h->linv_total + h->part_max + h->ypart_max);
     if (h->d_xb) bytes += B * es * (2 * h->panel_total + h->n + 2 * h->linv_total + 2 * h->lhat_total);
     if (h->opts.unsym) bytes += h->flipmap.size() + B * es * (2 * h->panel_total + h->lhat_total + h->linv_total);
+    if (h->d_yring) bytes += B * es * psi::kRing * (h->ypart_max + h->part_max);
+    bytes += 4 * (2 * (int64_t)h->nsn + h->nlevels + 1);  // level / parent / level offsets
     info->device_bytes = bytes;
   } else {
     info->device_bytes = 0;

@@ -73,6 +73,7 @@ constexpr int kTileN = 64;       // output tile columns
 
 // Tile-width variants of the tile GEMMs: BN = 8 << var.
 constexpr int kNumVar = 4;
+constexpr int kPersistentMaxVar = 0;  // the persistent kernel's tiles stop at BN = 8
 
 // Tile width of an output with `width` columns: the variant with the least
 // padded width ceil(width / BN) * BN, the wider tile on ties; complex tiles
@@ -136,6 +137,8 @@ struct pselinv_handle {
   psi::TaskList t_gemm2;  // step 3 partial-product tiles
   psi::TaskList t_trsm;   // factorisation: off-diagonal panel solve tiles
   psi::TaskList t_schur;  // factorisation: Schur-complement update tiles
+  psi::TaskList t_pgemm1; // persistent schedule: step-2 tiles, widths <= 16
+  psi::TaskList t_pgemm2; // persistent schedule: step-3 tiles, widths <= 16
 
   // ---- device state ----
   int device = -1;
@@ -150,6 +153,7 @@ struct pselinv_handle {
   void* d_flipmap = nullptr;
   void* d_tasks = nullptr;  // all task arrays back to back
   int64_t off_lhat = 0, off_gemm1 = 0, off_gemm2 = 0, off_trsm = 0, off_schur = 0, off_rect = 0;
+  int64_t off_pgemm1 = 0, off_pgemm2 = 0;
   void* d_levelsn = nullptr;
   void* d_L = nullptr;      // L panels (unit diagonal implied; D on the diagonal slots)
   void* d_X = nullptr;      // X panels
@@ -180,7 +184,10 @@ struct pselinv_handle {
   int64_t device_bytes = 0;
   void* d_plist = nullptr;  // persistent schedule
   void* d_pn = nullptr;     // pn1 then pn2
-  void* d_pctr = nullptr;   // c1, c2, cr counters, then per-level heads
+  void* d_pctr = nullptr;   // c1, c2, cr, cf counters, per-level finish counts, dequeue head
+  void* d_snlevel = nullptr; // level per supernode, supernodal parents, level offsets
+  void* d_yring = nullptr;   // persistent schedule: kRing level slots of step-2 partials
+  void* d_pring = nullptr;   // ... and of step-3 partials
   int pgrid = 0;
   void* pgraph_exec = nullptr;  // cudaGraphExec_t of the PERSISTENT schedule
   int debug_flags = 0;

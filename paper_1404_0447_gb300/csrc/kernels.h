@@ -94,14 +94,23 @@ struct PArgs {
   int* c1;              // [batch][nsn] finished step-2 tiles
   int* c2;              // [batch][nsn] finished step-3 tiles
   int* cr;              // [batch][nsn] finished slice reductions
+  int* cf;              // [batch][nsn] finished step-3 finish parts (X of the supernode final at kFinishParts)
+  int* lvl;             // [nlevels] finished finish parts of a level, all batch members
   const int32_t* n1;    // [nsn] step-2 tiles per supernode
   const int32_t* n2;    // [nsn] step-3 tiles per supernode
-  int* head;            // [nlevels] dequeue counters
+  const int32_t* snlevel;   // [nsn] level (0 = roots)
+  const int32_t* snparent;  // [nsn] supernodal parent, -1 = root
+  const int32_t* level_ptr; // [nlevels + 1] supernodes per level (prefix sums)
+  int* head;            // dequeue counter
   int nsn;
+  int64_t yslot, pslot; // elements of one level slot of the step-2 / step-3 partial buffers
   long long spin_ns;    // bound of every wait
 };
-cudaError_t launch_persistent_level(const KArgs& a, const PArgs& p, const PTask* list, int ntask, int level,
-                                    int grid, cudaStream_t st);
+// Slots of the partial-product ring: a level starts its step 2 only once the
+// level kRing above it has finished, so at most kRing levels hold partials.
+constexpr int kRing = 4;
+cudaError_t launch_persistent(const KArgs& a, const PArgs& p, const PTask* list, int64_t ntask, int grid,
+                              cudaStream_t st);
 cudaError_t persistent_grid(int dtype, int* grid);
 
 // ---- adjoint (adjoint.cu) ----

@@ -1,17 +1,25 @@
-// Persistent schedule: one launch per level of Algorithm 2 runs every piece
-// of that level's work -- step-2 tiles (all tile widths and k-slices), the
-// slice reductions, step-3 partial-product tiles and the step-3 finish --
-// from one task list, in cost order.  CTAs take tasks with an atomic
-// counter; a task whose inputs come from earlier tasks of the same launch
-// waits on per-supernode completion counters.
+// Persistent schedule: one launch runs the whole level loop of Algorithm 3
+// -- step-2 tiles (all tile widths and k-slices), slice reductions, step-3
+// partial-product tiles and the step-3 finish of every supernode -- from one
+// task list in level order (levels top-down, costliest supernode first
+// inside a level).  CTAs take tasks with an atomic counter; there is no
+// barrier between levels (the dynamic scheduling of Section 3.3 on one GPU):
+//   * a supernode's step 2 reads X of its ancestors that hold rows of C, and
+//     C_K lies in P and C_P for the supernodal parent P, so it waits only
+//     until P's X is final (all finish parts of P done);
+//   * partial products live in a ring of kRing level slots, so a level's
+//     step 2 also waits until the level kRing above it has finished;
+//   * reductions, step-3 tiles and the finish wait on per-supernode
+//     completion counters of the tasks before them.
 //
-// Why this cannot deadlock: tasks are taken in list order and a task only
-// waits on tasks earlier in the list, which are already held by running
-// CTAs that themselves only wait on still earlier tasks; the earliest
-// unfinished task never waits.  Every wait is bounded in time (spin_limit_ns
-// of %globaltimer); when one runs out the kernel raises a timeout flag in the
-// status words, every other wait returns at once, the remaining tasks are
-// skipped and the launch ends.  pselinv_sync_status reports it.
+// Why this cannot deadlock: every CTA of the grid is resident; tasks are
+// taken in list order and a task only waits on tasks earlier in the list,
+// which are held by running CTAs that themselves only wait on still earlier
+// tasks; the earliest unfinished task never waits.  Every wait is bounded in
+// time (spin_limit_ns of %globaltimer); when one runs out the kernel raises a
+// timeout flag in the status words, every other wait returns at once, the
+// remaining tasks are skipped and the launch ends.  pselinv_sync_status
+// reports it.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -66,44 +74,59 @@ __device__ void cta_signal(int* ctr) {
   }
 }
 
+// Publish one finished finish part: the supernode's and the level's counters.
+__device__ void cta_signal2(int* ctr1, int* ctr2) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr1, 1);
+    atomicAdd(ctr2, 1);
+  }
+}
+
 template <class T>
-__global__ void __launch_bounds__(TG_THREADS) k_persistent_level(KArgs a, PArgs p, const PTask* __restrict__ list,
-                                                                 int ntask, int level) {
-  constexpr int MAXBN = Sc<T>::P == 1 ? 64 : 32;
+__global__ void __launch_bounds__(TG_THREADS, Sc<T>::P == 1 ? 8 : 5) k_persistent(KArgs a, PArgs p, const PTask* __restrict__ list,
+                                                           int64_t ntask) {
+  constexpr int MAXBN = 8 << kPersistentMaxVar;  // the task lists stop at this width
   __shared__ __align__(16) unsigned char smraw[sizeof(TileSmem<T, MAXBN>)];
-  __shared__ int s_item;
+  __shared__ long long s_item;
   const int batch = a.sz.batch;
-  const int total = ntask * batch;
+  const long long total = ntask * batch;
   int* status = a.status;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(p.head + level, 1);
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(p.head, 1);
     __syncthreads();
-    const int item = s_item;
+    const long long item = s_item;
     __syncthreads();
     if (item >= total) break;
     const PTask pt = list[item / batch];
-    const int b = item % batch;
+    const int b = (int)(item % batch);
     const bool aborted = *(volatile int*)(status + 2) != 0;
     if (aborted) continue;  // drain the list
     const int64_t cb = (int64_t)b * p.nsn;
     switch (pt.kind) {
       case P_STEP2: {
         const Task tk = p.g1[pt.idx];
-        switch (pt.var) {
-          case 0: step2_tile<T, 8>(a, tk, b, *reinterpret_cast<TileSmem<T, 8>*>(smraw)); break;
-          case 1: step2_tile<T, 16>(a, tk, b, *reinterpret_cast<TileSmem<T, 16>*>(smraw)); break;
-          case 2: step2_tile<T, 32>(a, tk, b, *reinterpret_cast<TileSmem<T, 32>*>(smraw)); break;
-          default:
-            if constexpr (MAXBN == 64) step2_tile<T, 64>(a, tk, b, *reinterpret_cast<TileSmem<T, 64>*>(smraw));
-            break;
+        const int k = tk.sn, l = p.snlevel[k];
+        if (l >= kRing) {  // the level using the same partial-product slot has finished
+          const int lr = l - kRing;
+          const int target = (p.level_ptr[lr + 1] - p.level_ptr[lr]) * kFinishParts * batch;
+          if (!cta_wait(p.lvl + lr, target, p.spin_ns, status)) break;
         }
-        cta_signal(p.c1 + cb + tk.sn);
+        const int par = p.snparent[k];
+        if (par >= 0 && !cta_wait(p.cf + cb + par, kFinishParts, p.spin_ns, status)) break;
+        const int64_t yoff = (int64_t)(l % kRing) * p.yslot;
+        if (pt.var == 0)
+          step2_tile<T, 8>(a, tk, b, *reinterpret_cast<TileSmem<T, 8>*>(smraw), yoff);
+        else
+          step2_tile<T, MAXBN>(a, tk, b, *reinterpret_cast<TileSmem<T, MAXBN>*>(smraw), yoff);
+        cta_signal(p.c1 + cb + k);
         break;
       }
       case P_REDUCE: {
         const int k = pt.idx;
         if (!cta_wait(p.c1 + cb + k, p.n1[k], p.spin_ns, status)) break;
-        step2_reduce<T>(a, k, b, pt.var, kReduceGroups, true);
+        step2_reduce<T>(a, k, b, pt.var, kReduceGroups, true, (int64_t)(p.snlevel[k] % kRing) * p.yslot);
         cta_signal(p.cr + cb + k);
         break;
       }
@@ -113,22 +136,19 @@ __global__ void __launch_bounds__(TG_THREADS) k_persistent_level(KArgs a, PArgs 
         const bool split = a.meta[k].ksplit > 1;
         if (!cta_wait(split ? p.cr + cb + k : p.c1 + cb + k, split ? kReduceGroups : p.n1[k], p.spin_ns, status))
           break;
-        switch (pt.var) {
-          case 0: step3_tile<T, 8>(a, tk, b, *reinterpret_cast<TileSmem<T, 8>*>(smraw), true); break;
-          case 1: step3_tile<T, 16>(a, tk, b, *reinterpret_cast<TileSmem<T, 16>*>(smraw), true); break;
-          case 2: step3_tile<T, 32>(a, tk, b, *reinterpret_cast<TileSmem<T, 32>*>(smraw), true); break;
-          default:
-            if constexpr (MAXBN == 64) step3_tile<T, 64>(a, tk, b, *reinterpret_cast<TileSmem<T, 64>*>(smraw), true);
-            break;
-        }
+        const int64_t poff = (int64_t)(p.snlevel[k] % kRing) * p.pslot;
+        if (pt.var == 0)
+          step3_tile<T, 8>(a, tk, b, *reinterpret_cast<TileSmem<T, 8>*>(smraw), true, poff);
+        else
+          step3_tile<T, MAXBN>(a, tk, b, *reinterpret_cast<TileSmem<T, MAXBN>*>(smraw), true, poff);
         cta_signal(p.c2 + cb + k);
         break;
       }
       default: {  // P_FINISH
-        const int k = pt.idx;
+        const int k = pt.idx, l = p.snlevel[k];
         int target = p.n2[k];
         const int* ctr = p.c2 + cb + k;
-        if (target == 0) {  // no step-3 tiles (r = 0): nothing to wait for in this launch
+        if (target == 0) {  // no step-3 tiles (r = 0): nothing to wait for
           ctr = nullptr;
         }
         // failure-detection support: one armed finish task waits for a
@@ -141,20 +161,21 @@ __global__ void __launch_bounds__(TG_THREADS) k_persistent_level(KArgs a, PArgs 
           target = p.n2[k] + 1;
         }
         if (ctr && !cta_wait(ctr, target, p.spin_ns, status)) break;
-        step3_finish<T>(a, k, b, pt.var, kFinishParts, true);
+        step3_finish<T>(a, k, b, pt.var, kFinishParts, true, (int64_t)(l % kRing) * p.pslot);
+        cta_signal2(p.cf + cb + k, p.lvl + l);
         break;
       }
     }
   }
 }
 
-cudaError_t launch_persistent_level(const KArgs& a, const PArgs& p, const PTask* list, int ntask, int level,
-                                    int grid, cudaStream_t st) {
+cudaError_t launch_persistent(const KArgs& a, const PArgs& p, const PTask* list, int64_t ntask, int grid,
+                              cudaStream_t st) {
   if (ntask <= 0) return cudaSuccess;
   if (a.dtype == PSELINV_C128)
-    k_persistent_level<Cplx><<<grid, TG_THREADS, 0, st>>>(a, p, list, ntask, level);
+    k_persistent<Cplx><<<grid, TG_THREADS, 0, st>>>(a, p, list, ntask);
   else
-    k_persistent_level<double><<<grid, TG_THREADS, 0, st>>>(a, p, list, ntask, level);
+    k_persistent<double><<<grid, TG_THREADS, 0, st>>>(a, p, list, ntask);
   return cudaGetLastError();
 }
 
@@ -164,8 +185,8 @@ cudaError_t persistent_grid(int dtype, int* grid) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
     e = dtype == PSELINV_C128
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent_level<Cplx>, TG_THREADS, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent_level<double>, TG_THREADS, 0);
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<Cplx>, TG_THREADS, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<double>, TG_THREADS, 0);
   if (e == cudaSuccess) *grid = sms * (per > 0 ? per : 1);
   return e;
 }

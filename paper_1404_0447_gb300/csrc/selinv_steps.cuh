@@ -39,8 +39,11 @@ __device__ __forceinline__ T ld_maybe_cg(const T* p, bool cg) {
 // transposed form, X_{K,C}^T = -X_{C,C}^T Uhat_{K,C}^T, is this same tile
 // with X and XU swapped and Uhat^T in place of Lhat: it then writes the XU
 // panel rows.
+// yoff / poff (persistent schedule): element offset of the level's slot in
+// the step-2 / step-3 partial-product buffers (0 for the per-level launches).
 template <class T, int BN, bool UNSYM = false>
-__device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b, TileSmem<T, BN>& sm) {
+__device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b, TileSmem<T, BN>& sm,
+                                           int64_t yoff = 0) {
   const Sizes& sz = a.sz;
   const SnMeta m = a.meta[tk.sn];
   const int s = m.s, r = m.r, ld = s + r;
@@ -77,7 +80,7 @@ __device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b
       if (row < r && col < s) out[row + (int64_t)pcol(a, b, m.f, col) * ld] = -v;
     });
   } else {
-    T* out = (T*)a.ypart + b * sz.ypart + m.ypart + (int64_t)tk.c * r * s;
+    T* out = (T*)a.ypart + b * sz.ypart + yoff + m.ypart + (int64_t)tk.c * r * s;
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int row = tk.m0 + mm, col = tk.n0 + nn;
       if (row < r && col < s) out[row + (int64_t)col * r] = v;
@@ -88,12 +91,13 @@ __device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b
 // Step 2 finish of a split supernode k: X_{C,K} = -(sum of the slice
 // partial products, in slice order), columns col0, col0 + cstride, ...
 template <class T>
-__device__ __forceinline__ void step2_reduce(const KArgs& a, int k, int b, int col0, int cstride, bool cg) {
+__device__ __forceinline__ void step2_reduce(const KArgs& a, int k, int b, int col0, int cstride, bool cg,
+                                             int64_t yoff = 0) {
   const Sizes& sz = a.sz;
   const SnMeta m = a.meta[k];
   if (m.ksplit == 1) return;
   const int s = m.s, r = m.r, ld = s + r;
-  const T* yp = (const T*)a.ypart + b * sz.ypart + m.ypart;
+  const T* yp = (const T*)a.ypart + b * sz.ypart + yoff + m.ypart;
   T* out = (T*)a.X + b * sz.panel + m.panel + s;
   const int64_t rs = (int64_t)r * s;
   for (int j = col0; j < s; j += cstride) {
@@ -110,7 +114,8 @@ __device__ __forceinline__ void step2_reduce(const KArgs& a, int k, int b, int c
 // Step 3 partial product tile: P_c = Lhat_{rows c, K}^T X_{rows c, K} over a
 // chunk of kchunk3 rows of C (plain transpose; s x s output tiles).
 template <class T, int BN>
-__device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b, TileSmem<T, BN>& sm, bool cg) {
+__device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b, TileSmem<T, BN>& sm, bool cg,
+                                           int64_t poff = 0) {
   const Sizes& sz = a.sz;
   const SnMeta m = a.meta[tk.sn];
   const int s = m.s, r = m.r, ld = s + r;
@@ -128,7 +133,7 @@ __device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b
   };
   const int kb = tk.c * m.kchunk3, ke = min(r, kb + m.kchunk3);
   tile_mma<T, BN>(sm, kb, ke, [](int) { return true; }, la, lb, acc);
-  T* out = (T*)a.part + b * sz.part + m.part + (int64_t)tk.c * s * s;
+  T* out = (T*)a.part + b * sz.part + poff + m.part + (int64_t)tk.c * s * s;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
     if (row < s && col < s) out[row + col * s] = v;
@@ -143,12 +148,13 @@ __device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b
 // Non-symmetric handles (a.XU set): X_KK = Z as it is, and Z^T goes to the
 // diagonal block of the XU panel.
 template <class T>
-__device__ __forceinline__ void step3_finish(const KArgs& a, int k, int b, int part, int nparts, bool cg) {
+__device__ __forceinline__ void step3_finish(const KArgs& a, int k, int b, int part, int nparts, bool cg,
+                                             int64_t poff = 0) {
   const Sizes& sz = a.sz;
   const SnMeta m = a.meta[k];
   const int s = m.s, ld = m.s + m.r;
   T* XK = (T*)a.X + b * sz.panel + m.panel;
-  const T* pp = (const T*)a.part + b * sz.part + m.part;
+  const T* pp = (const T*)a.part + b * sz.part + poff + m.part;
   if (a.XU) {
     T* XUK = (T*)a.XU + b * sz.panel + m.panel;
     for (int e = threadIdx.x + part * blockDim.x; e < s * s; e += nparts * blockDim.x) {
