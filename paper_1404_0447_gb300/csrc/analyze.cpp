@@ -562,7 +562,7 @@ int build_schedule(pselinv_handle* h) {
   build(h->t_trsm, false, by_width, rect);
   build(h->t_gemm2, false, by_width, step3_tiles);
   // the persistent kernel holds one shared-memory tile for every task kind,
-  // so its lists stop at 64 x 16 tiles (register budget: more CTAs per SM)
+  // so its lists stop at 64 x (8 << kPersistentMaxVar) tiles (register budget: more CTAs per SM)
   auto by_width_narrow = [&](int32_t k) { return std::min(by_width(k), kPersistentMaxVar); };
   build(h->t_pgemm1, false, by_width_narrow, step2_tiles);
   build(h->t_pgemm2, false, by_width_narrow, step3_tiles);

@@ -137,8 +137,8 @@ struct pselinv_handle {
   psi::TaskList t_gemm2;  // step 3 partial-product tiles
   psi::TaskList t_trsm;   // factorisation: off-diagonal panel solve tiles
   psi::TaskList t_schur;  // factorisation: Schur-complement update tiles
-  psi::TaskList t_pgemm1; // persistent schedule: step-2 tiles, widths <= 16
-  psi::TaskList t_pgemm2; // persistent schedule: step-3 tiles, widths <= 16
+  psi::TaskList t_pgemm1; // persistent schedule: step-2 tiles, widths <= 8 << kPersistentMaxVar
+  psi::TaskList t_pgemm2; // persistent schedule: step-3 tiles, widths <= 8 << kPersistentMaxVar
 
   // ---- device state ----
   int device = -1;
