@@ -97,7 +97,7 @@ def oracle_sample_tflops(side=CPU_SAMPLE_SIDE):
     (TFLOP/s by the algorithmic count of that instance, seconds, flops)."""
     import oracle
     import synth
-    p = synth.config1(side)
+    p = synth.grid3d(side)
     sym = oracle.analyse(p.n, p.colptr, p.rowind, 128, 1)
     lcp, lri = oracle.supernodal_pattern(p.n, sym["sn_start"], sym["rcount"], sym["rrows"])
     lv, d = oracle.ldlt(p.n, sym["colptr"], sym["rowind"], p.values, lcp, lri)
@@ -210,7 +210,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     P.load_library()
 
-    prob = synth.config1(args.side)
+    prob = synth.grid3d(args.side)
     h = P.SelInv(prob.n, prob.colptr, prob.rowind, max_sn_width=128, relax=P.RELAX_AMALG, **tuning(args))
     info = h.info
     flops = info["flops_selinv"]
@@ -383,7 +383,7 @@ def run_workload(args):
     w = args.workload
     line = {"workload": w, "steps": args.steps, "warmup": args.warmup}
     if w == "grid2d_31":
-        p = synth.config0()
+        p = synth.grid2d_31()
         h = P.SelInv(p.n, p.colptr, p.rowind, max_sn_width=128, relax=P.RELAX_NONE, **tuning(args))
         vals = torch.tensor(p.values, dtype=torch.float64, device=dev)
         cplx = False
@@ -403,7 +403,7 @@ def run_workload(args):
     elif w == "indefinite80":
         # symmetric indefinite: the 80^3 grid Laplacian shifted by -0.5 into its spectrum
         # (2,908 negative eigenvalues), factored with Bunch-Kaufman 1x1/2x2 pivots inside supernodes
-        p = synth.config1(80, shift_const=-0.5)
+        p = synth.grid3d(80, shift_const=-0.5)
         h = P.SelInv(p.n, p.colptr, p.rowind, **tuning(args))
         vals = torch.tensor(p.values, dtype=torch.float64, device=dev)
         cplx = False
@@ -415,7 +415,7 @@ def run_workload(args):
         vals_up = torch.tensor(p.values_up, dtype=torch.float64, device=dev)
         cplx = False
     else:
-        mem = [synth.config4_member(s) for s in synth.uneven_batch_specs()]
+        mem = [synth.uneven_member(s) for s in synth.uneven_batch_specs()]
         h = P.SelInv([m.n for m in mem], [m.colptr for m in mem], [m.rowind for m in mem], **tuning(args))
         vals = torch.tensor(np.concatenate([m.values for m in mem]), dtype=torch.float64, device=dev)
         cplx = False

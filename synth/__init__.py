@@ -422,19 +422,19 @@ def grid_problem(dims, shift_lo, shift_hi, seed, shift_const=None, name=None):
                    nd_order(dims), dims=tuple(dims))
 
 
-def config0(shift_const=None):
+def grid2d_31(shift_const=None):
     """31x31 5-point grid, diag 4 + U(0.1, 1)."""
     return grid_problem((31, 31), 0.1, 1.0, BASE_SEED + 0, shift_const, "grid2d_31")
 
 
-def config1(side=80, shift_const=None):
+def grid3d(side=80, shift_const=None):
     """80^3 7-point grid, diag 6 + U(0.01, 0.1); ``side`` gives smaller
     members of the same family."""
     return grid_problem((side, side, side), 0.01, 0.1, BASE_SEED + 1, shift_const,
                         f"grid3d_{side}")
 
 
-def config2(side=48):
+def graph_laplacian3d(side=48):
     gl = GraphLaplacian((side, side, side))
     perm = nd_order(gl.dims)
     p = Problem(f"graphlap3d_{side}", gl.n, gl.colptr, gl.rowind, gl.assemble(), perm,
@@ -442,7 +442,7 @@ def config2(side=48):
     return p
 
 
-def config3(elems=(12, 12, 12), nb=48, npoles=16):
+def dg_poles(elems=(12, 12, 12), nb=48, npoles=16):
     n, cp, ri, hv, z = dg_block_matrix(elems, nb, npoles)
     vals = shifted_values(n, cp, ri, hv, z)
     perm = block_nd_order(elems, nb)
@@ -450,7 +450,7 @@ def config3(elems=(12, 12, 12), nb=48, npoles=16):
                    dims=tuple(elems), extra={"z": z, "H": hv})
 
 
-def config4_member(spec):
+def uneven_member(spec):
     dims, seed = spec
     return grid_problem(dims, 0.1, 1.0, seed, None, f"grid{'x'.join(map(str, dims))}")
 

@@ -57,7 +57,7 @@ def _compare(P, n, cp, ri, wmax, relax, perm=None):
 
 @pytest.mark.parametrize("wmax,relax", [(128, 0), (16, 1), (128, 1), (5, 1)])
 def test_structure_parity_grids(P, wmax, relax):
-    for prob in (synth.config0(), synth.config1(side=11), synth.grid_problem((7, 9, 5), .1, 1, 3)):
+    for prob in (synth.grid2d_31(), synth.grid3d(side=11), synth.grid_problem((7, 9, 5), .1, 1, 3)):
         _compare(P, prob.n, prob.colptr, prob.rowind, wmax, relax)
 
 

@@ -176,7 +176,7 @@ def test_bk_full_size_indefinite_grid_closed_form(P):
     1e-9 allows for that conditioning; measured about 8e-11 (the pivot-free
     factor gives 1.1e-10 on the same samples)."""
     shift = -0.5
-    p = synth.config1(80, shift_const=shift)
+    p = synth.grid3d(80, shift_const=shift)
     h = P.SelInv(p.n, p.colptr, p.rowind)
     h.factor_bk(dev(p.values))
     h.selinv(P.LEVEL)

@@ -68,8 +68,8 @@ def check_problem(P, n, cp, ri, vals, wmax=128, relax=1, perm=None, modes=(1,), 
     return h, outs, sym, Xo
 
 
-def test_config0_all_schedules_bitwise_equal(P):
-    p = synth.config0()
+def test_grid2d_31_all_schedules_bitwise_equal(P):
+    p = synth.grid2d_31()
     h, outs, sym, Xo = check_problem(P, p.n, p.colptr, p.rowind, p.values, 128, 0, modes=(0, 1, 2, 3, 1, 2, 3))
     # the schedules run identical per-supernode arithmetic: bitwise equal
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
@@ -150,7 +150,7 @@ def test_random_pattern_with_permutation(P):
 
 def test_batch_of_shifts_shares_one_analysis(P):
     import torch
-    p = synth.config0()
+    p = synth.grid2d_31()
     cols = np.repeat(np.arange(p.n), np.diff(p.colptr))
     dg = p.rowind == cols
     vals = np.stack([p.values + dg * sh for sh in (0.0, 0.3, 2.0)])
@@ -224,7 +224,7 @@ def test_logdet_and_selected_entries(P):
 
 def test_panels_into_pinned_host_memory(P):
     import torch
-    p = synth.config0()
+    p = synth.grid2d_31()
     h = P.SelInv(p.n, p.colptr, p.rowind)
     h.factor(torch_vals(p.values))
     h.selinv(P.LEVEL)
@@ -241,7 +241,7 @@ def test_selinv_to_host_matches_device_panels(P, case):
     has) reproduce the device panels bit for bit and cover every entry."""
     import torch
     if case == "grid48":
-        p = synth.config1(side=48)
+        p = synth.grid3d(side=48)
         h = P.SelInv(p.n, p.colptr, p.rowind)
         h.factor(torch_vals(p.values))
     elif case == "poles":
@@ -272,7 +272,7 @@ def test_selinv_to_host_matches_device_panels(P, case):
 
 def test_runs_are_bitwise_deterministic(P):
     import torch
-    p = synth.config1(side=20)
+    p = synth.grid3d(side=20)
     h = P.SelInv(p.n, p.colptr, p.rowind)
     h.factor(torch_vals(p.values))
     h.selinv(P.LEVEL)
@@ -293,7 +293,7 @@ def test_full_size_80cubed_against_closed_form_and_trace(P):
     identity E of Eq. (16) is checked over all of A's entries."""
     import torch
     side = 80
-    p = synth.config1(side, shift_const=0.055)
+    p = synth.grid3d(side, shift_const=0.055)
     h = P.SelInv(p.n, p.colptr, p.rowind)
     s = h.symbolic()
     h.factor(torch_vals(p.values))
@@ -319,7 +319,7 @@ def test_full_size_80cubed_against_closed_form_and_trace(P):
     scale = float(torch.max(torch.abs(X)).item())
     assert np.max(np.abs(got - want)) / scale <= TOL
     # random shifts: trace identity on the selected entries at A's positions
-    q = synth.config1(side)
+    q = synth.grid3d(side)
     h.factor(torch_vals(q.values))
     h.selinv(P.LEVEL)
     xa = h.selected()[0].cpu().numpy()

@@ -64,7 +64,7 @@ def test_full_uneven_batch_48_members_against_single_handles(P):
     every member satisfies the trace identity E of Eq. (16)."""
     import torch
     specs = synth.uneven_batch_specs()
-    mem = [synth.config4_member(s) for s in specs]
+    mem = [synth.uneven_member(s) for s in specs]
     h = P.SelInv([m.n for m in mem], [m.colptr for m in mem], [m.rowind for m in mem])
     vals = np.concatenate([m.values for m in mem])
     h.factor(torch.tensor(vals, dtype=torch.float64, device="cuda"))

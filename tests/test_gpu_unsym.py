@@ -121,7 +121,7 @@ def test_unsym_complex_values_and_width_cap(P):
 
 def test_unsym_on_symmetric_values_matches_symmetric_path(P):
     import torch
-    p = synth.config1(side=14)
+    p = synth.grid3d(side=14)
     hs = P.SelInv(p.n, p.colptr, p.rowind)
     hs.factor(dev(p.values))
     hs.selinv(P.LEVEL)

@@ -96,7 +96,7 @@ def test_bk_factors_a_saddle_point_matrix_the_pivot_free_path_cannot():
 
 
 def test_bk_on_diagonally_dominant_matrices_takes_no_pivoting_steps():
-    p = synth.config1(side=6)
+    p = synth.grid3d(side=6)
     sym, X, fac = oracle.selected_inverse_bk(p.n, p.colptr, p.rowind, p.values, 8, 1)
     assert all(np.array_equal(F["p"], np.arange(len(F["p"]))) and not F["ptype"].any() for F in fac)
     sym2, lv, d, xv, xd, lcp, lri = oracle.selected_inverse(p.n, p.colptr, p.rowind, p.values, 8, 1)

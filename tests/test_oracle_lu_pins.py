@@ -168,7 +168,7 @@ def test_ldu_reproduces_A(cplx):
 def test_lu_reduces_to_the_symmetric_form_bitwise():
     """On symmetric input the LDU path takes the same operations in the same
     order as the LDL^T path, so the results agree bit for bit."""
-    p = synth.config1(side=7)
+    p = synth.grid3d(side=7)
     res_s = oracle.selected_inverse(p.n, p.colptr, p.rowind, p.values, 8, 1)
     res_u = oracle.selected_inverse_lu(p.n, p.colptr, p.rowind, p.values, p.values, 8, 1)
     _, lv, d, xv, xd, _, _ = res_s

@@ -130,7 +130,7 @@ def test_grid_closed_form_is_the_inverse():
 
 def test_oracle_vs_grid_closed_form_nd_order():
     """31x31 grid (the smallest workload's shape) with a constant shift."""
-    p = synth.config0(shift_const=0.55)
+    p = synth.grid2d_31(shift_const=0.55)
     sym, lv, d, xv, xd, lcp, lri = oracle.selected_inverse(p.n, p.colptr, p.rowind, p.values,
                                                            0, 0, "supernodal")
     assert np.array_equal(sym["post"], np.arange(p.n))
@@ -249,7 +249,7 @@ def test_figure1_worked_example():
 
 
 def test_supernode_rule_properties():
-    p = synth.config1(side=10)
+    p = synth.grid3d(side=10)
     parent, lcp, lri = oracle.column_structure(p.n, p.colptr, p.rowind)
     cnt = np.diff(lcp)
     fund = oracle.supernodes(parent, lcp, 0, 0)
@@ -285,7 +285,7 @@ def test_supernode_rule_properties():
 
 
 def test_relative_indices_definition():
-    p = synth.config1(side=9)
+    p = synth.grid3d(side=9)
     sym = oracle.analyse(p.n, p.colptr, p.rowind, 16, 1)
     sn, rc, rr, rel = sym["sn_start"], sym["rcount"], sym["rrows"], sym["relidx"]
     col2sn = np.repeat(np.arange(len(sn) - 1), np.diff(sn))
@@ -342,8 +342,8 @@ def test_solve_vs_numpy(cplx):
     assert np.max(np.abs(x - want)) < 1e-13 * np.max(np.abs(want))
 
 
-def test_trace_identity_config0():
-    p = synth.config0()
+def test_trace_identity_grid2d_31():
+    p = synth.grid2d_31()
     sym, lv, d, xv, xd, lcp, lri = oracle.selected_inverse(p.n, p.colptr, p.rowind, p.values,
                                                            0, 0, "exact")
     # X at A's positions: diagonal from xd, off-diagonals looked up in the L pattern
