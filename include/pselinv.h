@@ -436,9 +436,10 @@ int pselinv_get_timing(pselinv_handle* h, double* h_ms, int64_t* h_launches);
  * first split_k_rows over {0, 512, 1024, 2048, 4096} with the current
  * small_cutoff, then small_cutoff over {-1, 32, 64} with the best split,
  * then level_tiles over {608, 1216, 2432} -- keeps the fastest in the
- * handle, and returns it in h_best[0] = split_k_rows, h_best[1] =
- * small_cutoff, h_best[2] = level_tiles (h_best holds 3 entries) and its
- * time in *h_best_ms.
+ * handle, then times the GRAPH and PERSISTENT modes on it, and returns
+ * h_best[0] = split_k_rows, h_best[1] = small_cutoff, h_best[2] =
+ * level_tiles, h_best[3] = the fastest mode (h_best holds 4 entries) and
+ * that mode's time in *h_best_ms.
  * Overwrites the X panels; drops a captured GRAPH schedule.  Synchronises.
  */
 int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void* stream);

@@ -337,15 +337,15 @@ class SelInv:
         return out.view(self.opts.batch, nnz)
 
     def autotune(self, stream=None):
-        """pselinv_autotune: returns {"split_k_rows", "small_cutoff", "level_tiles", "ms"} and keeps
-        that schedule."""
-        best = np.zeros(3, np.int32)
+        """pselinv_autotune: returns {"split_k_rows", "small_cutoff", "level_tiles", "mode", "ms"}
+        and keeps that schedule (pass "mode" to selinv)."""
+        best = np.zeros(4, np.int32)
         ms = np.zeros(1, np.float64)
         self._check(self._lib.pselinv_autotune(self._h, _ptr(best), _ptr(ms), _stream_ptr(stream)))
         self.opts.split_k_rows, self.opts.small_cutoff, self.opts.level_tiles = (int(best[0]), int(best[1]),
                                                                                   int(best[2]))
         return {"split_k_rows": int(best[0]), "small_cutoff": int(best[1]), "level_tiles": int(best[2]),
-                "ms": float(ms[0])}
+                "mode": int(best[3]), "ms": float(ms[0])}
 
     def set_timing(self, enable=True):
         self._check(self._lib.pselinv_set_timing(self._h, 1 if enable else 0))

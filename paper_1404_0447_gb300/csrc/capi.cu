@@ -1098,6 +1098,28 @@ int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void
     rc = psi::build_schedule(h);
     if (!rc) rc = upload_schedule(h);
   }
+  // last: the schedule mode on the chosen parameters (LEVEL was measured above)
+  int32_t best_mode = PSELINV_LEVEL;
+  for (int32_t mode : {PSELINV_GRAPH, PSELINV_PERSISTENT}) {
+    if (rc || (mode == PSELINV_PERSISTENT && h->opts.unsym)) continue;
+    rc = pselinv_selinv(h, mode, st);  // warm-up (captures the graph)
+    double best = 1e300;
+    for (int rep = 0; rep < 2 && !rc; ++rep) {
+      float t = 0.f;
+      cudaError_t e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) rc = pselinv_selinv(h, mode, st);
+      if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (!rc && e != cudaSuccess) rc = cuda_err(h, e, "autotune timing");
+      if (t < best) best = t;
+    }
+    if (!rc && mode == PSELINV_PERSISTENT) rc = pselinv_sync_status(h, st);
+    if (!rc && best < best_ms) {
+      best_ms = best;
+      best_mode = mode;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->timing = timing;
@@ -1105,6 +1127,7 @@ int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void
   h_best[0] = best_split;
   h_best[1] = best_cut;
   h_best[2] = best_tiles > 0 ? best_tiles : psi::kTargetTiles;
+  h_best[3] = best_mode;
   *h_best_ms = best_ms;
   h->inverted = false;  // X was overwritten by the trial runs
   return PSELINV_OK;
