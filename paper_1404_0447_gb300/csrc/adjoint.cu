@@ -33,7 +33,8 @@
 
 namespace psi {
 
-enum AdjOp { A_YBAR, A_LHBAR, A_LBAROFF, A_T1, A_Q, A_VPART, A_RPART, A_SYR2K };
+enum AdjOp { A_YBAR, A_LHBAR, A_LBAROFF, A_T1, A_Q, A_VPART, A_RPART, A_SYR2K,
+             A_DR1, A_DR3, A_DR4, A_DF2, A_DF3, A_DF4 };  // s x s products of the diagonal steps
 
 template <class T>
 __device__ __forceinline__ void atomic_add_t(T* p, T v) {
@@ -82,7 +83,8 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       const int i = m0 + mm, n = n0 + nn;
       if (i < r && n < s) Yb[i + (int64_t)n * r] = XbCK[i + (int64_t)n * ld] - v;
     });
-  } else if constexpr (OP == A_LHBAR) {  // Hb = -X_CC Yb - Y Zb^T
+  } else if constexpr (OP == A_LHBAR) {  // Hb = -X_CC Yb - Y Zb^T, k-slice tk.c of C (step-2 slices)
+    const int kb = tk.c * m.kchunk, ke = min(r, kb + m.kchunk);
     auto la1 = [&](int mm, int kk) {
       const int i = m0 + mm;
       if (i >= r) return zero;
@@ -91,14 +93,18 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       return X[cd.col + rel[cd.rel + hi]];
     };
     auto lb1 = [&](int kk, int nn) { const int n = n0 + nn; return n < s ? Yb[kk + (int64_t)n * r] : zero; };
-    tile_mma<T, BN>(sm, 0, r, upper_by_k, la1, lb1, acc);
-    const T* Y = X + m.panel + s;
-    auto la2 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Y[i + (int64_t)t * ld] : zero; };
-    auto lb2 = [&](int t, int nn) { const int n = n0 + nn; return n < s ? Z[n + t * s] : zero; };
-    tile_mma<T, BN>(sm, 0, s, none, la2, lb2, acc);
+    tile_mma<T, BN>(sm, kb, ke, upper_by_k, la1, lb1, acc);
+    if (tk.c == 0) {  // the s-long term rides with the first slice
+      const T* Y = X + m.panel + s;
+      auto la2 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Y[i + (int64_t)t * ld] : zero; };
+      auto lb2 = [&](int t, int nn) { const int n = n0 + nn; return n < s ? Z[n + t * s] : zero; };
+      tile_mma<T, BN>(sm, 0, s, none, la2, lb2, acc);
+    }
+    T* out = m.ksplit == 1 ? Hb : (T*)a.k.ypart + b * sz.ypart + m.ypart + (int64_t)tk.c * r * s;
+    const T sign = m.ksplit == 1 ? -Sc<T>::one() : Sc<T>::one();
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, n = n0 + nn;
-      if (i < r && n < s) Hb[i + (int64_t)n * r] = -v;
+      if (i < r && n < s) out[i + (int64_t)n * r] = sign * v;
     });
   } else if constexpr (OP == A_LBAROFF) {  // Lb_CK = Hb V^T
     auto la = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Hb[i + (int64_t)t * r] : zero; };
@@ -108,7 +114,8 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       const int i = m0 + mm, n = n0 + nn;
       if (i < r && n < s) Lb[m.panel + s + i + (int64_t)n * ld] = v;
     });
-  } else if constexpr (OP == A_T1) {  // T1 = (W + W^T) L_CK, W gathered from Fb (= Xb)
+  } else if constexpr (OP == A_T1) {  // T1 = (W + W^T) L_CK, W gathered from Fb (= Xb), k-slice tk.c
+    const int kb = tk.c * m.kchunk, ke = min(r, kb + m.kchunk);
     auto la = [&](int mm, int kk) {
       const int i = m0 + mm;
       if (i >= r) return zero;
@@ -118,10 +125,11 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       return i == kk ? 2.0 * w : w;
     };
     auto lb = [&](int kk, int nn) { const int n = n0 + nn; return n < s ? L[m.panel + s + kk + (int64_t)n * ld] : zero; };
-    tile_mma<T, BN>(sm, 0, r, upper_by_k, la, lb, acc);
+    tile_mma<T, BN>(sm, kb, ke, upper_by_k, la, lb, acc);
+    T* out = m.ksplit == 1 ? Yb : (T*)a.k.ypart + b * sz.ypart + m.ypart + (int64_t)tk.c * r * s;
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, n = n0 + nn;
-      if (i < r && n < s) Yb[i + (int64_t)n * r] = v;
+      if (i < r && n < s) out[i + (int64_t)n * r] = v;
     });
   } else if constexpr (OP == A_Q) {  // Q = (Lb_CK E - T1) V -> Fb_CK
     auto la = [&](int mm, int t) {
@@ -153,6 +161,46 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       const int i = m0 + mm, n = n0 + nn;
       if (i < s && n < s) out[i + n * s] = v;
     });
+  } else if constexpr (OP >= A_DR1) {
+    // s x s products of the diagonal-block steps, tile (m0, n0) of K's block:
+    //   DR1  W = V Zb            DR3  W = Vb V^T           DR4  Lb_KK = strict_lower(-V^T W)
+    //   DF2  P = strict_lower(L_KK^T W) E + diag(Db)       DF3  W = P V      DF4  Ab = V^T W
+    T* Zs = (T*)a.Zb + b * sz.linv + m.linv;
+    T* W = (T*)a.W1 + b * sz.linv + m.linv;
+    const T* Db = (const T*)a.Db + b * sz.n + m.f;
+    auto Lkk = [&](int i, int j) {
+      return i == j ? Sc<T>::one() : (i > j ? L[m.panel + i + (int64_t)j * ld] : zero);
+    };
+    auto la = [&](int mm, int q) -> T {
+      const int i = m0 + mm;
+      if (i >= s) return zero;
+      if constexpr (OP == A_DR1) return V[i + q * s];
+      if constexpr (OP == A_DR3) return Zs[i + q * s];
+      if constexpr (OP == A_DR4 || OP == A_DF4) return V[q + i * s];
+      if constexpr (OP == A_DF2) return Lkk(q, i);
+      return Zs[i + q * s];  // DF3: P held in Zb
+    };
+    auto lb = [&](int q, int nn) -> T {
+      const int j = n0 + nn;
+      if (j >= s) return zero;
+      if constexpr (OP == A_DR1) return Zs[q + j * s];
+      if constexpr (OP == A_DR3) return V[j + q * s];
+      if constexpr (OP == A_DF3) return V[q + j * s];
+      return W[q + j * s];  // DR4, DF2, DF4
+    };
+    constexpr bool by_k_a = OP == A_DR4 || OP == A_DF2 || OP == A_DF4;
+    tile_mma<T, BN>(sm, 0, s, [](int) { return by_k_a; }, la, lb, acc);
+    // DR1/DR3/DF3 write W and DF4 writes Zb (its inputs W, V are not written in the same launch)
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int i = m0 + mm, j = n0 + nn;
+      if (i >= s || j >= s) return;
+      if constexpr (OP == A_DR1 || OP == A_DR3 || OP == A_DF3) W[i + j * s] = v;
+      if constexpr (OP == A_DR4) {
+        if (i > j) Lb[m.panel + i + (int64_t)j * ld] = -v;
+      }
+      if constexpr (OP == A_DF2) Zs[i + j * s] = i > j ? v / d[j] : (i == j ? Db[i] : zero);
+      if constexpr (OP == A_DF4) Zs[i + j * s] = v;
+    });
   } else {  // A_SYR2K: ancestors' Xb += -(Yb Lhat^T + Lhat Yb^T), lower, diagonal halved
     auto la1 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Yb[i + (int64_t)t * r] : zero; };
     auto lb1 = [&](int t, int nn) { const int n = n0 + nn; return n < r ? Lh[n + (int64_t)t * r] : zero; };
@@ -173,17 +221,6 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
 // --------------------------------------------------------------------------
 // per-supernode kernels (one CTA each)
 // --------------------------------------------------------------------------
-
-// C = op(A) op(B) for s x s column-major blocks (ld s), by the whole CTA.
-template <class T, bool TA, bool TB>
-__device__ void cta_mm(int s, const T* A, const T* B, T* C) {
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-    const int i = e % s, j = e / s;
-    T acc = Sc<T>::zero();
-    for (int k = 0; k < s; ++k) acc += (TA ? A[k + i * s] : A[i + k * s]) * (TB ? B[j + k * s] : B[k + j * s]);
-    C[e] = acc;
-  }
-}
 
 // Seed of the reverse sweep (all supernodes; blockIdx.x is the supernode).
 // Symmetric G: Xb_KK = G (mirrored from its stored lower triangle) and
@@ -211,6 +248,47 @@ __global__ void k_adj_seed(AdjArgs a) {
     }
 }
 
+// Slice reduction of a split supernode (slices in order: deterministic):
+// Hb = -(sum of the partials) for the reverse sweep, T1 = sum for the
+// LDL^T adjoint; blockIdx.z strides over the columns.
+template <class T, bool HB>
+__global__ void k_adj_reduce(AdjArgs a, const int32_t* __restrict__ sns) {
+  const int k = sns[blockIdx.x], b = blockIdx.y;
+  const Sizes sz = a.k.sz;
+  const SnMeta m = a.k.meta[k];
+  if (m.ksplit == 1) return;
+  const int s = m.s, r = m.r;
+  const T* yp = (const T*)a.k.ypart + b * sz.ypart + m.ypart;
+  T* out = (T*)(HB ? a.Hb : a.Yb) + b * sz.lhat + m.lhat;
+  const int64_t rs = (int64_t)r * s;
+  for (int j = blockIdx.z; j < s; j += gridDim.z)
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      const int64_t e = i + (int64_t)j * r;
+      T acc = yp[e];
+      for (int c = 1; c < m.ksplit; ++c) acc += yp[c * rs + e];
+      out[e] = HB ? -acc : acc;
+    }
+}
+
+// Step-3 chunk partials of a supernode summed in chunk order into chunk 0
+// (VPART before the reverse diagonal step, RPART before the factor one);
+// blockIdx.z selects one of gridDim.z CTAs sharing the s x s entries.
+template <class T>
+__global__ void k_adj_sum_parts(AdjArgs a, const int32_t* __restrict__ sns) {
+  const int k = sns[blockIdx.x], b = blockIdx.y;
+  const Sizes sz = a.k.sz;
+  const SnMeta m = a.k.meta[k];
+  if (m.nchunk < 2) return;
+  const int s = m.s;
+  T* part = (T*)a.k.part + b * sz.part + m.part;
+  const int64_t ss = (int64_t)s * s;
+  for (int64_t e = threadIdx.x + (int64_t)blockIdx.z * blockDim.x; e < ss; e += (int64_t)gridDim.z * blockDim.x) {
+    T acc = part[e];
+    for (int c = 1; c < m.nchunk; ++c) acc += part[c * ss + e];
+    part[e] = acc;
+  }
+}
+
 // Zb = (Xb_KK + Xb_KK^T) / 2 for the supernodes of a level.
 template <class T>
 __global__ void k_adj_zbar(AdjArgs a, const int32_t* __restrict__ sns) {
@@ -226,22 +304,28 @@ __global__ void k_adj_zbar(AdjArgs a, const int32_t* __restrict__ sns) {
   }
 }
 
-// Diagonal-block adjoints of the reverse sweep: Vb, Db, Lb_KK.
+// Sum over a warp (all lanes get it).
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ Cplx warp_sum(Cplx v) { return {warp_sum(v.re), warp_sum(v.im)}; }
+
+// Reverse sweep, elementwise part of the diagonal step, between the DR1 and
+// DR3 products: Db_t = -(V Zb V^T)_tt / d_t^2 = -(sum_j G1[t, j] V[t, j]) / d_t^2
+// with G1 = V Zb in W1, and Vb = 2 E G1 + (L_CK^T Hb, summed chunk partials) -> Zb.
 template <class T>
-__global__ void k_adj_diag_rev(AdjArgs a, const int32_t* __restrict__ sns) {
+__global__ void k_adj_dr2(AdjArgs a, const int32_t* __restrict__ sns) {
   const int k = sns[blockIdx.x], b = blockIdx.y;
   const Sizes sz = a.k.sz;
   const SnMeta m = a.k.meta[k];
-  const int s = m.s, ld = s + m.r;
+  const int s = m.s;
   const T* V = (const T*)a.k.Linv + b * sz.linv + m.linv;
   const T* d = (const T*)a.k.D + b * sz.n + m.f;
   const T* part = (const T*)a.k.part + b * sz.part + m.part;
-  T* Z = (T*)a.Zb + b * sz.linv + m.linv;  // Zb in, Vb out
-  T* W = (T*)a.W1 + b * sz.linv + m.linv;
+  T* Z = (T*)a.Zb + b * sz.linv + m.linv;
+  const T* W = (const T*)a.W1 + b * sz.linv + m.linv;
   T* Db = (T*)a.Db + b * sz.n + m.f;
-  T* Lb = (T*)a.Lb + b * sz.panel + m.panel;
-  cta_mm<T, false, false>(s, V, Z, W);  // G1 = V Zb
-  __syncthreads();
   for (int t = threadIdx.x; t < s; t += blockDim.x) {
     T acc = Sc<T>::zero();
     for (int j = 0; j < s; ++j) acc += W[t + j * s] * V[t + j * s];
@@ -250,80 +334,64 @@ __global__ void k_adj_diag_rev(AdjArgs a, const int32_t* __restrict__ sns) {
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
     const int t = e % s;
     T vb = 2.0 * W[e] / d[t];
-    for (int c = 0; c < m.nchunk; ++c) vb += part[(int64_t)c * s * s + e];
-    Z[e] = vb;  // Vb (Zb no longer needed: G1 holds V Zb)
-  }
-  __syncthreads();
-  cta_mm<T, false, true>(s, Z, V, W);  // G2 = Vb V^T
-  __syncthreads();
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-    const int i = e % s, j = e / s;
-    if (i <= j) continue;
-    T acc = Sc<T>::zero();
-    for (int q = 0; q < s; ++q) acc += V[q + i * s] * W[q + j * s];
-    Lb[i + (int64_t)j * ld] = -acc;  // strict lower of -V^T Vb V^T
+    if (m.nchunk > 0) vb += part[e];  // chunk partials already summed into chunk 0
+    Z[e] = vb;
   }
 }
 
-// Diagonal-block step of the LDL^T adjoint: Db and Lb_KK updates from the
-// panel solve and the Schur update, then Fb_KK.
+// LDL^T adjoint, elementwise part before the DF2 product: Db_t -= 1/2
+// sum_i L_CK[i, t] T1[i, t] + sum_j L_KK[j, t] R[j, t] (R = Q^T L_CK, summed
+// chunk partials) and W1 = strict_lower(Lb_KK - R D).
 template <class T>
-__global__ void k_adj_diag_fac(AdjArgs a, const int32_t* __restrict__ sns) {
+__global__ void k_adj_df1(AdjArgs a, const int32_t* __restrict__ sns) {
   const int k = sns[blockIdx.x], b = blockIdx.y;
   const Sizes sz = a.k.sz;
   const SnMeta m = a.k.meta[k];
   const int s = m.s, r = m.r, ld = s + r;
   const T* Lp = (const T*)a.k.L + b * sz.panel + m.panel;
-  const T* V = (const T*)a.k.Linv + b * sz.linv + m.linv;
   const T* d = (const T*)a.k.D + b * sz.n + m.f;
   const T* part = (const T*)a.k.part + b * sz.part + m.part;
   const T* T1 = (const T*)a.Yb + b * sz.lhat + m.lhat;
   T* Db = (T*)a.Db + b * sz.n + m.f;
   const T* Lb = (const T*)a.Lb + b * sz.panel + m.panel;
   T* W = (T*)a.W1 + b * sz.linv + m.linv;
-  T* Pm = (T*)a.Zb + b * sz.linv + m.linv;
-  T* Fb = (T*)a.Xb + b * sz.panel + m.panel;
+  __shared__ T colsum[kMaxWidth];
   const T zero = Sc<T>::zero();
-  auto R = [&](int i, int j) {
-    T v = zero;
-    for (int c = 0; c < m.nchunk; ++c) v += part[(int64_t)c * s * s + i + j * s];
-    return v;
-  };
+  auto R = [&](int i, int j) { return m.nchunk > 0 ? part[i + j * s] : zero; };
   auto Lkk = [&](int i, int j) { return i == j ? Sc<T>::one() : (i > j ? Lp[i + (int64_t)j * ld] : zero); };
+  // one warp per column, lanes along the r rows
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int t = warp; t < s; t += nw) {
+    T acc = zero;
+    for (int i = lane; i < r; i += 32) acc += Lp[s + i + (int64_t)t * ld] * T1[i + (int64_t)t * r];
+    acc = warp_sum(acc);
+    if (lane == 0) colsum[t] = acc;
+  }
+  __syncthreads();
   for (int t = threadIdx.x; t < s; t += blockDim.x) {
-    T acc = zero, acc2 = zero;
-    for (int i = 0; i < r; ++i) acc += Lp[s + i + (int64_t)t * ld] * T1[i + (int64_t)t * r];
+    T acc2 = zero;
     for (int j = t; j < s; ++j) acc2 += Lkk(j, t) * R(j, t);
-    Db[t] = Db[t] - 0.5 * acc - acc2;
+    Db[t] = Db[t] - 0.5 * colsum[t] - acc2;
   }
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
     const int i = e % s, j = e / s;
-    W[e] = i > j ? Lb[i + (int64_t)j * ld] - R(i, j) * d[j] : zero;  // Lb_KK, strict lower
+    W[e] = i > j ? Lb[i + (int64_t)j * ld] - R(i, j) * d[j] : zero;
   }
-  __syncthreads();
+}
+
+// LDL^T adjoint, last diagonal part: Fb_KK (stored lower) = Ab_ij + Ab_ji
+// (i > j), Ab_ii with Ab = V^T P V (from DF4, in Zb).
+template <class T>
+__global__ void k_adj_df5(AdjArgs a, const int32_t* __restrict__ sns) {
+  const int k = sns[blockIdx.x], b = blockIdx.y;
+  const Sizes sz = a.k.sz;
+  const SnMeta m = a.k.meta[k];
+  const int s = m.s, ld = s + m.r;
+  const T* Ab = (const T*)a.Zb + b * sz.linv + m.linv;
+  T* Fb = (T*)a.Xb + b * sz.panel + m.panel;
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
     const int i = e % s, j = e / s;
-    T v = zero;
-    if (i > j) {
-      for (int q = i; q < s; ++q) v += Lkk(q, i) * W[q + j * s];
-      v = v / d[j];
-    } else if (i == j) {
-      v = Db[i];
-    }
-    Pm[e] = v;
-  }
-  __syncthreads();
-  cta_mm<T, false, false>(s, Pm, V, W);  // P V
-  __syncthreads();
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-    const int i = e % s, j = e / s;
-    if (i < j) continue;
-    T aij = zero, aji = zero;
-    for (int q = 0; q < s; ++q) {
-      aij += V[q + i * s] * W[q + j * s];
-      aji += V[q + j * s] * W[q + i * s];
-    }
-    Fb[i + (int64_t)j * ld] = i == j ? aij : aij + aji;
+    if (i >= j) Fb[i + (int64_t)j * ld] = i == j ? Ab[e] : Ab[e] + Ab[j + i * s];
   }
 }
 
@@ -342,6 +410,12 @@ static cudaError_t adj_tile_tb(int op, const AdjArgs& a, const Task* t, int64_t 
     case A_Q: k_adj_tile<T, BN, A_Q><<<grid, TG_THREADS, 0, st>>>(a, t); break;
     case A_VPART: k_adj_tile<T, BN, A_VPART><<<grid, TG_THREADS, 0, st>>>(a, t); break;
     case A_RPART: k_adj_tile<T, BN, A_RPART><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_DR1: k_adj_tile<T, BN, A_DR1><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_DR3: k_adj_tile<T, BN, A_DR3><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_DR4: k_adj_tile<T, BN, A_DR4><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_DF2: k_adj_tile<T, BN, A_DF2><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_DF3: k_adj_tile<T, BN, A_DF3><<<grid, TG_THREADS, 0, st>>>(a, t); break;
+    case A_DF4: k_adj_tile<T, BN, A_DF4><<<grid, TG_THREADS, 0, st>>>(a, t); break;
     default: k_adj_tile<T, BN, A_SYR2K><<<grid, TG_THREADS, 0, st>>>(a, t); break;
   }
   return cudaGetLastError();
@@ -361,7 +435,8 @@ static cudaError_t adj_tile_t(int op, int var, const AdjArgs& a, const Task* t, 
 }
 
 cudaError_t launch_adj_tiles(AdjKern k, int var, const AdjArgs& a, const Task* t, int64_t n, cudaStream_t st) {
-  static const int map[] = {A_YBAR, A_LHBAR, A_LBAROFF, A_T1, A_Q, A_VPART, A_RPART, A_SYR2K};
+  static const int map[] = {A_YBAR, A_LHBAR, A_LBAROFF, A_T1, A_Q, A_VPART, A_RPART, A_SYR2K,
+                            A_DR1, A_DR3, A_DR4, A_DF2, A_DF3, A_DF4};
   const int op = map[(int)k];
   return a.k.dtype == PSELINV_C128 ? adj_tile_t<Cplx>(op, var, a, t, n, st) : adj_tile_t<double>(op, var, a, t, n, st);
 }
@@ -373,8 +448,13 @@ static cudaError_t adj_sn_t(AdjSn k, const AdjArgs& a, const int32_t* sns, int n
   switch (k) {
     case AdjSn::Seed: k_adj_seed<T><<<grid, 256, 0, st>>>(a); break;
     case AdjSn::Zbar: k_adj_zbar<T><<<grid, 256, 0, st>>>(a, sns); break;
-    case AdjSn::DiagRev: k_adj_diag_rev<T><<<grid, 256, 0, st>>>(a, sns); break;
-    default: k_adj_diag_fac<T><<<grid, 256, 0, st>>>(a, sns); break;
+    case AdjSn::Dr2: k_adj_dr2<T><<<grid, 256, 0, st>>>(a, sns); break;
+    case AdjSn::Df1: k_adj_df1<T><<<grid, 256, 0, st>>>(a, sns); break;
+    case AdjSn::Df5: k_adj_df5<T><<<grid, 256, 0, st>>>(a, sns); break;
+    case AdjSn::SumParts: k_adj_sum_parts<T><<<dim3(nsn, a.k.sz.batch, 8), 256, 0, st>>>(a, sns); break;
+    case AdjSn::ReduceHb: k_adj_reduce<T, true><<<dim3(nsn, a.k.sz.batch, 16), 256, 0, st>>>(a, sns); break;
+    case AdjSn::ReduceT1: k_adj_reduce<T, false><<<dim3(nsn, a.k.sz.batch, 16), 256, 0, st>>>(a, sns); break;
+    default: break;
   }
   return cudaGetLastError();
 }

@@ -561,6 +561,11 @@ int build_schedule(pselinv_handle* h) {
   build(h->t_gemm1, false, by_width, step2_tiles);
   build(h->t_trsm, false, by_width, rect);
   build(h->t_gemm2, false, by_width, step3_tiles);
+  build(h->t_sq, false, by_width, [&](int32_t k, int bn, std::vector<Task>& out) {  // s x s, no chunks
+    const SnMeta& m = h->meta[k];
+    for (int32_t m0 = 0; m0 < m.s; m0 += kTileM)
+      for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, 0});
+  });
   // the persistent kernel holds one shared-memory tile for every task kind,
   // so its lists stop at 64 x (8 << kPersistentMaxVar) tiles (register budget: more CTAs per SM)
   auto by_width_narrow = [&](int32_t k) { return std::min(by_width(k), kPersistentMaxVar); };

@@ -177,6 +177,8 @@ int upload_schedule(pselinv_handle* h) {
   all.insert(all.end(), h->t_pgemm1.tasks.begin(), h->t_pgemm1.tasks.end());
   h->off_pgemm2 = (int64_t)all.size();
   all.insert(all.end(), h->t_pgemm2.tasks.begin(), h->t_pgemm2.tasks.end());
+  h->off_sq = (int64_t)all.size();
+  all.insert(all.end(), h->t_sq.tasks.begin(), h->t_sq.tasks.end());
   if ((rc = upload(h, &h->d_tasks, all))) return rc;
   const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
   if ((rc = alloc(h, &h->d_part, B * h->part_max * es))) return rc;
@@ -983,21 +985,33 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
     const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
     PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::Zbar, a, sns, nsl, st));
     PSI_CUDA(h, tiles(AdjKern::Ybar, h->t_rect, h->off_rect, l));
-    PSI_CUDA(h, tiles(AdjKern::Lhbar, h->t_rect, h->off_rect, l));
+    PSI_CUDA(h, tiles(AdjKern::Lhbar, h->t_gemm1, h->off_gemm1, l));  // step-2 slices of C
+    if (h->level_split[l]) PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::ReduceHb, a, sns, nsl, st));
     PSI_CUDA(h, tiles(AdjKern::Syr2k, h->t_schur, h->off_schur, l));
     PSI_CUDA(h, tiles(AdjKern::LbarOff, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Vpart, h->t_gemm2, h->off_gemm2, l));
-    PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::DiagRev, a, sns, nsl, st));
+    PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::SumParts, a, sns, nsl, st));
+    // diagonal step: the s x s products as tiles over all supernodes of the level
+    PSI_CUDA(h, tiles(AdjKern::Dr1, h->t_sq, h->off_sq, l));
+    PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::Dr2, a, sns, nsl, st));
+    PSI_CUDA(h, tiles(AdjKern::Dr3, h->t_sq, h->off_sq, l));
+    PSI_CUDA(h, tiles(AdjKern::Dr4, h->t_sq, h->off_sq, l));
   }
   // adjoint of the supernodal LDL^T, root -> leaves
   PSI_CUDA(h, cudaMemsetAsync(h->d_xb, 0, B * h->panel_total * es, st));
   for (int32_t l = 0; l < h->nlevels; ++l) {
     const int32_t* sns = lsn + h->level_ptr[l];
     const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
-    PSI_CUDA(h, tiles(AdjKern::T1, h->t_rect, h->off_rect, l));
+    PSI_CUDA(h, tiles(AdjKern::T1, h->t_gemm1, h->off_gemm1, l));
+    if (h->level_split[l]) PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::ReduceT1, a, sns, nsl, st));
     PSI_CUDA(h, tiles(AdjKern::Q, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Rpart, h->t_gemm2, h->off_gemm2, l));
-    PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::DiagFac, a, sns, nsl, st));
+    PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::SumParts, a, sns, nsl, st));
+    PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::Df1, a, sns, nsl, st));
+    PSI_CUDA(h, tiles(AdjKern::Df2, h->t_sq, h->off_sq, l));
+    PSI_CUDA(h, tiles(AdjKern::Df3, h->t_sq, h->off_sq, l));
+    PSI_CUDA(h, tiles(AdjKern::Df4, h->t_sq, h->off_sq, l));
+    PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::Df5, a, sns, nsl, st));
   }
   PSI_CUDA(h, psi::launch_gather_values(h->opts.dtype, h->d_xb, (const int64_t*)h->d_valmap, nullptr, h->nnz_a,
                                         d_gradA, sizes(h), st));
@@ -1153,7 +1167,7 @@ int pselinv_get_info(const pselinv_handle* h, pselinv_info* info) {
     const int64_t B = h->opts.batch, es = (int64_t)elem_size(h), tasks =
         (int64_t)(h->t_lhat.tasks.size() + h->t_gemm1.tasks.size() + h->t_gemm2.tasks.size() +
                   h->t_trsm.tasks.size() + h->t_schur.tasks.size() + h->t_rect.tasks.size() +
-                  h->t_pgemm1.tasks.size() + h->t_pgemm2.tasks.size());
+                  h->t_pgemm1.tasks.size() + h->t_pgemm2.tasks.size() + h->t_sq.tasks.size());
     int64_t bytes = (int64_t)(sizeof(psi::SnMeta) * h->meta.size() + sizeof(psi::ColDesc) * h->desc.size() +
                               4 * h->relidx.size() + 8 * h->valmap.size() + h->diagmask.size() +
                               4 * h->level_sn.size()) +

@@ -137,6 +137,7 @@ struct pselinv_handle {
   psi::TaskList t_gemm2;  // step 3 partial-product tiles
   psi::TaskList t_trsm;   // factorisation: off-diagonal panel solve tiles
   psi::TaskList t_schur;  // factorisation: Schur-complement update tiles
+  psi::TaskList t_sq;     // s x s tiles of each supernode's diagonal block (adjoint products)
   psi::TaskList t_pgemm1; // persistent schedule: step-2 tiles, widths <= 8 << kPersistentMaxVar
   psi::TaskList t_pgemm2; // persistent schedule: step-3 tiles, widths <= 8 << kPersistentMaxVar
 
@@ -153,7 +154,7 @@ struct pselinv_handle {
   void* d_flipmap = nullptr;
   void* d_tasks = nullptr;  // all task arrays back to back
   int64_t off_lhat = 0, off_gemm1 = 0, off_gemm2 = 0, off_trsm = 0, off_schur = 0, off_rect = 0;
-  int64_t off_pgemm1 = 0, off_pgemm2 = 0;
+  int64_t off_pgemm1 = 0, off_pgemm2 = 0, off_sq = 0;
   void* d_levelsn = nullptr;
   void* d_L = nullptr;      // L panels (unit diagonal implied; D on the diagonal slots)
   void* d_X = nullptr;      // X panels
