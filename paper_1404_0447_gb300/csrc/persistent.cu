@@ -84,7 +84,8 @@ __device__ void cta_signal2(int* ctr1, int* ctr2) {
   }
 }
 
-// 8 CTAs per SM for real data (64 registers, 20 KB of shared memory each), 5 for complex.
+// 8 CTAs per SM for real data (64 registers, 20 KB of shared memory each), 5 for complex; 10 (48
+// registers) measured slower.
 template <class T>
 __global__ void __launch_bounds__(TG_THREADS, Sc<T>::P == 1 ? 8 : 5) k_persistent(KArgs a, PArgs p, const PTask* __restrict__ list,
                                                            int64_t ntask) {
