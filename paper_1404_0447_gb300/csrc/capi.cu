@@ -605,10 +605,14 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
   for (int32_t l = h->nlevels - 1; l >= 0; --l) {
     const int32_t* sns = lsn + h->level_ptr[l];
     const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
+    // a level holding a wide supernode gets wide CTAs: the column steps of the
+    // diagonal factorisation are serial, the work inside each step is not
+    int wmax = 0;
+    for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) wmax = std::max(wmax, h->meta[h->level_sn[t]].s);
     PSI_CUDA(h, psi::launch_per_sn(unsym ? psi::Kern::FactorDiagLU
                                          : bk  ? psi::Kern::FactorDiagBK
                                                : psi::Kern::FactorDiag,
-                                   a, sns, nsl, st));
+                                   a, sns, nsl, st, wmax >= 64 ? 1024 : 256));
     for (int side = 0; side < (unsym ? 2 : 1); ++side) {
       const psi::KArgs& ka = side ? au : al;
       for (int v = 0; v < psi::kNumVar; ++v) {

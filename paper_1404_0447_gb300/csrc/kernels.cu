@@ -974,13 +974,13 @@ cudaError_t launch_tiles(Kern k, int var, const KArgs& a, const Task* t, int64_t
 }
 
 template <class T>
-static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st) {
+static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st, int threads) {
   if (nsn <= 0) return cudaSuccess;
   const dim3 grid(nsn, a.sz.batch);
   switch (k) {
     case Kern::FactorDiag:
-      k_factor_diag<T><<<grid, 256, diag_smem<T>(a.maxw), st>>>(a.meta, sns, (T*)a.L, (T*)a.D, (T*)a.Linv, a.sz,
-                                                                a.status);
+      k_factor_diag<T><<<grid, threads, diag_smem<T>(a.maxw), st>>>(a.meta, sns, (T*)a.L, (T*)a.D, (T*)a.Linv,
+                                                                    a.sz, a.status);
       break;
     case Kern::CopyBack:
       k_copyback<T><<<dim3(nsn, a.sz.batch, 16), 256, 0, st>>>(a.meta, sns, (T*)a.L, (const T*)a.Lhat, a.sz);
@@ -993,11 +993,11 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
       k_gemm1_reduce<T><<<dim3(nsn, a.sz.batch, 16), 256, 0, st>>>(a, sns);
       break;
     case Kern::FactorDiagLU:
-      k_factor_diag_lu<T><<<grid, 256, diag_smem_lu<T>(a.maxw), st>>>(a.meta, sns, (T*)a.L, (T*)a.U, (T*)a.D,
+      k_factor_diag_lu<T><<<grid, threads, diag_smem_lu<T>(a.maxw), st>>>(a.meta, sns, (T*)a.L, (T*)a.U, (T*)a.D,
                                                                       (T*)a.Linv, (T*)a.Uinv, a.sz, a.status);
       break;
     case Kern::FactorDiagBK:
-      k_factor_diag_bk<T><<<grid, 256, diag_smem<T>(a.maxw), st>>>(
+      k_factor_diag_bk<T><<<grid, threads > 512 ? 512 : threads, diag_smem<T>(a.maxw), st>>>(
           a.meta, sns, (T*)a.L, (T*)a.D, (T*)a.E, (int8_t*)a.ptype, (int32_t*)a.piv, (T*)a.Linv, a.sz, a.status);
       break;
     case Kern::CopyBackBK:
@@ -1016,8 +1016,9 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
   return cudaGetLastError();
 }
 
-cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st) {
-  return a.dtype == PSELINV_C128 ? per_sn_t<Cplx>(k, a, sns, nsn, st) : per_sn_t<double>(k, a, sns, nsn, st);
+cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st, int threads) {
+  return a.dtype == PSELINV_C128 ? per_sn_t<Cplx>(k, a, sns, nsn, st, threads)
+                                 : per_sn_t<double>(k, a, sns, nsn, st, threads);
 }
 
 cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st,

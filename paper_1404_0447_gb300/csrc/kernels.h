@@ -78,7 +78,9 @@ cudaError_t launch_gather_values(int dtype, const void* X, const int64_t* vmap, 
 cudaError_t launch_tiles(Kern k, int var, const KArgs& a, const Task* tasks, int64_t n, cudaStream_t st);
 // Per-supernode kernels (FactorDiag, CopyBack, NormDiag, DiagFinal, Gemm1Reduce) over the
 // nsn supernodes listed in sns (NormDiag: supernodes 0..nsn-1, sns unused).
-cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st);
+// threads: block size of the diagonal-factorisation kernels (FactorDiag,
+// FactorDiagLU, FactorDiagBK -- the last capped at 512); the others use 256.
+cudaError_t launch_per_sn(Kern k, const KArgs& a, const int32_t* sns, int nsn, cudaStream_t st, int threads = 256);
 cudaError_t launch_logdet(int dtype, const void* D, int64_t n, double* out, int batch, cudaStream_t st,
                           const int8_t* ptype = nullptr, const void* E = nullptr);
 cudaError_t launch_pole_sum(int dtype, const void* X, int64_t panel_total, int batch, const void* w, void* out,
