@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--split-k-rows", type=int, default=None, help="override the library default")
     ap.add_argument("--small-cutoff", type=int, default=None, help="override the library default")
     ap.add_argument("--level-tiles", type=int, default=None, help="override the library default")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP64 and low-precision MMA peaks of this GPU (the roofline denominators)")
     ap.add_argument("--min-slice-rows", type=int, default=None, help="override the library default")
     return ap.parse_args()
 
@@ -490,8 +492,131 @@ def run_workload(args):
     print(json.dumps(line), flush=True)
 
 
+# Compute-only throughput probe (no memory traffic in the timed loops):
+# independent DFMA chains and back-to-back mma.sync of several shapes on
+# register operands.
+PEAK_PROBE_CU = r"""
+#include <cstdio>
+#include <cuda_runtime.h>
+__global__ void dfma(double* out, int iters) {
+  double x[8];
+  for (int q = 0; q < 8; ++q) x[q] = threadIdx.x * 1e-9 + q;
+  const double a = 1.0 - 1e-12, c = 1e-13;
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = fma(x[q], a, c);
+  double s = 0; for (int q = 0; q < 8; ++q) s += x[q];
+  if (s == 12345.0) out[threadIdx.x] = s;
+}
+__global__ void dmma(double* out, int iters) {
+  double d[4][2] = {};
+  const double a = threadIdx.x * 1e-3, b = threadIdx.x * 2e-3;
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(d[q][0]), "+d"(d[q][1]) : "d"(a), "d"(b));
+  double s = 0; for (int q = 0; q < 4; ++q) s += d[q][0] + d[q][1];
+  if (s == 12345.0) out[threadIdx.x] = s;
+}
+__global__ void hmma_bf16(double* out, int iters) {
+  float d[4][4] = {};
+  const unsigned a0 = threadIdx.x, a1 = a0 * 3u, a2 = a0 * 5u, a3 = a0 * 7u, b0 = a0 * 11u, b1 = a0 * 13u;
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                   : "+f"(d[q][0]), "+f"(d[q][1]), "+f"(d[q][2]), "+f"(d[q][3])
+                   : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  float s = 0; for (int q = 0; q < 4; ++q) for (int i = 0; i < 4; ++i) s += d[q][i];
+  if (s == 12345.f) out[threadIdx.x] = s;
+}
+__global__ void imma_s8(double* out, int iters) {
+  int d[4][4] = {};
+  const unsigned a0 = threadIdx.x, a1 = a0 * 3u, a2 = a0 * 5u, a3 = a0 * 7u, b0 = a0 * 11u, b1 = a0 * 13u;
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                   : "+r"(d[q][0]), "+r"(d[q][1]), "+r"(d[q][2]), "+r"(d[q][3])
+                   : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  int s = 0; for (int q = 0; q < 4; ++q) for (int i = 0; i < 4; ++i) s += d[q][i];
+  if (s == 12345) out[threadIdx.x] = s;
+}
+int main() {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  double* buf = nullptr;
+  cudaMalloc(&buf, 4096 * sizeof(double));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int threads = 256, blocks = sms * 8;
+  const char* names[4] = {"dfma", "dmma_m8n8k4_f64", "mma_sync_m16n8k16_bf16", "mma_sync_m16n8k32_s8"};
+  const double flops[4] = {8.0 * 2, 4.0 * 8 * 8 * 4 * 2, 4.0 * 16 * 8 * 16 * 2, 4.0 * 16 * 8 * 32 * 2};
+  const double per_thread[4] = {1, 1.0 / 32, 1.0 / 32, 1.0 / 32};  // loop bodies: per thread (DFMA) or per warp (MMA)
+  const int iters[4] = {20000, 400, 4000, 1500};
+  for (int c = 0; c < 4; ++c) {
+    float ms = 0;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0);
+      if (c == 0) dfma<<<blocks, threads>>>(buf, iters[c]);
+      if (c == 1) dmma<<<blocks, threads>>>(buf, iters[c]);
+      if (c == 2) hmma_bf16<<<blocks, threads>>>(buf, iters[c]);
+      if (c == 3) imma_s8<<<blocks, threads>>>(buf, iters[c]);
+      cudaEventRecord(e1);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    const double units = (double)blocks * threads * per_thread[c] * iters[c];
+    printf("%s %.4f\n", names[c], units * flops[c] / (ms * 1e-3) / 1e12);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) printf("error %s\n", cudaGetErrorString(e));
+  return e != cudaSuccess;
+}
+"""
+
+
+def run_peaks(args):
+    """Measured peaks of this GPU: FP64 DFMA and DMMA, bf16 and int8 mma.sync
+    (compute-only probe, compiled here with nvcc), and cuBLAS DGEMM through
+    torch.matmul on float64 (8192^3, best of 3 after 2 warm-ups)."""
+    import subprocess
+    import tempfile
+    import torch
+    out = {"what": "peak probe", "unit": "TFLOP/s (int8: TOP/s)"}
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "peaks.cu")
+        exe = os.path.join(d, "peaks")
+        with open(src, "w") as f:
+            f.write(PEAK_PROBE_CU)
+        subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src])
+        for line in subprocess.check_output([exe], text=True).splitlines():
+            k, v = line.split()
+            out[k] = float(v)
+    a = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    bmat = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    best = 1e30
+    for it in range(5):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, bmat)
+        e1.record()
+        e1.synchronize()
+        if it >= 2:
+            best = min(best, e0.elapsed_time(e1))
+    out["cublas_dgemm_8192"] = 2 * 8192 ** 3 / (best * 1e-3) / 1e12
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.peaks:
+        run_peaks(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload != "grid3d_80":
