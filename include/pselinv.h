@@ -66,6 +66,8 @@ extern "C" {
 #define PSELINV_ERR_CUDA (-6)       /* CUDA runtime error or no device */
 #define PSELINV_ERR_TIMEOUT (-7)    /* a bounded device wait ran out */
 #define PSELINV_ERR_STATE (-8)      /* call out of order (e.g. selinv before factor) */
+#define PSELINV_ERR_RANGE (-9)      /* FP64 emulation: X is not positive definite (a diagonal entry
+                                       <= 0, or a scaled entry out of its slice range) */
 
 /* value types */
 #define PSELINV_F64 0
@@ -104,6 +106,19 @@ typedef struct {
   int32_t level_tiles;    /* a level whose step-2 (step-3) tiles number fewer than this gets its slices
                              (row chunks) of C shrunk until it has about this many; 0 = 16 per SM (2432) */
   int32_t min_slice_rows; /* smallest step-2 slice that shrinking makes; 0 = 128 (step-3 chunks: a quarter) */
+  int32_t fp64_emulation; /* 0: step 2 in FP64 (mma.sync f64).  1: step 2, X_{C,K} = -X_{C,C} Lhat_{C,K}
+                             (Algorithm 1), in FP64 accuracy on the bf16 tensor cores, for real symmetric
+                             positive definite A (dtype F64, unsym 0, pivot-free factor; PLAIN, LEVEL and
+                             GRAPH schedules).  With e_p = ceil(log2 sqrt(X_pp)), every entry of
+                             2^-(e_p+e_q) X has modulus < 1 (Cauchy-Schwarz for SPD X); the scaled X and
+                             the row-scaled Lhat are cut into 7 signed 8-bit slices each, the 28 slice
+                             products of weight >= 2^-48 are formed with exact FP32 sums over 32-row
+                             chunks and accumulated in 64-bit integers; the error per term is below
+                             2^-53 of 2^(e_i + F_j) (F_j: exponent of column j of the scaled Lhat).
+                             Costs 16 bytes per X panel entry and per Lhat entry of device memory.
+                             A matrix whose X is not positive definite is detected (X_pp <= 0 or a
+                             scaled entry >= 2) and reported as PSELINV_ERR_RANGE by
+                             pselinv_sync_status; that selinv's X is then invalid. */
 } pselinv_opts;
 
 /* Sizes and work counts of an analysed handle. */
@@ -149,7 +164,7 @@ typedef struct {
 
 /* Fill *o with defaults: F64, batch 1, w_max 128, RELAX_AMALG, padding-minimal
    tiles, split_k_rows 1024, no debug checks, 1 s spin limit, level_tiles and
-   min_slice_rows 0 (2432 and 128). */
+   min_slice_rows 0 (2432 and 128), fp64_emulation 0. */
 void pselinv_default_opts(pselinv_opts* o);
 
 /*
@@ -315,7 +330,9 @@ int pselinv_get_panels(pselinv_handle* h, int32_t which, void* out, void* stream
  * Synchronise `stream` and report device-side failures of earlier enqueued
  * work on h: PSELINV_ERR_TIMEOUT if a bounded wait of the PERSISTENT
  * schedule ran out (that call's results are invalid; the flag is cleared and
- * the handle stays usable).  Returns PSELINV_OK otherwise.
+ * the handle stays usable), PSELINV_ERR_RANGE if a selinv with
+ * opts.fp64_emulation met an X that is not positive definite (same
+ * treatment).  Returns PSELINV_OK otherwise.
  */
 int pselinv_sync_status(pselinv_handle* h, void* stream);
 

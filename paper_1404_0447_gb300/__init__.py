@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpselinv.so")
 
 PSELINV_OK = 0
 ERRORS = {-1: "ERR_ARG", -2: "ERR_NOT_LOWER", -3: "ERR_ZERO_PIVOT", -4: "ERR_NONFINITE",
-          -5: "ERR_OOM", -6: "ERR_CUDA", -7: "ERR_TIMEOUT", -8: "ERR_STATE"}
+          -5: "ERR_OOM", -6: "ERR_CUDA", -7: "ERR_TIMEOUT", -8: "ERR_STATE", -9: "ERR_RANGE"}
 F64, C128 = 0, 1
 RELAX_NONE, RELAX_AMALG = 0, 1
 PLAIN, LEVEL, GRAPH, PERSISTENT = 0, 1, 2, 3
@@ -44,7 +44,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("batch", ctypes.c_int32), ("max_sn_width", ctypes.c_int32),
                 ("relax", ctypes.c_int32), ("small_cutoff", ctypes.c_int32), ("split_k_rows", ctypes.c_int32),
                 ("debug_checks", ctypes.c_int32), ("unsym", ctypes.c_int32), ("spin_limit_ns", ctypes.c_int64),
-                ("level_tiles", ctypes.c_int32), ("min_slice_rows", ctypes.c_int32)]
+                ("level_tiles", ctypes.c_int32), ("min_slice_rows", ctypes.c_int32),
+                ("fp64_emulation", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -116,7 +117,10 @@ def load_library():
 def default_opts(**kw) -> Opts:
     o = Opts()
     load_library().pselinv_default_opts(ctypes.byref(o))
+    names = {f[0] for f in Opts._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown option {k!r}")
         setattr(o, k, v)
     return o
 

@@ -70,7 +70,7 @@ void free_device(pselinv_handle* h) {
                    &h->d_status, &h->d_flipmap, &h->d_U, &h->d_XU, &h->d_uhat, &h->d_uinv,
                    &h->d_piv, &h->d_ptype, &h->d_E, &h->d_snlevel, &h->d_yring, &h->d_pring,
                    &h->d_xb,   &h->d_lb,   &h->d_db,     &h->d_zb,     &h->d_w1,    &h->d_yb,   &h->d_hb,
-                   &h->d_plist, &h->d_pn,  &h->d_pctr};
+                   &h->d_plist, &h->d_pn,  &h->d_pctr, &h->d_xs, &h->d_ls, &h->d_sig, &h->d_lexp, &h->d_crow};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -136,6 +136,13 @@ int ensure_device(pselinv_handle* h) {
     if ((rc = alloc(h, &h->d_XU, B * h->panel_total * es))) return rc;
     if ((rc = alloc(h, &h->d_uhat, B * h->lhat_total * es))) return rc;
     if ((rc = alloc(h, &h->d_uinv, B * h->linv_total * es))) return rc;
+  }
+  if (h->opts.fp64_emulation) {
+    if ((rc = upload(h, &h->d_crow, h->rows))) return rc;
+    if ((rc = alloc(h, &h->d_xs, B * h->panel_total * 16))) return rc;
+    if ((rc = alloc(h, &h->d_ls, B * h->lhat_total * 16))) return rc;
+    if ((rc = alloc(h, &h->d_sig, B * h->n * (int64_t)sizeof(int32_t)))) return rc;
+    if ((rc = alloc(h, &h->d_lexp, B * h->n * (int64_t)sizeof(int32_t)))) return rc;
   }
   PSI_CUDA(h, cudaMemset(h->d_status, 0, sizeof(int) * kStatusWords));
   h->dev_sym = true;
@@ -360,6 +367,9 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
     return e;
   });
   if (rc) return rc;
+  // FP64 emulation of step 2: B' slices before it, X slices after the level
+  const bool emul = h->opts.fp64_emulation != 0;
+  const psi::EmArgs em{h->d_xs, h->d_ls, (int32_t*)h->d_sig, (int32_t*)h->d_lexp, (const int32_t*)h->d_crow, h->n};
   // one step: the given supernodes, with per-variant task ranges of steps 2 and 3
   auto step = [&](const int32_t* sns, int nsn_step, const psi::Range* r1, const psi::Range* r2, bool split) {
     int n1 = split ? 1 : 0, n2 = 0, e;
@@ -369,11 +379,13 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
     }
     // step 2 (ka = a), or step 4 (ka = a4) of a non-symmetric handle
     auto gemm1 = [&](const psi::KArgs& ka) {
-      return tm.run(1, n1, [&] {
-        cudaError_t x = cudaSuccess;
+      return tm.run(1, n1 + (emul ? 1 : 0), [&] {
+        cudaError_t x = emul ? psi::launch_em_split_lhat(ka, em, sns, nsn_step, st) : cudaSuccess;
         for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
-          x = psi::launch_tiles(Kern::Gemm1, v, ka, tasks_at(h, h->off_gemm1, r1[v].begin), r1[v].end - r1[v].begin,
-                                st);
+          x = emul ? psi::launch_em_gemm1(v, ka, em, tasks_at(h, h->off_gemm1, r1[v].begin), r1[v].end - r1[v].begin,
+                                          st)
+                   : psi::launch_tiles(Kern::Gemm1, v, ka, tasks_at(h, h->off_gemm1, r1[v].begin),
+                                       r1[v].end - r1[v].begin, st);
         if (split && x == cudaSuccess) x = psi::launch_per_sn(Kern::Gemm1Reduce, ka, sns, nsn_step, st);
         return x;
       });
@@ -387,7 +399,11 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
            return x;
          })))
       return e;
-    if ((e = tm.run(3, nsn_step > 0, [&] { return psi::launch_per_sn(Kern::DiagFinal, a, sns, nsn_step, st); })))
+    if ((e = tm.run(3, (nsn_step > 0) * (emul ? 2 : 1), [&] {
+           cudaError_t x = psi::launch_per_sn(Kern::DiagFinal, a, sns, nsn_step, st);
+           if (emul && x == cudaSuccess) x = psi::launch_em_split_x(a, em, sns, nsn_step, st);
+           return x;
+         })))
       return e;
     // step 4 reuses the step-2 partial-product buffer after step 2's reduction
     return unsym ? gemm1(a4) : PSELINV_OK;
@@ -690,6 +706,12 @@ int pselinv_selinv(pselinv_handle* h, int32_t mode, void* stream) {
   if (!h->factored) return set_err(h, PSELINV_ERR_STATE, "selinv called before a successful factor");
   if (mode == PSELINV_PERSISTENT && h->opts.unsym)
     return set_err(h, PSELINV_ERR_ARG, "the PERSISTENT schedule is for symmetric handles");
+  if (h->opts.fp64_emulation) {
+    if (mode == PSELINV_PERSISTENT)
+      return set_err(h, PSELINV_ERR_ARG, "fp64_emulation runs with the PLAIN, LEVEL and GRAPH schedules");
+    if (h->pivoted) return set_err(h, PSELINV_ERR_STATE, "fp64_emulation needs the pivot-free factor (SPD A)");
+    if (h->max_r > (int64_t)1 << 21) return set_err(h, PSELINV_ERR_ARG, "fp64_emulation: |C| above 2^21");
+  }
   cudaStream_t st = (cudaStream_t)stream;
   if (mode == PSELINV_PERSISTENT) {
     int rrc = ensure_ring(h);
@@ -827,6 +849,14 @@ int pselinv_sync_status(pselinv_handle* h, void* stream) {
     h->inverted = false;
     return set_err(h, PSELINV_ERR_TIMEOUT,
                    "a bounded device wait of the persistent schedule ran out; that selinv's results are invalid");
+  }
+  if (status[psi::kEmStatusWord]) {
+    PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + psi::kEmStatusWord, 0, sizeof(int), st));
+    PSI_CUDA(h, cudaStreamSynchronize(st));
+    h->inverted = false;
+    return set_err(h, PSELINV_ERR_RANGE,
+                   "FP64 emulation: X is not positive definite (a diagonal entry <= 0 or a scaled entry out of "
+                   "range); that selinv's results are invalid -- use fp64_emulation = 0");
   }
   return PSELINV_OK;
 }
@@ -1119,7 +1149,7 @@ int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void
   // last: the schedule mode on the chosen parameters (LEVEL was measured above)
   int32_t best_mode = PSELINV_LEVEL;
   for (int32_t mode : {PSELINV_GRAPH, PSELINV_PERSISTENT}) {
-    if (rc || (mode == PSELINV_PERSISTENT && h->opts.unsym)) continue;
+    if (rc || (mode == PSELINV_PERSISTENT && (h->opts.unsym || h->opts.fp64_emulation))) continue;
     rc = pselinv_selinv(h, mode, st);  // warm-up (captures the graph)
     double best = 1e300;
     for (int rep = 0; rep < 2 && !rc; ++rep) {

@@ -1,0 +1,361 @@
+// Step 2 of the selected inversion (X_{C,K} = -X_{C,C} Lhat_{C,K}, Algorithm 1)
+// in FP64 accuracy on the bf16 tensor cores, for real symmetric positive
+// definite matrices.
+//
+// Scaling.  For X = A^{-1} SPD, |X_pq| <= sqrt(X_pp X_qq).  With the power of
+// two 2^e_p >= sqrt(X_pp), e_p = ceil(E_p / 2) where X_pp < 2^E_p, every entry
+// of Xt = 2^-(e_p + e_q) X satisfies |Xt| < 1, and X_{C,C} Lhat =
+// diag(2^e_C) Xt_{C,C} B' with B' = diag(2^e_C) Lhat.  Column j of B' gets its
+// own exponent F_j (|B'_{:,j}| < 2^F_j).
+//
+// Slices.  a = Xt and b = B' 2^-F are fixed-point numbers in (-1, 1):
+// qa = floor(|a| 2^55), qb = floor(|b| 2^56), cut into 7 bytes from the top,
+// a = sum_t a_t 2^(-7-8t), b = sum_u b_u 2^(-8-8u), every slice an integer in
+// [-255, 255] carrying the entry's sign, exact in bf16.  The products
+// a_t b_u with t + u = g <= 6 (28 of the 49) are formed by mma.sync bf16 with
+// FP32 accumulation, one accumulator per g: over a chunk of 32 rows of C a
+// group sum is an integer below 7 * 32 * 255^2 < 2^24, so FP32 holds it
+// exactly.  After each chunk the seven group sums are folded into two 64-bit
+// integers, hi = S0 2^16 + S1 2^8 + S2 and lo = S3 2^24 + S4 2^16 + S5 2^8 + S6,
+// and at the end
+//   (X_{C,C} Lhat)_{ij} = 2^(e_{C_i} + F_j - 31) (hi + lo 2^-32),
+// the only FP64 arithmetic of the product.  The dropped products (g >= 7)
+// and the truncation of the slices each contribute below 2^-53 of
+// 2^(e_{C_i} + F_j) per term, the order of the FP64 rounding of the same sum.
+//
+// The slices of a supernode's X panel are cut once, right after its level
+// has finished (k_em_split_x), those of its B' right before its step 2
+// (k_em_split_lhat, once the exponents of the rows of C are known).
+#include <cfloat>
+#include <climits>
+#include <cstdint>
+
+#include "kernels.h"
+#include "tile_gemm.cuh"
+
+namespace psi {
+namespace {
+
+constexpr int kSl = 7;         // slices per entry
+constexpr int kKC = 32;        // rows of C per exact FP32 chunk
+constexpr int kKP = kKC + 8;   // shared row stride in bf16 elements (80 bytes: ldmatrix rows conflict-free)
+constexpr int kEmThreads = 128;
+
+// bf16 bits of the integer c in [0, 255] with sign bit sgn (0 or 0x8000):
+// c has at most 8 significant bits, so the low half of float(c) is zero.
+__device__ __forceinline__ uint32_t bf16_int(uint32_t c, uint32_t sgn) {
+  return c ? (__float_as_uint((float)c) >> 16) | sgn : 0u;
+}
+
+// The 7 slices of v as bf16 (slice t in halfword t): q = floor(|v| 2^(56 - E))
+// for |v| < 2^E, cut into bytes from the top.  Zero and subnormal v give
+// zero slices; Inf, NaN or |v| >= 2^E set bad.
+__device__ __forceinline__ uint4 split7(double v, int E, int& bad) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  uint4 o = make_uint4(0u, 0u, 0u, 0u);
+  if (ex == 0) return o;
+  const int sh = ex - 1019 - E;  // |v| 2^(56 - E) = mant 2^sh; |v| < 2^E <=> sh <= 3
+  if (ex == 0x7FF || sh > 3) {
+    bad = 1;
+    return o;
+  }
+  const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long q = sh >= 0 ? mant << sh : (sh > -64 ? mant >> (-sh) : 0ull);
+  const uint32_t sgn = (uint32_t)(bits >> 63) << 15;
+  uint32_t h[kSl];
+#pragma unroll
+  for (int t = 0; t < kSl; ++t) h[t] = bf16_int((uint32_t)(q >> (8 * (6 - t))) & 255u, sgn);
+  o.x = h[0] | (h[1] << 16);
+  o.y = h[2] | (h[3] << 16);
+  o.z = h[4] | (h[5] << 16);
+  o.w = h[6];
+  return o;
+}
+
+// Column groups of the split kernels: CTA z of a supernode handles its
+// columns z, z + kSplitGroups, ... (the top levels hold few, tall supernodes).
+constexpr int kSplitGroups = 32;
+
+// After the level of supernode K: e_p of K's columns, then the slices of
+// every panel entry of K that step 2 reads (the lower triangle of the
+// diagonal block and the rows of C).  Grid (supernodes, batch, column groups);
+// every CTA derives the s exponents itself, group 0 stores them.
+__global__ void __launch_bounds__(256) k_em_split_x(KArgs a, EmArgs e, const int32_t* __restrict__ sns) {
+  const int k = sns[blockIdx.x], b = blockIdx.y;
+  const SnMeta m = a.meta[k];
+  const int s = m.s, r = m.r, ld = s + r;
+  if ((int)blockIdx.z >= s) return;
+  const double* X = (const double*)a.X + b * a.sz.panel + m.panel;
+  uint4* xs = (uint4*)e.xs + b * a.sz.panel + m.panel;
+  int32_t* sig = e.sig + b * e.n;
+  const int32_t* crow = e.crow + m.desc;
+  __shared__ int se[kMaxWidth];
+  int bad = 0;
+  for (int j = threadIdx.x; j < s; j += blockDim.x) {
+    const double d = X[j + (int64_t)j * ld];
+    int E = 0;
+    if (d > 0.0 && d <= DBL_MAX) {
+      frexp(d, &E);      // d < 2^E
+      E = (E + 1) >> 1;  // ceil(E / 2): 2^e >= sqrt(d)
+    } else {
+      bad = 1;
+    }
+    se[j] = E;
+    if (blockIdx.z == 0) sig[m.f + j] = E;
+  }
+  __syncthreads();
+  for (int j = blockIdx.z; j < s; j += gridDim.z) {
+    const double* col = X + (int64_t)j * ld;
+    uint4* out = xs + (int64_t)j * ld;
+    const int ej = se[j] + 1;
+    for (int p = threadIdx.x; p < ld; p += blockDim.x) {
+      if (p < j) {
+        out[p] = make_uint4(0u, 0u, 0u, 0u);  // above the diagonal: never read
+        continue;
+      }
+      const int ep = p < s ? se[p] : sig[crow[p - s]];
+      out[p] = split7(col[p], ep + ej, bad);  // |X_pq| < 2^(e_p + e_q + 1)
+    }
+  }
+  if (bad) atomicOr(a.status + kEmStatusWord, 1);
+}
+
+// Before step 2 of supernode K: F_j and the slices of B' = diag(2^e_C) Lhat,
+// one warp per column.  Grid (supernodes, batch, column groups).
+__global__ void __launch_bounds__(256) k_em_split_lhat(KArgs a, EmArgs e, const int32_t* __restrict__ sns) {
+  const int k = sns[blockIdx.x], b = blockIdx.y;
+  const SnMeta m = a.meta[k];
+  const int s = m.s, r = m.r;
+  const double* Lh = (const double*)a.Lhat + b * a.sz.lhat + m.lhat;
+  uint4* ls = (uint4*)e.ls + b * a.sz.lhat + m.lhat;
+  const int32_t* sig = e.sig + b * e.n;
+  const int32_t* crow = e.crow + m.desc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int bad = 0;
+  for (int j = blockIdx.z * nw + warp; j < s; j += gridDim.z * nw) {
+    const double* col = Lh + (int64_t)j * r;
+    int mx = INT_MIN;
+    for (int i = lane; i < r; i += 32) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(col[i]);
+      const int ex = (int)((bits >> 52) & 0x7FF);
+      if (ex == 0x7FF)
+        bad = 1;
+      else if (ex != 0)
+        mx = max(mx, ex - 1023 + sig[crow[i]]);  // floor(log2 |B'_ij|)
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int F = mx == INT_MIN ? 0 : mx + 1;
+    if (lane == 0) e.lexp[b * e.n + m.f + j] = F;
+    for (int i = lane; i < r; i += 32) ls[i + (int64_t)j * r] = split7(col[i], F - sig[crow[i]], bad);
+  }
+  if (bad) atomicOr(a.status + kEmStatusWord, 1);
+}
+
+template <int NB>
+struct EmSmem {
+  uint16_t a[kSl][kTileM][kKP];  // slices of the X_{C,C} tile, [m][k]
+  uint16_t b[kSl][NB][kKP];      // slices of the B' tile, [n][k]
+  int32_t erow[kTileM];          // e of the tile's rows of C
+  int32_t fcol[kTileN];          // F of the task's columns
+};
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&d)[4], const void* p) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3])
+               : "r"(s));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t& d0, uint32_t& d1, const void* p) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(d0), "=r"(d1) : "r"(s));
+}
+// D(16x8, f32) += A(16x16, bf16, row) B(16x8, bf16, col)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Slice t of two entries (k, k+1 of one row) as one 32-bit word.
+__device__ __forceinline__ uint32_t pair_slice(const uint4& v0, const uint4& v1, int t) {
+  const uint32_t w0 = t < 2 ? v0.x : t < 4 ? v0.y : t < 6 ? v0.z : v0.w;
+  const uint32_t w1 = t < 2 ? v1.x : t < 4 ? v1.y : t < 6 ? v1.z : v1.w;
+  return (t & 1) ? (w0 >> 16) | (w1 & 0xFFFF0000u) : (w0 & 0xFFFFu) | (w1 << 16);
+}
+template <int R>
+__device__ __forceinline__ void stash_pair(uint16_t (&dst)[kSl][R][kKP], int row, int k, const uint4& v0,
+                                           const uint4& v1) {
+#pragma unroll
+  for (int t = 0; t < kSl; ++t) *reinterpret_cast<uint32_t*>(&dst[t][row][k]) = pair_slice(v0, v1, t);
+}
+
+// One step-2 task (tile origin m0, n0 of width BN, k-slice c) on the slices.
+// Four warps; warp w owns rows 16w..16w+15 of the tile and all NB columns of
+// the current column block (BN > 16: blocks of 16 in turn).
+//
+// Staging: a thread writes the 7 slices of two k-adjacent entries of one
+// row as 32-bit words.  Left of (or across) the tile's rows a warp covers 8
+// rows x 8 k (entries of X_{C,C} below the diagonal: rows contiguous in the
+// ancestors' panels); right of them 2 rows x 32 k (above the diagonal: k
+// contiguous).  Row stride 20 words: both maps hit 32 distinct banks.
+template <int BN>
+__global__ void __launch_bounds__(kEmThreads) k_em_gemm1(KArgs a, EmArgs e, const Task* __restrict__ tasks) {
+  constexpr int NB = BN < 16 ? BN : 16;
+  constexpr int NF = NB / 8;
+  __shared__ __align__(16) EmSmem<NB> sm;
+  const Task tk = tasks[blockIdx.x];
+  const int b = blockIdx.y;
+  const SnMeta m = a.meta[tk.sn];
+  const int s = m.s, r = m.r, ld = s + r;
+  const ColDesc* dk = a.desc + m.desc;
+  const int32_t* relidx = a.relidx;
+  const uint4* xs = (const uint4*)e.xs + b * a.sz.panel;
+  const uint4* ls = (const uint4*)e.ls + b * a.sz.lhat + m.lhat;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, q = lane & 3;
+  const int m0 = tk.m0;
+  const int kb = tk.c * m.kchunk, ke = min(r, kb + m.kchunk);
+  if (t < kTileM) {
+    const int i = m0 + t;
+    sm.erow[t] = i < r ? e.sig[b * e.n + e.crow[m.desc + i]] : 0;
+  } else {
+    const int c = tk.n0 + (t - kTileM);
+    sm.fcol[t - kTileM] = c < s ? e.lexp[b * e.n + m.f + c] : 0;
+  }
+  __syncthreads();
+  auto xt = [&](int i, int kg) {  // slices of Xt_{C_i, C_kg}, zero outside the tile's range
+    if (i >= r || kg >= ke) return make_uint4(0u, 0u, 0u, 0u);
+    const int lo_ = i < kg ? i : kg, hi_ = i < kg ? kg : i;
+    const ColDesc cd = dk[lo_];
+    return __ldg(xs + cd.col + relidx[cd.rel + hi_]);
+  };
+  for (int nb = tk.n0; nb < tk.n0 + BN && nb < s; nb += NB) {
+    long long hi[NF][4], lo[NF][4];
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+#pragma unroll
+      for (int x = 0; x < 4; ++x) hi[j][x] = lo[j][x] = 0;
+    for (int kt = kb; kt < ke; kt += kKC) {
+      if (kt >= m0 + kTileM) {
+#pragma unroll 2
+        for (int j = 0; j < 8; ++j) {
+          const int bi = warp * 8 + j;
+          const int row = (bi & 3) + 8 * (bi >> 2) + 4 * (lane >> 4), kk = 2 * (lane & 15);
+          const uint4 v0 = xt(m0 + row, kt + kk), v1 = xt(m0 + row, kt + kk + 1);
+          stash_pair<kTileM>(sm.a, row, kk, v0, v1);
+        }
+      } else {
+#pragma unroll 2
+        for (int j = 0; j < 8; ++j) {
+          const int bi = warp * 8 + j;
+          const int row = 8 * (bi & 7) + (lane & 7), kk = 2 * (4 * (bi >> 3) + (lane >> 3));
+          const uint4 v0 = xt(m0 + row, kt + kk), v1 = xt(m0 + row, kt + kk + 1);
+          stash_pair<kTileM>(sm.a, row, kk, v0, v1);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NB / 8; ++j) {
+        const int pi = j * kEmThreads + t, nn = pi >> 4, kk = 2 * (pi & 15), col = nb + nn;
+        uint4 v0 = make_uint4(0u, 0u, 0u, 0u), v1 = v0;
+        if (col < s) {
+          if (kt + kk < ke) v0 = __ldg(ls + kt + kk + (int64_t)col * r);
+          if (kt + kk + 1 < ke) v1 = __ldg(ls + kt + kk + 1 + (int64_t)col * r);
+        }
+        stash_pair<NB>(sm.b, nn, kk, v0, v1);
+      }
+      __syncthreads();
+      float S[kSl][NF][4];
+#pragma unroll
+      for (int gi = 0; gi < kSl; ++gi)
+#pragma unroll
+        for (int j = 0; j < NF; ++j)
+#pragma unroll
+          for (int x = 0; x < 4; ++x) S[gi][j][x] = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < kKC; ks += 16) {
+        uint32_t B[kSl][NF][2];
+#pragma unroll
+        for (int u = 0; u < kSl; ++u) {
+          if constexpr (NF == 2) {
+            uint32_t d[4];
+            ldsm_x4(d, &sm.b[u][(lane & 7) + ((lane >> 4) << 3)][ks + (((lane >> 3) & 1) << 3)]);
+            B[u][0][0] = d[0];
+            B[u][0][1] = d[1];
+            B[u][1][0] = d[2];
+            B[u][1][1] = d[3];
+          } else {
+            ldsm_x2(B[u][0][0], B[u][0][1], &sm.b[u][lane & 7][ks + (((lane >> 3) & 1) << 3)]);
+          }
+        }
+#pragma unroll
+        for (int ta = 0; ta < kSl; ++ta) {
+          uint32_t A[4];
+          ldsm_x4(A, &sm.a[ta][warp * 16 + (lane & 15)][ks + ((lane >> 4) << 3)]);
+#pragma unroll
+          for (int u = 0; u + ta < kSl; ++u)
+#pragma unroll
+            for (int j = 0; j < NF; ++j) mma_bf16(S[ta + u][j], A, B[u][j][0], B[u][j][1]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NF; ++j)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const long long s0 = __float2int_rn(S[0][j][x]), s1 = __float2int_rn(S[1][j][x]),
+                          s2 = __float2int_rn(S[2][j][x]), s3 = __float2int_rn(S[3][j][x]),
+                          s4 = __float2int_rn(S[4][j][x]), s5 = __float2int_rn(S[5][j][x]),
+                          s6 = __float2int_rn(S[6][j][x]);
+          hi[j][x] += s0 * 65536 + s1 * 256 + s2;
+          lo[j][x] += s3 * 16777216 + s4 * 65536 + s5 * 256 + s6;
+        }
+      __syncthreads();
+    }
+    // accumulator x of fragment j: row g + 8 (x >> 1), column 8 j + 2 q + (x & 1)
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int row = warp * 16 + g + 8 * (x >> 1), col = nb + 8 * j + 2 * q + (x & 1);
+        const int i = m0 + row;
+        if (i < r && col < s) {
+          const double v = ldexp((double)hi[j][x] + (double)lo[j][x] * 0x1p-32,
+                                 sm.erow[row] + sm.fcol[col - tk.n0] - 31);
+          if (m.ksplit == 1)
+            ((double*)a.X + b * a.sz.panel + m.panel + s)[i + (int64_t)col * ld] = -v;
+          else
+            ((double*)a.ypart + b * a.sz.ypart + m.ypart + (int64_t)tk.c * r * s)[i + (int64_t)col * r] = v;
+        }
+      }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_em_split_x(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, cudaStream_t st) {
+  if (nsn <= 0) return cudaSuccess;
+  k_em_split_x<<<dim3(nsn, a.sz.batch, kSplitGroups), 256, 0, st>>>(a, e, sns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_em_split_lhat(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, cudaStream_t st) {
+  if (nsn <= 0) return cudaSuccess;
+  k_em_split_lhat<<<dim3(nsn, a.sz.batch, kSplitGroups / 8), 256, 0, st>>>(a, e, sns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_em_gemm1(int var, const KArgs& a, const EmArgs& e, const Task* t, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)n, a.sz.batch);
+  switch (var) {
+    case 0: k_em_gemm1<8><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
+    case 1: k_em_gemm1<16><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
+    case 2: k_em_gemm1<32><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
+    default: k_em_gemm1<64><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace psi

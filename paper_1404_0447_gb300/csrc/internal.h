@@ -94,6 +94,14 @@ inline int pick_variant(int width, bool cplx, int small_cutoff = -1) {
   return best;
 }
 
+// Step-2 tile width: the FP64 kernel's padding-minimal choice, or with the
+// bf16 emulation (16-column passes) 64 x 16 tiles for every supernode wider
+// than 8 columns.
+inline int step2_variant(int width, bool cplx, const pselinv_opts& o) {
+  if (o.fp64_emulation) return width <= 8 ? 0 : 1;
+  return pick_variant(width, cplx, o.small_cutoff);
+}
+
 struct TaskList {
   std::vector<Task> tasks;
   std::vector<Range> per_lv;  // [level * kNumVar + var] (level 0 = root level)
@@ -174,6 +182,12 @@ struct pselinv_handle {
   void* d_XU = nullptr;     // XU panels (X_{j,i} at position (i, j))
   void* d_uhat = nullptr;   // Uhat^T / factor scratch of the U side
   void* d_uinv = nullptr;   // (U'_KK^T)^{-1}
+  // FP64 emulation of step 2 on the bf16 tensor cores (opts.fp64_emulation)
+  void* d_xs = nullptr;     // slices of the scaled X panels (16 bytes per entry)
+  void* d_ls = nullptr;     // slices of the scaled Lhat (16 bytes per entry)
+  void* d_sig = nullptr;    // int32 column exponents e_p, batch x n
+  void* d_lexp = nullptr;   // int32 column exponents F of B', batch x n
+  void* d_crow = nullptr;   // int32 global rows of every C (rows, at rowptr)
   // adjoint work buffers (allocated on first pselinv_selinv_adjoint)
   void* d_xb = nullptr;     // X-bar, then F-bar (panel layout)
   void* d_lb = nullptr;     // L-bar (panel layout)

@@ -89,6 +89,32 @@ cudaError_t launch_trace_sum(int dtype, const void* X, int64_t panel_total, cons
                              const uint8_t* diagmask, const void* vals, int64_t nnz, int batch, void* out,
                              cudaStream_t st);
 
+// ---- step 2 with FP64 arithmetic emulated on the bf16 tensor cores (emulate.cu) ----
+// Real symmetric positive definite X only: |X_pq| <= sqrt(X_pp X_qq), so with
+// e_p = ceil(log2 sqrt(X_pp)) every entry of Xt = 2^-(e_p + e_q) X has |Xt| < 1.
+// Each entry of Xt (and of B' = diag(2^e_C) Lhat over a per-column exponent)
+// is cut once into 7 signed 8-bit slices held as bf16; step 2 forms the 28
+// slice products of weight >= 2^-48 with exact FP32 sums over 32-row chunks
+// folded into 64-bit integers.
+struct EmArgs {
+  void* xs;              // [batch][panel_total] uint4: 7 bf16 slices of Xt per X panel entry
+  void* ls;              // [batch][lhat_total] uint4: 7 bf16 slices of B' per Lhat entry
+  int32_t* sig;          // [batch][n] e_p of every column (written when its level finishes)
+  int32_t* lexp;         // [batch][n] column exponent F of B' (|B'_{:,j}| < 2^F), per global column
+  const int32_t* crow;   // [sum r] global row of C[i] of supernode K at desc offset of K
+  int64_t n;
+};
+// Emulation status word: nonzero after an X diagonal <= 0 / not finite or a
+// scaled entry outside its slice range (X not positive definite).
+constexpr int kEmStatusWord = 4;
+// After steps 2-3 of a level: e_p of the level's columns and the slices of
+// its X panels.  Before step 2 of a level: F and the slices of its B'.
+cudaError_t launch_em_split_x(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, cudaStream_t st);
+cudaError_t launch_em_split_lhat(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, cudaStream_t st);
+// Step-2 tiles (the Gemm1 task list of tile variant var) on the slices.
+cudaError_t launch_em_gemm1(int var, const KArgs& a, const EmArgs& e, const Task* tasks, int64_t n,
+                            cudaStream_t st);
+
 // ---- persistent per-level schedule (persistent.cu) ----
 struct PArgs {
   const Task* g1;       // step-2 task array (t_gemm1)
