@@ -371,7 +371,9 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
   const bool emul = h->opts.fp64_emulation != 0;
   const psi::EmArgs em{h->d_xs, h->d_ls, (int32_t*)h->d_sig, (int32_t*)h->d_lexp, (const int32_t*)h->d_crow, h->n};
   // one step: the given supernodes, with per-variant task ranges of steps 2 and 3
-  auto step = [&](const int32_t* sns, int nsn_step, const psi::Range* r1, const psi::Range* r2, bool split) {
+  // maxr: the largest |C| among the step's supernodes
+  auto step = [&](const int32_t* sns, int nsn_step, const psi::Range* r1, const psi::Range* r2, bool split,
+                  int maxr) {
     int n1 = split ? 1 : 0, n2 = 0, e;
     for (int v = 0; v < psi::kNumVar; ++v) {
       n1 += r1[v].end > r1[v].begin;
@@ -380,7 +382,7 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
     // step 2 (ka = a), or step 4 (ka = a4) of a non-symmetric handle
     auto gemm1 = [&](const psi::KArgs& ka) {
       return tm.run(1, n1 + (emul ? 1 : 0), [&] {
-        cudaError_t x = emul ? psi::launch_em_split_lhat(ka, em, sns, nsn_step, st) : cudaSuccess;
+        cudaError_t x = emul ? psi::launch_em_split_lhat(ka, em, sns, nsn_step, maxr, st) : cudaSuccess;
         for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
           x = emul ? psi::launch_em_gemm1(v, ka, em, tasks_at(h, h->off_gemm1, r1[v].begin), r1[v].end - r1[v].begin,
                                           st)
@@ -416,13 +418,15 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
       psi::Range r1[psi::kNumVar], r2[psi::kNumVar];
       r1[h->t_gemm1.var[k]] = h->t_gemm1.per_sn[k];
       r2[h->t_gemm2.var[k]] = h->t_gemm2.per_sn[k];
-      if ((rc = step(lsn + pos[k], 1, r1, r2, h->meta[k].ksplit > 1))) return rc;
+      if ((rc = step(lsn + pos[k], 1, r1, r2, h->meta[k].ksplit > 1, h->meta[k].r))) return rc;
     }
   } else {
     for (int32_t l = 0; l < h->nlevels; ++l) {
+      int maxr = 0;
+      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) maxr = std::max(maxr, h->meta[h->level_sn[t]].r);
       if ((rc = step(lsn + h->level_ptr[l], h->level_ptr[l + 1] - h->level_ptr[l],
                      &h->t_gemm1.per_lv[(size_t)l * psi::kNumVar], &h->t_gemm2.per_lv[(size_t)l * psi::kNumVar],
-                     h->level_split[l] != 0)))
+                     h->level_split[l] != 0, maxr)))
         return rc;
       if (after_level && (rc = (*after_level)(l))) return rc;
     }

@@ -38,7 +38,6 @@ namespace {
 
 constexpr int kSl = 7;         // slices per entry
 constexpr int kKC = 32;        // rows of C per exact FP32 chunk
-constexpr int kKP = kKC + 8;   // shared row stride in bf16 elements (80 bytes: ldmatrix rows conflict-free)
 constexpr int kEmThreads = 128;
 
 // bf16 bits of the integer c in [0, 255] with sign bit sgn (0 or 0x8000):
@@ -121,44 +120,72 @@ __global__ void __launch_bounds__(256) k_em_split_x(KArgs a, EmArgs e, const int
   if (bad) atomicOr(a.status + kEmStatusWord, 1);
 }
 
-// Before step 2 of supernode K: F_j and the slices of B' = diag(2^e_C) Lhat,
-// one warp per column.  Grid (supernodes, batch, column groups).
-__global__ void __launch_bounds__(256) k_em_split_lhat(KArgs a, EmArgs e, const int32_t* __restrict__ sns) {
+// Rows of C whose exponents k_em_split_lhat keeps in shared memory at most
+// (a launch reserves the largest |C| of its supernodes, capped here; larger
+// |C| reads them from global memory).
+constexpr int kEcRows = 40960;
+
+// Before step 2 of supernode K: F_j and the slices of B' = diag(2^e_C) Lhat.
+// Grid (supernodes, batch, column groups); a CTA takes the exponents e of
+// the rows of C once, then its columns one at a time with all threads
+// (block-wide maximum for F_j, then the slices).
+__global__ void __launch_bounds__(256) k_em_split_lhat(KArgs a, EmArgs e, const int32_t* __restrict__ sns,
+                                                       int ec_cap) {
+  extern __shared__ int ec_smem[];
+  __shared__ int red[8];
   const int k = sns[blockIdx.x], b = blockIdx.y;
   const SnMeta m = a.meta[k];
   const int s = m.s, r = m.r;
+  if ((int)blockIdx.z >= s) return;
   const double* Lh = (const double*)a.Lhat + b * a.sz.lhat + m.lhat;
   uint4* ls = (uint4*)e.ls + b * a.sz.lhat + m.lhat;
   const int32_t* sig = e.sig + b * e.n;
   const int32_t* crow = e.crow + m.desc;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool cached = r <= ec_cap;
+  if (cached)
+    for (int i = threadIdx.x; i < r; i += blockDim.x) ec_smem[i] = sig[crow[i]];
+  __syncthreads();
+  auto ec = [&](int i) { return cached ? ec_smem[i] : sig[crow[i]]; };
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int bad = 0;
-  for (int j = blockIdx.z * nw + warp; j < s; j += gridDim.z * nw) {
+  for (int j = blockIdx.z; j < s; j += gridDim.z) {
     const double* col = Lh + (int64_t)j * r;
     int mx = INT_MIN;
-    for (int i = lane; i < r; i += 32) {
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
       const unsigned long long bits = (unsigned long long)__double_as_longlong(col[i]);
       const int ex = (int)((bits >> 52) & 0x7FF);
       if (ex == 0x7FF)
         bad = 1;
       else if (ex != 0)
-        mx = max(mx, ex - 1023 + sig[crow[i]]);  // floor(log2 |B'_ij|)
+        mx = max(mx, ex - 1023 + ec(i));  // floor(log2 |B'_ij|)
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    mx = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, red[w]);
     const int F = mx == INT_MIN ? 0 : mx + 1;
-    if (lane == 0) e.lexp[b * e.n + m.f + j] = F;
-    for (int i = lane; i < r; i += 32) ls[i + (int64_t)j * r] = split7(col[i], F - sig[crow[i]], bad);
+    if (threadIdx.x == 0) e.lexp[b * e.n + m.f + j] = F;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) ls[i + (int64_t)j * r] = split7(col[i], F - ec(i), bad);
+    __syncthreads();  // red[] is rewritten by the next column
   }
   if (bad) atomicOr(a.status + kEmStatusWord, 1);
 }
 
+constexpr int kKP = kKC + 8;  // shared row stride of a slice plane in bf16 (80 bytes: ldmatrix rows conflict-free)
+
+// Step-2 tile: the 7 slice planes of the X_{C,C} and B' tiles of one
+// 32-row chunk of C, the descriptors of the tile's rows and of the columns
+// of the current and the next chunk.
 template <int NB>
 struct EmSmem {
-  uint16_t a[kSl][kTileM][kKP];  // slices of the X_{C,C} tile, [m][k]
-  uint16_t b[kSl][NB][kKP];      // slices of the B' tile, [n][k]
+  uint16_t a[kSl][kTileM][kKP];  // X_{C,C} tile, [slice][m][k]
+  uint16_t b[kSl][NB][kKP];      // B' tile, [slice][n][k]
+  ColDesc rdesc[kTileM];         // desc of the tile's rows of C
+  ColDesc cdesc[2][kKC];         // desc of the columns of chunk c, slot c & 1
   int32_t erow[kTileM];          // e of the tile's rows of C
-  int32_t fcol[kTileN];          // F of the task's columns
+  int32_t fcol[kTileN];          // F of the tile's columns
 };
 
 __device__ __forceinline__ void ldsm_x4(uint32_t (&d)[4], const void* p) {
@@ -180,11 +207,11 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Slice t of two entries (k, k+1 of one row) as one 32-bit word.
+// Slice t of two entries (k, k+1 of one row) as one bf16x2 word.
 __device__ __forceinline__ uint32_t pair_slice(const uint4& v0, const uint4& v1, int t) {
   const uint32_t w0 = t < 2 ? v0.x : t < 4 ? v0.y : t < 6 ? v0.z : v0.w;
   const uint32_t w1 = t < 2 ? v1.x : t < 4 ? v1.y : t < 6 ? v1.z : v1.w;
-  return (t & 1) ? (w0 >> 16) | (w1 & 0xFFFF0000u) : (w0 & 0xFFFFu) | (w1 << 16);
+  return __byte_perm(w0, w1, (t & 1) ? 0x7632 : 0x5410);
 }
 template <int R>
 __device__ __forceinline__ void stash_pair(uint16_t (&dst)[kSl][R][kKP], int row, int k, const uint4& v0,
@@ -193,18 +220,20 @@ __device__ __forceinline__ void stash_pair(uint16_t (&dst)[kSl][R][kKP], int row
   for (int t = 0; t < kSl; ++t) *reinterpret_cast<uint32_t*>(&dst[t][row][k]) = pair_slice(v0, v1, t);
 }
 
-// One step-2 task (tile origin m0, n0 of width BN, k-slice c) on the slices.
-// Four warps; warp w owns rows 16w..16w+15 of the tile and all NB columns of
-// the current column block (BN > 16: blocks of 16 in turn).
+// One step-2 task (tile origin m0, n0, width NB in {8, 16}, k-slice c) on
+// the slices.  Four warps; warp w owns rows 16w..16w+15 and all NB columns.
 //
-// Staging: a thread writes the 7 slices of two k-adjacent entries of one
-// row as 32-bit words.  Left of (or across) the tile's rows a warp covers 8
-// rows x 8 k (entries of X_{C,C} below the diagonal: rows contiguous in the
-// ancestors' panels); right of them 2 rows x 32 k (above the diagonal: k
-// contiguous).  Row stride 20 words: both maps hit 32 distinct banks.
-template <int BN>
-__global__ void __launch_bounds__(kEmThreads) k_em_gemm1(KArgs a, EmArgs e, const Task* __restrict__ tasks) {
-  constexpr int NB = BN < 16 ? BN : 16;
+// Per chunk of 32 rows of C: the 16 entries of X_{C,C} a thread stages are
+// fetched together (their relative indices were loaded during the previous
+// chunk's products, the row descriptors are cached for the tile and the
+// column descriptors one chunk ahead), written to the slice planes as
+// 32-bit words holding one slice of two k-adjacent entries, and the 28
+// slice products run on ldmatrix fragments.  Pair p of a thread: right of
+// the tile's rows (entries above the diagonal of X_{C,C}, read along k) a
+// warp covers 2 rows x 32 k, else (rows contiguous in the ancestors'
+// panels) 8 rows x 8 k; both maps hit 32 distinct banks (row stride 20 words).
+template <int NB>
+__global__ void __launch_bounds__(kEmThreads, 3) k_em_gemm1(KArgs a, EmArgs e, const Task* __restrict__ tasks) {
   constexpr int NF = NB / 8;
   __shared__ __align__(16) EmSmem<NB> sm;
   const Task tk = tasks[blockIdx.x];
@@ -216,120 +245,166 @@ __global__ void __launch_bounds__(kEmThreads) k_em_gemm1(KArgs a, EmArgs e, cons
   const uint4* xs = (const uint4*)e.xs + b * a.sz.panel;
   const uint4* ls = (const uint4*)e.ls + b * a.sz.lhat + m.lhat;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, q = lane & 3;
-  const int m0 = tk.m0;
+  const int m0 = tk.m0, nb = tk.n0;
   const int kb = tk.c * m.kchunk, ke = min(r, kb + m.kchunk);
+  const int nck = ke > kb ? (ke - kb + kKC - 1) / kKC : 0;
   if (t < kTileM) {
     const int i = m0 + t;
     sm.erow[t] = i < r ? e.sig[b * e.n + e.crow[m.desc + i]] : 0;
+    if (i < r) sm.rdesc[t] = dk[i];
   } else {
-    const int c = tk.n0 + (t - kTileM);
+    const int c = nb + (t - kTileM);
     sm.fcol[t - kTileM] = c < s ? e.lexp[b * e.n + m.f + c] : 0;
   }
+  if (t < kKC && nck > 0 && kb + t < ke) sm.cdesc[0][t] = dk[kb + t];
   __syncthreads();
-  auto xt = [&](int i, int kg) {  // slices of Xt_{C_i, C_kg}, zero outside the tile's range
-    if (i >= r || kg >= ke) return make_uint4(0u, 0u, 0u, 0u);
-    const int lo_ = i < kg ? i : kg, hi_ = i < kg ? kg : i;
-    const ColDesc cd = dk[lo_];
-    return __ldg(xs + cd.col + relidx[cd.rel + hi_]);
+
+  // pair p (0..7) of this thread in chunk c: tile row and first k of the pair
+  auto pair_at = [&](int c, int p, int& row, int& kk) {
+    const int bi = warp * 8 + p;
+    if (kb + c * kKC >= m0 + kTileM) {
+      row = (bi & 3) + 8 * (bi >> 2) + 4 * (lane >> 4);
+      kk = 2 * (lane & 15);
+    } else {
+      row = 8 * (bi & 7) + (lane & 7);
+      kk = 2 * (4 * (bi >> 3) + (lane >> 3));
+    }
   };
-  for (int nb = tk.n0; nb < tk.n0 + BN && nb < s; nb += NB) {
-    long long hi[NF][4], lo[NF][4];
+  // entry (i, kg), i >= kg, of X_{C,C} sits in column desc[kg] at row
+  // relidx[desc[kg].rel + i]; above the diagonal the symmetric one
+  auto load_ri = [&](int c, int (&ri)[16]) {
+    const int kt = kb + c * kKC;
 #pragma unroll
-    for (int j = 0; j < NF; ++j)
+    for (int p = 0; p < 8; ++p) {
+      int row, kk;
+      pair_at(c, p, row, kk);
 #pragma unroll
-      for (int x = 0; x < 4; ++x) hi[j][x] = lo[j][x] = 0;
-    for (int kt = kb; kt < ke; kt += kKC) {
-      if (kt >= m0 + kTileM) {
-#pragma unroll 2
-        for (int j = 0; j < 8; ++j) {
-          const int bi = warp * 8 + j;
-          const int row = (bi & 3) + 8 * (bi >> 2) + 4 * (lane >> 4), kk = 2 * (lane & 15);
-          const uint4 v0 = xt(m0 + row, kt + kk), v1 = xt(m0 + row, kt + kk + 1);
-          stash_pair<kTileM>(sm.a, row, kk, v0, v1);
-        }
-      } else {
-#pragma unroll 2
-        for (int j = 0; j < 8; ++j) {
-          const int bi = warp * 8 + j;
-          const int row = 8 * (bi & 7) + (lane & 7), kk = 2 * (4 * (bi >> 3) + (lane >> 3));
-          const uint4 v0 = xt(m0 + row, kt + kk), v1 = xt(m0 + row, kt + kk + 1);
-          stash_pair<kTileM>(sm.a, row, kk, v0, v1);
+      for (int h = 0; h < 2; ++h) {
+        const int i = m0 + row, kg = kt + kk + h;
+        ri[2 * p + h] = 0;
+        if (i < r && kg < ke) {
+          const ColDesc& cd = i < kg ? sm.rdesc[row] : sm.cdesc[c & 1][kk + h];
+          ri[2 * p + h] = __ldg(relidx + cd.rel + (i < kg ? kg : i));
         }
       }
+    }
+  };
+
+  long long hi[NF][4], lo[NF][4];
+#pragma unroll
+  for (int j = 0; j < NF; ++j)
+#pragma unroll
+    for (int x = 0; x < 4; ++x) hi[j][x] = lo[j][x] = 0;
+  int ri[16];
+  if (nck > 0) load_ri(0, ri);
+  for (int c = 0; c < nck; ++c) {
+    const int kt = kb + c * kKC;
+    // column descriptors of the next chunk (stored after this chunk's staging)
+    ColDesc cdn{0, 0};
+    const bool have_cdn = t < kKC && c + 1 < nck && kt + kKC + t < ke;
+    if (have_cdn) cdn = dk[kt + kKC + t];
+    {
+      uint4 v[16];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        int row, kk;
+        pair_at(c, p, row, kk);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = m0 + row, kg = kt + kk + h;
+          v[2 * p + h] = make_uint4(0u, 0u, 0u, 0u);
+          if (i < r && kg < ke)
+            v[2 * p + h] = __ldg(xs + (i < kg ? sm.rdesc[row].col : sm.cdesc[c & 1][kk + h].col) + ri[2 * p + h]);
+        }
+      }
+      uint4 w[NB / 4];
 #pragma unroll
       for (int j = 0; j < NB / 8; ++j) {
         const int pi = j * kEmThreads + t, nn = pi >> 4, kk = 2 * (pi & 15), col = nb + nn;
-        uint4 v0 = make_uint4(0u, 0u, 0u, 0u), v1 = v0;
+        w[2 * j] = w[2 * j + 1] = make_uint4(0u, 0u, 0u, 0u);
         if (col < s) {
-          if (kt + kk < ke) v0 = __ldg(ls + kt + kk + (int64_t)col * r);
-          if (kt + kk + 1 < ke) v1 = __ldg(ls + kt + kk + 1 + (int64_t)col * r);
-        }
-        stash_pair<NB>(sm.b, nn, kk, v0, v1);
-      }
-      __syncthreads();
-      float S[kSl][NF][4];
-#pragma unroll
-      for (int gi = 0; gi < kSl; ++gi)
-#pragma unroll
-        for (int j = 0; j < NF; ++j)
-#pragma unroll
-          for (int x = 0; x < 4; ++x) S[gi][j][x] = 0.f;
-#pragma unroll
-      for (int ks = 0; ks < kKC; ks += 16) {
-        uint32_t B[kSl][NF][2];
-#pragma unroll
-        for (int u = 0; u < kSl; ++u) {
-          if constexpr (NF == 2) {
-            uint32_t d[4];
-            ldsm_x4(d, &sm.b[u][(lane & 7) + ((lane >> 4) << 3)][ks + (((lane >> 3) & 1) << 3)]);
-            B[u][0][0] = d[0];
-            B[u][0][1] = d[1];
-            B[u][1][0] = d[2];
-            B[u][1][1] = d[3];
-          } else {
-            ldsm_x2(B[u][0][0], B[u][0][1], &sm.b[u][lane & 7][ks + (((lane >> 3) & 1) << 3)]);
-          }
-        }
-#pragma unroll
-        for (int ta = 0; ta < kSl; ++ta) {
-          uint32_t A[4];
-          ldsm_x4(A, &sm.a[ta][warp * 16 + (lane & 15)][ks + ((lane >> 4) << 3)]);
-#pragma unroll
-          for (int u = 0; u + ta < kSl; ++u)
-#pragma unroll
-            for (int j = 0; j < NF; ++j) mma_bf16(S[ta + u][j], A, B[u][j][0], B[u][j][1]);
+          if (kt + kk < ke) w[2 * j] = __ldg(ls + kt + kk + (int64_t)col * r);
+          if (kt + kk + 1 < ke) w[2 * j + 1] = __ldg(ls + kt + kk + 1 + (int64_t)col * r);
         }
       }
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        int row, kk;
+        pair_at(c, p, row, kk);
+        stash_pair<kTileM>(sm.a, row, kk, v[2 * p], v[2 * p + 1]);
+      }
+#pragma unroll
+      for (int j = 0; j < NB / 8; ++j) {
+        const int pi = j * kEmThreads + t;
+        stash_pair<NB>(sm.b, pi >> 4, 2 * (pi & 15), w[2 * j], w[2 * j + 1]);
+      }
+    }
+    if (have_cdn) sm.cdesc[(c + 1) & 1][t] = cdn;
+    __syncthreads();
+    // relative indices of the next chunk, in flight during the products
+    if (c + 1 < nck) load_ri(c + 1, ri);
+    float S[kSl][NF][4];
+#pragma unroll
+    for (int gi = 0; gi < kSl; ++gi)
 #pragma unroll
       for (int j = 0; j < NF; ++j)
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
-          const long long s0 = __float2int_rn(S[0][j][x]), s1 = __float2int_rn(S[1][j][x]),
-                          s2 = __float2int_rn(S[2][j][x]), s3 = __float2int_rn(S[3][j][x]),
-                          s4 = __float2int_rn(S[4][j][x]), s5 = __float2int_rn(S[5][j][x]),
-                          s6 = __float2int_rn(S[6][j][x]);
-          hi[j][x] += s0 * 65536 + s1 * 256 + s2;
-          lo[j][x] += s3 * 16777216 + s4 * 65536 + s5 * 256 + s6;
+        for (int x = 0; x < 4; ++x) S[gi][j][x] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < kKC; ks += 16) {
+      uint32_t B[kSl][NF][2];
+#pragma unroll
+      for (int u = 0; u < kSl; ++u) {
+        if constexpr (NF == 2) {
+          uint32_t d[4];
+          ldsm_x4(d, &sm.b[u][(lane & 7) + ((lane >> 4) << 3)][ks + (((lane >> 3) & 1) << 3)]);
+          B[u][0][0] = d[0];
+          B[u][0][1] = d[1];
+          B[u][1][0] = d[2];
+          B[u][1][1] = d[3];
+        } else {
+          ldsm_x2(B[u][0][0], B[u][0][1], &sm.b[u][lane & 7][ks + (((lane >> 3) & 1) << 3)]);
         }
-      __syncthreads();
+      }
+#pragma unroll
+      for (int ta = 0; ta < kSl; ++ta) {
+        uint32_t A[4];
+        ldsm_x4(A, &sm.a[ta][warp * 16 + (lane & 15)][ks + ((lane >> 4) << 3)]);
+#pragma unroll
+        for (int u = 0; u + ta < kSl; ++u)
+#pragma unroll
+          for (int j = 0; j < NF; ++j) mma_bf16(S[ta + u][j], A, B[u][j][0], B[u][j][1]);
+      }
     }
-    // accumulator x of fragment j: row g + 8 (x >> 1), column 8 j + 2 q + (x & 1)
 #pragma unroll
     for (int j = 0; j < NF; ++j)
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
-        const int row = warp * 16 + g + 8 * (x >> 1), col = nb + 8 * j + 2 * q + (x & 1);
-        const int i = m0 + row;
-        if (i < r && col < s) {
-          const double v = ldexp((double)hi[j][x] + (double)lo[j][x] * 0x1p-32,
-                                 sm.erow[row] + sm.fcol[col - tk.n0] - 31);
-          if (m.ksplit == 1)
-            ((double*)a.X + b * a.sz.panel + m.panel + s)[i + (int64_t)col * ld] = -v;
-          else
-            ((double*)a.ypart + b * a.sz.ypart + m.ypart + (int64_t)tk.c * r * s)[i + (int64_t)col * r] = v;
-        }
+        const long long s0 = __float2int_rn(S[0][j][x]), s1 = __float2int_rn(S[1][j][x]),
+                        s2 = __float2int_rn(S[2][j][x]), s3 = __float2int_rn(S[3][j][x]),
+                        s4 = __float2int_rn(S[4][j][x]), s5 = __float2int_rn(S[5][j][x]),
+                        s6 = __float2int_rn(S[6][j][x]);
+        hi[j][x] += s0 * 65536 + s1 * 256 + s2;
+        lo[j][x] += s3 * 16777216 + s4 * 65536 + s5 * 256 + s6;
       }
+    __syncthreads();
   }
+  // accumulator x of fragment j: row g + 8 (x >> 1), column 8 j + 2 q + (x & 1)
+#pragma unroll
+  for (int j = 0; j < NF; ++j)
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int row = warp * 16 + g + 8 * (x >> 1), col = nb + 8 * j + 2 * q + (x & 1);
+      const int i = m0 + row;
+      if (i < r && col < s) {
+        const double v = ldexp((double)hi[j][x] + (double)lo[j][x] * 0x1p-32,
+                               sm.erow[row] + sm.fcol[col - nb] - 31);
+        if (m.ksplit == 1)
+          ((double*)a.X + b * a.sz.panel + m.panel + s)[i + (int64_t)col * ld] = -v;
+        else
+          ((double*)a.ypart + b * a.sz.ypart + m.ypart + (int64_t)tk.c * r * s)[i + (int64_t)col * r] = v;
+      }
+    }
 }
 
 }  // namespace
@@ -340,20 +415,31 @@ cudaError_t launch_em_split_x(const KArgs& a, const EmArgs& e, const int32_t* sn
   return cudaGetLastError();
 }
 
-cudaError_t launch_em_split_lhat(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, cudaStream_t st) {
+cudaError_t launch_em_split_lhat(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, int max_r,
+                                 cudaStream_t st) {
   if (nsn <= 0) return cudaSuccess;
-  k_em_split_lhat<<<dim3(nsn, a.sz.batch, kSplitGroups / 8), 256, 0, st>>>(a, e, sns);
+  const int cap = max_r < kEcRows ? max_r : kEcRows;
+  k_em_split_lhat<<<dim3(nsn, a.sz.batch, kSplitGroups), 256, sizeof(int) * cap, st>>>(a, e, sns, cap);
   return cudaGetLastError();
+}
+
+cudaError_t setup_em_kernels() {
+  cudaError_t err = cudaFuncSetAttribute(k_em_split_lhat, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(int) * kEcRows);
+  if (err != cudaSuccess) return err;
+  // static shared memory (< 48 KB): prefer the shared-memory carve-out (3 CTAs per SM)
+  err = cudaFuncSetAttribute(k_em_gemm1<8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (err != cudaSuccess) return err;
+  return cudaFuncSetAttribute(k_em_gemm1<16>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 cudaError_t launch_em_gemm1(int var, const KArgs& a, const EmArgs& e, const Task* t, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const dim3 grid((unsigned)n, a.sz.batch);
-  switch (var) {
+  switch (var) {  // the emulation's task lists hold 64 x 8 and 64 x 16 tiles only
     case 0: k_em_gemm1<8><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
     case 1: k_em_gemm1<16><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
-    case 2: k_em_gemm1<32><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
-    default: k_em_gemm1<64><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

@@ -868,6 +868,7 @@ static cudaError_t setup_t() {
 cudaError_t setup_kernels() {
   cudaError_t e = setup_t<double>();
   if (e != cudaSuccess) return e;
+  if ((e = setup_em_kernels()) != cudaSuccess) return e;
   return setup_t<Cplx>();
 }
 

@@ -110,8 +110,12 @@ constexpr int kEmStatusWord = 4;
 // After steps 2-3 of a level: e_p of the level's columns and the slices of
 // its X panels.  Before step 2 of a level: F and the slices of its B'.
 cudaError_t launch_em_split_x(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, cudaStream_t st);
-cudaError_t launch_em_split_lhat(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, cudaStream_t st);
-// Step-2 tiles (the Gemm1 task list of tile variant var) on the slices.
+// max_r: the largest |C| among the supernodes (sizes the shared memory).
+cudaError_t launch_em_split_lhat(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, int max_r,
+                                 cudaStream_t st);
+// Dynamic shared-memory limits of the step-2 kernels (called by setup_kernels).
+cudaError_t setup_em_kernels();
+// Step-2 tiles (the Gemm1 task list of tile variant var, 0 or 1) on the slices.
 cudaError_t launch_em_gemm1(int var, const KArgs& a, const EmArgs& e, const Task* tasks, int64_t n,
                             cudaStream_t st);
 
