@@ -38,6 +38,32 @@ FP64_PEAK_TFLOPS = 1.10
 # counters: profiles/k_gemm1_traffic_grid3d_80.md.  Set to None whenever
 # those kernels change until they are measured again.
 STEP2_TRAFFIC_BYTES_PER_LAUNCH = 460.55e6
+# bf16 dense peaks: MEASURED_PEAKS.json (cuBLAS, sustained over seconds) and
+# the warp-level mma.sync m16n8k16 rate of the same GPU (bench.py --peaks).
+MEASURED_BF16_SUSTAINED_TFLOPS = 1696.4
+MMA_SYNC_BF16_TFLOPS = 605.7
+
+
+def bf16_sustained_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"])
+    except (OSError, KeyError, ValueError):
+        return MEASURED_BF16_SUSTAINED_TFLOPS
+
+
+def emulated_step2_roofline(flops_gemm1, s2_ms):
+    """Step-2 class of the emulated path (B' split, slice products, slice
+    reductions) against the bf16 tensor peak: 28 bf16 slice products per
+    multiply-add of X_{C,C} Lhat."""
+    bf16 = 28 * flops_gemm1 / (s2_ms * 1e-3) / 1e12
+    peak = bf16_sustained_peak()
+    return {"bound": "tensor", "kernel": "step 2 emulated: k_em_split_lhat + k_em_gemm1 (mma.sync m16n8k16 "
+                                         "bf16) + slice reductions",
+            "achieved": bf16, "peak": peak, "unit": "TFLOP/s", "frac": bf16 / peak,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS); the warp-level mma.sync path of "
+                           "this GPU tops out near %.0f (bench.py --peaks)" % MMA_SYNC_BF16_TFLOPS,
+            "frac_of_mma_sync_peak": bf16 / MMA_SYNC_BF16_TFLOPS, "traffic": None}
 WORKLOAD = ("grid3d_80: 80^3 7-point Laplacian, n=512000, diag 6+U(0.01,0.1), geometric nested "
             "dissection, relaxed supernodes of width <= 128, FP64")
 # Oracle sample for the CPU baseline: the same grid family at a size the
@@ -68,7 +94,10 @@ def parse():
                     help="measure the FP64 and low-precision MMA peaks of this GPU (the roofline denominators)")
     ap.add_argument("--min-slice-rows", type=int, default=None, help="override the library default")
     ap.add_argument("--fp64-emulation", action="store_true",
-                    help="step 2 in FP64 accuracy on the bf16 tensor cores (opts.fp64_emulation = 1)")
+                    help="headline on the opt-in path with step 2 emulated on the bf16 tensor cores "
+                         "(opts.fp64_emulation = 1) instead of FP64 arithmetic")
+    ap.add_argument("--no-emulation", action="store_true",
+                    help="skip the secondary measurement of the emulated step 2 (config.fp64_emulation)")
     return ap.parse_args()
 
 
@@ -309,6 +338,12 @@ def run_ours(args):
                            "the X panels of each finished level copied to pinned host memory during the sweep)",
                "phases": phases}
 
+    # secondary: the opt-in step 2 emulated on the bf16 tensor cores, on its own
+    # handle, against this handle's FP64 X (not the headline: FP64 arithmetic is)
+    emul = None
+    if not args.fp64_emulation and not args.no_emulation:
+        emul = measure_emulation(args, prob, info, vals, h, stream, dev)
+
     value = whole_job_tflops(flops, world, ms)
     # roofline of the dominant kernel (step 2, X_{C,K} = -X_{C,C} Lhat): algorithmic
     # flops per launch over its event-timed average launch duration
@@ -334,6 +369,9 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": g1_alg_bytes / g1_launches,
                 "launches_per_step": g1_launches,
                 "whole_step_frac": value / world / FP64_PEAK_TFLOPS}
+    if args.fp64_emulation:
+        roofline = dict(emulated_step2_roofline(info["flops_gemm1"], kms[1] / args.steps),
+                        whole_step_fp64_equivalent_tflops=value / world)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, fl = oracle_sample_tflops()
@@ -343,7 +381,9 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None,
+                "dtype": "f64" if not args.fp64_emulation else "f64 (step 2: bf16 slice products, exact integer sums)",
+                "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": prob.n, "nnz_a_lower": info["nnz_a"],
                            "nnz_l": info["nnz_l"], "supernodes": info["nsn"], "levels": info["nlevels"],
                            "flops_per_step": flops, "schedule": "level (one grouped launch per kernel per level)",
@@ -353,12 +393,55 @@ def run_ours(args):
                                                   "step3_partials": kms[2] / args.steps,
                                                   "step3_finish": kms[3] / args.steps},
                            "l2": "no flush: the X panels (%.1f GB) exceed L2 (129 MB)" % (info["panel_entries"] * 8 / 1e9),
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "fp64_emulation": emul},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(sum(kl)), "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_emulation(args, prob, info, vals, h64, stream, dev):
+    """LEVEL selinv with opts.fp64_emulation = 1 on the same matrix: time,
+    kernel classes, max |X_em - X_fp64| / max |X_fp64| over every X panel
+    entry (h64 holds the FP64 selected inverse), and the step-2 class's bf16
+    tensor rate (28 slice products per multiply-add of X_{C,C} Lhat)."""
+    import torch
+    import paper_1404_0447_gb300 as P
+    he = P.SelInv(prob.n, prob.colptr, prob.rowind, max_sn_width=128, relax=P.RELAX_AMALG, fp64_emulation=1,
+                  **tuning(args))
+    with torch.cuda.stream(stream):
+        he.factor(vals, stream=stream)
+        for _ in range(max(1, args.warmup - 1)):
+            he.selinv(P.LEVEL, stream=stream)
+    he.sync_status(stream=stream)
+    torch.cuda.synchronize()
+    he.set_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        he.selinv(P.LEVEL, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    kms, kl = he.get_timing()
+    he.set_timing(False)
+    he.sync_status(stream=stream)
+    xe, x64 = he.panels(0, stream=stream)[0], h64.panels(0, stream=stream)[0]
+    torch.cuda.synchronize()
+    diff = float((torch.max(torch.abs(xe - x64)) / torch.max(torch.abs(x64))).item())
+    s2_ms = kms[1] / args.steps
+    out = {"ms_per_step": ms, "fp64_equivalent_tflops": info["flops_selinv"] / (ms * 1e-3) / 1e12,
+           "kernel_ms_per_step": {"normalise": kms[0] / args.steps, "step2_split_and_products": s2_ms,
+                                  "step3_partials": kms[2] / args.steps, "step3_finish_and_x_split": kms[3] / args.steps},
+           "max_rel_diff_vs_fp64_x": diff,
+           "step2_roofline": emulated_step2_roofline(info["flops_gemm1"], s2_ms),
+           "arithmetic": "step 2 on 7 x 8-bit bf16 slices of 2^-(e_p+e_q) X and of diag(2^e_C) Lhat, exact FP32 "
+                         "group sums over 32-row chunks, 64-bit integer accumulation; every other step FP64"}
+    del he
+    return out
 
 
 def _time(fn, steps, warmup, stream):
