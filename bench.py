@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--fp64-emulation", action="store_true",
                     help="headline on the opt-in path with step 2 emulated on the bf16 tensor cores "
                          "(opts.fp64_emulation = 1) instead of FP64 arithmetic")
+    ap.add_argument("--emulation-variant", type=int, default=1, choices=[1, 2],
+                    help="emulated step 2 on mma.sync (1) or tcgen05 (2)")
     ap.add_argument("--no-emulation", action="store_true",
                     help="skip the secondary measurement of the emulated step 2 (config.fp64_emulation)")
     return ap.parse_args()
@@ -228,7 +230,7 @@ def tuning(args):
     if args.min_slice_rows is not None:
         kw["min_slice_rows"] = args.min_slice_rows
     if args.fp64_emulation:
-        kw["fp64_emulation"] = 1
+        kw["fp64_emulation"] = args.emulation_variant
     return kw
 
 
@@ -409,8 +411,8 @@ def measure_emulation(args, prob, info, vals, h64, stream, dev):
     tensor rate (28 slice products per multiply-add of X_{C,C} Lhat)."""
     import torch
     import paper_1404_0447_gb300 as P
-    he = P.SelInv(prob.n, prob.colptr, prob.rowind, max_sn_width=128, relax=P.RELAX_AMALG, fp64_emulation=1,
-                  **tuning(args))
+    he = P.SelInv(prob.n, prob.colptr, prob.rowind, max_sn_width=128, relax=P.RELAX_AMALG,
+                  fp64_emulation=args.emulation_variant, **tuning(args))
     with torch.cuda.stream(stream):
         he.factor(vals, stream=stream)
         for _ in range(max(1, args.warmup - 1)):

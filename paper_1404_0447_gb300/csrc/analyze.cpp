@@ -171,7 +171,7 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
   if (wcap < 1 || wcap > kMaxWidth) return fail(h, PSELINV_ERR_ARG, "max_sn_width must be 0..128");
   if (o.unsym != 0 && o.unsym != 1) return fail(h, PSELINV_ERR_ARG, "unsym must be 0 or 1");
   if (o.unsym && o.dtype == PSELINV_C128) wcap = std::min(wcap, kMaxWidthLUComplex);
-  if (o.fp64_emulation != 0 && o.fp64_emulation != 1) return fail(h, PSELINV_ERR_ARG, "fp64_emulation must be 0 or 1");
+  if (o.fp64_emulation < 0 || o.fp64_emulation > 2) return fail(h, PSELINV_ERR_ARG, "fp64_emulation must be 0, 1 or 2");
   if (o.fp64_emulation && (o.dtype != PSELINV_F64 || o.unsym))
     return fail(h, PSELINV_ERR_ARG, "fp64_emulation is for real symmetric handles");
   if (o.relax != PSELINV_RELAX_NONE && o.relax != PSELINV_RELAX_AMALG)
@@ -477,13 +477,13 @@ int build_schedule(pselinv_handle* h) {
         const int bn = 8 << pick_variant(m.s, cplx, o.small_cutoff);
         const int bn2 = 8 << step2_variant(m.s, cplx, o);
         const int64_t mt = (m.r + kTileM - 1) / kTileM, nt = (m.s + bn - 1) / bn, st = (m.s + kTileM - 1) / kTileM;
-        const int64_t nt2 = (m.s + bn2 - 1) / bn2;
+        const int64_t nt2 = (m.s + bn2 - 1) / bn2, mt2 = (m.r + step2_rows(o) - 1) / step2_rows(o);
         m.ksplit = 1;
         m.kchunk = m.r;
         if (o.split_k_rows > 0 && m.r > o.split_k_rows) m.ksplit = slices(m.r, o.split_k_rows, &m.kchunk);
         m.nchunk = m.r > 0 ? slices(m.r, kChunkRows, &m.kchunk3) : 0;
         if (m.r == 0) m.kchunk3 = kChunkRows;
-        t2 += mt * nt2 * m.ksplit;
+        t2 += mt2 * nt2 * m.ksplit;
         t3 += (int64_t)m.nchunk * st * nt;
       }
       if (o.split_k_rows > 0 && t2 > 0 && t2 < target) {
@@ -554,7 +554,7 @@ int build_schedule(pselinv_handle* h) {
   auto step2_tiles = [&](int32_t k, int bn, std::vector<Task>& out) {  // step 2: + k-parts
     const SnMeta& m = h->meta[k];
     for (int32_t c = 0; c < m.ksplit; ++c)
-      for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
+      for (int32_t m0 = 0; m0 < m.r; m0 += step2_rows(o))
         for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, c});
   };
   auto step3_tiles = [&](int32_t k, int bn, std::vector<Task>& out) {

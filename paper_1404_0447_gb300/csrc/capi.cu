@@ -385,7 +385,7 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
         cudaError_t x = emul ? psi::launch_em_split_lhat(ka, em, sns, nsn_step, maxr, st) : cudaSuccess;
         for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
           x = emul ? psi::launch_em_gemm1(v, ka, em, tasks_at(h, h->off_gemm1, r1[v].begin), r1[v].end - r1[v].begin,
-                                          st)
+                                          st, h->opts.fp64_emulation == 2)
                    : psi::launch_tiles(Kern::Gemm1, v, ka, tasks_at(h, h->off_gemm1, r1[v].begin),
                                        r1[v].end - r1[v].begin, st);
         if (split && x == cudaSuccess) x = psi::launch_per_sn(Kern::Gemm1Reduce, ka, sns, nsn_step, st);

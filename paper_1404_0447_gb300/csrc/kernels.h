@@ -115,9 +115,11 @@ cudaError_t launch_em_split_lhat(const KArgs& a, const EmArgs& e, const int32_t*
                                  cudaStream_t st);
 // Dynamic shared-memory limits of the step-2 kernels (called by setup_kernels).
 cudaError_t setup_em_kernels();
-// Step-2 tiles (the Gemm1 task list of tile variant var, 0 or 1) on the slices.
+// Step-2 tiles (the Gemm1 task list of tile variant var) on the slices: tc =
+// false: 64 x 8 / 64 x 16 tiles on mma.sync (var 0, 1); tc = true: 128 x 16
+// tiles on tcgen05 (var 1).
 cudaError_t launch_em_gemm1(int var, const KArgs& a, const EmArgs& e, const Task* tasks, int64_t n,
-                            cudaStream_t st);
+                            cudaStream_t st, bool tc);
 
 // ---- persistent per-level schedule (persistent.cu) ----
 struct PArgs {

@@ -1,6 +1,7 @@
 """GPU parity of step 2 with its FP64 arithmetic emulated on the bf16 tensor
-cores (opts.fp64_emulation = 1: scaled X and Lhat cut into 8-bit slices,
-exact integer accumulation of the slice products) against the oracle,
+cores (opts.fp64_emulation = 1 on mma.sync, 2 on tcgen05: scaled X and Lhat
+cut into 8-bit slices, exact integer accumulation of the slice products)
+against the oracle,
 through the C ABI: SPD grids and graph Laplacians over the tile widths,
 k-slices and ragged tails, the PLAIN / LEVEL / GRAPH schedules, batches,
 and the report of an X that is not positive definite.  Tolerance 1e-10 of
@@ -52,6 +53,10 @@ def run(P, p, wmax=128, relax=1, modes=(1,), emulate=1, **opts):
     return h, outs
 
 
+VARIANTS = [pytest.param(1, id="mma_sync"), pytest.param(2, id="tcgen05")]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("case,wmax,relax,opts", [
     ("grid2d_31", 128, 0, {}),
     ("grid3d_12", 16, 1, {}),
@@ -60,7 +65,7 @@ def run(P, p, wmax=128, relax=1, modes=(1,), emulate=1, **opts):
     ("grid3d_20", 128, 1, {"split_k_rows": 48}),      # k-slices of C with ordered reductions
     ("graphlap_10", 128, 1, {}),                      # random weights, uneven degrees
 ])
-def test_emulated_step2_against_oracle_and_fp64_path(P, case, wmax, relax, opts):
+def test_emulated_step2_against_oracle_and_fp64_path(P, case, wmax, relax, opts, variant):
     if case == "grid2d_31":
         p = synth.grid2d_31()
     elif case.startswith("grid3d"):
@@ -68,7 +73,7 @@ def test_emulated_step2_against_oracle_and_fp64_path(P, case, wmax, relax, opts)
     else:
         p = synth.graph_laplacian3d(int(case.split("_")[1]))
     off, Xo = oracle_x(p, wmax, relax)
-    h, outs = run(P, p, wmax, relax, modes=(0, 1, 2), **opts)
+    h, outs = run(P, p, wmax, relax, modes=(0, 1, 2), emulate=variant, **opts)
     assert np.array_equal(h.symbolic()["panel_off"], off)
     for m, x in outs.items():
         assert rel(x, Xo) <= TOL, (m, rel(x, Xo))
@@ -81,7 +86,8 @@ def test_emulated_step2_against_oracle_and_fp64_path(P, case, wmax, relax, opts)
     assert d <= 1e-12
 
 
-def test_emulated_batch_members(P):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_emulated_batch_members(P, variant):
     gl = synth.GraphLaplacian((9, 8, 7))
     base = gl.assemble()
     diag = np.asarray(gl.colptr[:-1])
@@ -92,7 +98,7 @@ def test_emulated_batch_members(P):
         v[diag] += sh
         probs.append(synth.Problem("gl", gl.n, gl.colptr, gl.rowind, v, perm))
     p0 = probs[0]
-    h = P.SelInv(p0.n, p0.colptr, p0.rowind, batch=3, fp64_emulation=1)
+    h = P.SelInv(p0.n, p0.colptr, p0.rowind, batch=3, fp64_emulation=variant)
     h.factor(dev(np.concatenate([q.values for q in probs])))
     h.selinv(P.LEVEL)
     h.sync_status()
@@ -102,12 +108,13 @@ def test_emulated_batch_members(P):
         assert rel(X[b], Xo) <= TOL
 
 
-def test_not_positive_definite_is_reported_and_the_handle_recovers(P):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_not_positive_definite_is_reported_and_the_handle_recovers(P, variant):
     """A = -(SPD): every X_pp < 0, so the scaling has no exponent; the
     selinv is reported as ERR_RANGE and its X is not offered.  The same
     handle then inverts an SPD matrix correctly."""
     p = synth.grid3d(10)
-    h = P.SelInv(p.n, p.colptr, p.rowind, fp64_emulation=1)
+    h = P.SelInv(p.n, p.colptr, p.rowind, fp64_emulation=variant)
     h.factor(dev(-p.values))
     h.selinv(P.LEVEL)
     with pytest.raises(P.PselinvError, match="ERR_RANGE"):
@@ -130,13 +137,14 @@ def test_persistent_schedule_is_refused(P):
 
 
 @pytest.mark.slow
-def test_full_size_80cubed_emulated_against_closed_form_and_fp64(P):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_full_size_80cubed_emulated_against_closed_form_and_fp64(P, variant):
     """The benchmark workload at full size (n = 512,000) with the emulated
     step 2: sampled entries against the separable closed form, and every X
     panel entry against the FP64 path."""
     import torch
     p = synth.grid3d(80, shift_const=0.055)
-    h = P.SelInv(p.n, p.colptr, p.rowind, fp64_emulation=1)
+    h = P.SelInv(p.n, p.colptr, p.rowind, fp64_emulation=variant)
     s = h.symbolic()
     h.factor(dev(p.values))
     h.selinv(P.LEVEL)
@@ -162,5 +170,5 @@ def test_full_size_80cubed_emulated_against_closed_form_and_fp64(P):
     h64.selinv(P.LEVEL)
     X64 = h64.panels(0)[0]
     d = float(torch.max(torch.abs(X - X64)).item()) / scale
-    print("full-size emulated: closed-form error", err, "max |X_em - X_fp64| / max|X|", d)
+    print("full-size emulated", variant, ": closed-form error", err, "max |X_em - X_fp64| / max|X|", d)
     assert err <= TOL and d <= 1e-12
