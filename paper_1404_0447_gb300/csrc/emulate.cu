@@ -72,6 +72,23 @@ __device__ __forceinline__ uint4 split7(double v, int E, int& bad) {
   return o;
 }
 
+// acc += x * scale (32 x 32 -> 64-bit signed multiply-add, one instruction)
+__device__ __forceinline__ void madw(long long& acc, int x, int scale) {
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(x), "r"(scale));
+}
+// Fold the seven exact FP32 group sums of one entry into hi (groups 0-2) and
+// lo (groups 3-6): hi += S0 2^16 + S1 2^8 + S2, lo += S3 2^24 + S4 2^16 + S5 2^8 + S6.
+__device__ __forceinline__ void fold7(long long& hi, long long& lo, float s0, float s1, float s2, float s3,
+                                      float s4, float s5, float s6) {
+  madw(hi, __float2int_rn(s0), 65536);
+  madw(hi, __float2int_rn(s1), 256);
+  madw(hi, __float2int_rn(s2), 1);
+  madw(lo, __float2int_rn(s3), 16777216);
+  madw(lo, __float2int_rn(s4), 65536);
+  madw(lo, __float2int_rn(s5), 256);
+  madw(lo, __float2int_rn(s6), 1);
+}
+
 // Column groups of the split kernels: CTA z of a supernode handles its
 // columns z, z + kSplitGroups, ... (the top levels hold few, tall supernodes).
 constexpr int kSplitGroups = 32;
@@ -380,12 +397,8 @@ __global__ void __launch_bounds__(kEmThreads, 3) k_em_gemm1(KArgs a, EmArgs e, c
     for (int j = 0; j < NF; ++j)
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
-        const long long s0 = __float2int_rn(S[0][j][x]), s1 = __float2int_rn(S[1][j][x]),
-                        s2 = __float2int_rn(S[2][j][x]), s3 = __float2int_rn(S[3][j][x]),
-                        s4 = __float2int_rn(S[4][j][x]), s5 = __float2int_rn(S[5][j][x]),
-                        s6 = __float2int_rn(S[6][j][x]);
-        hi[j][x] += s0 * 65536 + s1 * 256 + s2;
-        lo[j][x] += s3 * 16777216 + s4 * 65536 + s5 * 256 + s6;
+        fold7(hi[j][x], lo[j][x], S[0][j][x], S[1][j][x], S[2][j][x], S[3][j][x], S[4][j][x], S[5][j][x],
+              S[6][j][x]);
       }
     __syncthreads();
   }
@@ -649,15 +662,9 @@ __global__ void __launch_bounds__(kEmThreads, 2) k_em_gemm1_tc(KArgs a, EmArgs e
       for (int gi = 0; gi < kSl; ++gi) {
         uint32_t rg[16];
         tc_ld16(taddr + (uint32_t)(kTcCols * gi), rg);
-        const int sh = gi < 3 ? 8 * (2 - gi) : 8 * (6 - gi);
+        const int scale = 1 << (gi < 3 ? 8 * (2 - gi) : 8 * (6 - gi));
 #pragma unroll
-        for (int j = 0; j < kTcCols; ++j) {
-          const long long sv = (long long)__float2int_rn(__uint_as_float(rg[j])) * (1LL << sh);
-          if (gi < 3)
-            hi[j] += sv;
-          else
-            lo[j] += sv;
-        }
+        for (int j = 0; j < kTcCols; ++j) madw(gi < 3 ? hi[j] : lo[j], __float2int_rn(__uint_as_float(rg[j])), scale);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
