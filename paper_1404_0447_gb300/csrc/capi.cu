@@ -70,7 +70,7 @@ void free_device(pselinv_handle* h) {
                    &h->d_status, &h->d_flipmap, &h->d_U, &h->d_XU, &h->d_uhat, &h->d_uinv,
                    &h->d_piv, &h->d_ptype, &h->d_E, &h->d_snlevel, &h->d_yring, &h->d_pring,
                    &h->d_xb,   &h->d_lb,   &h->d_db,     &h->d_zb,     &h->d_w1,    &h->d_yb,   &h->d_hb,
-                   &h->d_plist, &h->d_pn,  &h->d_pctr, &h->d_xs, &h->d_ls, &h->d_sig, &h->d_lexp, &h->d_crow};
+                   &h->d_plist, &h->d_pn,  &h->d_pctr, &h->d_xs, &h->d_ls, &h->d_sig, &h->d_lexp, &h->d_gexp, &h->d_crow};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -143,6 +143,7 @@ int ensure_device(pselinv_handle* h) {
     if ((rc = alloc(h, &h->d_ls, B * h->lhat_total * 16))) return rc;
     if ((rc = alloc(h, &h->d_sig, B * h->n * (int64_t)sizeof(int32_t)))) return rc;
     if ((rc = alloc(h, &h->d_lexp, B * h->n * (int64_t)sizeof(int32_t)))) return rc;
+    if ((rc = alloc(h, &h->d_gexp, B * h->n * (int64_t)sizeof(int32_t)))) return rc;
   }
   PSI_CUDA(h, cudaMemset(h->d_status, 0, sizeof(int) * kStatusWords));
   h->dev_sym = true;
@@ -369,7 +370,8 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
   if (rc) return rc;
   // FP64 emulation of step 2: B' slices before it, X slices after the level
   const bool emul = h->opts.fp64_emulation != 0;
-  const psi::EmArgs em{h->d_xs, h->d_ls, (int32_t*)h->d_sig, (int32_t*)h->d_lexp, (const int32_t*)h->d_crow, h->n};
+  const psi::EmArgs em{h->d_xs,         h->d_ls, (int32_t*)h->d_sig, (int32_t*)h->d_lexp, (int32_t*)h->d_gexp,
+                       (const int32_t*)h->d_crow, h->n};
   // one step: the given supernodes, with per-variant task ranges of steps 2 and 3
   // maxr: the largest |C| among the step's supernodes
   auto step = [&](const int32_t* sns, int nsn_step, const psi::Range* r1, const psi::Range* r2, bool split,
@@ -393,11 +395,14 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
       });
     };
     if ((e = gemm1(a))) return e;
-    if ((e = tm.run(2, n2, [&] {
-           cudaError_t x = cudaSuccess;
+    // step 3 partial products; emulated: slices of diag(2^-e_C) X_{C,K} first
+    if ((e = tm.run(2, n2 + (emul && n2 > 0 ? 1 : 0), [&] {
+           cudaError_t x = emul ? psi::launch_em_split_xck(a, em, sns, nsn_step, maxr, st) : cudaSuccess;
            for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
-             x = psi::launch_tiles(Kern::Gemm2, v, a3, tasks_at(h, h->off_gemm2, r2[v].begin),
-                                   r2[v].end - r2[v].begin, st);
+             x = emul ? psi::launch_em_gemm2(v, a, em, tasks_at(h, h->off_gemm2, r2[v].begin),
+                                             r2[v].end - r2[v].begin, st)
+                      : psi::launch_tiles(Kern::Gemm2, v, a3, tasks_at(h, h->off_gemm2, r2[v].begin),
+                                          r2[v].end - r2[v].begin, st);
            return x;
          })))
       return e;

@@ -142,31 +142,23 @@ __global__ void __launch_bounds__(256) k_em_split_x(KArgs a, EmArgs e, const int
 // |C| reads them from global memory).
 constexpr int kEcRows = 40960;
 
-// Before step 2 of supernode K: F_j and the slices of B' = diag(2^e_C) Lhat.
-// Grid (supernodes, batch, column groups); a CTA takes the exponents e of
-// the rows of C once, then its columns one at a time with all threads
-// (block-wide maximum for F_j, then the slices).
-__global__ void __launch_bounds__(256) k_em_split_lhat(KArgs a, EmArgs e, const int32_t* __restrict__ sns,
-                                                       int ec_cap) {
-  extern __shared__ int ec_smem[];
-  __shared__ int red[8];
-  const int k = sns[blockIdx.x], b = blockIdx.y;
-  const SnMeta m = a.meta[k];
-  const int s = m.s, r = m.r;
-  if ((int)blockIdx.z >= s) return;
-  const double* Lh = (const double*)a.Lhat + b * a.sz.lhat + m.lhat;
-  uint4* ls = (uint4*)e.ls + b * a.sz.lhat + m.lhat;
-  const int32_t* sig = e.sig + b * e.n;
-  const int32_t* crow = e.crow + m.desc;
+// The columns of an r x s block scaled by rows, V = diag(2^(esign e_C)) W,
+// cut into slices column by column: exponent E_j with |V_{:,j}| < 2^E_j to
+// exps[j], the slices of V_{:,j} 2^-E_j to dst.  Grid (supernodes, batch,
+// column groups); a CTA takes the exponents e of the rows of C once, then its
+// columns one at a time with all threads (block-wide maximum, then slices).
+__device__ __forceinline__ void split_columns(const double* W, int64_t wld, uint4* dst, int64_t dld, int r, int s,
+                                              int esign, int32_t* exps, const int32_t* sig, const int32_t* crow,
+                                              int ec_cap, int* ec_smem, int* red, int* status) {
   const bool cached = r <= ec_cap;
   if (cached)
-    for (int i = threadIdx.x; i < r; i += blockDim.x) ec_smem[i] = sig[crow[i]];
+    for (int i = threadIdx.x; i < r; i += blockDim.x) ec_smem[i] = esign * sig[crow[i]];
   __syncthreads();
-  auto ec = [&](int i) { return cached ? ec_smem[i] : sig[crow[i]]; };
+  auto ec = [&](int i) { return cached ? ec_smem[i] : esign * sig[crow[i]]; };
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int bad = 0;
   for (int j = blockIdx.z; j < s; j += gridDim.z) {
-    const double* col = Lh + (int64_t)j * r;
+    const double* col = W + (int64_t)j * wld;
     int mx = INT_MIN;
     for (int i = threadIdx.x; i < r; i += blockDim.x) {
       const unsigned long long bits = (unsigned long long)__double_as_longlong(col[i]);
@@ -174,7 +166,7 @@ __global__ void __launch_bounds__(256) k_em_split_lhat(KArgs a, EmArgs e, const 
       if (ex == 0x7FF)
         bad = 1;
       else if (ex != 0)
-        mx = max(mx, ex - 1023 + ec(i));  // floor(log2 |B'_ij|)
+        mx = max(mx, ex - 1023 + ec(i));  // floor(log2 |V_ij|)
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -182,12 +174,41 @@ __global__ void __launch_bounds__(256) k_em_split_lhat(KArgs a, EmArgs e, const 
     __syncthreads();
     mx = red[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, red[w]);
-    const int F = mx == INT_MIN ? 0 : mx + 1;
-    if (threadIdx.x == 0) e.lexp[b * e.n + m.f + j] = F;
-    for (int i = threadIdx.x; i < r; i += blockDim.x) ls[i + (int64_t)j * r] = split7(col[i], F - ec(i), bad);
+    const int E = mx == INT_MIN ? 0 : mx + 1;
+    if (threadIdx.x == 0) exps[j] = E;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) dst[i + (int64_t)j * dld] = split7(col[i], E - ec(i), bad);
     __syncthreads();  // red[] is rewritten by the next column
   }
-  if (bad) atomicOr(a.status + kEmStatusWord, 1);
+  if (bad) atomicOr(status + kEmStatusWord, 1);
+}
+
+// Before step 2 of supernode K: F_j and the slices of B' = diag(2^e_C) Lhat.
+__global__ void __launch_bounds__(256) k_em_split_lhat(KArgs a, EmArgs e, const int32_t* __restrict__ sns,
+                                                       int ec_cap) {
+  extern __shared__ int ec_smem[];
+  __shared__ int red[8];
+  const int k = sns[blockIdx.x], b = blockIdx.y;
+  const SnMeta m = a.meta[k];
+  if ((int)blockIdx.z >= m.s) return;
+  split_columns((const double*)a.Lhat + b * a.sz.lhat + m.lhat, m.r, (uint4*)e.ls + b * a.sz.lhat + m.lhat, m.r,
+                m.r, m.s, 1, e.lexp + b * e.n + m.f, e.sig + b * e.n, e.crow + m.desc, ec_cap, ec_smem, red,
+                a.status);
+}
+
+// After step 2 of supernode K (before step 3): G_j and the slices of
+// X'' = diag(2^-e_C) X_{C,K}, kept in the slice array at the rows of C of
+// K's panel until the level's own slices replace them.
+__global__ void __launch_bounds__(256) k_em_split_xck(KArgs a, EmArgs e, const int32_t* __restrict__ sns,
+                                                      int ec_cap) {
+  extern __shared__ int ec_smem[];
+  __shared__ int red[8];
+  const int k = sns[blockIdx.x], b = blockIdx.y;
+  const SnMeta m = a.meta[k];
+  if ((int)blockIdx.z >= m.s) return;
+  const int64_t ld = m.s + m.r;
+  split_columns((const double*)a.X + b * a.sz.panel + m.panel + m.s, ld,
+                (uint4*)e.xs + b * a.sz.panel + m.panel + m.s, ld, m.r, m.s, -1, e.gexp + b * e.n + m.f,
+                e.sig + b * e.n, e.crow + m.desc, ec_cap, ec_smem, red, a.status);
 }
 
 constexpr int kKP = kKC + 8;  // shared row stride of a slice plane in bf16 (80 bytes: ldmatrix rows conflict-free)
@@ -235,6 +256,56 @@ __device__ __forceinline__ void stash_pair(uint16_t (&dst)[kSl][R][kKP], int row
                                            const uint4& v1) {
 #pragma unroll
   for (int t = 0; t < kSl; ++t) *reinterpret_cast<uint32_t*>(&dst[t][row][k]) = pair_slice(v0, v1, t);
+}
+
+// The 28 slice products of the chunk in the planes (7 group sums per
+// fragment entry, exact in FP32), folded into hi / lo.  Warp w takes rows
+// 16w..16w+15 of the 64-row tile and all NB columns; accumulator x of
+// fragment j is row g + 8 (x >> 1), column 8 j + 2 q + (x & 1).
+template <int NB>
+__device__ __forceinline__ void em_products(EmSmem<NB>& sm, long long (&hi)[NB / 8][4],
+                                            long long (&lo)[NB / 8][4]) {
+  constexpr int NF = NB / 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float S[kSl][NF][4];
+#pragma unroll
+  for (int gi = 0; gi < kSl; ++gi)
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+#pragma unroll
+      for (int x = 0; x < 4; ++x) S[gi][j][x] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < kKC; ks += 16) {
+    uint32_t B[kSl][NF][2];
+#pragma unroll
+    for (int u = 0; u < kSl; ++u) {
+      if constexpr (NF == 2) {
+        uint32_t d[4];
+        ldsm_x4(d, &sm.b[u][(lane & 7) + ((lane >> 4) << 3)][ks + (((lane >> 3) & 1) << 3)]);
+        B[u][0][0] = d[0];
+        B[u][0][1] = d[1];
+        B[u][1][0] = d[2];
+        B[u][1][1] = d[3];
+      } else {
+        ldsm_x2(B[u][0][0], B[u][0][1], &sm.b[u][lane & 7][ks + (((lane >> 3) & 1) << 3)]);
+      }
+    }
+#pragma unroll
+    for (int ta = 0; ta < kSl; ++ta) {
+      uint32_t A[4];
+      ldsm_x4(A, &sm.a[ta][warp * 16 + (lane & 15)][ks + ((lane >> 4) << 3)]);
+#pragma unroll
+      for (int u = 0; u + ta < kSl; ++u)
+#pragma unroll
+        for (int j = 0; j < NF; ++j) mma_bf16(S[ta + u][j], A, B[u][j][0], B[u][j][1]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NF; ++j)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+      fold7(hi[j][x], lo[j][x], S[0][j][x], S[1][j][x], S[2][j][x], S[3][j][x], S[4][j][x], S[5][j][x],
+            S[6][j][x]);
 }
 
 // One step-2 task (tile origin m0, n0, width NB in {8, 16}, k-slice c) on
@@ -360,46 +431,7 @@ __global__ void __launch_bounds__(kEmThreads, 3) k_em_gemm1(KArgs a, EmArgs e, c
     __syncthreads();
     // relative indices of the next chunk, in flight during the products
     if (c + 1 < nck) load_ri(c + 1, ri);
-    float S[kSl][NF][4];
-#pragma unroll
-    for (int gi = 0; gi < kSl; ++gi)
-#pragma unroll
-      for (int j = 0; j < NF; ++j)
-#pragma unroll
-        for (int x = 0; x < 4; ++x) S[gi][j][x] = 0.f;
-#pragma unroll
-    for (int ks = 0; ks < kKC; ks += 16) {
-      uint32_t B[kSl][NF][2];
-#pragma unroll
-      for (int u = 0; u < kSl; ++u) {
-        if constexpr (NF == 2) {
-          uint32_t d[4];
-          ldsm_x4(d, &sm.b[u][(lane & 7) + ((lane >> 4) << 3)][ks + (((lane >> 3) & 1) << 3)]);
-          B[u][0][0] = d[0];
-          B[u][0][1] = d[1];
-          B[u][1][0] = d[2];
-          B[u][1][1] = d[3];
-        } else {
-          ldsm_x2(B[u][0][0], B[u][0][1], &sm.b[u][lane & 7][ks + (((lane >> 3) & 1) << 3)]);
-        }
-      }
-#pragma unroll
-      for (int ta = 0; ta < kSl; ++ta) {
-        uint32_t A[4];
-        ldsm_x4(A, &sm.a[ta][warp * 16 + (lane & 15)][ks + ((lane >> 4) << 3)]);
-#pragma unroll
-        for (int u = 0; u + ta < kSl; ++u)
-#pragma unroll
-          for (int j = 0; j < NF; ++j) mma_bf16(S[ta + u][j], A, B[u][j][0], B[u][j][1]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < NF; ++j)
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        fold7(hi[j][x], lo[j][x], S[0][j][x], S[1][j][x], S[2][j][x], S[3][j][x], S[4][j][x], S[5][j][x],
-              S[6][j][x]);
-      }
+    em_products<NB>(sm, hi, lo);
     __syncthreads();
   }
   // accumulator x of fragment j: row g + 8 (x >> 1), column 8 j + 2 q + (x & 1)
@@ -418,6 +450,91 @@ __global__ void __launch_bounds__(kEmThreads, 3) k_em_gemm1(KArgs a, EmArgs e, c
           ((double*)a.ypart + b * a.sz.ypart + m.ypart + (int64_t)tk.c * r * s)[i + (int64_t)col * r] = v;
       }
     }
+}
+
+// Step 3 partial product on the slices: P_c = Lhat_{rows c, K}^T X_{rows c, K}
+// for one task of the step-3 list (tile origin m0, n0 of width BN over the
+// s x s output, row chunk c of C), P_mn = 2^(F_m + G_n - 32) (hi + lo 2^-32)
+// from the slices of B' (exponents F) and of X'' (exponents G).  Both
+// operands are read along the rows of C (contiguous); columns in blocks of 16.
+template <int BN>
+__global__ void __launch_bounds__(kEmThreads, 3) k_em_gemm2(KArgs a, EmArgs e, const Task* __restrict__ tasks) {
+  constexpr int NB = BN < 16 ? BN : 16;
+  constexpr int NF = NB / 8;
+  __shared__ __align__(16) EmSmem<NB> sm;
+  const Task tk = tasks[blockIdx.x];
+  const int b = blockIdx.y;
+  const SnMeta m = a.meta[tk.sn];
+  const int s = m.s, r = m.r, ld = s + r;
+  const uint4* xk = (const uint4*)e.xs + b * a.sz.panel + m.panel + s;  // X'' slices, column stride ld
+  const uint4* ls = (const uint4*)e.ls + b * a.sz.lhat + m.lhat;          // B' slices, column stride r
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, q = lane & 3;
+  const int m0 = tk.m0;
+  const int kb = tk.c * m.kchunk3, ke = min(r, kb + m.kchunk3);
+  if (t < kTileM) {
+    sm.erow[t] = m0 + t < s ? e.lexp[b * e.n + m.f + m0 + t] : 0;
+  } else {
+    const int c = tk.n0 + (t - kTileM);
+    sm.fcol[t - kTileM] = c < s ? e.gexp[b * e.n + m.f + c] : 0;
+  }
+  __syncthreads();
+  double* out = (double*)a.part + b * a.sz.part + m.part + (int64_t)tk.c * s * s;
+  for (int nb = tk.n0; nb < tk.n0 + BN && nb < s; nb += NB) {
+    long long hi[NF][4], lo[NF][4];
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+#pragma unroll
+      for (int x = 0; x < 4; ++x) hi[j][x] = lo[j][x] = 0;
+    for (int kt = kb; kt < ke; kt += kKC) {
+      // A = B'^T: row mm of the tile is column m0 + mm of B', read along k (2 rows x 32 k per warp)
+      uint4 v[16];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const int bi = warp * 8 + p;
+        const int row = (bi & 3) + 8 * (bi >> 2) + 4 * (lane >> 4), kk = 2 * (lane & 15);
+        const int i = m0 + row;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          v[2 * p + h] = make_uint4(0u, 0u, 0u, 0u);
+          if (i < s && kt + kk + h < ke) v[2 * p + h] = __ldg(ls + kt + kk + h + (int64_t)i * r);
+        }
+      }
+      uint4 w[NB / 4];
+#pragma unroll
+      for (int j = 0; j < NB / 8; ++j) {
+        const int pi = j * kEmThreads + t, nn = pi >> 4, kk = 2 * (pi & 15), col = nb + nn;
+        w[2 * j] = w[2 * j + 1] = make_uint4(0u, 0u, 0u, 0u);
+        if (col < s) {
+          if (kt + kk < ke) w[2 * j] = __ldg(xk + kt + kk + (int64_t)col * ld);
+          if (kt + kk + 1 < ke) w[2 * j + 1] = __ldg(xk + kt + kk + 1 + (int64_t)col * ld);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const int bi = warp * 8 + p;
+        stash_pair<kTileM>(sm.a, (bi & 3) + 8 * (bi >> 2) + 4 * (lane >> 4), 2 * (lane & 15), v[2 * p],
+                           v[2 * p + 1]);
+      }
+#pragma unroll
+      for (int j = 0; j < NB / 8; ++j) {
+        const int pi = j * kEmThreads + t;
+        stash_pair<NB>(sm.b, pi >> 4, 2 * (pi & 15), w[2 * j], w[2 * j + 1]);
+      }
+      __syncthreads();
+      em_products<NB>(sm, hi, lo);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int row = warp * 16 + g + 8 * (x >> 1), col = nb + 8 * j + 2 * q + (x & 1);
+        const int i = m0 + row;
+        if (i < s && col < s)
+          out[i + (int64_t)col * s] = ldexp((double)hi[j][x] + (double)lo[j][x] * 0x1p-32,
+                                            sm.erow[row] + sm.fcol[col - tk.n0] - 32);
+      }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -711,9 +828,31 @@ cudaError_t launch_em_split_lhat(const KArgs& a, const EmArgs& e, const int32_t*
   return cudaGetLastError();
 }
 
+cudaError_t launch_em_split_xck(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, int max_r,
+                                cudaStream_t st) {
+  if (nsn <= 0) return cudaSuccess;
+  const int cap = max_r < kEcRows ? max_r : kEcRows;
+  k_em_split_xck<<<dim3(nsn, a.sz.batch, kSplitGroups), 256, sizeof(int) * cap, st>>>(a, e, sns, cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_em_gemm2(int var, const KArgs& a, const EmArgs& e, const Task* t, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)n, a.sz.batch);
+  switch (var) {
+    case 0: k_em_gemm2<8><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
+    case 1: k_em_gemm2<16><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
+    case 2: k_em_gemm2<32><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
+    default: k_em_gemm2<64><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t setup_em_kernels() {
   cudaError_t err = cudaFuncSetAttribute(k_em_split_lhat, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(int) * kEcRows);
+  if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(k_em_split_xck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(int) * kEcRows);
   if (err != cudaSuccess) return err;
   err = cudaFuncSetAttribute(k_em_gemm1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
   if (err != cudaSuccess) return err;

@@ -190,6 +190,7 @@ struct pselinv_handle {
   void* d_ls = nullptr;     // slices of the scaled Lhat (16 bytes per entry)
   void* d_sig = nullptr;    // int32 column exponents e_p, batch x n
   void* d_lexp = nullptr;   // int32 column exponents F of B', batch x n
+  void* d_gexp = nullptr;   // int32 column exponents G of the scaled X_{C,K} (step 3), batch x n
   void* d_crow = nullptr;   // int32 global rows of every C (rows, at rowptr)
   // adjoint work buffers (allocated on first pselinv_selinv_adjoint)
   void* d_xb = nullptr;     // X-bar, then F-bar (panel layout)

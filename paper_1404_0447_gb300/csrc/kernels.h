@@ -101,6 +101,7 @@ struct EmArgs {
   void* ls;              // [batch][lhat_total] uint4: 7 bf16 slices of B' per Lhat entry
   int32_t* sig;          // [batch][n] e_p of every column (written when its level finishes)
   int32_t* lexp;         // [batch][n] column exponent F of B' (|B'_{:,j}| < 2^F), per global column
+  int32_t* gexp;         // [batch][n] column exponent G of X'' = diag(2^-e_C) X_{C,K} (step 3)
   const int32_t* crow;   // [sum r] global row of C[i] of supernode K at desc offset of K
   int64_t n;
 };
@@ -113,6 +114,12 @@ cudaError_t launch_em_split_x(const KArgs& a, const EmArgs& e, const int32_t* sn
 // max_r: the largest |C| among the supernodes (sizes the shared memory).
 cudaError_t launch_em_split_lhat(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, int max_r,
                                  cudaStream_t st);
+// After step 2 of a level (step 3 emulated): G and the slices of X'' for its
+// supernodes, written over the slice array at the rows of C of their panels.
+cudaError_t launch_em_split_xck(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, int max_r,
+                                cudaStream_t st);
+// Step-3 partial products (the Gemm2 task list of tile variant var) on the slices.
+cudaError_t launch_em_gemm2(int var, const KArgs& a, const EmArgs& e, const Task* tasks, int64_t n, cudaStream_t st);
 // Dynamic shared-memory limits of the step-2 kernels (called by setup_kernels).
 cudaError_t setup_em_kernels();
 // Step-2 tiles (the Gemm1 task list of tile variant var) on the slices: tc =
