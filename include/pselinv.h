@@ -106,9 +106,10 @@ typedef struct {
   int32_t level_tiles;    /* a level whose step-2 (step-3) tiles number fewer than this gets its slices
                              (row chunks) of C shrunk until it has about this many; 0 = 16 per SM (2432) */
   int32_t min_slice_rows; /* smallest step-2 slice that shrinking makes; 0 = 128 (step-3 chunks: a quarter) */
-  int32_t fp64_emulation; /* 0: step 2 in FP64 (mma.sync f64).  1 (mma.sync bf16) or 2 (tcgen05, 128-row
-                             tiles): step 2, X_{C,K} = -X_{C,C} Lhat_{C,K}
-                             (Algorithm 1), in FP64 accuracy on the bf16 tensor cores, for real symmetric
+  int32_t fp64_emulation; /* 0: steps 2 and 3 in FP64 (mma.sync f64).  1 (mma.sync bf16) or 2 (step 2 on
+                             tcgen05, 128-row tiles): step 2, X_{C,K} = -X_{C,C} Lhat_{C,K}, and step 3's
+                             Lhat_{C,K}^T X_{C,K} (Algorithm 1),
+                             in FP64 accuracy on the bf16 tensor cores, for real symmetric
                              positive definite A (dtype F64, unsym 0, pivot-free factor; PLAIN, LEVEL and
                              GRAPH schedules).  With e_p = ceil(log2 sqrt(X_pp)), every entry of
                              2^-(e_p+e_q) X has modulus < 1 (Cauchy-Schwarz for SPD X); the scaled X and
