@@ -384,7 +384,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
-                "dtype": "f64" if not args.fp64_emulation else "f64 (step 2: bf16 slice products, exact integer sums)",
+                "dtype": "f64" if not args.fp64_emulation else "f64 (steps 2, 3: bf16 slice products, exact integer sums)",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": prob.n, "nnz_a_lower": info["nnz_a"],
                            "nnz_l": info["nnz_l"], "supernodes": info["nsn"], "levels": info["nlevels"],
@@ -456,11 +456,13 @@ def measure_emulation(args, prob, info, vals, h64, stream, dev):
     out = {"ms_per_step": ms, "fp64_equivalent_tflops": info["flops_selinv"] / (ms * 1e-3) / 1e12,
            "e2e_ms_per_step": e2e_ms,
            "kernel_ms_per_step": {"normalise": kms[0] / args.steps, "step2_split_and_products": s2_ms,
-                                  "step3_partials": kms[2] / args.steps, "step3_finish_and_x_split": kms[3] / args.steps},
+                                  "step3_split_and_partials": kms[2] / args.steps,
+                                  "step3_finish_and_x_split": kms[3] / args.steps},
            "max_rel_diff_vs_fp64_x": diff,
            "step2_roofline": emulated_step2_roofline(info["flops_gemm1"], s2_ms),
-           "arithmetic": "step 2 on 7 x 8-bit bf16 slices of 2^-(e_p+e_q) X and of diag(2^e_C) Lhat, exact FP32 "
-                         "group sums over 32-row chunks, 64-bit integer accumulation; every other step FP64"}
+           "arithmetic": "steps 2 and 3 on 7 x 8-bit bf16 slices of 2^-(e_p+e_q) X, of diag(2^e_C) Lhat and of "
+                         "diag(2^-e_C) X_CK, exact FP32 group sums over 32-row chunks, 64-bit integer "
+                         "accumulation; every other step FP64"}
     del he
     return out
 
