@@ -1,6 +1,6 @@
-// Step 2 of the selected inversion (X_{C,K} = -X_{C,C} Lhat_{C,K}, Algorithm 1)
-// in FP64 accuracy on the bf16 tensor cores, for real symmetric positive
-// definite matrices.
+// Steps 2 and 3 of the selected inversion (X_{C,K} = -X_{C,C} Lhat_{C,K} and
+// the partial products Lhat_{C,K}^T X_{C,K}, Algorithm 1) in FP64 accuracy on
+// the bf16 tensor cores, for real symmetric positive definite matrices.
 //
 // Scaling.  For X = A^{-1} SPD, |X_pq| <= sqrt(X_pp X_qq).  With the power of
 // two 2^e_p >= sqrt(X_pp), e_p = ceil(E_p / 2) where X_pp < 2^E_p, every entry
@@ -25,7 +25,12 @@
 //
 // The slices of a supernode's X panel are cut once, right after its level
 // has finished (k_em_split_x), those of its B' right before its step 2
-// (k_em_split_lhat, once the exponents of the rows of C are known).
+// (k_em_split_lhat, once the exponents of the rows of C are known).  Step 3,
+// Lhat^T X_{C,K} = B'^T X'' with X'' = diag(2^-e_C) X_{C,K}, takes B' and the
+// slices of X'' over a per-column exponent G_j (k_em_split_xck, right after
+// step 2): P_mn = 2^(F_m + G_n - 32) (hi + lo 2^-32), both operands cut at
+// 2^56.  Step 2 runs on mma.sync (k_em_gemm1, 64-row tiles) or on tcgen05
+// (k_em_gemm1_tc, 128-row tiles); step 3 on mma.sync (k_em_gemm2).
 #include <cfloat>
 #include <climits>
 #include <cstdint>
