@@ -218,17 +218,19 @@ __global__ void __launch_bounds__(256) k_em_split_xck(KArgs a, EmArgs e, const i
 
 constexpr int kKP = kKC + 8;  // shared row stride of a slice plane in bf16 (80 bytes: ldmatrix rows conflict-free)
 
-// Step-2 tile: the 7 slice planes of the X_{C,C} and B' tiles of one
-// 32-row chunk of C, the descriptors of the tile's rows and of the columns
-// of the current and the next chunk.
+// A 64-row tile on mma.sync: the 7 slice planes of the A and B operands of
+// one 32-row chunk of C (step 2: X_{C,C} and B'; step 3: B'^T and X''), the
+// descriptors of the tile's rows and of the columns of the current and the
+// next chunk (step 2 only), and the row / column exponents (step 2: e of the
+// rows of C and F; step 3: F and G).
 template <int NB>
 struct EmSmem {
   uint16_t a[kSl][kTileM][kKP];  // X_{C,C} tile, [slice][m][k]
   uint16_t b[kSl][NB][kKP];      // B' tile, [slice][n][k]
   ColDesc rdesc[kTileM];         // desc of the tile's rows of C
   ColDesc cdesc[2][kKC];         // desc of the columns of chunk c, slot c & 1
-  int32_t erow[kTileM];          // e of the tile's rows of C
-  int32_t fcol[kTileN];          // F of the tile's columns
+  int32_t erow[kTileM];          // exponents of the tile's rows
+  int32_t fcol[kTileN];          // exponents of the task's columns
 };
 
 __device__ __forceinline__ void ldsm_x4(uint32_t (&d)[4], const void* p) {
