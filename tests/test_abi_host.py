@@ -120,3 +120,19 @@ def test_figure1_partition_levels_match_algorithm2(P):
     M = M | M.T
     cp, ri, v = lower_from_dense(np.where(M, 1.0, 0.0))
     _compare(P, n, cp, ri, 128, 0)
+
+
+def test_opts_structure_matches_the_c_layout(P):
+    """pselinv_default_opts zeroes exactly sizeof(pselinv_opts) bytes and sets
+    its defaults: run it on a sentinel-filled buffer larger than the ctypes
+    Opts and check the extent it wrote and the fields at the ctypes offsets."""
+    import ctypes
+    n = ctypes.sizeof(P.Opts)
+    buf = (ctypes.c_uint8 * (n + 64))(*([0xA5] * (n + 64)))
+    P.load_library().pselinv_default_opts(ctypes.cast(buf, ctypes.POINTER(P.Opts)))
+    assert all(b == 0xA5 for b in buf[n:]), "the C structure is larger than the ctypes one"
+    o = P.Opts.from_buffer(buf)
+    assert (o.dtype, o.batch, o.max_sn_width, o.relax, o.small_cutoff, o.split_k_rows) == (P.F64, 1, 128,
+                                                                                          P.RELAX_AMALG, -1, 1024)
+    assert (o.debug_checks, o.unsym, o.spin_limit_ns, o.level_tiles, o.min_slice_rows, o.fp64_emulation) == (
+        0, 0, 1000000000, 0, 0, 0)
