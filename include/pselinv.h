@@ -332,7 +332,8 @@ int pselinv_get_panels(pselinv_handle* h, int32_t which, void* out, void* stream
  * Synchronise `stream` and report device-side failures of earlier enqueued
  * work on h: PSELINV_ERR_TIMEOUT if a bounded wait of the PERSISTENT
  * schedule ran out (that call's results are invalid; the flag is cleared and
- * the handle stays usable), PSELINV_ERR_RANGE if a selinv with
+ * the handle stays usable) or a bounded wait of the tcgen05 step-2 kernel
+ * (opts.fp64_emulation = 2) ran out, PSELINV_ERR_RANGE if a selinv with
  * opts.fp64_emulation met an X that is not positive definite (same
  * treatment).  Returns PSELINV_OK otherwise.
  */

@@ -860,9 +860,13 @@ int pselinv_sync_status(pselinv_handle* h, void* stream) {
                    "a bounded device wait of the persistent schedule ran out; that selinv's results are invalid");
   }
   if (status[psi::kEmStatusWord]) {
+    const int em = status[psi::kEmStatusWord];
     PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + psi::kEmStatusWord, 0, sizeof(int), st));
     PSI_CUDA(h, cudaStreamSynchronize(st));
     h->inverted = false;
+    if (em & psi::kEmTimeout)
+      return set_err(h, PSELINV_ERR_TIMEOUT,
+                     "a bounded mbarrier wait of the tcgen05 step-2 kernel ran out; that selinv's results are invalid");
     return set_err(h, PSELINV_ERR_RANGE,
                    "FP64 emulation: X is not positive definite (a diagonal entry <= 0 or a scaled entry out of "
                    "range); that selinv's results are invalid -- use fp64_emulation = 0");

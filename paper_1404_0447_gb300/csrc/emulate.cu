@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) k_em_split_x(KArgs a, EmArgs e, const int
       out[p] = split7(col[p], ep + ej, bad);  // |X_pq| < 2^(e_p + e_q + 1)
     }
   }
-  if (bad) atomicOr(a.status + kEmStatusWord, 1);
+  if (bad) atomicOr(a.status + kEmStatusWord, kEmRange);
 }
 
 // Rows of C whose exponents k_em_split_lhat keeps in shared memory at most
@@ -184,7 +184,7 @@ __device__ __forceinline__ void split_columns(const double* W, int64_t wld, uint
     for (int i = threadIdx.x; i < r; i += blockDim.x) dst[i + (int64_t)j * dld] = split7(col[i], E - ec(i), bad);
     __syncthreads();  // red[] is rewritten by the next column
   }
-  if (bad) atomicOr(status + kEmStatusWord, 1);
+  if (bad) atomicOr(status + kEmStatusWord, kEmRange);
 }
 
 // Before step 2 of supernode K: F_j and the slices of B' = diag(2^e_C) Lhat.
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(kEmThreads, 2) k_em_gemm1_tc(KArgs a, EmArgs e
     if (sm.abort) break;
   }
   if (sm.abort) {
-    if (t == 0) atomicOr(a.status + kEmStatusWord, 2);
+    if (t == 0) atomicOr(a.status + kEmStatusWord, kEmTimeout);
   } else {
     const int row = warp * 32 + lane, i = m0 + row;
     if (i < r) {

@@ -105,9 +105,12 @@ struct EmArgs {
   const int32_t* crow;   // [sum r] global row of C[i] of supernode K at desc offset of K
   int64_t n;
 };
-// Emulation status word: nonzero after an X diagonal <= 0 / not finite or a
-// scaled entry outside its slice range (X not positive definite).
+// Emulation status word: kEmRange after an X diagonal <= 0 / not finite or a
+// scaled entry outside its slice range (X not positive definite), kEmTimeout
+// after a bounded mbarrier wait of the tcgen05 kernel ran out.
 constexpr int kEmStatusWord = 4;
+constexpr int kEmRange = 1;
+constexpr int kEmTimeout = 2;
 // After steps 2-3 of a level: e_p of the level's columns and the slices of
 // its X panels.  Before step 2 of a level: F and the slices of its B'.
 cudaError_t launch_em_split_x(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, cudaStream_t st);
