@@ -469,9 +469,8 @@ int pselinv_export_symbolic(const pselinv_handle* h, pselinv_symbolic* view);
 
 /*
  * Allocation-free inverse of a batch of small dense blocks from their LDL^T
- * factors: d_M[b] = L_b^{-T} D_b^{-1} L_b^{-1} (= A_b^{-1} when A_b = L_b D_b
- * L_b^T), the diagonal-block term of step 3 above.  The paper has no
- * counterpart: this exists for callers that may not call cudaMalloc or
+ * factors: d_M[b] = L_b^{-T} D_b^{-1} L_b^{-1}, which equals A_b^{-1} when
+ * A_b = L_b D_b L_b^T.  The paper has no counterpart: this exists for callers that may not call cudaMalloc or
  * cudaFree (cudaFree synchronises the device and cudaMalloc can stall) --
  * code running inside another framework's memory pool or under a fixed
  * memory budget, loops that must never block on the allocator.  It calls no

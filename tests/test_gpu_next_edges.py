@@ -152,9 +152,12 @@ def test_bk_dense_block_matches_lapack_pivots(P, cplx):
     two = np.abs(np.diag(d, -1)) > 0
     assert np.array_equal(ty[0][:-1] == 1, two)
     h.selinv(P.LEVEL)
-    Xi = np.linalg.inv(A)
     c = np.repeat(np.arange(n), np.diff(cp))
-    assert np.max(np.abs(h.selected()[0].cpu().numpy() - Xi[ri, c])) / np.abs(Xi).max() <= 1e-9
+    sel = h.selected()[0].cpu().numpy()
+    _, Xo, _ = oracle.selected_inverse_bk(n, cp, ri, v, 128, 1)     # same pivots (checked above)
+    assert np.max(np.abs(sel - Xo[ri, c])) / np.abs(Xo).max() <= TOL
+    Xi = np.linalg.inv(A)                                            # sanity: the inverse itself
+    assert np.max(np.abs(sel - Xi[ri, c])) / np.abs(Xi).max() <= 1e-9
 
 
 def test_bk_uneven_batch(P):
@@ -172,7 +175,9 @@ def test_bk_uneven_batch(P):
     off = 0
     for A, (cp, ri, v) in zip(mats, low):
         n = A.shape[0]
-        Xi = np.linalg.inv(A)
         c = np.repeat(np.arange(n), np.diff(cp))
+        _, Xo, _ = oracle.selected_inverse_bk(n, cp, ri, v, 128, 1)
+        assert np.max(np.abs(sel[off:off + len(ri)] - Xo[ri, c])) / np.abs(Xo).max() <= TOL
+        Xi = np.linalg.inv(A)                                        # sanity: the inverse itself
         assert np.max(np.abs(sel[off:off + len(ri)] - Xi[ri, c])) / np.abs(Xi).max() <= 1e-9
         off += len(ri)
