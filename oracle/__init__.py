@@ -39,14 +39,15 @@ c128p = np.ctypeslib.ndpointer(dtype=np.complex128, flags="C_CONTIGUOUS")
 
 def build(force: bool = False) -> str:
     """Compile oracle.c into _liboracle.so with gcc (no FMA contraction so
-    x86 and Arm hosts round identically)."""
+    x86 and Arm hosts round identically; OpenMP for the row-parallel
+    timing variant of the column recurrence)."""
     src = [os.path.join(_HERE, "oracle.c")]
     deps = src + [os.path.join(_HERE, "oracle_num.h")]
     if (not force and os.path.exists(_SO)
             and all(os.path.getmtime(_SO) >= os.path.getmtime(s) for s in deps)):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                            "-o", tmp] + src + ["-lm"])
     os.replace(tmp, _SO)
     return _SO
@@ -78,6 +79,8 @@ def lib():
             f.argtypes = [ctypes.c_int32, i64p, i32p, vp, i64p, i32p, vp, vp]
             f = getattr(L, f"orc_selinv_{sfx}")
             f.argtypes = [ctypes.c_int32, i64p, i32p, vp, vp, vp, vp]
+            f = getattr(L, f"orc_selinv_omp_{sfx}")
+            f.argtypes = [ctypes.c_int32, i64p, i32p, vp, vp, vp, vp, ctypes.c_int32]
             f = getattr(L, f"orc_solve_{sfx}")
             f.argtypes = [ctypes.c_int32, i64p, i32p, vp, vp, vp]
             f = getattr(L, f"orc_ldu_{sfx}")
@@ -234,15 +237,21 @@ def ldlt(n, colptr, rowind, values, lcolptr, lrowind):
     return lv, d
 
 
-def selinv(n, lcolptr, lrowind, lvals, d):
-    """Column selected inversion: X on the L pattern (xv) and its diagonal (xd)."""
+def selinv(n, lcolptr, lrowind, lvals, d, threads=None):
+    """Column selected inversion: X on the L pattern (xv) and its diagonal (xd).
+    threads=None: the plain single-thread recurrence; threads=t: the OpenMP
+    row-parallel variant on t threads (bitwise the same result)."""
     cz = _cplx(lvals)
     dt = np.complex128 if cz else np.float64
     xv = np.zeros(len(lrowind), dt)
     xd = np.zeros(n, dt)
-    f = lib().orc_selinv_z if cz else lib().orc_selinv_d
-    st = f(n, _i64(lcolptr), _i32(lrowind), np.ascontiguousarray(lvals, dt),
-           np.ascontiguousarray(d, dt), xv, xd)
+    args = (n, _i64(lcolptr), _i32(lrowind), np.ascontiguousarray(lvals, dt), np.ascontiguousarray(d, dt), xv, xd)
+    if threads is None:
+        f = lib().orc_selinv_z if cz else lib().orc_selinv_d
+        st = f(*args)
+    else:
+        f = lib().orc_selinv_omp_z if cz else lib().orc_selinv_omp_d
+        st = f(*args, int(threads))
     if st < 0:
         raise ValueError(f"pattern not elimination-closed at column {-st - 1}")
     return xv, xd

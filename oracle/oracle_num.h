@@ -114,6 +114,151 @@ int ORC_SFX(orc_selinv)(int32_t n, const int64_t* lcp, const int32_t* lri, const
 }
 
 /*
+ * The same recurrence on `nthreads` OpenMP threads (timing at scale only),
+ * with every X entry formed by one thread by the scalar operations of
+ * orc_selinv in the same order, so the result is bitwise that of
+ * orc_selinv.  Column j needs only the columns of its ancestors in the
+ * elimination tree (C = struct(j) lies on its path to the root), so the
+ * columns of one depth of the tree are independent:
+ *  - a depth holding many columns: one column per thread, each by the
+ *    orc_selinv column step;
+ *  - otherwise column by column, the rows of C cut into one contiguous
+ *    block [a0, a1) per thread: the thread runs the loop of orc_selinv over
+ *    b restricted to its own y entries -- for b < a0 the walk of struct(C[b])
+ *    over the rows C[a0..a1) only (started by a binary search), for b in
+ *    [a0, a1) the whole walk -- so every y entry receives the same terms in
+ *    the same order as there; X_jj by one thread.
+ */
+static int ORC_SFX(orc_selinv_column)(int32_t j, const int64_t* lcp, const int32_t* lri, const ORC_T* lv,
+                                      const ORC_T* d, ORC_T* xv, ORC_T* xd, ORC_T* y) {
+  const int64_t p0 = lcp[j], r = lcp[j + 1] - lcp[j];
+  const int32_t* C = lri + p0;
+  const ORC_T* Lj = lv + p0;
+  for (int64_t a = 0; a < r; ++a) y[a] = 0;
+  for (int64_t b = 0; b < r; ++b) {
+    int32_t k = C[b];
+    ORC_T lkj = Lj[b];
+    y[b] += xd[k] * lkj;
+    int64_t q = lcp[k], qend = lcp[k + 1];
+    for (int64_t a = b + 1; a < r; ++a) {
+      while (q < qend && lri[q] != C[a]) ++q;
+      if (q == qend) return -(j + 1);
+      ORC_T x = xv[q];
+      y[a] += x * lkj;
+      y[b] += x * Lj[a];
+    }
+  }
+  ORC_T acc = 0;
+  for (int64_t a = 0; a < r; ++a) {
+    xv[p0 + a] = -y[a];
+    acc += Lj[a] * xv[p0 + a];
+  }
+  xd[j] = 1.0 / d[j] - acc;
+  return 0;
+}
+
+int ORC_SFX(orc_selinv_omp)(int32_t n, const int64_t* lcp, const int32_t* lri, const ORC_T* lv,
+                            const ORC_T* d, ORC_T* xv, ORC_T* xd, int32_t nthreads) {
+  int status = 0;
+  if (nthreads < 1) nthreads = 1;
+  if (n <= 0) return 0;
+  /* depth of each column below its root (parent(j) = min struct(j)), columns grouped by depth */
+  int32_t* depth = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t maxd = 0;
+  int64_t maxr = 0;
+  for (int32_t j = n - 1; j >= 0; --j) {
+    const int64_t r = lcp[j + 1] - lcp[j];
+    depth[j] = r > 0 ? depth[lri[lcp[j]]] + 1 : 0;
+    if (depth[j] > maxd) maxd = depth[j];
+    if (r > maxr) maxr = r;
+  }
+  int64_t* dptr = (int64_t*)calloc((size_t)maxd + 2, sizeof(int64_t));
+  int32_t* dcol = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  for (int32_t j = 0; j < n; ++j) dptr[depth[j] + 1]++;
+  for (int32_t t = 0; t <= maxd; ++t) dptr[t + 1] += dptr[t];
+  for (int32_t j = 0; j < n; ++j) dcol[dptr[depth[j]]++] = j;
+  for (int32_t t = maxd; t > 0; --t) dptr[t] = dptr[t - 1];
+  dptr[0] = 0;
+  ORC_T* ybuf = (ORC_T*)calloc((size_t)nthreads * (size_t)(maxr > 0 ? maxr : 1), sizeof(ORC_T));
+#pragma omp parallel num_threads(nthreads)
+  {
+    int tid = 0, nt = 1;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+    nt = omp_get_num_threads();
+#endif
+    ORC_T* y = ybuf + (size_t)tid * (size_t)(maxr > 0 ? maxr : 1);
+    for (int32_t t = 0; t <= maxd; ++t) {
+      const int64_t c0 = dptr[t], c1 = dptr[t + 1];
+      if (c1 - c0 >= 4 * (int64_t)nt) {
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t c = c0; c < c1; ++c) {
+          const int st = ORC_SFX(orc_selinv_column)(dcol[c], lcp, lri, lv, d, xv, xd, y);
+          if (st) {
+#pragma omp atomic write
+            status = st;
+          }
+        }
+        continue;
+      }
+      for (int64_t c = c0; c < c1; ++c) {
+        const int32_t j = dcol[c];
+        const int64_t p0 = lcp[j], r = lcp[j + 1] - lcp[j];
+        const int32_t* C = lri + p0;
+        const ORC_T* Lj = lv + p0;
+        const int64_t a0 = r * tid / nt, a1 = r * (tid + 1) / nt;
+        for (int64_t a = a0; a < a1; ++a) y[a - a0] = 0;
+        int bad = 0;
+        for (int64_t b = 0; b < a1 && !bad; ++b) {
+          const int32_t k = C[b];
+          const ORC_T lkj = Lj[b];
+          int64_t q = lcp[k], qend = lcp[k + 1];
+          if (b < a0) {                       /* rows C[a0..a1) of column k */
+            int64_t lo = q, hi = qend;
+            while (lo < hi) {
+              const int64_t mid = lo + (hi - lo) / 2;
+              if (lri[mid] < C[a0]) lo = mid + 1; else hi = mid;
+            }
+            q = lo;
+            for (int64_t a = a0; a < a1; ++a) {
+              while (q < qend && lri[q] != C[a]) ++q;
+              if (q == qend) { bad = 1; break; }
+              y[a - a0] += xv[q] * lkj;
+            }
+            continue;
+          }
+          y[b - a0] += xd[k] * lkj;           /* b in [a0, a1): the loop of orc_selinv */
+          for (int64_t a = b + 1; a < r; ++a) {
+            while (q < qend && lri[q] != C[a]) ++q;
+            if (q == qend) { bad = 1; break; }
+            const ORC_T x = xv[q];
+            if (a < a1) y[a - a0] += x * lkj;
+            y[b - a0] += x * Lj[a];
+          }
+        }
+        if (bad) {
+#pragma omp atomic write
+          status = -(j + 1);
+        }
+        for (int64_t a = a0; a < a1; ++a) xv[p0 + a] = -y[a - a0];
+#pragma omp barrier
+#pragma omp single
+        {
+          ORC_T acc = 0;
+          for (int64_t a = 0; a < r; ++a) acc += Lj[a] * xv[p0 + a];
+          xd[j] = 1.0 / d[j] - acc;
+        }
+      }
+    }
+  }
+  free(ybuf);
+  free(depth);
+  free(dptr);
+  free(dcol);
+  return status;
+}
+
+/*
  * Solve A x = b with A = L D L^T (in place on b): L z = b, z /= d, L^T x = z.
  * This is the direct inversion of Eq. (6) one right-hand side at a time,
  * used to check columns of the inverse.

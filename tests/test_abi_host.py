@@ -94,14 +94,13 @@ def test_analyze_rejects_bad_input(P):
     with pytest.raises(P.PselinvError) as e:
         P.SelInv(2, cp, ri, max_sn_width=500)
     assert e.value.code == -1
-    # FP64 emulation of step 2: real symmetric handles only; 1 = mma.sync, 2 = tcgen05
-    for kw in ({"fp64_emulation": 3}, {"fp64_emulation": -1}, {"fp64_emulation": 1, "dtype": P.C128},
-               {"fp64_emulation": 2, "unsym": 1}):
+    # FP64 emulation of steps 2 and 3 (opt-in): real symmetric handles only
+    for kw in ({"fp64_emulation": 2}, {"fp64_emulation": -1}, {"fp64_emulation": 1, "dtype": P.C128},
+               {"fp64_emulation": 1, "unsym": 1}):
         with pytest.raises(P.PselinvError) as e:
             P.SelInv(2, cp, ri, **kw)
         assert e.value.code == -1, kw
     P.SelInv(2, cp, ri, fp64_emulation=1)
-    P.SelInv(2, cp, ri, fp64_emulation=2)
     with pytest.raises(TypeError):
         P.SelInv(2, cp, ri, no_such_option=1)
 

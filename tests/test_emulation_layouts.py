@@ -1,8 +1,7 @@
 """CPU checks of the index maps of the emulated step-2/3 kernels (the maps
 in paper_1404_0447_gb300/csrc/emulate.cu, restated here): every staging map
 covers its tile exactly once and stays in bounds, the 32-bit plane stores of
-one warp instruction hit 32 distinct shared-memory banks, and the tcgen05
-operand layout (8-row x 16-byte core matrices) fills its planes exactly.
+one warp instruction hit 32 distinct shared-memory banks.
 These are the checks made before the kernels first ran on a GPU."""
 import itertools
 
@@ -62,69 +61,3 @@ def test_ldmatrix_rows_hit_distinct_16_byte_bank_groups():
             groups = {((r0 + i) * KP * 2 + kofs * 2) // 16 % 8 for i in range(8)}
             assert len(groups) == 8
             assert all(((r0 + i) * KP * 2 + kofs * 2) % 16 == 0 for i in range(8))
-
-
-# ---- tcgen05 kernel (k_em_gemm1_tc): core-matrix planes, pair maps ----
-
-TC_M, TC_N = 128, 16
-
-
-def core_off(row, k):
-    return (((row >> 3) << 2) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2
-
-
-def pair_tc(warp, lane, p, right_of_rows):
-    combo = p * 4 + warp
-    rb, kq = combo >> 2, combo & 3
-    if right_of_rows:
-        return 8 * rb + (lane >> 2), 8 * kq + 2 * (lane & 3)
-    return 8 * rb + (lane & 7), 8 * kq + 2 * (lane >> 3)
-
-
-def test_core_matrix_layout_fills_the_planes_exactly():
-    offs = sorted(core_off(r, k) for r in range(TC_M) for k in range(KC))
-    assert offs == list(range(0, TC_M * KC * 2, 2))
-    offs_b = sorted(core_off(n, k) for n in range(TC_N) for k in range(KC))
-    assert offs_b == list(range(0, TC_N * KC * 2, 2))
-    # descriptor strides: next core along K is +128 B, next 8 rows +512 B
-    assert core_off(0, 8) - core_off(0, 0) == 128 and core_off(8, 0) - core_off(0, 0) == 512
-    # the second 16-row step of a chunk starts two cores (256 B) further along K
-    assert core_off(0, 16) - core_off(0, 0) == 256
-
-
-@pytest.mark.parametrize("right", [False, True])
-def test_tc_pair_map_covers_the_tile_once_and_stores_without_conflicts(right):
-    seen = np.zeros((TC_M, KC), int)
-    for warp, p in itertools.product(range(4), range(16)):
-        words = []
-        for lane in range(32):
-            row, k = pair_tc(warp, lane, p, right)
-            assert 0 <= row < TC_M and 0 <= k <= KC - 2 and k % 2 == 0
-            seen[row, k] += 1
-            seen[row, k + 1] += 1
-            off = core_off(row, k)
-            assert off + 4 <= TC_M * KC * 2
-            words.append(off // 4)
-        assert len(set(banks_of_words(words))) == 32, (warp, p)
-    assert np.all(seen == 1)
-
-
-def test_tc_b_pair_map_covers_the_b_tile():
-    seen = np.zeros((TC_N, KC), int)
-    for j, warp, lane in itertools.product(range(2), range(4), range(32)):
-        combo = j * 4 + warp
-        n = 8 * (combo >> 2) + (lane >> 2)
-        k = 8 * (combo & 3) + 2 * (lane & 3)
-        assert core_off(n, k) + 4 <= TC_N * KC * 2
-        seen[n, k] += 1
-        seen[n, k + 1] += 1
-    assert np.all(seen == 1)
-
-
-def test_tc_tmem_columns_of_the_groups_fit_the_allocation():
-    # group g of a 16-column tile in columns 16 g .. 16 g + 15; 128 columns allocated
-    used = {16 * g + j for g in range(7) for j in range(16)}
-    assert max(used) < 128 and len(used) == 112
-    # instruction descriptor: f32 accumulator, bf16 A and B, K-major, N = 16, M = 128
-    idesc = (1 << 4) | (1 << 7) | (1 << 10) | ((16 >> 3) << 17) | ((128 >> 4) << 24)
-    assert idesc == 0x08040490

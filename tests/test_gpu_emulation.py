@@ -1,5 +1,5 @@
 """GPU parity of step 2 with its FP64 arithmetic emulated on the bf16 tensor
-cores (opts.fp64_emulation = 1 on mma.sync, 2 on tcgen05: scaled X and Lhat
+cores (opts.fp64_emulation = 1, mma.sync: scaled X and Lhat
 cut into 8-bit slices, exact integer accumulation of the slice products)
 against the oracle,
 through the C ABI: SPD grids and graph Laplacians over the tile widths,
@@ -53,7 +53,7 @@ def run(P, p, wmax=128, relax=1, modes=(1,), emulate=1, **opts):
     return h, outs
 
 
-VARIANTS = [pytest.param(1, id="mma_sync"), pytest.param(2, id="tcgen05")]
+VARIANTS = [pytest.param(1, id="mma_sync")]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
