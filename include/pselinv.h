@@ -106,8 +106,8 @@ typedef struct {
   int32_t level_tiles;    /* a level whose step-2 (step-3) tiles number fewer than this gets its slices
                              (row chunks) of C shrunk until it has about this many; 0 = 16 per SM (2432) */
   int32_t min_slice_rows; /* smallest step-2 slice that shrinking makes; 0 = 128 (step-3 chunks: a quarter) */
-  int32_t fp64_emulation; /* 0: steps 2 and 3 in FP64 (mma.sync f64).  1 (mma.sync bf16) or 2 (step 2 on
-                             tcgen05, 128-row tiles): step 2, X_{C,K} = -X_{C,C} Lhat_{C,K}, and step 3's
+  int32_t fp64_emulation; /* 0: steps 2 and 3 in FP64 (mma.sync f64).  1 (mma.sync bf16, opt-in, outside
+                             the FP64 hot path): step 2, X_{C,K} = -X_{C,C} Lhat_{C,K}, and step 3's
                              Lhat_{C,K}^T X_{C,K} (Algorithm 1),
                              in FP64 accuracy on the bf16 tensor cores, for real symmetric
                              positive definite A (dtype F64, unsym 0, pivot-free factor; PLAIN, LEVEL and
@@ -332,8 +332,7 @@ int pselinv_get_panels(pselinv_handle* h, int32_t which, void* out, void* stream
  * Synchronise `stream` and report device-side failures of earlier enqueued
  * work on h: PSELINV_ERR_TIMEOUT if a bounded wait of the PERSISTENT
  * schedule ran out (that call's results are invalid; the flag is cleared and
- * the handle stays usable) or a bounded wait of the tcgen05 step-2 kernel
- * (opts.fp64_emulation = 2) ran out, PSELINV_ERR_RANGE if a selinv with
+ * the handle stays usable), PSELINV_ERR_RANGE if a selinv with
  * opts.fp64_emulation met an X that is not positive definite (same
  * treatment).  Returns PSELINV_OK otherwise.
  */

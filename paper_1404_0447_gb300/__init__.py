@@ -144,7 +144,7 @@ class SelInv:
     inversion, ``panels()`` / ``selected()`` return CUDA tensors.  With
     ``unsym=1`` the matrix is non-symmetric with a symmetric pattern:
     ``factor_unsym(lower, upper)`` and ``selected_upper()``.  With
-    ``fp64_emulation=1`` (or ``2``, step 2 on tcgen05) steps 2 and 3 of an SPD
+    ``fp64_emulation=1`` steps 2 and 3 of an SPD
     matrix run on bf16 slices with exact integer sums (pselinv_opts in
     include/pselinv.h); call ``sync_status()`` after ``selinv`` to learn
     whether X was positive definite (PselinvError ERR_RANGE otherwise).  Option

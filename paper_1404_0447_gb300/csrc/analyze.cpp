@@ -171,7 +171,7 @@ int analyze(pselinv_handle* h, int64_t n, const int64_t* cp, const int32_t* ri,
   if (wcap < 1 || wcap > kMaxWidth) return fail(h, PSELINV_ERR_ARG, "max_sn_width must be 0..128");
   if (o.unsym != 0 && o.unsym != 1) return fail(h, PSELINV_ERR_ARG, "unsym must be 0 or 1");
   if (o.unsym && o.dtype == PSELINV_C128) wcap = std::min(wcap, kMaxWidthLUComplex);
-  if (o.fp64_emulation < 0 || o.fp64_emulation > 2) return fail(h, PSELINV_ERR_ARG, "fp64_emulation must be 0, 1 or 2");
+  if (o.fp64_emulation < 0 || o.fp64_emulation > 1) return fail(h, PSELINV_ERR_ARG, "fp64_emulation must be 0 or 1");
   if (o.fp64_emulation && (o.dtype != PSELINV_F64 || o.unsym))
     return fail(h, PSELINV_ERR_ARG, "fp64_emulation is for real symmetric handles");
   if (o.relax != PSELINV_RELAX_NONE && o.relax != PSELINV_RELAX_AMALG)

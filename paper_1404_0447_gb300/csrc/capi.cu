@@ -387,7 +387,7 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
         cudaError_t x = emul ? psi::launch_em_split_lhat(ka, em, sns, nsn_step, maxr, st) : cudaSuccess;
         for (int v = 0; v < psi::kNumVar && x == cudaSuccess; ++v)
           x = emul ? psi::launch_em_gemm1(v, ka, em, tasks_at(h, h->off_gemm1, r1[v].begin), r1[v].end - r1[v].begin,
-                                          st, h->opts.fp64_emulation == 2)
+                                          st)
                    : psi::launch_tiles(Kern::Gemm1, v, ka, tasks_at(h, h->off_gemm1, r1[v].begin),
                                        r1[v].end - r1[v].begin, st);
         if (split && x == cudaSuccess) x = psi::launch_per_sn(Kern::Gemm1Reduce, ka, sns, nsn_step, st);
@@ -864,9 +864,6 @@ int pselinv_sync_status(pselinv_handle* h, void* stream) {
     PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + psi::kEmStatusWord, 0, sizeof(int), st));
     PSI_CUDA(h, cudaStreamSynchronize(st));
     h->inverted = false;
-    if (em & psi::kEmTimeout)
-      return set_err(h, PSELINV_ERR_TIMEOUT,
-                     "a bounded mbarrier wait of the tcgen05 step-2 kernel ran out; that selinv's results are invalid");
     return set_err(h, PSELINV_ERR_RANGE,
                    "FP64 emulation: X is not positive definite (a diagonal entry <= 0 or a scaled entry out of "
                    "range); that selinv's results are invalid -- use fp64_emulation = 0");

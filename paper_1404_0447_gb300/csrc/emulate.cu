@@ -29,8 +29,8 @@
 // Lhat^T X_{C,K} = B'^T X'' with X'' = diag(2^-e_C) X_{C,K}, takes B' and the
 // slices of X'' over a per-column exponent G_j (k_em_split_xck, right after
 // step 2): P_mn = 2^(F_m + G_n - 32) (hi + lo 2^-32), both operands cut at
-// 2^56.  Step 2 runs on mma.sync (k_em_gemm1, 64-row tiles) or on tcgen05
-// (k_em_gemm1_tc, 128-row tiles); step 3 on mma.sync (k_em_gemm2).
+// 2^56.  Step 2 runs on mma.sync (k_em_gemm1, 64-row tiles), step 3 on
+// mma.sync (k_em_gemm2).
 #include <cfloat>
 #include <climits>
 #include <cstdint>
@@ -544,281 +544,6 @@ __global__ void __launch_bounds__(kEmThreads, 3) k_em_gemm2(KArgs a, EmArgs e, c
   }
 }
 
-// ---------------------------------------------------------------------------
-// The same step-2 task on the 5th-generation tensor cores (tcgen05, sm_103a):
-// 128 x 16 output tile (UMMA M = 128, N = 16, K = 16 per instruction), the 7
-// slice planes of the X_{C,C} and B' tiles of one 32-row chunk of C in shared
-// memory as K-major matrices without swizzle (8-row x 16-byte core matrices,
-// core (row/8, k/8) at ((row/8) * 4 + k/8) * 128 bytes: leading byte offset
-// 128 = next core along K, stride byte offset 512 = next 8 rows), the seven
-// group sums in 112 TMEM columns (group g in columns 16 g .. 16 g + 15, row i
-// in lane i).  Per chunk one thread issues the 56 MMAs (28 slice pairs x 2
-// steps of 16 rows of C), the first product of each group overwriting its
-// columns, and commits them to an mbarrier; every warp then reads its 32
-// lanes (its 32 rows) group by group and folds them into 64-bit integers.
-// While the MMAs run the threads load the relative indices and the first
-// half of the next chunk's gathers.  Every mbarrier wait is bounded.
-// ---------------------------------------------------------------------------
-constexpr int kTcRows = 128;            // tile rows (UMMA M)
-constexpr int kTcCols = 16;             // tile columns (UMMA N)
-constexpr int kTcPlaneA = kTcRows * kKC * 2;  // bytes of one A slice plane (8 KB)
-constexpr int kTcPlaneB = kTcCols * kKC * 2;  // bytes of one B slice plane (1 KB)
-constexpr int kTcTmemCols = 128;        // 7 x 16 columns used
-constexpr unsigned long long kTcWaitNs = 1000000000ull;
-
-struct TcSmem {
-  uint8_t a[kSl][kTcPlaneA];   // 56 KB
-  uint8_t b[kSl][kTcPlaneB];   // 7 KB
-  ColDesc rdesc[kTcRows];      // desc of the tile's rows of C
-  ColDesc cdesc[2][kKC];       // desc of the columns of chunk c, slot c & 1
-  int32_t erow[kTcRows];
-  int32_t fcol[kTcCols];
-  uint64_t mbar;
-  uint32_t tmem;
-  int32_t abort;
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// byte offset of element (row, k) in a K-major no-swizzle plane of 32 k
-__device__ __forceinline__ uint32_t core_off(int row, int k) {
-  return (uint32_t)((((row >> 3) << 2) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
-}
-// shared-memory matrix descriptor: start, leading byte offset (K), stride byte
-// offset (8-row groups), sm_100-family version bits, no swizzle
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(512 >> 4) << 32) |
-         ((uint64_t)1 << 46);
-}
-// instruction descriptor: f32 accumulator, bf16 A and B, both K-major, N = 16, M = 128
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcCols >> 3) << 17) |
-                              ((uint32_t)(kTcRows >> 4) << 24);
-
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(da), "l"(db), "r"(kTcIdesc), "r"(acc));
-}
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-// bounded wait for phase `parity` of the mbarrier; false after kTcWaitNs
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  const uint64_t t0 = gtimer();
-  for (;;) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (gtimer() - t0 > kTcWaitNs) return false;
-  }
-}
-
-__global__ void __launch_bounds__(kEmThreads, 2) k_em_gemm1_tc(KArgs a, EmArgs e, const Task* __restrict__ tasks) {
-  extern __shared__ __align__(128) unsigned char tc_raw[];
-  TcSmem& sm = *reinterpret_cast<TcSmem*>(tc_raw);
-  const Task tk = tasks[blockIdx.x];
-  const int b = blockIdx.y;
-  const SnMeta m = a.meta[tk.sn];
-  const int s = m.s, r = m.r, ld = s + r;
-  const ColDesc* dk = a.desc + m.desc;
-  const int32_t* relidx = a.relidx;
-  const uint4* xs = (const uint4*)e.xs + b * a.sz.panel;
-  const uint4* ls = (const uint4*)e.ls + b * a.sz.lhat + m.lhat;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int m0 = tk.m0, nb = tk.n0;
-  const int kb = tk.c * m.kchunk, ke = min(r, kb + m.kchunk);
-  const int nck = ke > kb ? (ke - kb + kKC - 1) / kKC : 0;
-  {
-    const int i = m0 + t;
-    sm.erow[t] = i < r ? e.sig[b * e.n + e.crow[m.desc + i]] : 0;
-    if (i < r) sm.rdesc[t] = dk[i];
-    if (t < kTcCols) sm.fcol[t] = nb + t < s ? e.lexp[b * e.n + m.f + nb + t] : 0;
-    if (t < kKC && nck > 0 && kb + t < ke) sm.cdesc[0][t] = dk[kb + t];
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
-                 "r"(kTcTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar)));
-    sm.abort = 0;
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = sm.tmem;
-  const uint32_t mbar = smem_u32(&sm.mbar);
-
-  // pair p (0..15) of this thread in chunk c: tile row and first k of the
-  // pair; the 32 lanes of a warp cover the 32 words of one core matrix
-  // (8 rows x 4 k-pairs), so the 32-bit plane stores are conflict-free.
-  // Right of the tile's rows four lanes run along k (128 contiguous bytes of
-  // one row of the ancestor's panel), else eight lanes run along the rows.
-  auto pair_at = [&](int c, int p, int& row, int& kk) {
-    const int combo = p * 4 + warp;  // 64 cores: 16 row blocks x 4 k blocks
-    const int rb = combo >> 2, kq = combo & 3;
-    if (kb + c * kKC >= m0 + kTcRows) {
-      row = 8 * rb + (lane >> 2);
-      kk = 8 * kq + 2 * (lane & 3);
-    } else {
-      row = 8 * rb + (lane & 7);
-      kk = 8 * kq + 2 * (lane >> 3);
-    }
-  };
-  auto load_ri = [&](int c, int (&ri)[32]) {
-    const int kt = kb + c * kKC;
-#pragma unroll
-    for (int p = 0; p < 16; ++p) {
-      int row, kk;
-      pair_at(c, p, row, kk);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int i = m0 + row, kg = kt + kk + h;
-        ri[2 * p + h] = 0;
-        if (i < r && kg < ke) {
-          const ColDesc& cd = i < kg ? sm.rdesc[row] : sm.cdesc[c & 1][kk + h];
-          ri[2 * p + h] = __ldg(relidx + cd.rel + (i < kg ? kg : i));
-        }
-      }
-    }
-  };
-  // the 16 entries of half `half` (pairs 8 half .. 8 half + 7) of chunk c
-  auto gather = [&](int c, int half, const int (&ri)[32], uint4 (&v)[16]) {
-    const int kt = kb + c * kKC;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int p = 8 * half + q;
-      int row, kk;
-      pair_at(c, p, row, kk);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int i = m0 + row, kg = kt + kk + h;
-        v[2 * q + h] = make_uint4(0u, 0u, 0u, 0u);
-        if (i < r && kg < ke)
-          v[2 * q + h] = __ldg(xs + (i < kg ? sm.rdesc[row].col : sm.cdesc[c & 1][kk + h].col) + ri[2 * p + h]);
-      }
-    }
-  };
-  auto stash = [&](int c, int half, const uint4 (&v)[16]) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int row, kk;
-      pair_at(c, 8 * half + q, row, kk);
-      const uint32_t off = core_off(row, kk);
-#pragma unroll
-      for (int tt = 0; tt < kSl; ++tt)
-        *reinterpret_cast<uint32_t*>(sm.a[tt] + off) = pair_slice(v[2 * q], v[2 * q + 1], tt);
-    }
-  };
-
-  long long hi[kTcCols], lo[kTcCols];
-#pragma unroll
-  for (int j = 0; j < kTcCols; ++j) hi[j] = lo[j] = 0;
-  int ri[32];
-  uint4 v[16];
-  if (nck > 0) {
-    load_ri(0, ri);
-    gather(0, 0, ri, v);
-  }
-  for (int c = 0; c < nck; ++c) {
-    const int kt = kb + c * kKC;
-    stash(c, 0, v);
-    gather(c, 1, ri, v);
-    stash(c, 1, v);
-    // B' tile: 16 columns x 32 rows of C, two k-pairs per thread
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int combo = j * 4 + warp, nbk = combo >> 2, kq = combo & 3;
-      const int n = 8 * nbk + (lane >> 2), kk = 8 * kq + 2 * (lane & 3), col = nb + n;
-      uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
-      if (col < s) {
-        if (kt + kk < ke) w0 = __ldg(ls + kt + kk + (int64_t)col * r);
-        if (kt + kk + 1 < ke) w1 = __ldg(ls + kt + kk + 1 + (int64_t)col * r);
-      }
-      const uint32_t off = core_off(n, kk);
-#pragma unroll
-      for (int tt = 0; tt < kSl; ++tt) *reinterpret_cast<uint32_t*>(sm.b[tt] + off) = pair_slice(w0, w1, tt);
-    }
-    if (t < kKC && c + 1 < nck && kt + kKC + t < ke) sm.cdesc[(c + 1) & 1][t] = dk[kt + kKC + t];
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (t == 0) {
-      const uint32_t a0 = smem_u32(sm.a[0]), b0 = smem_u32(sm.b[0]);
-#pragma unroll
-      for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-        for (int ta = 0; ta < kSl; ++ta)
-#pragma unroll
-          for (int u = 0; u + ta < kSl; ++u)
-            tc_mma(tmem + (uint32_t)(kTcCols * (ta + u)), umma_desc(a0 + ta * kTcPlaneA + ks * 256),
-                   umma_desc(b0 + u * kTcPlaneB + ks * 256), (ks | ta) ? 1u : 0u);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                   : "memory");
-    }
-    // next chunk's relative indices and first half of its gathers, in flight during the products
-    if (c + 1 < nck) {
-      load_ri(c + 1, ri);
-      gather(c + 1, 0, ri, v);
-    }
-    const bool ok = mbar_wait(mbar, (uint32_t)(c & 1));
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok) sm.abort = 1;
-    if (ok) {
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
-      for (int gi = 0; gi < kSl; ++gi) {
-        uint32_t rg[16];
-        tc_ld16(taddr + (uint32_t)(kTcCols * gi), rg);
-        const int scale = 1 << (gi < 3 ? 8 * (2 - gi) : 8 * (6 - gi));
-#pragma unroll
-        for (int j = 0; j < kTcCols; ++j) madw(gi < 3 ? hi[j] : lo[j], __float2int_rn(__uint_as_float(rg[j])), scale);
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (sm.abort) break;
-  }
-  if (sm.abort) {
-    if (t == 0) atomicOr(a.status + kEmStatusWord, kEmTimeout);
-  } else {
-    const int row = warp * 32 + lane, i = m0 + row;
-    if (i < r) {
-#pragma unroll
-      for (int j = 0; j < kTcCols; ++j) {
-        const int col = nb + j;
-        if (col < s) {
-          const double val =
-              ldexp((double)hi[j] + (double)lo[j] * 0x1p-32, sm.erow[row] + sm.fcol[j] - 31);
-          if (m.ksplit == 1)
-            ((double*)a.X + b * a.sz.panel + m.panel + s)[i + (int64_t)col * ld] = -val;
-          else
-            ((double*)a.ypart + b * a.sz.ypart + m.ypart + (int64_t)tk.c * r * s)[i + (int64_t)col * r] = val;
-        }
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
-}
-
 }  // namespace
 
 cudaError_t launch_em_split_x(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, cudaStream_t st) {
@@ -861,23 +586,15 @@ cudaError_t setup_em_kernels() {
   if (err != cudaSuccess) return err;
   err = cudaFuncSetAttribute(k_em_split_xck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(int) * kEcRows);
   if (err != cudaSuccess) return err;
-  err = cudaFuncSetAttribute(k_em_gemm1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
-  if (err != cudaSuccess) return err;
   // static shared memory (< 48 KB): prefer the shared-memory carve-out (3 CTAs per SM)
   err = cudaFuncSetAttribute(k_em_gemm1<8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (err != cudaSuccess) return err;
   return cudaFuncSetAttribute(k_em_gemm1<16>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
-cudaError_t launch_em_gemm1(int var, const KArgs& a, const EmArgs& e, const Task* t, int64_t n, cudaStream_t st,
-                            bool tc) {
+cudaError_t launch_em_gemm1(int var, const KArgs& a, const EmArgs& e, const Task* t, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const dim3 grid((unsigned)n, a.sz.batch);
-  if (tc) {  // 128 x 16 tiles only
-    if (var != 1) return cudaErrorInvalidValue;
-    k_em_gemm1_tc<<<grid, kEmThreads, sizeof(TcSmem), st>>>(a, e, t);
-    return cudaGetLastError();
-  }
   switch (var) {  // the emulation's task lists hold 64 x 8 and 64 x 16 tiles only
     case 0: k_em_gemm1<8><<<grid, kEmThreads, 0, st>>>(a, e, t); break;
     case 1: k_em_gemm1<16><<<grid, kEmThreads, 0, st>>>(a, e, t); break;

@@ -95,15 +95,13 @@ inline int pick_variant(int width, bool cplx, int small_cutoff = -1) {
 }
 
 // Step-2 tile width: the FP64 kernel's padding-minimal choice; with the bf16
-// emulation on mma.sync 64 x 16 tiles for every supernode wider than 8
-// columns, on tcgen05 128 x 16 tiles for all.
+// emulation 64 x 16 tiles for every supernode wider than 8 columns.
 inline int step2_variant(int width, bool cplx, const pselinv_opts& o) {
-  if (o.fp64_emulation == 2) return 1;
   if (o.fp64_emulation) return width <= 8 ? 0 : 1;
   return pick_variant(width, cplx, o.small_cutoff);
 }
-// Step-2 tile rows: 128 for the tcgen05 emulation (UMMA M = 128), else 64.
-inline int step2_rows(const pselinv_opts& o) { return o.fp64_emulation == 2 ? 128 : kTileM; }
+// Step-2 tile rows.
+inline int step2_rows(const pselinv_opts&) { return kTileM; }
 
 struct TaskList {
   std::vector<Task> tasks;

@@ -106,11 +106,9 @@ struct EmArgs {
   int64_t n;
 };
 // Emulation status word: kEmRange after an X diagonal <= 0 / not finite or a
-// scaled entry outside its slice range (X not positive definite), kEmTimeout
-// after a bounded mbarrier wait of the tcgen05 kernel ran out.
+// scaled entry outside its slice range (X not positive definite).
 constexpr int kEmStatusWord = 4;
 constexpr int kEmRange = 1;
-constexpr int kEmTimeout = 2;
 // After steps 2-3 of a level: e_p of the level's columns and the slices of
 // its X panels.  Before step 2 of a level: F and the slices of its B'.
 cudaError_t launch_em_split_x(const KArgs& a, const EmArgs& e, const int32_t* sns, int nsn, cudaStream_t st);
@@ -125,11 +123,10 @@ cudaError_t launch_em_split_xck(const KArgs& a, const EmArgs& e, const int32_t* 
 cudaError_t launch_em_gemm2(int var, const KArgs& a, const EmArgs& e, const Task* tasks, int64_t n, cudaStream_t st);
 // Dynamic shared-memory limits of the step-2 kernels (called by setup_kernels).
 cudaError_t setup_em_kernels();
-// Step-2 tiles (the Gemm1 task list of tile variant var) on the slices: tc =
-// false: 64 x 8 / 64 x 16 tiles on mma.sync (var 0, 1); tc = true: 128 x 16
-// tiles on tcgen05 (var 1).
+// Step-2 tiles (the Gemm1 task list of tile variant var) on the slices:
+// 64 x 8 / 64 x 16 tiles on mma.sync (var 0, 1).
 cudaError_t launch_em_gemm1(int var, const KArgs& a, const EmArgs& e, const Task* tasks, int64_t n,
-                            cudaStream_t st, bool tc);
+                            cudaStream_t st);
 
 // ---- persistent per-level schedule (persistent.cu) ----
 struct PArgs {
