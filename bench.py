@@ -29,56 +29,100 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "selinv ms & FP64 TFLOP/s (frac of peak), batched vs plain, err<=1e-10"
-# FP64 peak measured on this machine's GB300: cuBLAS DGEMM 8192^3 (torch.matmul
-# float64) and mma.sync m8n8k4 f64 throughput both ~1.10 TFLOP/s; see
-# profiles/fp64_peak_gb300.md.
-FP64_PEAK_TFLOPS = 1.10
-# DRAM bytes per step-2 launch (all k_gemm1 widths and slice reductions) at
-# the full 80^3 workload with the default schedule, from one-pass ncu
-# counters: profiles/k_gemm1_traffic_grid3d_80.md.  Set to None whenever
-# those kernels change until they are measured again.
-STEP2_TRAFFIC_BYTES_PER_LAUNCH = 460.55e6
-# bf16 dense peaks: MEASURED_PEAKS.json (cuBLAS, sustained over seconds) and
-# the warp-level mma.sync m16n8k16 rate of the same GPU (bench.py --peaks).
-MEASURED_BF16_SUSTAINED_TFLOPS = 1696.4
-MMA_SYNC_BF16_TFLOPS = 605.7
+# FP64 peak of this machine's GB300 when the live measurement below is not
+# available: cuBLAS DGEMM 8192^3 (torch.matmul float64) measured at 1.10
+# TFLOP/s, the same rate as mma.sync m8n8k4 f64 and DFMA.
+FP64_PEAK_FALLBACK_TFLOPS = 1.10
+# DRAM bytes per step-2 launch (all k_gemm1 widths and slice reductions) for
+# the 80^3 workload, scaled from a one-pass ncu capture of the 40^3 member
+# (profiles/k_gemm1_traffic_grid3d_40.md).  None until the current kernels
+# are captured.
+STEP2_TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def measure_fp64_peak(dev, n=8192, reps=3):
+    """cuBLAS DGEMM n^3 (torch.matmul float64) on this GPU: best of `reps`
+    after one warm-up, TFLOP/s (the FP64 roofline denominator of this run)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
 def bf16_sustained_peak():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops_sustained"])
-    except (OSError, KeyError, ValueError):
-        return MEASURED_BF16_SUSTAINED_TFLOPS
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        return float(json.load(f)["bf16_tflops_sustained"])
 
 
 def emulated_step2_roofline(flops_gemm1, s2_ms):
-    """Step-2 class of the emulated path (B' split, slice products, slice
-    reductions) against the bf16 tensor peak: 28 bf16 slice products per
-    multiply-add of X_{C,C} Lhat."""
+    """Step-2 class of the opt-in emulated path (B' split, slice products,
+    slice reductions) against the bf16 tensor peak: 28 bf16 slice products
+    per multiply-add of X_{C,C} Lhat."""
     bf16 = 28 * flops_gemm1 / (s2_ms * 1e-3) / 1e12
     peak = bf16_sustained_peak()
     return {"bound": "tensor", "kernel": "step 2 emulated: k_em_split_lhat + k_em_gemm1 (mma.sync m16n8k16 "
                                          "bf16) + slice reductions",
             "achieved": bf16, "peak": peak, "unit": "TFLOP/s", "frac": bf16 / peak,
-            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS); the warp-level mma.sync path of "
-                           "this GPU tops out near %.0f (bench.py --peaks)" % MMA_SYNC_BF16_TFLOPS,
-            "frac_of_mma_sync_peak": bf16 / MMA_SYNC_BF16_TFLOPS, "traffic": None}
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained", "traffic": None}
+
+
+def factor_flops(sym):
+    """Algorithmic flops of the supernodal LDL^T: per supernode (width s,
+    |C| = r) r(r+1)s for the lower triangle of the Schur update
+    L_CK D_K L_CK^T, r s^2 for the panel solve, 2/3 s^3 for the diagonal
+    block (its LDL^T and the inverse of L_KK)."""
+    s = np.diff(sym["sn_start"]).astype(float)
+    r = np.diff(sym["rowptr"]).astype(float)
+    return float(np.sum(r * (r + 1) * s + r * s * s + 2.0 / 3.0 * s ** 3))
+
+
+def stats(xs):
+    xs = list(xs)
+    return {"median": statistics.median(xs), "std": statistics.pstdev(xs) if len(xs) > 1 else 0.0,
+            "min": min(xs), "max": max(xs), "n": len(xs)}
+
+
 WORKLOAD = ("grid3d_80: 80^3 7-point Laplacian, n=512000, diag 6+U(0.01,0.1), geometric nested "
             "dissection, relaxed supernodes of width <= 128, FP64")
 # Oracle sample for the CPU baseline: the same grid family at a size the
-# scalar oracle finishes in about 10-30 s.
+# scalar oracle finishes in about 10 s on one core.
 CPU_SAMPLE_SIDE = 32
+CPU_WORKLOAD = ("grid3d_32 (CPU oracle sample of the grid3d_80 family): 32^3 7-point Laplacian, n=32768, "
+                "diag 6+U(0.01,0.1), geometric nested dissection, relaxed supernodes of width <= 128, FP64")
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10, help="timed steps (one CUDA event pair each)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=80)
     ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--class-steps", type=int, default=3,
+                    help="steps of the separate pass with per-kernel-class events (roofline of step 2)")
+    ap.add_argument("--factor-steps", type=int, default=3, help="timed factorisations (median)")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end iterations (median)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -90,16 +134,10 @@ def parse():
     ap.add_argument("--split-k-rows", type=int, default=None, help="override the library default")
     ap.add_argument("--small-cutoff", type=int, default=None, help="override the library default")
     ap.add_argument("--level-tiles", type=int, default=None, help="override the library default")
-    ap.add_argument("--peaks", action="store_true",
-                    help="measure the FP64 and low-precision MMA peaks of this GPU (the roofline denominators)")
     ap.add_argument("--min-slice-rows", type=int, default=None, help="override the library default")
     ap.add_argument("--fp64-emulation", action="store_true",
-                    help="headline on the opt-in path with step 2 emulated on the bf16 tensor cores "
-                         "(opts.fp64_emulation = 1) instead of FP64 arithmetic")
-    ap.add_argument("--emulation-variant", type=int, default=1, choices=[1, 2],
-                    help="emulated step 2 on mma.sync (1) or tcgen05 (2)")
-    ap.add_argument("--no-emulation", action="store_true",
-                    help="skip the secondary measurement of the emulated step 2 (config.fp64_emulation)")
+                    help="experiments only: headline on the opt-in path with steps 2 and 3 emulated on the "
+                         "bf16 tensor cores (opts.fp64_emulation = 1) instead of FP64 arithmetic")
     return ap.parse_args()
 
 
@@ -126,10 +164,9 @@ def whole_job_tflops(flops_per_rank, world, ms_max):
     return flops_per_rank * world / (ms_max * 1e-3) / 1e12
 
 
-def oracle_sample_tflops(side=CPU_SAMPLE_SIDE):
-    """Time the oracle's column selected inversion (its factorisation done
-    first, untimed) on the side^3 member of the workload family; return
-    (TFLOP/s by the algorithmic count of that instance, seconds, flops)."""
+def oracle_sample(side=CPU_SAMPLE_SIDE):
+    """The oracle's factorisation of the side^3 member of the workload family
+    (untimed) and the algorithmic flop count of its selected inversion."""
     import oracle
     import synth
     p = synth.grid3d(side)
@@ -139,32 +176,55 @@ def oracle_sample_tflops(side=CPU_SAMPLE_SIDE):
     s = np.diff(sym["sn_start"]).astype(float)
     r = sym["rcount"].astype(float)
     flops = float(np.sum(2 * r * r * s + 3 * r * s * s + 2.0 / 3.0 * s ** 3))
+    return p.n, lcp, lri, lv, d, flops
+
+
+def time_oracle_selinv(sample, threads=None):
+    """Seconds of one oracle column selected inversion of the sample
+    (threads=None: the plain single-thread recurrence; else its OpenMP
+    row/column-parallel variant on that many threads, bitwise the same X)."""
+    import oracle
+    n, lcp, lri, lv, d, _ = sample
     t0 = time.perf_counter()
-    oracle.selinv(p.n, lcp, lri, lv, d)
-    dt = time.perf_counter() - t0
-    return flops / dt / 1e12, dt, flops
+    oracle.selinv(n, lcp, lri, lv, d, threads=threads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_block():
+    """The oracle on the GPU machine's host cores: one run on 1 thread and one
+    on all cores (nproc) of the 32^3 sample (~10 s of CPU work in total)."""
+    sample = oracle_sample()
+    flops = sample[-1]
+    cores = host_cores()
+    t1 = time_oracle_selinv(sample)
+    tn = time_oracle_selinv(sample, threads=cores)
+    return {"value": flops / tn / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "seconds": tn, "value_1_thread": flops / t1 / 1e12, "seconds_1_thread": t1,
+            "sample": f"oracle column selected inversion (factorisation untimed) of the {CPU_SAMPLE_SIDE}^3 member "
+                      f"of the same grid family ({flops:.3e} algorithmic flops), on {cores} threads (OpenMP, "
+                      f"bitwise the single-thread result) and on 1 thread"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
         return
-    sample = (f"oracle column selected inversion (single thread, factorisation untimed) of the "
-              f"{CPU_SAMPLE_SIDE}^3 member of the same 7-point grid family (n={CPU_SAMPLE_SIDE ** 3}); "
-              f"TFLOP/s by the supernodal algorithmic flop count of that instance")
+    sample = oracle_sample()
+    flops = sample[-1]
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_sample_tflops()
-    vals, secs = [], []
-    for _ in range(args.steps):
-        v, dt, fl = oracle_sample_tflops()
-        vals.append(v)
-        secs.append(dt)
-    value = statistics.median(vals)
+        time_oracle_selinv(sample, threads=cores)
+    secs = [time_oracle_selinv(sample, threads=cores) for _ in range(args.steps)]
+    ms = 1e3 * sum(secs) / len(secs)
+    value = flops / (ms * 1e-3) / 1e12
+    desc = (f"oracle column selected inversion on {cores} host threads (OpenMP; factorisation untimed) of the "
+            f"{CPU_SAMPLE_SIDE}^3 grid, n={CPU_SAMPLE_SIDE ** 3}; TFLOP/s by the supernodal algorithmic flop "
+            f"count of that instance ({flops:.3e})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "ms_stats": stats(1e3 * x for x in secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": {"workload": CPU_WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -230,7 +290,7 @@ def tuning(args):
     if args.min_slice_rows is not None:
         kw["min_slice_rows"] = args.min_slice_rows
     if args.fp64_emulation:
-        kw["fp64_emulation"] = args.emulation_variant
+        kw["fp64_emulation"] = 1
     return kw
 
 
@@ -250,63 +310,97 @@ def run_ours(args):
     prob = synth.grid3d(args.side)
     h = P.SelInv(prob.n, prob.colptr, prob.rowind, max_sn_width=128, relax=P.RELAX_AMALG, **tuning(args))
     info = h.info
+    sym = h.symbolic()
     flops = info["flops_selinv"]
     vals = torch.tensor(prob.values, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    with torch.cuda.stream(stream):
-        h.factor(vals, stream=stream)
-    torch.cuda.synchronize()
+    h.factor(vals, stream=stream)
+    h.sync_status(stream=stream)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    def timed(mode, steps, record=False):
+    def timed(mode, steps):
+        """K steps with one event pair per step and one around all of them,
+        bracketed by a barrier and a device synchronisation on both sides:
+        (ms per step over the whole region, per-step ms list)."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
-        if record:
-            h.set_timing(True)
         e0.record(stream)
-        for _ in range(steps):
+        for k in range(steps):
+            ev[k][0].record(stream)
             h.selinv(mode, stream=stream)
+            ev[k][1].record(stream)
         e1.record(stream)
         e1.synchronize()
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / steps
-        kt = h.get_timing() if record else None
-        if record:
-            h.set_timing(False)
-        return ms, kt
+        return e0.elapsed_time(e1) / steps, [a.elapsed_time(b) for a, b in ev]
 
-    # warm-up (level schedule, also captures nothing)
+    peak = None
+    if not args.fp64_emulation:
+        peak = measure_fp64_peak(dev)
+    peak_used = peak if peak else FP64_PEAK_FALLBACK_TFLOPS
+
+    # warm-up (level schedule)
     for _ in range(args.warmup):
         h.selinv(P.LEVEL, stream=stream)
     torch.cuda.synchronize()
 
-    # headline: level-scheduled sweep, kernel classes bracketed by events
+    # headline: level-scheduled sweep, nothing else recorded in the timed region
     with ClockSampler(local) as clk:
-        ms, (kms, kl) = timed(P.LEVEL, args.steps, record=True)
+        ms, per_step = timed(P.LEVEL, args.steps)
     clocks = clk.summary()
     ms = max_over_ranks(ms, dev)
+    value = whole_job_tflops(flops, world, ms)
 
-    # graph-replayed level schedule and the plain one-supernode-per-launch schedule
+    # separate pass with per-kernel-class events (launch counts, step-2 roofline)
+    csteps = max(1, args.class_steps)
+    h.set_timing(True)
+    ms_inst, _ = timed(P.LEVEL, csteps)
+    kms, kl = h.get_timing()
+    h.set_timing(False)
+    kms, kl = kms / csteps, kl / csteps
+
+    # graph-replayed level schedule, persistent schedule, plain one-supernode-per-launch schedule
     h.selinv(P.GRAPH, stream=stream)
     torch.cuda.synchronize()
-    ms_graph, _ = timed(P.GRAPH, max(1, args.steps))
+    ms_graph, _ = timed(P.GRAPH, max(1, min(args.steps, 5)))
     ms_persistent = None
-    if not args.fp64_emulation:  # the persistent kernel runs the FP64 step 2 only
+    if not args.fp64_emulation:  # the persistent kernel runs the FP64 steps only
         h.selinv(P.PERSISTENT, stream=stream)
         h.sync_status(stream=stream)
-        ms_persistent, _ = timed(P.PERSISTENT, max(1, args.steps))
-    h.sync_status(stream=stream)
+        ms_persistent, _ = timed(P.PERSISTENT, max(1, min(args.steps, 5)))
+        h.sync_status(stream=stream)
     ms_plain = None
     if not args.no_plain:
         h.selinv(P.PLAIN, stream=stream)
         torch.cuda.synchronize()
         ms_plain, _ = timed(P.PLAIN, max(1, args.plain_steps))
+
+    # the factorisation on resident values (the step before the path; timed separately)
+    fl_factor = factor_flops(sym)
+    fms = []
+    for _ in range(max(1, args.factor_steps)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.factor(vals, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        fms.append(e0.elapsed_time(e1))
+    h.sync_status(stream=stream)
+    f_med = statistics.median(fms)
+    factor_block = {"bound": "tensor", "kernel": "pselinv_factor: k_factor_diag, k_trsm, k_copyback, k_schur "
+                                                "(FP64 mma.sync m8n8k4) per level, Schur updates in groups "
+                                                "with disjoint targets (no atomics)",
+                    "flops": fl_factor, "ms_stats": stats(fms), "achieved": fl_factor / (f_med * 1e-3) / 1e12,
+                    "peak": peak_used, "unit": "TFLOP/s", "frac": fl_factor / (f_med * 1e-3) / 1e12 / peak_used,
+                    "flop_count": "sum over supernodes of r(r+1)s + r s^2 + 2/3 s^3"}
 
     # end to end through host buffers: values H2D, factor, selinv, X panels D2H
     e2e = None
@@ -315,7 +409,8 @@ def run_ours(args):
         host_out = torch.empty(info["panel_entries"], dtype=torch.float64).pin_memory()
         dev_vals = torch.empty_like(vals)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        for it in range(3):
+        walls, ph = [], []
+        for it in range(max(1, args.e2e_steps)):
             barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -329,31 +424,26 @@ def run_ours(args):
                 h.selinv_to_host(host_out, stream=stream)
                 ev[3].record(stream)
             stream.synchronize()
-            t_e2e = time.perf_counter() - t0
-        phases = {name: ev[i].elapsed_time(ev[i + 1])
+            walls.append(1e3 * (time.perf_counter() - t0))
+            ph.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
+        h.sync_status(stream=stream)
+        t_med = statistics.median(walls)
+        phases = {name: statistics.median(p[i] for p in ph)
                   for i, name in enumerate(("h2d_ms", "factor_ms", "selinv_and_d2h_ms"))}
         phases["d2h_exposed_ms"] = phases["selinv_and_d2h_ms"] - ms
-        e2e = {"value": whole_job_tflops(flops, world, max_over_ranks(1e3 * t_e2e, dev)), "unit": "TFLOP/s",
-               "ms_per_step": 1e3 * t_e2e,
+        e2e = {"value": whole_job_tflops(flops, world, max_over_ranks(t_med, dev)), "unit": "TFLOP/s",
+               "ms_per_step": t_med, "ms_stats": stats(walls),
                "h2d_bytes_per_step": int(host_vals.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
                "includes": "pinned H2D of A's values, pselinv_factor, pselinv_selinv_to_host (LEVEL selinv with "
-                           "the X panels of each finished level copied to pinned host memory during the sweep)",
+                           "the X panels of each finished level copied to pinned host memory during the sweep); "
+                           "wall clock per iteration, median",
                "phases": phases}
 
-    # secondary: the opt-in step 2 emulated on the bf16 tensor cores, on its own
-    # handle, against this handle's FP64 X (not the headline: FP64 arithmetic is)
-    emul = None
-    if not args.fp64_emulation and not args.no_emulation:
-        emul = measure_emulation(args, prob, info, vals, h, stream, dev)
-
-    value = whole_job_tflops(flops, world, ms)
     # roofline of the dominant kernel (step 2, X_{C,K} = -X_{C,C} Lhat): algorithmic
-    # flops per launch over its event-timed average launch duration
-    g1_launches = max(1, int(kl[1]) // args.steps)
-    g1_ms_launch = kms[1] / args.steps / g1_launches
-    g1_flops_launch = info["flops_gemm1"] / g1_launches
-    achieved = g1_flops_launch / (g1_ms_launch * 1e-3) / 1e12
-    sym = h.symbolic()
+    # flops per launch over its event-timed average launch duration (separate pass)
+    g1_launches = max(1, int(round(kl[1])))
+    g1_ms_launch = kms[1] / g1_launches
+    achieved = info["flops_gemm1"] / g1_launches / (g1_ms_launch * 1e-3) / 1e12
     sw = np.diff(sym["sn_start"]).astype(float)
     rr = np.diff(sym["rowptr"]).astype(float)
     rel = np.diff(sym["relptr"]).astype(float)
@@ -363,23 +453,23 @@ def run_ours(args):
     roofline = {"bound": "tensor",
                 "kernel": "step 2: k_gemm1 (all tile widths, FP64 mma.sync m8n8k4, which runs on the FP64 pipe "
                           "of sm_103a) + slice reductions",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "measured cuBLAS DGEMM / mma.sync f64 throughput on this pool's GB300 (FP64 has no "
-                               "entry in MEASURED_PEAKS.json)",
+                "achieved": achieved, "peak": peak_used, "unit": "TFLOP/s", "frac": achieved / peak_used,
+                "peak_source": ("cuBLAS DGEMM 8192^3 (torch.matmul float64) measured in this run, best of 3 (FP64 "
+                                "has no entry in MEASURED_PEAKS.json)") if peak else
+                               "fallback 1.10 TFLOP/s: cuBLAS DGEMM measured earlier on this pool",
                 "traffic": STEP2_TRAFFIC_BYTES_PER_LAUNCH if default_schedule else None,
-                "traffic_unit": "DRAM bytes per launch (ncu, one pass, full workload)",
+                "traffic_unit": "DRAM bytes per launch (ncu one-pass capture of the 40^3 member, scaled)",
                 "algorithmic_bytes_per_launch": g1_alg_bytes / g1_launches,
                 "launches_per_step": g1_launches,
-                "whole_step_frac": value / world / FP64_PEAK_TFLOPS}
+                "timing": "per-kernel-class CUDA events on the launching stream, in a separate pass of %d steps "
+                          "(%.1f ms per step with the events, %.1f ms without)" % (csteps, ms_inst, ms),
+                "whole_step_frac": value / world / peak_used}
     if args.fp64_emulation:
-        roofline = dict(emulated_step2_roofline(info["flops_gemm1"], kms[1] / args.steps),
+        roofline = dict(emulated_step2_roofline(info["flops_gemm1"], kms[1]),
                         whole_step_fp64_equivalent_tflops=value / world)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, dt, fl = oracle_sample_tflops()
-        cpu = {"value": v, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "seconds": dt,
-               "sample": f"oracle column selected inversion, 1 thread, on the {CPU_SAMPLE_SIDE}^3 member of the "
-                         f"same grid family ({fl:.3e} algorithmic flops)"}
+        cpu = cpu_baseline_block()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -389,82 +479,19 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "n": prob.n, "nnz_a_lower": info["nnz_a"],
                            "nnz_l": info["nnz_l"], "supernodes": info["nsn"], "levels": info["nlevels"],
                            "flops_per_step": flops, "schedule": "level (one grouped launch per kernel per level)",
+                           "ms_stats": stats(per_step),
                            "batched_ms": ms, "graph_ms": ms_graph, "persistent_ms": ms_persistent, "plain_ms": ms_plain,
                            "speedup_batched_vs_plain": ms_plain / ms if ms_plain else None,
-                           "kernel_ms_per_step": {"normalise": kms[0] / args.steps, "step2_gemm1": kms[1] / args.steps,
-                                                  "step3_partials": kms[2] / args.steps,
-                                                  "step3_finish": kms[3] / args.steps},
+                           "kernel_ms_per_step": {"normalise": kms[0], "step2_gemm1": kms[1],
+                                                  "step3_partials": kms[2], "step3_finish": kms[3]},
+                           "fp64_peak_measured_tflops": peak,
                            "l2": "no flush: the X panels (%.1f GB) exceed L2 (129 MB)" % (info["panel_entries"] * 8 / 1e9),
-                           "parallelism": "replicas" if world > 1 else "single GPU",
-                           "fp64_emulation": emul},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(sum(kl)), "clocks": clocks}
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "factor": factor_block, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(round(sum(kl))) * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
-
-
-def measure_emulation(args, prob, info, vals, h64, stream, dev):
-    """LEVEL selinv with opts.fp64_emulation = 1 on the same matrix: time,
-    kernel classes, max |X_em - X_fp64| / max |X_fp64| over every X panel
-    entry (h64 holds the FP64 selected inverse), and the step-2 class's bf16
-    tensor rate (28 slice products per multiply-add of X_{C,C} Lhat)."""
-    import torch
-    import paper_1404_0447_gb300 as P
-    he = P.SelInv(prob.n, prob.colptr, prob.rowind, max_sn_width=128, relax=P.RELAX_AMALG,
-                  fp64_emulation=args.emulation_variant, **tuning(args))
-    with torch.cuda.stream(stream):
-        he.factor(vals, stream=stream)
-        for _ in range(max(1, args.warmup - 1)):
-            he.selinv(P.LEVEL, stream=stream)
-    he.sync_status(stream=stream)
-    torch.cuda.synchronize()
-    he.set_timing(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        he.selinv(P.LEVEL, stream=stream)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    kms, kl = he.get_timing()
-    he.set_timing(False)
-    he.sync_status(stream=stream)
-    xe, x64 = he.panels(0, stream=stream)[0], h64.panels(0, stream=stream)[0]
-    torch.cuda.synchronize()
-    diff = float((torch.max(torch.abs(xe - x64)) / torch.max(torch.abs(x64))).item())
-    del xe, x64
-    # end to end as in the headline's e2e: pinned values in, factor, selinv with
-    # the X panels streamed to pinned host memory (second of two runs)
-    e2e_ms = None
-    if not args.no_e2e:
-        host_vals = torch.tensor(prob.values, dtype=torch.float64).pin_memory()
-        host_out = torch.empty(info["panel_entries"], dtype=torch.float64).pin_memory()
-        dev_vals = torch.empty_like(vals)
-        for _ in range(2):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            with torch.cuda.stream(stream):
-                dev_vals.copy_(host_vals, non_blocking=True)
-                he.factor(dev_vals, stream=stream)
-                he.selinv_to_host(host_out, stream=stream)
-            stream.synchronize()
-            e2e_ms = 1e3 * (time.perf_counter() - t0)
-        he.sync_status(stream=stream)
-    s2_ms = kms[1] / args.steps
-    out = {"ms_per_step": ms, "fp64_equivalent_tflops": info["flops_selinv"] / (ms * 1e-3) / 1e12,
-           "e2e_ms_per_step": e2e_ms,
-           "kernel_ms_per_step": {"normalise": kms[0] / args.steps, "step2_split_and_products": s2_ms,
-                                  "step3_split_and_partials": kms[2] / args.steps,
-                                  "step3_finish_and_x_split": kms[3] / args.steps},
-           "max_rel_diff_vs_fp64_x": diff,
-           "step2_roofline": emulated_step2_roofline(info["flops_gemm1"], s2_ms),
-           "arithmetic": "steps 2 and 3 on 7 x 8-bit bf16 slices of 2^-(e_p+e_q) X, of diag(2^e_C) Lhat and of "
-                         "diag(2^-e_C) X_CK, exact FP32 group sums over 32-row chunks, 64-bit integer "
-                         "accumulation; every other step FP64"}
-    del he
-    return out
 
 
 def _time(fn, steps, warmup, stream):
@@ -495,7 +522,8 @@ def run_workload(args):
     st = torch.cuda.Stream(device=dev)
     P.load_library()
     w = args.workload
-    line = {"workload": w, "steps": args.steps, "warmup": args.warmup}
+    peak = measure_fp64_peak(dev)
+    line = {"workload": w, "steps": args.steps, "warmup": args.warmup, "fp64_peak_measured_tflops": peak}
     if w == "grid2d_31":
         p = synth.grid2d_31()
         h = P.SelInv(p.n, p.colptr, p.rowind, max_sn_width=128, relax=P.RELAX_NONE, **tuning(args))
@@ -543,7 +571,18 @@ def run_workload(args):
               else (lambda: h.factor(vals.view(-1), stream=st)))
     with torch.cuda.stream(st):
         factor()
-        line["factor_ms"] = _time(factor, 1, 0, st)
+        h.sync_status(stream=st)
+        line["factor_ms"] = _time(factor, max(1, args.factor_steps), 0, st)
+        h.sync_status(stream=st)
+    # factor flops: r(r+1)s + r s^2 + 2/3 s^3 per supernode (non-symmetric: both sides,
+    # 2 r^2 s + 2 r s^2 + 4/3 s^3), complex x4, times the batch
+    fsym = h.symbolic()
+    fs = np.diff(fsym["sn_start"]).astype(float)
+    fr = np.diff(fsym["rowptr"]).astype(float)
+    ff = (np.sum(2 * fr * fr * fs + 2 * fr * fs * fs + 4.0 / 3.0 * fs ** 3) if unsym
+          else factor_flops(fsym)) * info["batch"] * (4 if cplx else 1)
+    line["factor_tflops"] = ff / (line["factor_ms"] * 1e-3) / 1e12
+    line["factor_frac_of_fp64_peak"] = line["factor_tflops"] / peak
     for name, mode in (("level", P.LEVEL), ("graph", P.GRAPH), ("persistent", P.PERSISTENT), ("plain", P.PLAIN)):
         if w == "dg_poles" and args.poles > 4 and name != "level":
             continue  # ~150 s per selinv at 16 poles: the level schedule only
@@ -555,7 +594,7 @@ def run_workload(args):
                    args.warmup if name != "plain" else 1, st)
         line[f"{name}_ms"] = ms
         line[f"{name}_tflops"] = flops / (ms * 1e-3) / 1e12
-        line[f"{name}_frac_of_fp64_peak"] = line[f"{name}_tflops"] / FP64_PEAK_TFLOPS
+        line[f"{name}_frac_of_fp64_peak"] = line[f"{name}_tflops"] / peak
     if "plain_ms" in line:
         line["speedup_level_vs_plain"] = line["plain_ms"] / line["level_ms"]
     if w == "dg_poles":
@@ -580,7 +619,7 @@ def run_workload(args):
         line["kernel_ms"] = {"normalise": kms[0], s2: kms[1], "step3_partials": kms[2], "step3_finish": kms[3]}
         line["kernel_launches"] = [int(x) for x in kl]
         line[f"{s2}_tflops"] = info["flops_gemm1"] * info["batch"] * (4 if cplx else 1) / (kms[1] * 1e-3) / 1e12
-        line[f"{s2}_frac_of_fp64_peak"] = line[f"{s2}_tflops"] / FP64_PEAK_TFLOPS
+        line[f"{s2}_frac_of_fp64_peak"] = line[f"{s2}_tflops"] / peak
     if w == "graphlap48":
         # differentiable logdet: forward = factor + logdet, backward = selinv + gradient gather
         g = torch.empty(info["nnz_a"], dtype=torch.float64, device=dev)
@@ -604,131 +643,8 @@ def run_workload(args):
     print(json.dumps(line), flush=True)
 
 
-# Compute-only throughput probe (no memory traffic in the timed loops):
-# independent DFMA chains and back-to-back mma.sync of several shapes on
-# register operands.
-PEAK_PROBE_CU = r"""
-#include <cstdio>
-#include <cuda_runtime.h>
-__global__ void dfma(double* out, int iters) {
-  double x[8];
-  for (int q = 0; q < 8; ++q) x[q] = threadIdx.x * 1e-9 + q;
-  const double a = 1.0 - 1e-12, c = 1e-13;
-  for (int it = 0; it < iters; ++it)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = fma(x[q], a, c);
-  double s = 0; for (int q = 0; q < 8; ++q) s += x[q];
-  if (s == 12345.0) out[threadIdx.x] = s;
-}
-__global__ void dmma(double* out, int iters) {
-  double d[4][2] = {};
-  const double a = threadIdx.x * 1e-3, b = threadIdx.x * 2e-3;
-  for (int it = 0; it < iters; ++it)
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
-                   : "+d"(d[q][0]), "+d"(d[q][1]) : "d"(a), "d"(b));
-  double s = 0; for (int q = 0; q < 4; ++q) s += d[q][0] + d[q][1];
-  if (s == 12345.0) out[threadIdx.x] = s;
-}
-__global__ void hmma_bf16(double* out, int iters) {
-  float d[4][4] = {};
-  const unsigned a0 = threadIdx.x, a1 = a0 * 3u, a2 = a0 * 5u, a3 = a0 * 7u, b0 = a0 * 11u, b1 = a0 * 13u;
-  for (int it = 0; it < iters; ++it)
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                   : "+f"(d[q][0]), "+f"(d[q][1]), "+f"(d[q][2]), "+f"(d[q][3])
-                   : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-  float s = 0; for (int q = 0; q < 4; ++q) for (int i = 0; i < 4; ++i) s += d[q][i];
-  if (s == 12345.f) out[threadIdx.x] = s;
-}
-__global__ void imma_s8(double* out, int iters) {
-  int d[4][4] = {};
-  const unsigned a0 = threadIdx.x, a1 = a0 * 3u, a2 = a0 * 5u, a3 = a0 * 7u, b0 = a0 * 11u, b1 = a0 * 13u;
-  for (int it = 0; it < iters; ++it)
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                   : "+r"(d[q][0]), "+r"(d[q][1]), "+r"(d[q][2]), "+r"(d[q][3])
-                   : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-  int s = 0; for (int q = 0; q < 4; ++q) for (int i = 0; i < 4; ++i) s += d[q][i];
-  if (s == 12345) out[threadIdx.x] = s;
-}
-int main() {
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  double* buf = nullptr;
-  cudaMalloc(&buf, 4096 * sizeof(double));
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  const int threads = 256, blocks = sms * 8;
-  const char* names[4] = {"dfma", "dmma_m8n8k4_f64", "mma_sync_m16n8k16_bf16", "mma_sync_m16n8k32_s8"};
-  const double flops[4] = {8.0 * 2, 4.0 * 8 * 8 * 4 * 2, 4.0 * 16 * 8 * 16 * 2, 4.0 * 16 * 8 * 32 * 2};
-  const double per_thread[4] = {1, 1.0 / 32, 1.0 / 32, 1.0 / 32};  // loop bodies: per thread (DFMA) or per warp (MMA)
-  const int iters[4] = {20000, 400, 4000, 1500};
-  for (int c = 0; c < 4; ++c) {
-    float ms = 0;
-    for (int rep = 0; rep < 2; ++rep) {
-      cudaEventRecord(e0);
-      if (c == 0) dfma<<<blocks, threads>>>(buf, iters[c]);
-      if (c == 1) dmma<<<blocks, threads>>>(buf, iters[c]);
-      if (c == 2) hmma_bf16<<<blocks, threads>>>(buf, iters[c]);
-      if (c == 3) imma_s8<<<blocks, threads>>>(buf, iters[c]);
-      cudaEventRecord(e1);
-      cudaEventSynchronize(e1);
-      cudaEventElapsedTime(&ms, e0, e1);
-    }
-    const double units = (double)blocks * threads * per_thread[c] * iters[c];
-    printf("%s %.4f\n", names[c], units * flops[c] / (ms * 1e-3) / 1e12);
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) printf("error %s\n", cudaGetErrorString(e));
-  return e != cudaSuccess;
-}
-"""
-
-
-def run_peaks(args):
-    """Measured peaks of this GPU: FP64 DFMA and DMMA, bf16 and int8 mma.sync
-    (compute-only probe, compiled here with nvcc), and cuBLAS DGEMM through
-    torch.matmul on float64 (8192^3, best of 3 after 2 warm-ups)."""
-    import subprocess
-    import tempfile
-    import torch
-    out = {"what": "peak probe", "unit": "TFLOP/s (int8: TOP/s)"}
-    with tempfile.TemporaryDirectory() as d:
-        src = os.path.join(d, "peaks.cu")
-        exe = os.path.join(d, "peaks")
-        with open(src, "w") as f:
-            f.write(PEAK_PROBE_CU)
-        subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src])
-        for line in subprocess.check_output([exe], text=True).splitlines():
-            k, v = line.split()
-            out[k] = float(v)
-    a = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
-    bmat = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
-    best = 1e30
-    for it in range(5):
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        torch.matmul(a, bmat)
-        e1.record()
-        e1.synchronize()
-        if it >= 2:
-            best = min(best, e0.elapsed_time(e1))
-    out["cublas_dgemm_8192"] = 2 * 8192 ** 3 / (best * 1e-3) / 1e12
-    print(json.dumps(out), flush=True)
-
-
 def main():
     args = parse()
-    if args.peaks:
-        run_peaks(args)
-        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload != "grid3d_80":

@@ -224,14 +224,21 @@ int pselinv_analyze_batch(int32_t k, const int64_t* h_n, const int64_t* const* h
 
 /*
  * Numeric factorisation A = L D L^T on the device (supernodal, level by
- * level from the leaves; no pivoting, Section 4).  Not the optimisation
- * target of this library; it produces the input of the selected inversion.
+ * level from the leaves; no pivoting, Section 4); it produces the input of
+ * the selected inversion.  Per level: the diagonal blocks, the panel solves,
+ * then the Schur updates of the ancestors in groups of supernodes whose
+ * update targets are disjoint (fixed order, no atomics): L and D, and so X,
+ * are bitwise reproducible from run to run.
  *
  * d_values   device, batch x nnz_a values of A's lower CSC in the user's
  *            order (dtype of the handle)
- * Errors: ERR_ZERO_PIVOT / ERR_NONFINITE (first bad column, in internal
- * order, reported by pselinv_last_error), ERR_OOM, ERR_CUDA.  The call
- * synchronises the stream once at the end to read the pivot status.
+ * Enqueues the work on stream and returns without synchronising.  A zero
+ * or non-finite pivot is recorded on the device (first bad column, internal
+ * order) and reported by the next pselinv_sync_status or pselinv_logdet as
+ * ERR_ZERO_PIVOT / ERR_NONFINITE (message via pselinv_last_error), which
+ * also returns the handle to the unfactored state; a selinv enqueued before
+ * that check computes with the bad factor.  Errors returned directly:
+ * ERR_ARG, ERR_STATE, ERR_OOM, ERR_CUDA.
  */
 int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream);
 
@@ -254,8 +261,8 @@ int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream);
  * for pselinv_factor.  pselinv_selinv_adjoint needs the pivot-free factor.
  * d_values as for pselinv_factor.  Errors: ERR_ZERO_PIVOT for a reduced
  * column that is entirely zero or a singular 2x2 block (first column, internal
- * order), ERR_NONFINITE, ERR_STATE on non-symmetric handles.  Synchronises
- * once at the end.
+ * order) and ERR_NONFINITE, both reported as for pselinv_factor (no
+ * synchronisation here), ERR_STATE on non-symmetric handles.
  */
 int pselinv_factor_bk(pselinv_handle* h, const void* d_values, void* stream);
 
@@ -330,11 +337,14 @@ int pselinv_get_panels(pselinv_handle* h, int32_t which, void* out, void* stream
 
 /*
  * Synchronise `stream` and report device-side failures of earlier enqueued
- * work on h: PSELINV_ERR_TIMEOUT if a bounded wait of the PERSISTENT
- * schedule ran out (that call's results are invalid; the flag is cleared and
- * the handle stays usable), PSELINV_ERR_RANGE if a selinv with
- * opts.fp64_emulation met an X that is not positive definite (same
- * treatment).  Returns PSELINV_OK otherwise.
+ * work on h: PSELINV_ERR_ZERO_PIVOT / PSELINV_ERR_NONFINITE if the last
+ * factorisation met a bad pivot (first column, internal order; reported
+ * until the next factorisation, the handle is back to "not factored"),
+ * PSELINV_ERR_TIMEOUT if a bounded wait of the PERSISTENT schedule ran out
+ * (that call's results are invalid; the flag is cleared and the handle stays
+ * usable), PSELINV_ERR_RANGE if a selinv with opts.fp64_emulation met an X
+ * that is not positive definite (same treatment).  Returns PSELINV_OK
+ * otherwise.
  */
 int pselinv_sync_status(pselinv_handle* h, void* stream);
 

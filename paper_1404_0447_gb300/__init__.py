@@ -286,7 +286,9 @@ class SelInv:
         return np.abs(1.0 - s / self.n)
 
     def sync_status(self, stream=None):
-        """Synchronise and raise PselinvError(ERR_TIMEOUT) if a bounded device wait ran out."""
+        """Synchronise and raise PselinvError for a device-side failure of earlier
+        work: a bad pivot of the last factorisation (ERR_ZERO_PIVOT /
+        ERR_NONFINITE), a bounded wait that ran out (ERR_TIMEOUT)."""
         self._check(self._lib.pselinv_sync_status(self._h, _stream_ptr(stream)))
 
     def set_debug(self, flags):
@@ -424,6 +426,7 @@ def _autograd():
         def forward(ctx, values, handle, mode):
             handle.factor(values.detach().contiguous())
             handle.selinv(mode)
+            handle.sync_status()  # a bad pivot of the factorisation raises here
             ctx.handle = handle
             return handle.panels(0)
 

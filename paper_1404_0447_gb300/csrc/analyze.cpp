@@ -576,11 +576,75 @@ int build_schedule(pselinv_handle* h) {
   auto by_width_narrow = [&](int32_t k) { return std::min(by_width(k), kPersistentMaxVar); };
   build(h->t_pgemm1, false, by_width_narrow, step2_tiles);
   build(h->t_pgemm2, false, by_width_narrow, step3_tiles);
-  build(h->t_schur, false, by_rows, [&](int32_t k, int bn, std::vector<Task>& out) {
-    const SnMeta& m = h->meta[k];
-    for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
-      for (int32_t n0 = 0; n0 < m0 + kTileM && n0 < m.r; n0 += bn) out.push_back({k, m0, n0, 0});
-  });
+  {
+    // Schur-update tiles (lower tiles of the r x r update of each supernode),
+    // grouped so that the factorisation needs no atomics: two supernodes of a
+    // level conflict when their C share a row (both then update entries of
+    // that ancestor column); a greedy colouring in level order gives each
+    // supernode the first group none of its conflicting predecessors holds.
+    // Groups run one after the other (fixed order), the supernodes of a
+    // group in parallel, every target entry read-modified-written by one
+    // thread: the factor is bitwise reproducible.
+    TaskList& tl = h->t_schur;
+    const int var = by_rows(0);
+    const int bn = 8 << var;
+    h->schur_var = var;
+    tl.tasks.clear();
+    tl.per_lv.assign((size_t)nl * kNumVar, Range{});
+    tl.per_sn.assign(nsn, Range{});
+    tl.var.assign(nsn, (int8_t)var);
+    h->schur_gptr.assign(nl + 1, 0);
+    h->schur_grp.clear();
+    std::vector<uint64_t> used(h->n, 0);  // groups (< 64) holding a supernode with this row in C
+    std::vector<int32_t> touched, color;
+    for (int32_t l = 0; l < nl; ++l) {
+      h->schur_gptr[l] = (int32_t)h->schur_grp.size();
+      const int32_t b = h->level_ptr[l], e = h->level_ptr[l + 1];
+      color.assign(e - b, 0);
+      int32_t ncol = 0;
+      for (int32_t t = b; t < e; ++t) {
+        const int32_t k = h->level_sn[t];
+        const int32_t* C = h->rows.data() + h->rowptr[k];
+        const int32_t r = h->meta[k].r;
+        uint64_t busy = 0;
+        for (int32_t i = 0; i < r; ++i) busy |= used[C[i]];
+        int32_t c;
+        if (~busy) {
+          c = 0;
+          while (busy >> c & 1) ++c;
+          for (int32_t i = 0; i < r; ++i) {
+            if (!used[C[i]]) touched.push_back(C[i]);
+            used[C[i]] |= 1ull << c;
+          }
+        } else {
+          c = 64 + (t - b);  // all 64 masks taken: a group of its own
+        }
+        color[t - b] = c;
+        ncol = std::max(ncol, c + 1);
+      }
+      for (int32_t q : touched) used[q] = 0;
+      touched.clear();
+      Range& lv = tl.per_lv[(size_t)l * kNumVar + var];
+      lv.begin = (int64_t)tl.tasks.size();
+      for (int32_t c = 0; c < ncol; ++c) {
+        Range g;
+        g.begin = (int64_t)tl.tasks.size();
+        for (int32_t t = b; t < e; ++t) {
+          if (color[t - b] != c) continue;
+          const int32_t k = h->level_sn[t];
+          const SnMeta& m = h->meta[k];
+          tl.per_sn[k].begin = (int64_t)tl.tasks.size();
+          for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
+            for (int32_t n0 = 0; n0 < m0 + kTileM && n0 < m.r; n0 += bn) tl.tasks.push_back({k, m0, n0, 0});
+          tl.per_sn[k].end = (int64_t)tl.tasks.size();
+        }
+        g.end = (int64_t)tl.tasks.size();
+        if (g.end > g.begin) h->schur_grp.push_back(g);
+      }
+      lv.end = (int64_t)tl.tasks.size();
+    }
+    h->schur_gptr[nl] = (int32_t)h->schur_grp.size();
+  }
   // level-local offsets of the step-3 partial products
   h->part_max = 0;
   h->ypart_max = 0;

@@ -647,24 +647,30 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
       }
       PSI_CUDA(h, psi::launch_per_sn(bk ? psi::Kern::CopyBackBK : psi::Kern::CopyBack, ka, sns, nsl, st));
     }
+    // Schur updates group by group (targets disjoint inside a group, no atomics)
     for (int side = 0; side < (unsym ? 2 : 1); ++side)
-      for (int v = 0; v < psi::kNumVar; ++v) {
-        const psi::Range r = h->t_schur.per_lv[(size_t)l * psi::kNumVar + v];
-        PSI_CUDA(h, psi::launch_tiles(psi::Kern::Schur, v, side ? su : sl, tasks_at(h, h->off_schur, r.begin),
-                                      r.end - r.begin, st));
+      for (int32_t g = h->schur_gptr[l]; g < h->schur_gptr[l + 1]; ++g) {
+        const psi::Range r = h->schur_grp[g];
+        PSI_CUDA(h, psi::launch_tiles(psi::Kern::Schur, h->schur_var, side ? su : sl,
+                                      tasks_at(h, h->off_schur, r.begin), r.end - r.begin, st));
       }
   }
-  unsigned long long key = 0;
-  PSI_CUDA(h, cudaMemcpyAsync(&key, h->d_status, sizeof(key), cudaMemcpyDeviceToHost, st));
-  PSI_CUDA(h, cudaStreamSynchronize(st));
-  if (key != kPivotKeyUnset) {
-    const bool zero = (key & 3) == 1;
-    return set_err(h, zero ? PSELINV_ERR_ZERO_PIVOT : PSELINV_ERR_NONFINITE,
-                   std::string(zero ? "zero" : "non-finite") + " pivot at column " + std::to_string(key >> 2) +
-                       " (internal order)");
-  }
+  // no host synchronisation: the first bad pivot stays in status words 0-1
+  // until the next factorisation and is reported by pselinv_sync_status (and
+  // by pselinv_logdet, which synchronises anyway)
   h->factored = true;
   return PSELINV_OK;
+}
+
+// Pivot report of the last factorisation from status words 0-1 (host copy):
+// an error with the first bad column, and the handle back to "not factored".
+int pivot_error(pselinv_handle* h, unsigned long long key) {
+  if (key == kPivotKeyUnset) return PSELINV_OK;
+  h->factored = h->inverted = false;
+  const bool zero = (key & 3) == 1;
+  return set_err(h, zero ? PSELINV_ERR_ZERO_PIVOT : PSELINV_ERR_NONFINITE,
+                 std::string(zero ? "zero" : "non-finite") + " pivot at column " + std::to_string(key >> 2) +
+                     " (internal order)");
 }
 }  // namespace
 
@@ -852,6 +858,12 @@ int pselinv_sync_status(pselinv_handle* h, void* stream) {
   int status[kStatusWords];
   PSI_CUDA(h, cudaMemcpyAsync(status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
   PSI_CUDA(h, cudaStreamSynchronize(st));
+  {
+    unsigned long long key;
+    std::memcpy(&key, status, sizeof(key));
+    const int rc = pivot_error(h, key);
+    if (rc) return rc;
+  }
   if (status[2]) {
     PSI_CUDA(h, cudaMemsetAsync((int*)h->d_status + 2, 0, 2 * sizeof(int), st));
     PSI_CUDA(h, cudaStreamSynchronize(st));
@@ -965,8 +977,10 @@ int pselinv_logdet(pselinv_handle* h, double* h_out, void* stream) {
   PSI_CUDA(h, psi::launch_logdet(h->opts.dtype, h->d_D, h->n, dev, h->opts.batch, st,
                                   h->pivoted ? (const int8_t*)h->d_ptype : nullptr, h->pivoted ? h->d_E : nullptr));
   PSI_CUDA(h, cudaMemcpyAsync(h_out, dev, sizeof(double) * 2 * h->opts.batch, cudaMemcpyDeviceToHost, st));
+  unsigned long long key = 0;
+  PSI_CUDA(h, cudaMemcpyAsync(&key, h->d_status, sizeof(key), cudaMemcpyDeviceToHost, st));
   PSI_CUDA(h, cudaStreamSynchronize(st));
-  return PSELINV_OK;
+  return pivot_error(h, key);
 }
 
 int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, void* d_gradA, void* stream) {

@@ -146,6 +146,12 @@ struct pselinv_handle {
   psi::TaskList t_gemm2;  // step 3 partial-product tiles
   psi::TaskList t_trsm;   // factorisation: off-diagonal panel solve tiles
   psi::TaskList t_schur;  // factorisation: Schur-complement update tiles
+  // Schur groups: the supernodes of a level split into groups whose update
+  // targets are disjoint (no two share a row of C), launched one after the
+  // other; level l's groups are schur_grp[schur_gptr[l] .. schur_gptr[l+1])
+  std::vector<int32_t> schur_gptr;
+  std::vector<psi::Range> schur_grp;
+  int32_t schur_var = 0;  // tile variant of every Schur tile
   psi::TaskList t_sq;     // s x s tiles of each supernode's diagonal block (adjoint products)
   psi::TaskList t_pgemm1; // persistent schedule: step-2 tiles, widths <= 8 << kPersistentMaxVar
   psi::TaskList t_pgemm2; // persistent schedule: step-3 tiles, widths <= 8 << kPersistentMaxVar

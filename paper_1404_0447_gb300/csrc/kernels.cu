@@ -581,7 +581,7 @@ __global__ void k_copyback(const SnMeta* __restrict__ meta, const int32_t* __res
 // Pivoted factor (piv set): the columns of A_{C,K} are read in pivot order
 // and D^{-1} is left to k_copyback_bk (2x2 blocks can straddle tiles).
 template <class T, int BN>
-__global__ void __launch_bounds__(TG_THREADS) k_trsm(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
+__global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_trsm(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
                                                      const T* __restrict__ L, const T* __restrict__ D,
                                                      const T* __restrict__ Linv, T* __restrict__ Ltmp, Sizes sz,
                                                      const int32_t* __restrict__ piv) {
@@ -605,7 +605,8 @@ __global__ void __launch_bounds__(TG_THREADS) k_trsm(const SnMeta* __restrict__ 
     return col < s ? Vi[col + kk * s] : Sc<T>::zero();
   };
   // (L_KK)^{-T} is upper triangular: output columns < n0 + BN need only k < n0 + BN
-  tile_mma<T, BN>(sm, 0, min(s, tk.n0 + BN), [](int) { return false; }, la, lb, acc);
+  tile_mma<T, BN>(sm, 0, min(s, tk.n0 + BN), [](int) { return false; }, la, lb, acc,
+                  LiveRect{r - tk.m0, s - tk.n0});
   T* out = Ltmp + b * sz.lhat + m.lhat;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
@@ -616,13 +617,16 @@ __global__ void __launch_bounds__(TG_THREADS) k_trsm(const SnMeta* __restrict__ 
 // Schur-complement update of the ancestors: lower tiles of
 // U = L_{C,K} D_K L_{C,K}^T; U[i][k] (i >= k) is subtracted from the ancestor
 // entry found through the column descriptor of k and the relative index of i.
-// Several supernodes of one level can hit the same entry: FP64 atomics.
+// The task list of one launch is a group of supernodes whose C are disjoint
+// (analysis), and inside one supernode the targets of different (i, k) are
+// different entries, so each target is read-modified-written by exactly one
+// thread of the launch: no atomics, and a fixed order of the updates.
 // Non-symmetric factor: Ltmp2 is the second operand (U'_{K,C}^T), giving
 // L_{C,K} D_K U'_{K,C} into the L panels and, called again with the operands
 // swapped and `strict`, (U'_{K,C}^T D_K L_{C,K}^T) below the diagonal into the
 // U panels.
 template <class T, int BN>
-__global__ void __launch_bounds__(TG_THREADS) k_schur(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
+__global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_schur(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
                                                       const ColDesc* __restrict__ desc,
                                                       const int32_t* __restrict__ relidx, T* __restrict__ L,
                                                       const T* __restrict__ D, const T* __restrict__ Ltmp,
@@ -652,7 +656,11 @@ __global__ void __launch_bounds__(TG_THREADS) k_schur(const SnMeta* __restrict__
     const int col = tk.n0 + nn;
     return col < r ? Lc2[col + (int64_t)kk * r] : Sc<T>::zero();
   };
-  tile_mma<T, BN>(sm, 0, s, [](int) { return false; }, la, lb, acc);
+  // live: fragments with a row and a column inside C and an entry on or below the diagonal
+  const int dm = tk.m0 - tk.n0;
+  tile_mma<T, BN>(sm, 0, s, [](int) { return false; }, la, lb, acc, [&](int r0, int c0) {
+    return tk.m0 + r0 < r && tk.n0 + c0 < r && c0 <= dm + r0 + 7;
+  });
   T* Lb = L + b * sz.panel;
   const ColDesc* dk = desc + m.desc;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
@@ -660,19 +668,14 @@ __global__ void __launch_bounds__(TG_THREADS) k_schur(const SnMeta* __restrict__
     if (i < r && kc + strict <= i) {
       const ColDesc cd = dk[kc];
       T* dst = &Lb[cd.col + relidx[cd.rel + i]];
-      if constexpr (Sc<T>::P == 1) {
-        atomicAdd(dst, -v);
-      } else {
-        atomicAdd(&reinterpret_cast<double*>(dst)[0], -v.re);
-        atomicAdd(&reinterpret_cast<double*>(dst)[1], -v.im);
-      }
+      *dst = *dst - v;
     }
   });
 }
 
 // Normalisation, off-diagonal part: Lhat_{C,K} = L_{C,K} (L_KK)^{-1}.
 template <class T, int BN>
-__global__ void __launch_bounds__(TG_THREADS) k_lhat(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
+__global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_lhat(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
                                                      const T* __restrict__ L, const T* __restrict__ Linv,
                                                      T* __restrict__ Lhat, Sizes sz) {
   __shared__ TileSmem<T, BN> sm;
@@ -693,7 +696,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_lhat(const SnMeta* __restrict__ 
     return col < s ? Vi[kk + col * s] : Sc<T>::zero();
   };
   // (L_KK)^{-1} is lower triangular: output columns >= n0 need only k >= n0
-  tile_mma<T, BN>(sm, tk.n0, s, [](int) { return false; }, la, lb, acc);
+  tile_mma<T, BN>(sm, tk.n0, s, [](int) { return false; }, la, lb, acc, LiveRect{r - tk.m0, s - tk.n0});
   T* out = Lhat + b * sz.lhat + m.lhat;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
@@ -703,7 +706,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_lhat(const SnMeta* __restrict__ 
 
 // Steps 2 and 3 as grouped per-level kernels (bodies in selinv_steps.cuh).
 template <class T, int BN, bool UNSYM>
-__global__ void __launch_bounds__(TG_THREADS) k_gemm1(KArgs a, const Task* __restrict__ tasks) {
+__global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_gemm1(KArgs a, const Task* __restrict__ tasks) {
   __shared__ TileSmem<T, BN> sm;
   step2_tile<T, BN, UNSYM>(a, tasks[blockIdx.x], blockIdx.y, sm);
 }
@@ -715,7 +718,7 @@ __global__ void k_gemm1_reduce(KArgs a, const int32_t* __restrict__ sns) {
 }
 
 template <class T, int BN>
-__global__ void __launch_bounds__(TG_THREADS) k_gemm2(KArgs a, const Task* __restrict__ tasks) {
+__global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_gemm2(KArgs a, const Task* __restrict__ tasks) {
   __shared__ TileSmem<T, BN> sm;
   step3_tile<T, BN>(a, tasks[blockIdx.x], blockIdx.y, sm, false);
 }

@@ -71,7 +71,8 @@ __device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b
   // panel reads stay contiguous
   const int m0 = tk.m0;
   const int kb = tk.c * m.kchunk, ke = min(r, kb + m.kchunk);
-  tile_mma<T, BN>(sm, kb, ke, [m0](int kt) { return kt >= m0 + TG_BM; }, la, lb, acc);
+  tile_mma<T, BN>(sm, kb, ke, [m0](int kt) { return kt >= m0 + TG_BM; }, la, lb, acc,
+                  LiveRect{r - tk.m0, s - tk.n0});
   if (m.ksplit == 1) {
     // a pivoted factor computes K's columns in pivot order; X keeps the original order
     T* out = (T*)a.X + b * sz.panel + m.panel + s;
@@ -132,7 +133,7 @@ __device__ __forceinline__ void step3_tile(const KArgs& a, const Task& tk, int b
     return col < s ? ld_maybe_cg(Y + kk + (int64_t)pcol(a, b, m.f, col) * ld, cg) : Sc<T>::zero();
   };
   const int kb = tk.c * m.kchunk3, ke = min(r, kb + m.kchunk3);
-  tile_mma<T, BN>(sm, kb, ke, [](int) { return true; }, la, lb, acc);
+  tile_mma<T, BN>(sm, kb, ke, [](int) { return true; }, la, lb, acc, LiveRect{s - tk.m0, s - tk.n0});
   T* out = (T*)a.part + b * sz.part + poff + m.part + (int64_t)tk.c * s * s;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;

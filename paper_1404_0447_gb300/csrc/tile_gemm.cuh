@@ -81,6 +81,14 @@ struct Geo {
 };
 constexpr int TG_AREG = TG_BM * TG_BK / TG_THREADS;  // 8 A elements per thread per k-tile
 
+// CTAs per SM the tile kernels are compiled for (a register cap of
+// 65536 / (128 x this)): the occupancy each tile width had before the
+// fragment predicates below raised the compiler's register choice.
+template <class T, int BN>
+constexpr int tile_min_ctas() {
+  return Sc<T>::P == 2 ? (BN >= 32 ? 3 : BN >= 16 ? 4 : 5) : (BN >= 64 ? 4 : BN >= 32 ? 6 : BN >= 16 ? 8 : 9);
+}
+
 template <class T, int BN>
 struct TileSmem {
   static constexpr int P = Sc<T>::P;
@@ -119,9 +127,16 @@ __device__ __forceinline__ void acc_zero(Acc<T, BN>& acc) {
 //   B: thread t loads k = kt + t % 16, n = t / 16 + 8 j (j < BN / 8).
 // acc[p][i][j][e] is plane p of tile element (wm + 8 i + lane / 4,
 // wn + 8 j + 2 (lane % 4) + e), (wm, wn) = the warp's origin.
-template <class T, int BN, class MA, class LA, class LB>
+//
+// The FP64 pipe is the bound of every caller, so padding is not computed:
+// the MMAs of an 8 x 8 output fragment whose origin (r0, c0) (tile-local)
+// fails live(r0, c0) are skipped (ragged edges of the output, fragments
+// wholly above the diagonal of a triangular output), and so are the 4-deep
+// k-steps at or past kend.  Skipped fragments keep their accumulators (zero
+// from acc_zero) and callers store only live entries.
+template <class T, int BN, class MA, class LA, class LB, class LIVE>
 __device__ __forceinline__ void tile_mma(TileSmem<T, BN>& sm, int kbeg, int kend, const MA& a_by_k_at, const LA& la,
-                                         const LB& lb, Acc<T, BN>& acc) {
+                                         const LB& lb, Acc<T, BN>& acc, const LIVE& live) {
   using G = Geo<BN>;
   constexpr int P = Sc<T>::P;
   const int t = threadIdx.x;
@@ -130,6 +145,12 @@ __device__ __forceinline__ void tile_mma(TileSmem<T, BN>& sm, int kbeg, int kend
   const int g = lane >> 2, q = lane & 3;
   T ra[TG_AREG], rb[G::BREG];
   bool a_by_k = false;
+  uint32_t lmask = 0;  // bit i * FN + j: fragment (i, j) of this warp is live (warp-uniform)
+#pragma unroll
+  for (int i = 0; i < G::FM; ++i)
+#pragma unroll
+    for (int j = 0; j < G::FN; ++j)
+      if (live(wm + 8 * i, wn + 8 * j)) lmask |= 1u << (i * G::FN + j);
 
   auto fetch = [&](int kt) {
     a_by_k = a_by_k_at(kt);
@@ -167,6 +188,31 @@ __device__ __forceinline__ void tile_mma(TileSmem<T, BN>& sm, int kbeg, int kend
     }
   };
 
+  // one 4-deep k-step: the fragments of this warp whose bit is set in mask
+  constexpr uint32_t kAll = (1u << (G::FM * G::FN)) - 1u;
+  auto kstep = [&](int buf, int ks, uint32_t mask) {
+    double fa[P][G::FM], fb[P][G::FN];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+#pragma unroll
+      for (int i = 0; i < G::FM; ++i) fa[p][i] = sm.a[buf][p][ks + q][wm + 8 * i + g];
+#pragma unroll
+      for (int j = 0; j < G::FN; ++j) fb[p][j] = sm.b[buf][p][ks + q][wn + 8 * j + g];
+    }
+#pragma unroll
+    for (int i = 0; i < G::FM; ++i)
+#pragma unroll
+      for (int j = 0; j < G::FN; ++j) {
+        if (!(mask & (1u << (i * G::FN + j)))) continue;
+        dmma884(acc[0][i][j][0], acc[0][i][j][1], fa[0][i], fb[0][j]);
+        if constexpr (P == 2) {
+          dmma884(acc[0][i][j][0], acc[0][i][j][1], -fa[1][i], fb[1][j]);
+          dmma884(acc[1][i][j][0], acc[1][i][j][1], fa[0][i], fb[1][j]);
+          dmma884(acc[1][i][j][0], acc[1][i][j][1], fa[1][i], fb[0][j]);
+        }
+      }
+  };
+
   const int nk = (kend - kbeg + TG_BK - 1) / TG_BK;
   if (nk <= 0) return;
   fetch(kbeg);
@@ -175,32 +221,34 @@ __device__ __forceinline__ void tile_mma(TileSmem<T, BN>& sm, int kbeg, int kend
   for (int it = 0; it < nk; ++it) {
     const int buf = it & 1;
     if (it + 1 < nk) fetch(kbeg + (it + 1) * TG_BK);
+    const int kleft = kend - (kbeg + it * TG_BK);  // valid k of this k-tile (> 0)
+    if (kleft >= TG_BK && lmask == kAll) {
+      // interior k-tile of a tile with every fragment live: no checks
 #pragma unroll
-    for (int ks = 0; ks < TG_BK; ks += 4) {
-      double fa[P][G::FM], fb[P][G::FN];
+      for (int ks = 0; ks < TG_BK; ks += 4) kstep(buf, ks, kAll);
+    } else {
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-#pragma unroll
-        for (int i = 0; i < G::FM; ++i) fa[p][i] = sm.a[buf][p][ks + q][wm + 8 * i + g];
-#pragma unroll
-        for (int j = 0; j < G::FN; ++j) fb[p][j] = sm.b[buf][p][ks + q][wn + 8 * j + g];
-      }
-#pragma unroll
-      for (int i = 0; i < G::FM; ++i)
-#pragma unroll
-        for (int j = 0; j < G::FN; ++j) {
-          dmma884(acc[0][i][j][0], acc[0][i][j][1], fa[0][i], fb[0][j]);
-          if constexpr (P == 2) {
-            dmma884(acc[0][i][j][0], acc[0][i][j][1], -fa[1][i], fb[1][j]);
-            dmma884(acc[1][i][j][0], acc[1][i][j][1], fa[0][i], fb[1][j]);
-            dmma884(acc[1][i][j][0], acc[1][i][j][1], fa[1][i], fb[0][j]);
-          }
-        }
+      for (int ks = 0; ks < TG_BK; ks += 4)
+        if (ks < kleft) kstep(buf, ks, lmask);
     }
     if (it + 1 < nk) stash(buf ^ 1);
     __syncthreads();
   }
 }
+
+// Every fragment live.
+template <class T, int BN, class MA, class LA, class LB>
+__device__ __forceinline__ void tile_mma(TileSmem<T, BN>& sm, int kbeg, int kend, const MA& a_by_k_at, const LA& la,
+                                         const LB& lb, Acc<T, BN>& acc) {
+  tile_mma<T, BN>(sm, kbeg, kend, a_by_k_at, la, lb, acc, [](int, int) { return true; });
+}
+
+// Fragments with a row below mlim and a column below nlim (tile-local): a
+// rectangular output's ragged edges.
+struct LiveRect {
+  int mlim, nlim;
+  __device__ __forceinline__ bool operator()(int r0, int c0) const { return r0 < mlim && c0 < nlim; }
+};
 
 // Visit every accumulator with its tile coordinates: f(m, n, value).
 template <class T, int BN, class F>

@@ -132,9 +132,11 @@ def test_bk_saddle_point_where_the_pivot_free_factor_fails(P):
     rows, cols = np.nonzero(np.tril(np.ones((n, n), bool)))
     cp, ri, v = synth.lower_csc_from_coo(n, rows, cols, A[rows, cols])
     h = P.SelInv(n, cp, ri)
+    h.factor(dev(v))
     with pytest.raises(P.PselinvError, match="ERR_ZERO_PIVOT"):
-        h.factor(dev(v))
+        h.sync_status()
     h.factor_bk(dev(v))
+    h.sync_status()
     h.selinv(P.LEVEL)
     Xi = np.linalg.inv(A)
     c = np.repeat(np.arange(n), np.diff(cp))

@@ -49,8 +49,9 @@ def test_pole_batch_matches_oracle(P, elems, nb, wmax):
 
 def test_conjugate_pole_gives_conjugate_inverse(P):
     """H is real, so X(conj z) = conj(X(z)).  The complex kernels mirror every
-    real operation; only the order of the factorisation's atomic updates may
-    differ between the two members, so they agree to rounding."""
+    real operation (conjugated inputs give negated imaginary parts, rounded
+    symmetrically) and the factorisation runs in a fixed order, so the two
+    members are exact conjugates."""
     n, cp, ri, hv, z = synth.dg_block_matrix((4, 3, 3), 10, 1, seed=7)
     perm = synth.block_nd_order((4, 3, 3), 10)
     zz = np.array([z[0], np.conj(z[0])])
@@ -60,7 +61,7 @@ def test_conjugate_pole_gives_conjugate_inverse(P):
     h.factor(tvals(v2))
     h.selinv(P.GRAPH)
     X = h.panels(0).cpu().numpy()
-    assert np.max(np.abs(X[1] - np.conj(X[0]))) <= 1e-13 * np.max(np.abs(X[0]))
+    assert np.array_equal(X[1], np.conj(X[0]))
 
 
 def test_complex_logdet_and_selected_entries(P):
@@ -113,8 +114,9 @@ def test_pole_sum_and_trace_error_per_pole(P):
 def test_full_size_dg_two_poles_trace_identity_and_batch_equivalence(P):
     """The 12^3-element, 48-dof DG-like matrix (n = 82,944) with its first two
     poles: the trace identity E(z) of Eq. (16) per pole, and the batched run
-    equal to a single-pole run of the same pole (to the rounding of the
-    factorisation's atomic updates)."""
+    bitwise equal to a single-pole run of the same pole (the schedule does
+    not depend on the batch size and the factorisation runs in a fixed
+    order)."""
     import torch
     n, cp, ri, hv, z = synth.dg_block_matrix((12, 12, 12), 48, 16)
     perm = synth.block_nd_order((12, 12, 12), 48)
@@ -133,4 +135,4 @@ def test_full_size_dg_two_poles_trace_identity_and_batch_equivalence(P):
     h1.factor(tvals(vals[1:2]))
     h1.selinv(P.LEVEL)
     x1 = h1.panels(0)[0]
-    assert (torch.max(torch.abs(x1 - x_batch)) / torch.max(torch.abs(x_batch))).item() <= 1e-12
+    assert torch.equal(x1, x_batch)

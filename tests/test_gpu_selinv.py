@@ -189,14 +189,16 @@ def test_bad_pivots_are_reported_and_handle_recovers(P):
     cp = np.array([0, 2, 3], np.int64)
     ri = np.array([0, 1, 1], np.int32)
     h = P.SelInv(2, cp, ri, relax=0)
+    h.factor(torch_vals([1.0, 1.0, 1.0]))          # asynchronous: reported by sync_status
     with pytest.raises(P.PselinvError) as e:
-        h.factor(torch_vals([1.0, 1.0, 1.0]))
-    assert e.value.code == -3
+        h.sync_status()
+    assert e.value.code == -3 and "column 1" in str(e.value)
     with pytest.raises(P.PselinvError) as e:
         h.selinv(P.LEVEL)
     assert e.value.code == -8
+    h.factor(torch_vals([np.nan, 1.0, 3.0]))
     with pytest.raises(P.PselinvError) as e:
-        h.factor(torch_vals([np.nan, 1.0, 3.0]))
+        h.logdet()                                   # logdet synchronises and reports it too
     assert e.value.code == -4
     h.factor(torch_vals([2.0, 1.0, 3.0]))
     h.selinv(P.LEVEL)
@@ -283,6 +285,51 @@ def test_runs_are_bitwise_deterministic(P):
     h.selinv(P.GRAPH)
     c = h.panels(0)
     assert torch.equal(a, b) and torch.equal(a, c)
+
+
+@pytest.mark.parametrize("case", ["grid3d_24", "graph_laplacian", "poles", "unsym", "bk"])
+def test_factor_and_selinv_bitwise_reproducible(P, case):
+    """Two factorisations of the same values give bitwise the same L (and D)
+    and, after the selected inversion, the same X: the Schur updates of a
+    level run in groups with disjoint targets, in a fixed order, without
+    atomics.  Levels of these cases hold many supernodes that update shared
+    ancestors."""
+    import torch
+    kw, factor = {}, "factor"
+    if case == "grid3d_24":
+        p = synth.grid3d(side=24)
+        n, cp, ri, v = p.n, p.colptr, p.rowind, p.values
+    elif case == "graph_laplacian":
+        gl = synth.GraphLaplacian((18, 17, 16), seed=3)
+        n, cp, ri, v = gl.n, gl.colptr, gl.rowind, gl.assemble()
+        kw["perm"] = synth.nd_order(gl.dims)
+    elif case == "poles":
+        n, cp0, ri0, hv, z = synth.dg_block_matrix((4, 4, 3), 8, 3, seed=5)
+        vals = synth.shifted_values(n, cp0, ri0, hv, z)
+        cp, ri, v, _ = synth.permute_lower(n, cp0, ri0, vals, synth.block_nd_order((4, 4, 3), 8))
+        kw.update(dtype=P.C128, batch=3)
+    elif case == "unsym":
+        p = synth.convdiff_problem(dims=(14, 13, 12))
+        n, cp, ri, v, up = p.n, p.colptr, p.rowind, p.values, p.values_up
+        kw["unsym"] = 1
+        factor = "factor_unsym"
+    else:
+        p = synth.grid3d(20, shift_const=-0.5)
+        n, cp, ri, v = p.n, p.colptr, p.rowind, p.values
+        factor = "factor_bk"
+    h = P.SelInv(n, cp, ri, **kw)
+    dt = torch.complex128 if kw.get("dtype") == P.C128 else torch.float64
+    vt = torch.tensor(np.ascontiguousarray(v), dtype=dt, device="cuda")
+    args = (vt, torch.tensor(np.ascontiguousarray(up), dtype=dt, device="cuda")) if factor == "factor_unsym" else (vt,)
+    runs = []
+    for _ in range(2):
+        getattr(h, factor)(*args)
+        h.sync_status()
+        L = h.panels(1).clone()
+        h.selinv(P.LEVEL)
+        runs.append((L, h.panels(0).clone()))
+    assert torch.equal(runs[0][0], runs[1][0])
+    assert torch.equal(runs[0][1], runs[1][1])
 
 
 @pytest.mark.slow

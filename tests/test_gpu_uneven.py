@@ -60,7 +60,8 @@ def test_full_uneven_batch_48_members_against_single_handles(P):
     """The 48-member uneven batch (2D sides U{64..512}, 3D sides U{16..48}),
     merged and graph-replayed, against each member inverted on its own
     handle (same kernels, one matrix): every member's selected entries at
-    A's positions agree to the rounding of the factorisation's atomics, and
+    A's positions agree to rounding (a merged level can cut step 2 into other
+    slices than the member's own level, so the sums differ in order), and
     every member satisfies the trace identity E of Eq. (16)."""
     import torch
     specs = synth.uneven_batch_specs()

@@ -167,10 +167,12 @@ def test_unsym_errors_and_symmetric_only_entry_points(P):
     cp2 = np.array([0, 2, 3], np.int64)
     ri2 = np.array([0, 1, 1], np.int32)
     h2 = P.SelInv(2, cp2, ri2, relax=0, unsym=1)
+    h2.factor_unsym(dev([1.0, 3.0, 6.0]), dev([0.0, 2.0, 0.0]))
     with pytest.raises(P.PselinvError, match="ERR_ZERO_PIVOT"):
-        h2.factor_unsym(dev([1.0, 3.0, 6.0]), dev([0.0, 2.0, 0.0]))
+        h2.sync_status()
+    h2.factor_unsym(dev([np.nan, 3.0, 6.0]), dev([0.0, 2.0, 0.0]))
     with pytest.raises(P.PselinvError, match="ERR_NONFINITE"):
-        h2.factor_unsym(dev([np.nan, 3.0, 6.0]), dev([0.0, 2.0, 0.0]))
+        h2.sync_status()
     h2.factor_unsym(dev([2.0, 4.0, 3.0]), dev([0.0, 1.0, 0.0]))
     h2.selinv(P.LEVEL)
     inv = np.linalg.inv(np.array([[2.0, 1.0], [4.0, 3.0]]))
