@@ -36,16 +36,6 @@ namespace psi {
 enum AdjOp { A_YBAR, A_LHBAR, A_LBAROFF, A_T1, A_Q, A_VPART, A_RPART, A_SYR2K,
              A_DR1, A_DR3, A_DR4, A_DF2, A_DF3, A_DF4 };  // s x s products of the diagonal steps
 
-template <class T>
-__device__ __forceinline__ void atomic_add_t(T* p, T v) {
-  if constexpr (Sc<T>::P == 1) {
-    atomicAdd(p, v);
-  } else {
-    atomicAdd(&reinterpret_cast<double*>(p)[0], v.re);
-    atomicAdd(&reinterpret_cast<double*>(p)[1], v.im);
-  }
-}
-
 template <class T, int BN, int OP>
 __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* __restrict__ tasks) {
   __shared__ TileSmem<T, BN> sm;
@@ -202,6 +192,8 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       if constexpr (OP == A_DF4) Zs[i + j * s] = v;
     });
   } else {  // A_SYR2K: ancestors' Xb += -(Yb Lhat^T + Lhat Yb^T), lower, diagonal halved
+    // launched per Schur group (supernodes of a level whose C are disjoint):
+    // every target entry is updated by one thread of the launch, no atomics
     auto la1 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Yb[i + (int64_t)t * r] : zero; };
     auto lb1 = [&](int t, int nn) { const int n = n0 + nn; return n < r ? Lh[n + (int64_t)t * r] : zero; };
     tile_mma<T, BN>(sm, 0, s, none, la1, lb1, acc);
@@ -212,7 +204,8 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       const int i = m0 + mm, kc = n0 + nn;
       if (i < r && kc <= i) {
         const ColDesc cd = dk[kc];
-        atomic_add_t(&Xb[cd.col + rel[cd.rel + i]], (i == kc ? -0.5 : -1.0) * v);
+        T* dst = &Xb[cd.col + rel[cd.rel + i]];
+        *dst = *dst + (i == kc ? -0.5 : -1.0) * v;
       }
     });
   }

@@ -1045,7 +1045,11 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
     PSI_CUDA(h, tiles(AdjKern::Ybar, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Lhbar, h->t_gemm1, h->off_gemm1, l));  // step-2 slices of C
     if (h->level_split[l]) PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::ReduceHb, a, sns, nsl, st));
-    PSI_CUDA(h, tiles(AdjKern::Syr2k, h->t_schur, h->off_schur, l));
+    for (int32_t g = h->schur_gptr[l]; g < h->schur_gptr[l + 1]; ++g) {  // disjoint targets per group
+      const psi::Range r = h->schur_grp[g];
+      PSI_CUDA(h, psi::launch_adj_tiles(AdjKern::Syr2k, h->schur_var, a, tasks_at(h, h->off_schur, r.begin),
+                                        r.end - r.begin, st));
+    }
     PSI_CUDA(h, tiles(AdjKern::LbarOff, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Vpart, h->t_gemm2, h->off_gemm2, l));
     PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::SumParts, a, sns, nsl, st));

@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_trsm(c
   };
   // (L_KK)^{-T} is upper triangular: output columns < n0 + BN need only k < n0 + BN
   tile_mma<T, BN>(sm, 0, min(s, tk.n0 + BN), [](int) { return false; }, la, lb, acc,
-                  LiveRect{r - tk.m0, s - tk.n0});
+                  LiveRect{r - tk.m0, s - tk.n0}, KUpperB<BN>{tk.n0});
   T* out = Ltmp + b * sz.lhat + m.lhat;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
@@ -696,7 +696,8 @@ __global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_lhat(c
     return col < s ? Vi[kk + col * s] : Sc<T>::zero();
   };
   // (L_KK)^{-1} is lower triangular: output columns >= n0 need only k >= n0
-  tile_mma<T, BN>(sm, tk.n0, s, [](int) { return false; }, la, lb, acc, LiveRect{r - tk.m0, s - tk.n0});
+  tile_mma<T, BN>(sm, tk.n0, s, [](int) { return false; }, la, lb, acc, LiveRect{r - tk.m0, s - tk.n0},
+                  KLowerB<BN>{tk.n0});
   T* out = Lhat + b * sz.lhat + m.lhat;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;

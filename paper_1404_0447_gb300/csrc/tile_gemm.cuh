@@ -133,10 +133,19 @@ __device__ __forceinline__ void acc_zero(Acc<T, BN>& acc) {
 // fails live(r0, c0) are skipped (ragged edges of the output, fragments
 // wholly above the diagonal of a triangular output), and so are the 4-deep
 // k-steps at or past kend.  Skipped fragments keep their accumulators (zero
-// from acc_zero) and callers store only live entries.
-template <class T, int BN, class MA, class LA, class LB, class LIVE>
+// from acc_zero) and callers store only live entries.  A triangular B
+// operand adds klive: klive.frag(kk, c0) is false when B is zero on rows
+// kk..kk+3 for the fragment's columns, and klive.all(kt) is true when no
+// fragment has such zero rows in the k-tile [kt, kt + 16).
+struct KAllLive {
+  __device__ __forceinline__ bool all(int) const { return true; }
+  __device__ __forceinline__ bool frag(int, int) const { return true; }
+};
+
+template <class T, int BN, class MA, class LA, class LB, class LIVE, class KLIVE = KAllLive>
 __device__ __forceinline__ void tile_mma(TileSmem<T, BN>& sm, int kbeg, int kend, const MA& a_by_k_at, const LA& la,
-                                         const LB& lb, Acc<T, BN>& acc, const LIVE& live) {
+                                         const LB& lb, Acc<T, BN>& acc, const LIVE& live,
+                                         const KLIVE& klive = KAllLive{}) {
   using G = Geo<BN>;
   constexpr int P = Sc<T>::P;
   const int t = threadIdx.x;
@@ -221,15 +230,24 @@ __device__ __forceinline__ void tile_mma(TileSmem<T, BN>& sm, int kbeg, int kend
   for (int it = 0; it < nk; ++it) {
     const int buf = it & 1;
     if (it + 1 < nk) fetch(kbeg + (it + 1) * TG_BK);
-    const int kleft = kend - (kbeg + it * TG_BK);  // valid k of this k-tile (> 0)
-    if (kleft >= TG_BK && lmask == kAll) {
+    const int kt = kbeg + it * TG_BK;
+    const int kleft = kend - kt;  // valid k of this k-tile (> 0)
+    if (kleft >= TG_BK && lmask == kAll && klive.all(kt)) {
       // interior k-tile of a tile with every fragment live: no checks
 #pragma unroll
       for (int ks = 0; ks < TG_BK; ks += 4) kstep(buf, ks, kAll);
     } else {
 #pragma unroll
-      for (int ks = 0; ks < TG_BK; ks += 4)
-        if (ks < kleft) kstep(buf, ks, lmask);
+      for (int ks = 0; ks < TG_BK; ks += 4) {
+        if (ks >= kleft) continue;
+        uint32_t m = lmask;
+#pragma unroll
+        for (int j = 0; j < G::FN; ++j)
+          if (!klive.frag(kt + ks, wn + 8 * j))
+#pragma unroll
+            for (int i = 0; i < G::FM; ++i) m &= ~(1u << (i * G::FN + j));
+        kstep(buf, ks, m);
+      }
     }
     if (it + 1 < nk) stash(buf ^ 1);
     __syncthreads();
@@ -248,6 +266,23 @@ __device__ __forceinline__ void tile_mma(TileSmem<T, BN>& sm, int kbeg, int kend
 struct LiveRect {
   int mlim, nlim;
   __device__ __forceinline__ bool operator()(int r0, int c0) const { return r0 < mlim && c0 < nlim; }
+};
+
+// B lower triangular in (k, global column): B[k][n] = 0 for k < n; n0 = the
+// tile's first column.
+template <int BN>
+struct KLowerB {
+  int n0;
+  __device__ __forceinline__ bool all(int kt) const { return kt + 3 >= n0 + BN - 8; }
+  __device__ __forceinline__ bool frag(int kk, int c0) const { return kk + 3 >= n0 + c0; }
+};
+
+// B upper triangular in (k, global column): B[k][n] = 0 for k > n.
+template <int BN>
+struct KUpperB {
+  int n0;
+  __device__ __forceinline__ bool all(int kt) const { return kt + TG_BK - 4 <= n0 + 7; }
+  __device__ __forceinline__ bool frag(int kk, int c0) const { return kk <= n0 + c0 + 7; }
 };
 
 // Visit every accumulator with its tile coordinates: f(m, n, value).
