@@ -543,7 +543,7 @@ int build_schedule(pselinv_handle* h) {
       }
   };
   auto by_width = [&](int32_t k) { return pick_variant(h->meta[k].s, cplx, o.small_cutoff); };
-  auto by_rows = [&](int32_t) { return cplx ? 2 : 3; };
+  auto by_rows = [&](int32_t) { return 2; };  // Schur tiles 64 x 32 (short tiles: small last wave)
   auto rect = [&](int32_t k, int bn, std::vector<Task>& out) {  // r x s output tiles
     const SnMeta& m = h->meta[k];
     for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)

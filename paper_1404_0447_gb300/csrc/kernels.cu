@@ -109,10 +109,61 @@ __device__ void unit_lower_inverse(const T* Tp, int s, T* V) {
   }
 }
 
+// V = (L_KK)^{-1} for the unit lower triangle held packed in Tp (shared
+// memory), by 16 x 16 blocks so that the whole CTA works at every step:
+// first the diagonal blocks V_ii = (L_ii)^{-1} (one column per thread),
+// then, for block distance d = 1, 2, ... (all block pairs (i, j) with
+// i - j = d at once), S = sum_{k=j}^{i-1} L_ik V_kj and V_ij = -V_ii S.
+// V is written column-major to global memory (ld s, zeros above the
+// diagonal) and read back by the later steps of this CTA; S (shared) holds
+// (ceil(s/16) - 1) blocks of 16 x 16.
+template <class T>
+__device__ void unit_lower_inverse_blocked(const T* Tp, int s, T* V, T* S) {
+  constexpr int B = 16;
+  const int nb = (s + B - 1) / B;
+  const int nt = blockDim.x, t = threadIdx.x;
+  for (int c = t; c < s; c += nt) {
+    const int i1 = min((c / B + 1) * B, s);
+    for (int i = 0; i < c; ++i) V[i + c * s] = Sc<T>::zero();
+    V[c + c * s] = Sc<T>::one();
+    for (int i = c + 1; i < i1; ++i) {
+      T acc = Sc<T>::zero();
+      for (int q = c; q < i; ++q) acc += Tp[pk(i, q, s)] * V[q + c * s];
+      V[i + c * s] = -acc;
+    }
+    for (int i = i1; i < s; ++i) V[i + c * s] = Sc<T>::zero();  // off-diagonal blocks: set below
+  }
+  __syncthreads();
+  for (int d = 1; d < nb; ++d) {
+    const int npair = nb - d;  // pairs (j + d, j), j = 0 .. nb - d - 1
+    for (int e = t; e < npair * B * B; e += nt) {
+      const int j = e / (B * B), rr = (e / B) % B, cc = e % B;
+      const int row = (j + d) * B + rr, col = j * B + cc;
+      T acc = Sc<T>::zero();
+      if (row < s && col < s)
+        for (int q = j * B; q < (j + d) * B; ++q) acc += Tp[pk(row, q, s)] * V[q + col * s];
+      S[e] = acc;
+    }
+    __syncthreads();
+    for (int e = t; e < npair * B * B; e += nt) {
+      const int j = e / (B * B), rr = (e / B) % B, cc = e % B;
+      const int i0 = (j + d) * B, row = i0 + rr, col = j * B + cc;
+      if (row >= s || col >= s) continue;
+      T acc = Sc<T>::zero();
+      for (int q = 0; q <= rr; ++q) acc += V[row + (i0 + q) * s] * S[j * B * B + q * B + cc];
+      V[row + col * s] = -acc;
+    }
+    __syncthreads();
+  }
+}
+
 // Factorisation, one CTA per supernode of the level: right-looking LDL^T of
 // the s x s diagonal block (lower part, already holding A_KK minus all
 // descendant updates) in shared memory; L_KK (unit diagonal implied, d_j on
 // the diagonal slot) back to the panel, d to D, (L_KK)^{-1} to linv.
+// Column step j: u = column j below the diagonal, then L_ij = u_i / d_j and
+// the trailing lower triangle T_ik -= L_ij u_k, one warp per column k (no
+// integer division, only lower-triangle entries visited).
 template <class T>
 __global__ void k_factor_diag(const SnMeta* __restrict__ meta, const int32_t* __restrict__ sns, T* __restrict__ L,
                               T* __restrict__ D, T* __restrict__ Linv, Sizes sz, int* status) {
@@ -122,30 +173,37 @@ __global__ void k_factor_diag(const SnMeta* __restrict__ meta, const int32_t* __
   const int b = blockIdx.y;
   const SnMeta m = meta[k];
   const int s = m.s, ld = m.s + m.r;
+  T* u = Tp + s * (s + 1) / 2;
+  T* S = u + s;
   T* P = L + b * sz.panel + m.panel;
   const int nt = blockDim.x, t = threadIdx.x;
-  for (int e = t; e < s * s; e += nt) {
-    const int i = e % s, j = e / s;
-    if (i >= j) Tp[pk(i, j, s)] = P[i + (int64_t)j * ld];
+  const int lane = t & 31, warp = t >> 5, nw = nt >> 5;
+  for (int j = warp; j < s; j += nw) {
+    const int cb = pk(j, j, s);
+    for (int i = j + lane; i < s; i += 32) Tp[cb + i - j] = P[i + (int64_t)j * ld];
   }
   __syncthreads();
   for (int j = 0; j < s; ++j) {
-    const T d = Tp[pk(j, j, s)];
+    const int cj = pk(j, j, s);
+    const T d = Tp[cj];
     if (t == 0 && Sc<T>::bad(d)) report_pivot(status, m.f + j, Sc<T>::is_zero(d));
-    for (int i = j + 1 + t; i < s; i += nt) Tp[pk(i, j, s)] = Tp[pk(i, j, s)] / d;
+    for (int i = j + 1 + t; i < s; i += nt) {
+      const T v = Tp[cj + i - j];
+      u[i] = v;
+      Tp[cj + i - j] = v / d;
+    }
     __syncthreads();
-    const int w = s - j - 1;
-    for (int e = t; e < w * w; e += nt) {
-      const int ii = j + 1 + e % w, kk = j + 1 + e / w;
-      if (ii >= kk) Tp[pk(ii, kk, s)] -= Tp[pk(ii, j, s)] * Tp[pk(kk, j, s)] * d;
+    for (int kk = j + 1 + warp; kk < s; kk += nw) {
+      const int ck = pk(kk, kk, s);
+      const T uk = u[kk];
+      for (int i = kk + lane; i < s; i += 32) Tp[ck + i - kk] -= Tp[cj + i - j] * uk;
     }
     __syncthreads();
   }
-  T* V = Linv + b * sz.linv + m.linv;
-  unit_lower_inverse(Tp, s, V);
-  for (int e = t; e < s * s; e += nt) {
-    const int i = e % s, j = e / s;
-    if (i >= j) P[i + (int64_t)j * ld] = Tp[pk(i, j, s)];
+  unit_lower_inverse_blocked(Tp, s, Linv + b * sz.linv + m.linv, S);
+  for (int j = warp; j < s; j += nw) {
+    const int cb = pk(j, j, s);
+    for (int i = j + lane; i < s; i += 32) P[i + (int64_t)j * ld] = Tp[cb + i - j];
   }
   for (int j = t; j < s; j += nt) D[b * sz.n + m.f + j] = Tp[pk(j, j, s)];
 }
@@ -844,6 +902,14 @@ static size_t diag_smem(int maxw) {
   return sizeof(T) * ((size_t)maxw * (maxw + 1) / 2 + 2 * (size_t)maxw) + sizeof(int) * (size_t)maxw;
 }
 
+// the symmetric diagonal factorisation: packed lower triangle, the column u,
+// and the 16 x 16 blocks S of the blocked inverse
+template <class T>
+static size_t diag_smem_fd(int maxw) {
+  const size_t nb = (size_t)(maxw + 15) / 16;
+  return sizeof(T) * ((size_t)maxw * (maxw + 1) / 2 + (size_t)maxw + 256 * (nb > 1 ? nb - 1 : 1));
+}
+
 // two packed triangles of the non-symmetric diagonal factorisation
 template <class T>
 static size_t diag_smem_lu(int maxw) {
@@ -853,7 +919,7 @@ static size_t diag_smem_lu(int maxw) {
 template <class T>
 static cudaError_t setup_t() {
   cudaError_t e = cudaFuncSetAttribute(k_factor_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)diag_smem<T>(kMaxWidth));
+                                       (int)diag_smem_fd<T>(kMaxWidth));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_norm_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)diag_smem<T>(kMaxWidth));
@@ -984,7 +1050,7 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
   const dim3 grid(nsn, a.sz.batch);
   switch (k) {
     case Kern::FactorDiag:
-      k_factor_diag<T><<<grid, threads, diag_smem<T>(a.maxw), st>>>(a.meta, sns, (T*)a.L, (T*)a.D, (T*)a.Linv,
+      k_factor_diag<T><<<grid, threads, diag_smem_fd<T>(a.maxw), st>>>(a.meta, sns, (T*)a.L, (T*)a.D, (T*)a.Linv,
                                                                     a.sz, a.status);
       break;
     case Kern::CopyBack:
