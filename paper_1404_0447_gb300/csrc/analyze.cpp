@@ -470,6 +470,9 @@ int build_schedule(pselinv_handle* h) {
       *chunk = ((r + parts - 1) / parts + 15) / 16 * 16;
       return (r + *chunk - 1) / *chunk;
     };
+    h->s2var.assign(h->nsn, 0);
+    h->s3var.assign(h->nsn, 0);
+    h->trvar.assign(h->nsn, 0);
     for (int32_t l = 0; l < h->nlevels; ++l) {
       int64_t t2 = 0, t3 = 0;
       for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
@@ -502,6 +505,34 @@ int build_schedule(pselinv_handle* h) {
           const int32_t rows = std::max<int32_t>(min3, (int32_t)((m.r + m.nchunk * f - 1) / (m.nchunk * f)));
           m.nchunk = slices(m.r, rows, &m.kchunk3);
         }
+      }
+      // A level that still offers fewer tiles than the target (short slices
+      // cannot go below the minimum) takes the narrowest tiles, 64 x 8, for
+      // steps 2 and 3: up to 8x the tiles at the same padding (dead 8 x 8
+      // fragments are skipped), so the few wide supernodes near the root
+      // spread over the SMs.
+      int64_t t2f = 0, t3f = 0;
+      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+        const int32_t k = h->level_sn[t];
+        const SnMeta& m = h->meta[k];
+        h->s2var[k] = (int8_t)step2_variant(m.s, cplx, o);
+        h->s3var[k] = (int8_t)pick_variant(m.s, cplx, o.small_cutoff);
+        const int64_t bn2 = 8 << h->s2var[k], bn3 = 8 << h->s3var[k];
+        t2f += (m.r + step2_rows(o) - 1) / step2_rows(o) * ((m.s + bn2 - 1) / bn2) * m.ksplit;
+        t3f += (int64_t)m.nchunk * ((m.s + kTileM - 1) / kTileM) * ((m.s + bn3 - 1) / bn3);
+      }
+      // the factorisation's panel solve (r x s tiles, k <= s) likewise
+      int64_t ttf = 0;
+      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+        const SnMeta& m = h->meta[h->level_sn[t]];
+        const int64_t bn = 8 << pick_variant(m.s, cplx, o.small_cutoff);
+        ttf += (m.r + kTileM - 1) / kTileM * ((m.s + bn - 1) / bn);
+      }
+      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+        const int32_t k = h->level_sn[t];
+        if (t2f < target && !o.fp64_emulation) h->s2var[k] = 0;
+        if (t3f < target && !o.fp64_emulation) h->s3var[k] = 0;
+        h->trvar[k] = (int8_t)(ttf < target ? 0 : pick_variant(h->meta[k].s, cplx, o.small_cutoff));
       }
     }
   }
@@ -543,7 +574,7 @@ int build_schedule(pselinv_handle* h) {
       }
   };
   auto by_width = [&](int32_t k) { return pick_variant(h->meta[k].s, cplx, o.small_cutoff); };
-  auto by_rows = [&](int32_t) { return 2; };  // Schur tiles 64 x 32 (short tiles: small last wave)
+  auto by_rows = [&](int32_t) { return cplx ? 2 : 3; };
   auto rect = [&](int32_t k, int bn, std::vector<Task>& out) {  // r x s output tiles
     const SnMeta& m = h->meta[k];
     for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
@@ -563,9 +594,9 @@ int build_schedule(pselinv_handle* h) {
       for (int32_t m0 = 0; m0 < m.s; m0 += kTileM)
         for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, c});
   };
-  build(h->t_gemm1, false, [&](int32_t k) { return step2_variant(h->meta[k].s, cplx, o); }, step2_tiles);
-  build(h->t_trsm, false, by_width, rect);
-  build(h->t_gemm2, false, by_width, step3_tiles);
+  build(h->t_gemm1, false, [&](int32_t k) { return (int)h->s2var[k]; }, step2_tiles);
+  build(h->t_trsm, false, [&](int32_t k) { return (int)h->trvar[k]; }, rect);
+  build(h->t_gemm2, false, [&](int32_t k) { return (int)h->s3var[k]; }, step3_tiles);
   build(h->t_sq, false, by_width, [&](int32_t k, int bn, std::vector<Task>& out) {  // s x s, no chunks
     const SnMeta& m = h->meta[k];
     for (int32_t m0 = 0; m0 < m.s; m0 += kTileM)

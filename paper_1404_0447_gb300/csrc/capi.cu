@@ -645,7 +645,10 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
         PSI_CUDA(h, psi::launch_tiles(psi::Kern::Trsm, v, ka, tasks_at(h, h->off_trsm, r.begin), r.end - r.begin,
                                       st));
       }
-      PSI_CUDA(h, psi::launch_per_sn(bk ? psi::Kern::CopyBackBK : psi::Kern::CopyBack, ka, sns, nsl, st));
+      // the pivoted copy-back also divides the scratch by 2x2 blocks of D, which the Schur
+      // update reads: per level; the plain one only fills the panels (nothing in the
+      // factorisation reads L_{C,K} from them): once for all levels, after the loop
+      if (bk) PSI_CUDA(h, psi::launch_per_sn(psi::Kern::CopyBackBK, ka, sns, nsl, st));
     }
     // Schur updates group by group (targets disjoint inside a group, no atomics)
     for (int side = 0; side < (unsym ? 2 : 1); ++side)
@@ -655,6 +658,9 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
                                       tasks_at(h, h->off_schur, r.begin), r.end - r.begin, st));
       }
   }
+  if (!bk)
+    for (int side = 0; side < (unsym ? 2 : 1); ++side)
+      PSI_CUDA(h, psi::launch_per_sn(psi::Kern::CopyBack, side ? au : al, lsn, h->nsn, st));
   // no host synchronisation: the first bad pivot stays in status words 0-1
   // until the next factorisation and is reported by pselinv_sync_status (and
   // by pselinv_logdet, which synchronises anyway)

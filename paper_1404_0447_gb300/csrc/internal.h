@@ -152,6 +152,7 @@ struct pselinv_handle {
   std::vector<int32_t> schur_gptr;
   std::vector<psi::Range> schur_grp;
   int32_t schur_var = 0;  // tile variant of every Schur tile
+  std::vector<int8_t> s2var, s3var, trvar;  // step-2 / step-3 / panel-solve tile variant per supernode
   psi::TaskList t_sq;     // s x s tiles of each supernode's diagonal block (adjoint products)
   psi::TaskList t_pgemm1; // persistent schedule: step-2 tiles, widths <= 8 << kPersistentMaxVar
   psi::TaskList t_pgemm2; // persistent schedule: step-3 tiles, widths <= 8 << kPersistentMaxVar

@@ -183,20 +183,30 @@ __global__ void k_factor_diag(const SnMeta* __restrict__ meta, const int32_t* __
     for (int i = j + lane; i < s; i += 32) Tp[cb + i - j] = P[i + (int64_t)j * ld];
   }
   __syncthreads();
+  // rd[0] = 1 / d_j of the current step: one division per column, by the
+  // thread that last wrote the pivot (thread 0 here, then warp 0 lane 0 of
+  // the update, which owns entry (j+1, j+1))
+  T* rd = S;
+  if (t == 0) rd[0] = Sc<T>::one() / Tp[0];
+  __syncthreads();
   for (int j = 0; j < s; ++j) {
     const int cj = pk(j, j, s);
-    const T d = Tp[cj];
+    const T d = Tp[cj], rdj = rd[0];
     if (t == 0 && Sc<T>::bad(d)) report_pivot(status, m.f + j, Sc<T>::is_zero(d));
     for (int i = j + 1 + t; i < s; i += nt) {
       const T v = Tp[cj + i - j];
       u[i] = v;
-      Tp[cj + i - j] = v / d;
+      Tp[cj + i - j] = v * rdj;
     }
     __syncthreads();
     for (int kk = j + 1 + warp; kk < s; kk += nw) {
       const int ck = pk(kk, kk, s);
       const T uk = u[kk];
-      for (int i = kk + lane; i < s; i += 32) Tp[ck + i - kk] -= Tp[cj + i - j] * uk;
+      for (int i = kk + lane; i < s; i += 32) {
+        const T x = Tp[ck + i - kk] - Tp[cj + i - j] * uk;
+        Tp[ck + i - kk] = x;
+        if (i == j + 1 && kk == j + 1) rd[0] = Sc<T>::one() / x;
+      }
     }
     __syncthreads();
   }
