@@ -676,6 +676,16 @@ int build_schedule(pselinv_handle* h) {
     }
     h->schur_gptr[nl] = (int32_t)h->schur_grp.size();
   }
+  // counters of the split step-2 output tiles (one per (supernode, m-tile, n-tile))
+  h->tctr_total = 0;
+  for (int32_t k = 0; k < nsn; ++k) {
+    SnMeta& m = h->meta[k];
+    m.tctr = (int32_t)h->tctr_total;
+    if (m.ksplit > 1) {
+      const int64_t bn = 8 << h->t_gemm1.var[k];
+      h->tctr_total += (m.r + step2_rows(o) - 1) / step2_rows(o) * ((m.s + bn - 1) / bn);
+    }
+  }
   // level-local offsets of the step-3 partial products
   h->part_max = 0;
   h->ypart_max = 0;

@@ -155,7 +155,7 @@ int ensure_device(pselinv_handle* h) {
 int upload_schedule(pselinv_handle* h) {
   int rc;
   void** old[] = {&h->d_meta, &h->d_tasks, &h->d_part, &h->d_ypart, &h->d_plist, &h->d_pn, &h->d_pctr,
-                   &h->d_yring, &h->d_pring};
+                   &h->d_yring, &h->d_pring, &h->d_tctr};
   for (void** p : old)
     if (*p) {
       cudaFree(*p);
@@ -191,6 +191,8 @@ int upload_schedule(pselinv_handle* h) {
   const int64_t B = h->opts.batch, es = (int64_t)elem_size(h);
   if ((rc = alloc(h, &h->d_part, B * h->part_max * es))) return rc;
   if ((rc = alloc(h, &h->d_ypart, B * h->ypart_max * es))) return rc;
+  if ((rc = alloc(h, &h->d_tctr, (int64_t)sizeof(int) * std::max<int64_t>(1, B * h->tctr_total)))) return rc;
+  PSI_CUDA(h, cudaMemset(h->d_tctr, 0, sizeof(int) * std::max<int64_t>(1, B * h->tctr_total)));
   if ((rc = upload(h, &h->d_plist, h->plist))) return rc;
   std::vector<int32_t> pn(h->pn1);
   pn.insert(pn.end(), h->pn2.begin(), h->pn2.end());
@@ -270,6 +272,8 @@ psi::KArgs kargs(pselinv_handle* h) {
   a.part = h->d_part;
   a.ypart = h->d_ypart;
   a.status = (int*)h->d_status;
+  a.tctr = nullptr;  // step-2 slices reduced by the separate kernel unless a schedule sets it
+  a.tctr_n = h->tctr_total;
   a.sz = sizes(h);
   a.U = h->d_U;
   a.Uinv = h->d_uinv;
@@ -374,9 +378,16 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
                        (const int32_t*)h->d_crow, h->n};
   // one step: the given supernodes, with per-variant task ranges of steps 2 and 3
   // maxr: the largest |C| among the step's supernodes
+  // FP64 step 2 (and step 4): the last slice CTA of each split output tile
+  // sums the slices in order (tile counters); the emulated step 2 keeps the
+  // separate reduction kernel
+  psi::KArgs a2 = a, a4f = a4;
+  if (!emul) {
+    a2.tctr = a4f.tctr = (int*)h->d_tctr;
+  }
   auto step = [&](const int32_t* sns, int nsn_step, const psi::Range* r1, const psi::Range* r2, bool split,
                   int maxr) {
-    int n1 = split ? 1 : 0, n2 = 0, e;
+    int n1 = (split && emul) ? 1 : 0, n2 = 0, e;
     for (int v = 0; v < psi::kNumVar; ++v) {
       n1 += r1[v].end > r1[v].begin;
       n2 += r2[v].end > r2[v].begin;
@@ -390,11 +401,11 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
                                           st)
                    : psi::launch_tiles(Kern::Gemm1, v, ka, tasks_at(h, h->off_gemm1, r1[v].begin),
                                        r1[v].end - r1[v].begin, st);
-        if (split && x == cudaSuccess) x = psi::launch_per_sn(Kern::Gemm1Reduce, ka, sns, nsn_step, st);
+        if (split && emul && x == cudaSuccess) x = psi::launch_per_sn(Kern::Gemm1Reduce, ka, sns, nsn_step, st);
         return x;
       });
     };
-    if ((e = gemm1(a))) return e;
+    if ((e = gemm1(a2))) return e;
     // step 3 partial products; emulated: slices of diag(2^-e_C) X_{C,K} first
     if ((e = tm.run(2, n2 + (emul && n2 > 0 ? 1 : 0), [&] {
            cudaError_t x = emul ? psi::launch_em_split_xck(a, em, sns, nsn_step, maxr, st) : cudaSuccess;
@@ -413,7 +424,7 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
          })))
       return e;
     // step 4 reuses the step-2 partial-product buffer after step 2's reduction
-    return unsym ? gemm1(a4) : PSELINV_OK;
+    return unsym ? gemm1(a4f) : PSELINV_OK;
   };
   if (mode == PSELINV_PLAIN) {
     // one supernode per launch, reverse postorder (descending index)

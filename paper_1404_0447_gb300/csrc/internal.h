@@ -27,7 +27,7 @@ struct SnMeta {
   int32_t kchunk;  // rows of C per step-2 partial product
   int64_t ypart;   // level-local offset of the step-2 partial products (ksplit * r * s)
   int32_t kchunk3; // rows of C per step-3 partial product (nchunk = ceil(r / kchunk3))
-  int32_t pad_;
+  int32_t tctr;    // split step 2: first of this supernode's output-tile counters (per batch member)
 };
 
 // Where column k of X_{C,C} (k-th row of C) lives: element offset of that
@@ -136,6 +136,7 @@ struct pselinv_handle {
   std::vector<int32_t> pn1, pn2;     // step-2 / step-3 tiles per supernode
   int64_t panel_total = 0, lhat_total = 0, linv_total = 0, part_max = 0, ypart_max = 0;
   int64_t nnz_l = 0, max_r = 0;
+  int64_t tctr_total = 0;       // output-tile counters of the split step-2 supernodes (per batch member)
   int32_t max_width = 0;
   double flops_selinv = 0, flops_gemm1 = 0, bytes_selinv = 0;
 
@@ -179,6 +180,7 @@ struct pselinv_handle {
   void* d_linv = nullptr;   // inverses of the diagonal blocks
   void* d_part = nullptr;   // step-3 partial products (level-local)
   void* d_ypart = nullptr;  // step-2 partial products (level-local)
+  void* d_tctr = nullptr;   // int, batch x tctr_total: slices of a step-2 output tile finished (reset to 0)
   void* d_status = nullptr; // device status words
   // Bunch-Kaufman pivoted factor (pselinv_factor_bk), batch x n each
   bool pivoted = false;

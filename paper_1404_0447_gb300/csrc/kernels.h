@@ -39,6 +39,11 @@ struct KArgs {
   void* part;
   void* ypart;
   int* status;
+  // split step 2: per-output-tile counters (batch x tctr_total, zero between
+  // launches); set: the last slice CTA of a tile sums the slices in slice
+  // order and writes X_{C,K} (no separate reduction); nullptr: partials only
+  int* tctr;
+  int64_t tctr_n;  // counters per batch member
   Sizes sz;
   // non-symmetric handles (nullptr / 0 for symmetric ones)
   void* U;     // U panels: U'_{j,i} at panel position (i, j)

@@ -81,10 +81,37 @@ __device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b
       if (row < r && col < s) out[row + (int64_t)pcol(a, b, m.f, col) * ld] = -v;
     });
   } else {
-    T* out = (T*)a.ypart + b * sz.ypart + yoff + m.ypart + (int64_t)tk.c * r * s;
+    T* yp = (T*)a.ypart + b * sz.ypart + yoff + m.ypart;
+    T* out = yp + (int64_t)tk.c * r * s;
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int row = tk.m0 + mm, col = tk.n0 + nn;
       if (row < r && col < s) out[row + (int64_t)col * r] = v;
+    });
+    if (!a.tctr) return;  // a separate kernel sums the slices
+    // The CTA that finishes a tile's last slice sums all slices of the tile in
+    // slice order, its own from registers, and writes X_{C,K}: the same
+    // arithmetic as step2_reduce, without its launch and its pass over HBM.
+    // Its counter goes back to zero for the next sweep.  No CTA waits.
+    __shared__ int last;
+    __threadfence();  // this CTA's partial before the count
+    __syncthreads();
+    int* ctr = a.tctr + (int64_t)b * a.tctr_n + m.tctr + (tk.m0 / TG_BM) * ((s + BN - 1) / BN) + tk.n0 / BN;
+    if (threadIdx.x == 0) {
+      last = atomicAdd(ctr, 1) == m.ksplit - 1;
+      if (last) *ctr = 0;
+      __threadfence();
+    }
+    __syncthreads();
+    if (!last) return;
+    const int64_t rs = (int64_t)r * s;
+    T* xo = (T*)a.X + b * sz.panel + m.panel + s;
+    tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+      const int row = tk.m0 + mm, col = tk.n0 + nn;
+      if (row >= r || col >= s) return;
+      const int64_t e = row + (int64_t)col * r;
+      T sum = tk.c == 0 ? v : ld_cg(yp + e);
+      for (int c = 1; c < m.ksplit; ++c) sum += c == tk.c ? v : ld_cg(yp + c * rs + e);
+      xo[row + (int64_t)pcol(a, b, m.f, col) * ld] = -sum;
     });
   }
 }
