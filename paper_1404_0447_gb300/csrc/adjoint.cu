@@ -195,14 +195,14 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
     // launched per Schur group (supernodes of a level whose C are disjoint):
     // every target entry is updated by one thread of the launch, no atomics
     auto la1 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Yb[i + (int64_t)t * r] : zero; };
-    auto lb1 = [&](int t, int nn) { const int n = n0 + nn; return n < r ? Lh[n + (int64_t)t * r] : zero; };
+    auto lb1 = [&](int t, int nn) { const int n = n0 + nn; return n < tk.c ? Lh[n + (int64_t)t * r] : zero; };
     tile_mma<T, BN>(sm, 0, s, none, la1, lb1, acc);
     auto la2 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Lh[i + (int64_t)t * r] : zero; };
-    auto lb2 = [&](int t, int nn) { const int n = n0 + nn; return n < r ? Yb[n + (int64_t)t * r] : zero; };
+    auto lb2 = [&](int t, int nn) { const int n = n0 + nn; return n < tk.c ? Yb[n + (int64_t)t * r] : zero; };
     tile_mma<T, BN>(sm, 0, s, none, la2, lb2, acc);
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, kc = n0 + nn;
-      if (i < r && kc <= i) {
+      if (i < r && kc < tk.c && kc <= i) {  // tk.c: the Schur tile's column end
         const ColDesc cd = dk[kc];
         T* dst = &Xb[cd.col + rel[cd.rel + i]];
         *dst = *dst + (i == kc ? -0.5 : -1.0) * v;

@@ -625,6 +625,7 @@ int build_schedule(pselinv_handle* h) {
     tl.per_sn.assign(nsn, Range{});
     tl.var.assign(nsn, (int8_t)var);
     h->schur_gptr.assign(nl + 1, 0);
+    h->schur_fptr.assign(nl + 1, 0);
     h->schur_grp.clear();
     std::vector<uint64_t> used(h->n, 0);  // groups (< 64) holding a supernode with this row in C
     std::vector<int32_t> touched, color;
@@ -655,26 +656,42 @@ int build_schedule(pselinv_handle* h) {
       }
       for (int32_t q : touched) used[q] = 0;
       touched.clear();
+      // Each supernode's tiles split at np, the number of rows of C inside its
+      // parent P: "near" tiles (target columns in P, level l - 1) and "far"
+      // tiles (columns above P, levels <= l - 2).  Task.c holds the tile's
+      // column end.  A level's near groups come first, then its far groups.
       Range& lv = tl.per_lv[(size_t)l * kNumVar + var];
       lv.begin = (int64_t)tl.tasks.size();
-      for (int32_t c = 0; c < ncol; ++c) {
-        Range g;
-        g.begin = (int64_t)tl.tasks.size();
-        for (int32_t t = b; t < e; ++t) {
-          if (color[t - b] != c) continue;
-          const int32_t k = h->level_sn[t];
-          const SnMeta& m = h->meta[k];
-          tl.per_sn[k].begin = (int64_t)tl.tasks.size();
-          for (int32_t m0 = 0; m0 < m.r; m0 += kTileM)
-            for (int32_t n0 = 0; n0 < m0 + kTileM && n0 < m.r; n0 += bn) tl.tasks.push_back({k, m0, n0, 0});
-          tl.per_sn[k].end = (int64_t)tl.tasks.size();
+      for (int part = 0; part < 2; ++part) {
+        if (part == 1) h->schur_fptr[l] = (int32_t)h->schur_grp.size();
+        for (int32_t c = 0; c < ncol; ++c) {
+          Range g;
+          g.begin = (int64_t)tl.tasks.size();
+          for (int32_t t = b; t < e; ++t) {
+            if (color[t - b] != c) continue;
+            const int32_t k = h->level_sn[t];
+            const SnMeta& m = h->meta[k];
+            const int32_t* C = h->rows.data() + h->rowptr[k];
+            int32_t np = m.r;
+            const int32_t pk = h->sn_parent[k];
+            if (pk >= 0) {
+              const int32_t pend = h->meta[pk].f + h->meta[pk].s;
+              np = (int32_t)(std::lower_bound(C, C + m.r, pend) - C);
+            }
+            const int32_t c0 = part == 0 ? 0 : np, c1 = part == 0 ? np : m.r;
+            for (int32_t n0 = c0; n0 < c1; n0 += bn) {
+              const int32_t ce = std::min(n0 + bn, c1);
+              for (int32_t m0 = n0 / kTileM * kTileM; m0 < m.r; m0 += kTileM) tl.tasks.push_back({k, m0, n0, ce});
+            }
+          }
+          g.end = (int64_t)tl.tasks.size();
+          if (g.end > g.begin) h->schur_grp.push_back(g);
         }
-        g.end = (int64_t)tl.tasks.size();
-        if (g.end > g.begin) h->schur_grp.push_back(g);
       }
       lv.end = (int64_t)tl.tasks.size();
     }
     h->schur_gptr[nl] = (int32_t)h->schur_grp.size();
+    h->schur_fptr[nl] = h->schur_gptr[nl];
   }
   // counters of the split step-2 output tiles (one per (supernode, m-tile, n-tile))
   h->tctr_total = 0;

@@ -87,6 +87,11 @@ void free_device(pselinv_handle* h) {
   h->xfer_ev.clear();
   if (h->xfer_stream) cudaStreamDestroy((cudaStream_t)h->xfer_stream);
   h->xfer_stream = nullptr;
+  for (void* e : h->fev) cudaEventDestroy((cudaEvent_t)e);
+  h->fev.clear();
+  if (h->fs_hi) cudaStreamDestroy((cudaStream_t)h->fs_hi);
+  if (h->fs_lo) cudaStreamDestroy((cudaStream_t)h->fs_lo);
+  h->fs_hi = h->fs_lo = nullptr;
   h->dev_sym = false;
   h->device_bytes = 0;
 }
@@ -594,6 +599,27 @@ int pselinv_analyze_batch(int32_t k, const int64_t* h_n, const int64_t* const* h
 }  // extern "C"
 
 namespace {
+// The factorisation's two streams (high and low priority) and its events
+// (2 per level + 3), created on first use.
+int ensure_factor_streams(pselinv_handle* h) {
+  if (!h->fs_hi) {
+    int least = 0, greatest = 0;
+    PSI_CUDA(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    cudaStream_t s;
+    PSI_CUDA(h, cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest));
+    h->fs_hi = s;
+    PSI_CUDA(h, cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, least));
+    h->fs_lo = s;
+  }
+  const size_t need = 2 * (size_t)h->nlevels + 3;
+  while (h->fev.size() < need) {
+    cudaEvent_t e;
+    PSI_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->fev.push_back(e);
+  }
+  return PSELINV_OK;
+}
+
 // Supernodal factorisation, level by level from the leaves.  Symmetric:
 // A = L D L^T.  Non-symmetric (d_upper set): A = L D U', the U side running
 // the same panel-solve, copy and Schur kernels through swapped pointers.
@@ -637,8 +663,34 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
     su.Uhat = h->d_lhat;
     su.strict = 1;
   }
+  // Two streams (look-ahead): `hi` (high priority) runs each level's
+  // diagonal blocks, panel solves and "near" Schur tiles (those updating the
+  // parents' columns, which the next level's diagonal blocks need); `lo` runs
+  // the "far" Schur tiles (columns above the parents), so the far update of
+  // level l overlaps the diagonal blocks and panel solves of level l - 1.
+  // Events keep every target's updates in a fixed order: far(l) waits for
+  // the panel solves of l (its operand); near(l) waits for far(l + 1), the
+  // last earlier update of level l - 1's panels.
+  int rc;
+  if ((rc = ensure_factor_streams(h))) return rc;
+  cudaStream_t hi = (cudaStream_t)h->fs_hi, lo = (cudaStream_t)h->fs_lo;
+  cudaEvent_t* ev = (cudaEvent_t*)h->fev.data();  // [0] start, [1 + l] solves of l, [1 + nl + l] far of l
+  const int32_t nl = h->nlevels;
+  PSI_CUDA(h, cudaEventRecord(ev[0], st));
+  PSI_CUDA(h, cudaStreamWaitEvent(hi, ev[0], 0));
+  PSI_CUDA(h, cudaStreamWaitEvent(lo, ev[0], 0));
   const auto* lsn = (const int32_t*)h->d_levelsn;
-  for (int32_t l = h->nlevels - 1; l >= 0; --l) {
+  auto schur = [&](int32_t g0, int32_t g1, cudaStream_t s) -> cudaError_t {
+    for (int side = 0; side < (unsym ? 2 : 1); ++side)
+      for (int32_t g = g0; g < g1; ++g) {  // group by group: disjoint targets inside a group, no atomics
+        const psi::Range r = h->schur_grp[g];
+        cudaError_t e = psi::launch_tiles(psi::Kern::Schur, h->schur_var, side ? su : sl,
+                                          tasks_at(h, h->off_schur, r.begin), r.end - r.begin, s);
+        if (e != cudaSuccess) return e;
+      }
+    return cudaSuccess;
+  };
+  for (int32_t l = nl - 1; l >= 0; --l) {
     const int32_t* sns = lsn + h->level_ptr[l];
     const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
     // a level holding a wide supernode gets wide CTAs: the column steps of the
@@ -648,27 +700,30 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
     PSI_CUDA(h, psi::launch_per_sn(unsym ? psi::Kern::FactorDiagLU
                                          : bk  ? psi::Kern::FactorDiagBK
                                                : psi::Kern::FactorDiag,
-                                   a, sns, nsl, st, wmax >= 64 ? 1024 : 256));
+                                   a, sns, nsl, hi, wmax >= 64 ? 1024 : 256));
     for (int side = 0; side < (unsym ? 2 : 1); ++side) {
       const psi::KArgs& ka = side ? au : al;
       for (int v = 0; v < psi::kNumVar; ++v) {
         const psi::Range r = h->t_trsm.per_lv[(size_t)l * psi::kNumVar + v];
         PSI_CUDA(h, psi::launch_tiles(psi::Kern::Trsm, v, ka, tasks_at(h, h->off_trsm, r.begin), r.end - r.begin,
-                                      st));
+                                      hi));
       }
       // the pivoted copy-back also divides the scratch by 2x2 blocks of D, which the Schur
       // update reads: per level; the plain one only fills the panels (nothing in the
       // factorisation reads L_{C,K} from them): once for all levels, after the loop
-      if (bk) PSI_CUDA(h, psi::launch_per_sn(psi::Kern::CopyBackBK, ka, sns, nsl, st));
+      if (bk) PSI_CUDA(h, psi::launch_per_sn(psi::Kern::CopyBackBK, ka, sns, nsl, hi));
     }
-    // Schur updates group by group (targets disjoint inside a group, no atomics)
-    for (int side = 0; side < (unsym ? 2 : 1); ++side)
-      for (int32_t g = h->schur_gptr[l]; g < h->schur_gptr[l + 1]; ++g) {
-        const psi::Range r = h->schur_grp[g];
-        PSI_CUDA(h, psi::launch_tiles(psi::Kern::Schur, h->schur_var, side ? su : sl,
-                                      tasks_at(h, h->off_schur, r.begin), r.end - r.begin, st));
-      }
+    PSI_CUDA(h, cudaEventRecord(ev[1 + l], hi));
+    PSI_CUDA(h, cudaStreamWaitEvent(lo, ev[1 + l], 0));
+    PSI_CUDA(h, schur(h->schur_fptr[l], h->schur_gptr[l + 1], lo));
+    PSI_CUDA(h, cudaEventRecord(ev[1 + nl + l], lo));
+    if (l + 1 < nl) PSI_CUDA(h, cudaStreamWaitEvent(hi, ev[1 + nl + l + 1], 0));
+    PSI_CUDA(h, schur(h->schur_gptr[l], h->schur_fptr[l], hi));
   }
+  PSI_CUDA(h, cudaEventRecord(ev[1 + 2 * nl], hi));
+  PSI_CUDA(h, cudaStreamWaitEvent(st, ev[1 + 2 * nl], 0));
+  PSI_CUDA(h, cudaEventRecord(ev[2 + 2 * nl], lo));
+  PSI_CUDA(h, cudaStreamWaitEvent(st, ev[2 + 2 * nl], 0));
   if (!bk)
     for (int side = 0; side < (unsym ? 2 : 1); ++side)
       PSI_CUDA(h, psi::launch_per_sn(psi::Kern::CopyBack, side ? au : al, lsn, h->nsn, st));
@@ -1175,7 +1230,7 @@ int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void
   }
   // third coordinate: the per-level tile target of the slice shrinking
   int32_t best_tiles = h->opts.level_tiles;
-  for (int32_t tiles : {4 * 152, 8 * 152, 16 * 152}) {
+  for (int32_t tiles : {16 * 152, 32 * 152, 64 * 152}) {
     if (rc || tiles == (best_tiles > 0 ? best_tiles : psi::kTargetTiles)) continue;
     h->opts.level_tiles = tiles;
     if ((rc = measure(best_split, best_cut, &ms))) break;

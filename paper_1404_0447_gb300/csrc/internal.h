@@ -66,7 +66,7 @@ struct Range {
 constexpr int kMaxWidth = 128;   // widest supernode the kernels accept
 constexpr int kMaxWidthLUComplex = 112;  // complex non-symmetric: two packed triangles in shared memory
 constexpr int kChunkRows = 512;  // rows per step-3 partial product (before the per-level boost)
-constexpr int kTargetTiles = 16 * 152;  // tiles a level should offer the GPU (16 per SM)
+constexpr int kTargetTiles = 64 * 152;  // tiles a level should offer the GPU (64 per SM: short tails)
 constexpr int kMinSlice2 = 128;   // smallest step-2 slice the per-level boost makes
 constexpr int kTileM = 64;       // output tile rows of the grouped GEMMs
 constexpr int kTileN = 64;       // output tile columns
@@ -149,8 +149,10 @@ struct pselinv_handle {
   psi::TaskList t_schur;  // factorisation: Schur-complement update tiles
   // Schur groups: the supernodes of a level split into groups whose update
   // targets are disjoint (no two share a row of C), launched one after the
-  // other; level l's groups are schur_grp[schur_gptr[l] .. schur_gptr[l+1])
-  std::vector<int32_t> schur_gptr;
+  // other; level l's groups are schur_grp[schur_gptr[l] .. schur_gptr[l+1]),
+  // those before schur_fptr[l] updating the parents' columns ("near"), the
+  // rest the columns above the parents ("far")
+  std::vector<int32_t> schur_gptr, schur_fptr;
   std::vector<psi::Range> schur_grp;
   int32_t schur_var = 0;  // tile variant of every Schur tile
   std::vector<int8_t> s2var, s3var, trvar;  // step-2 / step-3 / panel-solve tile variant per supernode
@@ -224,6 +226,10 @@ struct pselinv_handle {
   std::vector<int32_t> xfer_ptr;            // [nlevels + 2]: level l's ranges, then the tail
   void* xfer_stream = nullptr;              // copy stream (cudaStream_t)
   std::vector<void*> xfer_ev;               // [nlevels + 1] cudaEvent_t
+  // factorisation look-ahead: high- and low-priority streams, events
+  void* fs_hi = nullptr;
+  void* fs_lo = nullptr;
+  std::vector<void*> fev;
 
   // optional kernel timing (pselinv_set_timing)
   bool timing = false;

@@ -685,6 +685,7 @@ __global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_trsm(c
 // Schur-complement update of the ancestors: lower tiles of
 // U = L_{C,K} D_K L_{C,K}^T; U[i][k] (i >= k) is subtracted from the ancestor
 // entry found through the column descriptor of k and the relative index of i.
+// Task.c is the tile's column end (a tile covers columns [n0, c) of C).
 // The task list of one launch is a group of supernodes whose C are disjoint
 // (analysis), and inside one supernode the targets of different (i, k) are
 // different entries, so each target is read-modified-written by exactly one
@@ -722,18 +723,18 @@ __global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_schur(
   };
   auto lb = [&](int kk, int nn) {
     const int col = tk.n0 + nn;
-    return col < r ? Lc2[col + (int64_t)kk * r] : Sc<T>::zero();
+    return col < tk.c ? Lc2[col + (int64_t)kk * r] : Sc<T>::zero();
   };
   // live: fragments with a row and a column inside C and an entry on or below the diagonal
   const int dm = tk.m0 - tk.n0;
   tile_mma<T, BN>(sm, 0, s, [](int) { return false; }, la, lb, acc, [&](int r0, int c0) {
-    return tk.m0 + r0 < r && tk.n0 + c0 < r && c0 <= dm + r0 + 7;
+    return tk.m0 + r0 < r && tk.n0 + c0 < tk.c && c0 <= dm + r0 + 7;
   });
   T* Lb = L + b * sz.panel;
   const ColDesc* dk = desc + m.desc;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int i = tk.m0 + mm, kc = tk.n0 + nn;
-    if (i < r && kc + strict <= i) {
+    if (i < r && kc < tk.c && kc + strict <= i) {
       const ColDesc cd = dk[kc];
       T* dst = &Lb[cd.col + relidx[cd.rel + i]];
       *dst = *dst - v;
