@@ -61,13 +61,14 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
   auto none = [](int) { return false; };
   auto by_k = [](int) { return true; };
   auto upper_by_k = [m0](int kt) { return kt >= m0 + TG_BM; };
+  const LiveRect rect{r - m0, s - n0};  // r x s outputs: fragments inside the output
   Acc<T, BN> acc;
   acc_zero<T, BN>(acc);
 
   if constexpr (OP == A_YBAR) {  // Yb = Xb_CK - Lhat Zb
     auto la = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Lh[i + (int64_t)t * r] : zero; };
     auto lb = [&](int t, int nn) { const int n = n0 + nn; return n < s ? Z[t + n * s] : zero; };
-    tile_mma<T, BN>(sm, 0, s, none, la, lb, acc);
+    tile_mma<T, BN>(sm, 0, s, none, la, lb, acc, rect);
     const T* XbCK = Xb + m.panel + s;
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, n = n0 + nn;
@@ -83,12 +84,12 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       return X[cd.col + rel[cd.rel + hi]];
     };
     auto lb1 = [&](int kk, int nn) { const int n = n0 + nn; return n < s ? Yb[kk + (int64_t)n * r] : zero; };
-    tile_mma<T, BN>(sm, kb, ke, upper_by_k, la1, lb1, acc);
+    tile_mma<T, BN>(sm, kb, ke, upper_by_k, la1, lb1, acc, rect);
     if (tk.c == 0) {  // the s-long term rides with the first slice
       const T* Y = X + m.panel + s;
       auto la2 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Y[i + (int64_t)t * ld] : zero; };
       auto lb2 = [&](int t, int nn) { const int n = n0 + nn; return n < s ? Z[n + t * s] : zero; };
-      tile_mma<T, BN>(sm, 0, s, none, la2, lb2, acc);
+      tile_mma<T, BN>(sm, 0, s, none, la2, lb2, acc, rect);
     }
     T* out = m.ksplit == 1 ? Hb : (T*)a.k.ypart + b * sz.ypart + m.ypart + (int64_t)tk.c * r * s;
     const T sign = m.ksplit == 1 ? -Sc<T>::one() : Sc<T>::one();
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
   } else if constexpr (OP == A_LBAROFF) {  // Lb_CK = Hb V^T
     auto la = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Hb[i + (int64_t)t * r] : zero; };
     auto lb = [&](int t, int nn) { const int n = n0 + nn; return n < s ? V[n + t * s] : zero; };
-    tile_mma<T, BN>(sm, 0, s, none, la, lb, acc);
+    tile_mma<T, BN>(sm, 0, min(s, n0 + BN), none, la, lb, acc, rect, KUpperB<BN>{n0});
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, n = n0 + nn;
       if (i < r && n < s) Lb[m.panel + s + i + (int64_t)n * ld] = v;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       return i == kk ? 2.0 * w : w;
     };
     auto lb = [&](int kk, int nn) { const int n = n0 + nn; return n < s ? L[m.panel + s + kk + (int64_t)n * ld] : zero; };
-    tile_mma<T, BN>(sm, kb, ke, upper_by_k, la, lb, acc);
+    tile_mma<T, BN>(sm, kb, ke, upper_by_k, la, lb, acc, rect);
     T* out = m.ksplit == 1 ? Yb : (T*)a.k.ypart + b * sz.ypart + m.ypart + (int64_t)tk.c * r * s;
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, n = n0 + nn;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       return i < r ? Lb[m.panel + s + i + (int64_t)t * ld] / d[t] - Yb[i + (int64_t)t * r] : zero;
     };
     auto lb = [&](int t, int nn) { const int n = n0 + nn; return n < s ? V[t + n * s] : zero; };
-    tile_mma<T, BN>(sm, 0, s, none, la, lb, acc);
+    tile_mma<T, BN>(sm, n0, s, none, la, lb, acc, rect, KLowerB<BN>{n0});
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, n = n0 + nn;
       if (i < r && n < s) Xb[m.panel + s + i + (int64_t)n * ld] = v;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       if (n >= s) return zero;
       return OP == A_VPART ? Hb[kk + (int64_t)n * r] : L[m.panel + s + kk + (int64_t)n * ld];
     };
-    tile_mma<T, BN>(sm, kb, ke, by_k, la, lb, acc);
+    tile_mma<T, BN>(sm, kb, ke, by_k, la, lb, acc, LiveRect{s - m0, s - n0});
     T* out = (T*)a.k.part + b * sz.part + m.part + (int64_t)tk.c * s * s;
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, n = n0 + nn;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       return W[q + j * s];  // DR4, DF2, DF4
     };
     constexpr bool by_k_a = OP == A_DR4 || OP == A_DF2 || OP == A_DF4;
-    tile_mma<T, BN>(sm, 0, s, [](int) { return by_k_a; }, la, lb, acc);
+    tile_mma<T, BN>(sm, 0, s, [](int) { return by_k_a; }, la, lb, acc, LiveRect{s - m0, s - n0});
     // DR1/DR3/DF3 write W and DF4 writes Zb (its inputs W, V are not written in the same launch)
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, j = n0 + nn;
@@ -196,10 +197,12 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
     // every target entry is updated by one thread of the launch, no atomics
     auto la1 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Yb[i + (int64_t)t * r] : zero; };
     auto lb1 = [&](int t, int nn) { const int n = n0 + nn; return n < tk.c ? Lh[n + (int64_t)t * r] : zero; };
-    tile_mma<T, BN>(sm, 0, s, none, la1, lb1, acc);
+    const int dm = m0 - n0;  // fragments with a row inside C, a column below the tile's end, on/below the diagonal
+    auto tri = [&](int r0, int c0) { return m0 + r0 < r && n0 + c0 < tk.c && c0 <= dm + r0 + 7; };
+    tile_mma<T, BN>(sm, 0, s, none, la1, lb1, acc, tri);
     auto la2 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Lh[i + (int64_t)t * r] : zero; };
     auto lb2 = [&](int t, int nn) { const int n = n0 + nn; return n < tk.c ? Yb[n + (int64_t)t * r] : zero; };
-    tile_mma<T, BN>(sm, 0, s, none, la2, lb2, acc);
+    tile_mma<T, BN>(sm, 0, s, none, la2, lb2, acc, tri);
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, kc = n0 + nn;
       if (i < r && kc < tk.c && kc <= i) {  // tk.c: the Schur tile's column end
