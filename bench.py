@@ -629,6 +629,17 @@ def run_workload(args):
         G = torch.randn(info["panel_entries"], dtype=torch.float64, device=dev)
         h.selinv(P.LEVEL, stream=st)
         line["adjoint_ms"] = _time(lambda: h.adjoint(G, stream=st), 3, 1, st)
+        # adjoint work per supernode: r^2 s terms -X_CC Yb, the scatter -(Yb Lhat^T + Lhat Yb^T)
+        # (lower triangle) and (W + W^T) L_CK; r s^2 terms Ybar, Y Zb^T, Hb V^T, L_CK^T Hb, the
+        # solve with V and Q^T L_CK; six s x s products of the diagonal steps
+        asym = h.symbolic()
+        a_s = np.diff(asym["sn_start"]).astype(float)
+        a_r = np.diff(asym["rowptr"]).astype(float)
+        adj_flops = float(np.sum(6 * a_r * a_r * a_s + 2 * a_r * a_s + 10 * a_r * a_s * a_s
+                                 + 6 * a_s * a_s * (a_s + 1)))
+        line["adjoint_flops"] = adj_flops
+        line["adjoint_tflops"] = adj_flops / (line["adjoint_ms"] * 1e-3) / 1e12
+        line["adjoint_frac_of_fp64_peak"] = line["adjoint_tflops"] / peak
     if w == "uneven48":
         # the same members one handle at a time (level schedule each)
         hs = []
