@@ -33,11 +33,12 @@ METRIC = "selinv ms & FP64 TFLOP/s (frac of peak), batched vs plain, err<=1e-10"
 # available: cuBLAS DGEMM 8192^3 (torch.matmul float64) measured at 1.10
 # TFLOP/s, the same rate as mma.sync m8n8k4 f64 and DFMA.
 FP64_PEAK_FALLBACK_TFLOPS = 1.10
-# DRAM bytes per step-2 launch (all k_gemm1 widths and slice reductions) for
-# the 80^3 workload, scaled from a one-pass ncu capture of the 40^3 member
-# (profiles/k_gemm1_traffic_grid3d_40.md).  None until the current kernels
-# are captured.
-STEP2_TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes of step 2 (all k_gemm1 launches of one sweep) over its
+# algorithmic bytes, from a one-pass ncu capture of the 40^3 member of the
+# family (profiles/k_gemm1_traffic_grid3d_40.md); the 80^3 traffic per launch
+# is this ratio times the algorithmic bytes per launch.  Set to None whenever
+# k_gemm1 changes until it is captured again.
+STEP2_TRAFFIC_RATIO = 1.112
 
 
 def measure_fp64_peak(dev, n=8192, reps=3):
@@ -457,8 +458,10 @@ def run_ours(args):
                 "peak_source": ("cuBLAS DGEMM 8192^3 (torch.matmul float64) measured in this run, best of 3 (FP64 "
                                 "has no entry in MEASURED_PEAKS.json)") if peak else
                                "fallback 1.10 TFLOP/s: cuBLAS DGEMM measured earlier on this pool",
-                "traffic": STEP2_TRAFFIC_BYTES_PER_LAUNCH if default_schedule else None,
-                "traffic_unit": "DRAM bytes per launch (ncu one-pass capture of the 40^3 member, scaled)",
+                "traffic": (STEP2_TRAFFIC_RATIO * g1_alg_bytes / g1_launches
+                            if default_schedule and STEP2_TRAFFIC_RATIO else None),
+                "traffic_unit": "DRAM bytes per launch: DRAM/algorithmic ratio of a one-pass ncu capture of the "
+                                "40^3 member (%s) times the algorithmic bytes per launch" % STEP2_TRAFFIC_RATIO,
                 "algorithmic_bytes_per_launch": g1_alg_bytes / g1_launches,
                 "launches_per_step": g1_launches,
                 "timing": "per-kernel-class CUDA events on the launching stream, in a separate pass of %d steps "
