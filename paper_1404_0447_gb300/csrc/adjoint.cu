@@ -29,12 +29,31 @@
 
 #include "internal.h"
 #include "kernels.h"
+#include "selinv_steps.cuh"
 #include "tile_gemm.cuh"
 
 namespace psi {
 
 enum AdjOp { A_YBAR, A_LHBAR, A_LBAROFF, A_T1, A_Q, A_VPART, A_RPART, A_SYR2K,
              A_DR1, A_DR3, A_DR4, A_DF2, A_DF3, A_DF4 };  // s x s products of the diagonal steps
+
+// The last slice CTA of a split (r x s) tile: out = (-)(sum of the slice
+// partials in slice order), its own slice from registers.  Hb = -sum for the
+// reverse sweep, T1 = sum for the LDL^T adjoint.
+template <class T, int BN>
+__device__ __forceinline__ void slice_sum(const Acc<T, BN>& acc, const SnMeta& m, const Task& tk, const T* yp, T* out,
+                                          bool negate) {
+  const int r = m.r, s = m.s;
+  const int64_t rs = (int64_t)r * s;
+  tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
+    const int i = tk.m0 + mm, n = tk.n0 + nn;
+    if (i >= r || n >= s) return;
+    const int64_t e = i + (int64_t)n * r;
+    T sum = tk.c == 0 ? v : ld_cg(yp + e);
+    for (int c = 1; c < m.ksplit; ++c) sum += c == tk.c ? v : ld_cg(yp + c * rs + e);
+    out[e] = negate ? -sum : sum;
+  });
+}
 
 template <class T, int BN, int OP>
 __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* __restrict__ tasks) {
@@ -91,12 +110,14 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       auto lb2 = [&](int t, int nn) { const int n = n0 + nn; return n < s ? Z[n + t * s] : zero; };
       tile_mma<T, BN>(sm, 0, s, none, la2, lb2, acc, rect);
     }
-    T* out = m.ksplit == 1 ? Hb : (T*)a.k.ypart + b * sz.ypart + m.ypart + (int64_t)tk.c * r * s;
+    T* yp = (T*)a.k.ypart + b * sz.ypart + m.ypart;
+    T* out = m.ksplit == 1 ? Hb : yp + (int64_t)tk.c * r * s;
     const T sign = m.ksplit == 1 ? -Sc<T>::one() : Sc<T>::one();
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, n = n0 + nn;
       if (i < r && n < s) out[i + (int64_t)n * r] = sign * v;
     });
+    if (m.ksplit > 1 && a.k.tctr && last_slice<BN>(a.k, m, tk, b)) slice_sum<T, BN>(acc, m, tk, yp, Hb, true);
   } else if constexpr (OP == A_LBAROFF) {  // Lb_CK = Hb V^T
     auto la = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Hb[i + (int64_t)t * r] : zero; };
     auto lb = [&](int t, int nn) { const int n = n0 + nn; return n < s ? V[n + t * s] : zero; };
@@ -117,11 +138,13 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
     };
     auto lb = [&](int kk, int nn) { const int n = n0 + nn; return n < s ? L[m.panel + s + kk + (int64_t)n * ld] : zero; };
     tile_mma<T, BN>(sm, kb, ke, upper_by_k, la, lb, acc, rect);
-    T* out = m.ksplit == 1 ? Yb : (T*)a.k.ypart + b * sz.ypart + m.ypart + (int64_t)tk.c * r * s;
+    T* yp = (T*)a.k.ypart + b * sz.ypart + m.ypart;
+    T* out = m.ksplit == 1 ? Yb : yp + (int64_t)tk.c * r * s;
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, n = n0 + nn;
       if (i < r && n < s) out[i + (int64_t)n * r] = v;
     });
+    if (m.ksplit > 1 && a.k.tctr && last_slice<BN>(a.k, m, tk, b)) slice_sum<T, BN>(acc, m, tk, yp, Yb, false);
   } else if constexpr (OP == A_Q) {  // Q = (Lb_CK E - T1) V -> Fb_CK
     auto la = [&](int mm, int t) {
       const int i = m0 + mm;
@@ -241,28 +264,6 @@ __global__ void k_adj_seed(AdjArgs a) {
       else
         v = i >= j ? G[e] : G[j + (int64_t)i * ld];
       Xb[e] = v;
-    }
-}
-
-// Slice reduction of a split supernode (slices in order: deterministic):
-// Hb = -(sum of the partials) for the reverse sweep, T1 = sum for the
-// LDL^T adjoint; blockIdx.z strides over the columns.
-template <class T, bool HB>
-__global__ void k_adj_reduce(AdjArgs a, const int32_t* __restrict__ sns) {
-  const int k = sns[blockIdx.x], b = blockIdx.y;
-  const Sizes sz = a.k.sz;
-  const SnMeta m = a.k.meta[k];
-  if (m.ksplit == 1) return;
-  const int s = m.s, r = m.r;
-  const T* yp = (const T*)a.k.ypart + b * sz.ypart + m.ypart;
-  T* out = (T*)(HB ? a.Hb : a.Yb) + b * sz.lhat + m.lhat;
-  const int64_t rs = (int64_t)r * s;
-  for (int j = blockIdx.z; j < s; j += gridDim.z)
-    for (int i = threadIdx.x; i < r; i += blockDim.x) {
-      const int64_t e = i + (int64_t)j * r;
-      T acc = yp[e];
-      for (int c = 1; c < m.ksplit; ++c) acc += yp[c * rs + e];
-      out[e] = HB ? -acc : acc;
     }
 }
 
@@ -448,8 +449,6 @@ static cudaError_t adj_sn_t(AdjSn k, const AdjArgs& a, const int32_t* sns, int n
     case AdjSn::Df1: k_adj_df1<T><<<grid, 256, 0, st>>>(a, sns); break;
     case AdjSn::Df5: k_adj_df5<T><<<grid, 256, 0, st>>>(a, sns); break;
     case AdjSn::SumParts: k_adj_sum_parts<T><<<dim3(nsn, a.k.sz.batch, 8), 256, 0, st>>>(a, sns); break;
-    case AdjSn::ReduceHb: k_adj_reduce<T, true><<<dim3(nsn, a.k.sz.batch, 16), 256, 0, st>>>(a, sns); break;
-    case AdjSn::ReduceT1: k_adj_reduce<T, false><<<dim3(nsn, a.k.sz.batch, 16), 256, 0, st>>>(a, sns); break;
     default: break;
   }
   return cudaGetLastError();

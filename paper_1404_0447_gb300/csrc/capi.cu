@@ -1078,6 +1078,7 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
   cudaStream_t st = (cudaStream_t)stream;
   psi::AdjArgs a;
   a.k = kargs(h);
+  a.k.tctr = (int*)h->d_tctr;  // split X_CC Yb and (W + W^T) L_CK summed by their last slice CTA
   a.G = d_G;
   a.g_kind = g_kind;
   a.Xb = h->d_xb;
@@ -1116,7 +1117,6 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
     PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::Zbar, a, sns, nsl, st));
     PSI_CUDA(h, tiles(AdjKern::Ybar, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Lhbar, h->t_gemm1, h->off_gemm1, l));  // step-2 slices of C
-    if (h->level_split[l]) PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::ReduceHb, a, sns, nsl, st));
     for (int32_t g = h->schur_gptr[l]; g < h->schur_gptr[l + 1]; ++g) {  // disjoint targets per group
       const psi::Range r = h->schur_grp[g];
       PSI_CUDA(h, psi::launch_adj_tiles(AdjKern::Syr2k, h->schur_var, a, tasks_at(h, h->off_schur, r.begin),
@@ -1137,7 +1137,6 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
     const int32_t* sns = lsn + h->level_ptr[l];
     const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];
     PSI_CUDA(h, tiles(AdjKern::T1, h->t_gemm1, h->off_gemm1, l));
-    if (h->level_split[l]) PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::ReduceT1, a, sns, nsl, st));
     PSI_CUDA(h, tiles(AdjKern::Q, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Rpart, h->t_gemm2, h->off_gemm2, l));
     PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::SumParts, a, sns, nsl, st));

@@ -173,7 +173,7 @@ struct AdjArgs {
   void* Hb;       // r x s per supernode: Lhat-bar
 };
 enum class AdjKern { Ybar, Lhbar, LbarOff, T1, Q, Vpart, Rpart, Syr2k, Dr1, Dr3, Dr4, Df2, Df3, Df4 };
-enum class AdjSn { Seed, Zbar, Dr2, Df1, Df5, ReduceHb, ReduceT1, SumParts };
+enum class AdjSn { Seed, Zbar, Dr2, Df1, Df5, SumParts };
 cudaError_t launch_adj_tiles(AdjKern k, int var, const AdjArgs& a, const Task* tasks, int64_t n, cudaStream_t st);
 cudaError_t launch_adj_per_sn(AdjSn k, const AdjArgs& a, const int32_t* sns, int nsn, cudaStream_t st);
 

@@ -26,6 +26,25 @@ __device__ __forceinline__ T ld_maybe_cg(const T* p, bool cg) {
   return cg ? ld_cg(p) : *p;
 }
 
+// Split tiles (m.ksplit slices of C): every slice CTA has stored its
+// partial tile; this counts the CTA on the tile's counter and returns true
+// in the one CTA that brings the count to ksplit (it then sums the slices
+// and resets the counter).  No CTA waits for another.
+template <int BN>
+__device__ __forceinline__ bool last_slice(const KArgs& a, const SnMeta& m, const Task& tk, int b) {
+  __shared__ int last;
+  __threadfence();  // this CTA's partial before the count
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int* ctr = a.tctr + (int64_t)b * a.tctr_n + m.tctr + (tk.m0 / TG_BM) * ((m.s + BN - 1) / BN) + tk.n0 / BN;
+    last = atomicAdd(ctr, 1) == m.ksplit - 1;
+    if (last) *ctr = 0;
+    __threadfence();
+  }
+  __syncthreads();
+  return last != 0;
+}
+
 // Step 2 tile: X_{C,K} = -X_{C,C} Lhat_{C,K} over rows [m0, m0+64), columns
 // [n0, n0+BN) and the k-slice tk.c of C.  X_{C,C} is read straight from the
 // ancestors' X panels: entry (i, k) with i >= k (rows of C are sorted) sits
@@ -91,18 +110,7 @@ __device__ __forceinline__ void step2_tile(const KArgs& a, const Task& tk, int b
     // The CTA that finishes a tile's last slice sums all slices of the tile in
     // slice order, its own from registers, and writes X_{C,K}: the same
     // arithmetic as step2_reduce, without its launch and its pass over HBM.
-    // Its counter goes back to zero for the next sweep.  No CTA waits.
-    __shared__ int last;
-    __threadfence();  // this CTA's partial before the count
-    __syncthreads();
-    int* ctr = a.tctr + (int64_t)b * a.tctr_n + m.tctr + (tk.m0 / TG_BM) * ((s + BN - 1) / BN) + tk.n0 / BN;
-    if (threadIdx.x == 0) {
-      last = atomicAdd(ctr, 1) == m.ksplit - 1;
-      if (last) *ctr = 0;
-      __threadfence();
-    }
-    __syncthreads();
-    if (!last) return;
+    if (!last_slice<BN>(a, m, tk, b)) return;
     const int64_t rs = (int64_t)r * s;
     T* xo = (T*)a.X + b * sz.panel + m.panel + s;
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
