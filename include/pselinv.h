@@ -104,7 +104,7 @@ typedef struct {
                              diagonal-block factorisation) */
   int64_t spin_limit_ns;  /* limit for bounded device waits; <= 0 = 1e9 */
   int32_t level_tiles;    /* a level whose step-2 (step-3) tiles number fewer than this gets its slices
-                             (row chunks) of C shrunk until it has about this many; 0 = 64 per SM (9728) */
+                             (row chunks) of C shrunk until it has about this many; 0 = 128 per SM (19456) */
   int32_t min_slice_rows; /* smallest step-2 slice that shrinking makes; 0 = 128 (step-3 chunks: a quarter) */
   int32_t fp64_emulation; /* 0: steps 2 and 3 in FP64 (mma.sync f64).  1 (mma.sync bf16, opt-in, outside
                              the FP64 hot path): step 2, X_{C,K} = -X_{C,C} Lhat_{C,K}, and step 3's
@@ -166,7 +166,7 @@ typedef struct {
 
 /* Fill *o with defaults: F64, batch 1, w_max 128, RELAX_AMALG, padding-minimal
    tiles, split_k_rows 1024, no debug checks, 1 s spin limit, level_tiles and
-   min_slice_rows 0 (9728 and 128), fp64_emulation 0. */
+   min_slice_rows 0 (19456 and 128), fp64_emulation 0. */
 void pselinv_default_opts(pselinv_opts* o);
 
 /*
@@ -464,7 +464,7 @@ int pselinv_get_timing(pselinv_handle* h, double* h_ms, int64_t* h_launches);
  * `stream`, best of two after a warm-up) for each candidate schedule --
  * first split_k_rows over {0, 512, 1024, 2048, 4096} with the current
  * small_cutoff, then small_cutoff over {-1, 32, 64} with the best split,
- * then level_tiles over {2432, 4864, 9728} -- keeps the fastest in the
+ * then level_tiles over {4864, 9728, 19456} -- keeps the fastest in the
  * handle, then times the GRAPH and PERSISTENT modes on it, and returns
  * h_best[0] = split_k_rows, h_best[1] = small_cutoff, h_best[2] =
  * level_tiles, h_best[3] = the fastest mode (h_best holds 4 entries) and

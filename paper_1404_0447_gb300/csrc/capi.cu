@@ -1229,7 +1229,7 @@ int pselinv_autotune(pselinv_handle* h, int32_t* h_best, double* h_best_ms, void
   }
   // third coordinate: the per-level tile target of the slice shrinking
   int32_t best_tiles = h->opts.level_tiles;
-  for (int32_t tiles : {16 * 152, 32 * 152, 64 * 152}) {
+  for (int32_t tiles : {32 * 152, 64 * 152, 128 * 152}) {
     if (rc || tiles == (best_tiles > 0 ? best_tiles : psi::kTargetTiles)) continue;
     h->opts.level_tiles = tiles;
     if ((rc = measure(best_split, best_cut, &ms))) break;

@@ -66,7 +66,7 @@ struct Range {
 constexpr int kMaxWidth = 128;   // widest supernode the kernels accept
 constexpr int kMaxWidthLUComplex = 112;  // complex non-symmetric: two packed triangles in shared memory
 constexpr int kChunkRows = 512;  // rows per step-3 partial product (before the per-level boost)
-constexpr int kTargetTiles = 64 * 152;  // tiles a level should offer the GPU (64 per SM: short tails)
+constexpr int kTargetTiles = 128 * 152;  // tiles a level should offer the GPU (128 per SM: short tails)
 constexpr int kMinSlice2 = 128;   // smallest step-2 slice the per-level boost makes
 constexpr int kTileM = 64;       // output tile rows of the grouped GEMMs
 constexpr int kTileN = 64;       // output tile columns

@@ -103,7 +103,7 @@ def test_autotune_keeps_a_correct_schedule(P):
     h.factor(torch_vals(p.values))
     best = h.autotune()
     assert best["split_k_rows"] in (0, 512, 1024, 2048, 4096) and best["small_cutoff"] in (-1, 32, 64)
-    assert best["level_tiles"] in (2432, 4864, 9728)
+    assert best["level_tiles"] in (4864, 9728, 19456)
     assert best["mode"] in (P.LEVEL, P.GRAPH, P.PERSISTENT)
     assert best["ms"] > 0
     sym, off, Xo, Lo, do = oracle_panels(p.n, p.colptr, p.rowind, p.values, 128, 1)
