@@ -96,7 +96,8 @@ typedef struct {
   int32_t small_cutoff;   /* supernodes narrower than this use the narrowest padding-minimal tiles,
                              wider ones prefer 64-column tiles; < 0 = padding-minimal everywhere */
   int32_t split_k_rows;   /* step 2 of a supernode with |C| = r is split into ceil(r / split_k_rows)
-                             partial products reduced in a fixed order; <= 0 = no split */
+                             partial products summed in slice order (by the CTA that finishes a
+                             tile's last slice); <= 0 = no split */
   int32_t debug_checks;   /* nonzero: kernels bounds-check every index and report */
   int32_t unsym;          /* 0: symmetric A = L D L^T.  1: non-symmetric A with a symmetric pattern,
                              A = L D U' (pselinv_factor_unsym; Algorithm 1 with step 4); complex
@@ -433,9 +434,11 @@ int pselinv_logdet(pselinv_handle* h, double* h_out, void* stream);
  * Requires a prior pselinv_selinv on the same factor (uses X, L, D;
  * recomputes Lhat and (L_KK)^{-1}).  Reverse sweep leaves -> root of the
  * recurrence of Algorithm 1 (steps 3, 2, 1 in that order per supernode,
- * scattering into the ancestors' adjoints through the relative indices),
- * then the adjoint of the supernodal LDL^T root -> leaves.  Allocates its
- * work buffers on first use.  Symmetric handles only (ERR_STATE otherwise).
+ * scattering into the ancestors' adjoints through the relative indices, in
+ * the factorisation's groups of supernodes with disjoint targets: no
+ * atomics, bitwise reproducible), then the adjoint of the supernodal LDL^T
+ * root -> leaves.  Allocates its work buffers on first use.  Symmetric
+ * handles only (ERR_STATE otherwise).
  */
 #define PSELINV_G_SYMMETRIC 0
 #define PSELINV_G_PANEL 1
