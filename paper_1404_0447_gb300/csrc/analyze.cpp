@@ -497,8 +497,11 @@ int build_schedule(pselinv_handle* h) {
           if (m.r > rows) m.ksplit = slices(m.r, rows, &m.kchunk);
         }
       }
-      if (t3 > 0 && t3 < target) {
-        const int64_t f = (target + t3 - 1) / t3;
+      // step 3 aims at half the step-2 target: every extra row chunk is one
+      // more s x s partial for the finish to read
+      const int64_t target3 = target / 2;
+      if (t3 > 0 && t3 < target3) {
+        const int64_t f = (target3 + t3 - 1) / t3;
         for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
           SnMeta& m = h->meta[h->level_sn[t]];
           if (m.r == 0) continue;
@@ -531,7 +534,7 @@ int build_schedule(pselinv_handle* h) {
       for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
         const int32_t k = h->level_sn[t];
         if (t2f < target && !o.fp64_emulation) h->s2var[k] = 0;
-        if (t3f < target && !o.fp64_emulation) h->s3var[k] = 0;
+        if (t3f < target / 2 && !o.fp64_emulation) h->s3var[k] = 0;
         h->trvar[k] = (int8_t)(ttf < target ? 0 : pick_variant(h->meta[k].s, cplx, o.small_cutoff));
       }
     }

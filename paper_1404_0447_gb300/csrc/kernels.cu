@@ -1092,7 +1092,9 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
                                                                  (T*)a.X, a.sz);
       break;
     default:
-      k_diag_final<T><<<dim3(nsn, a.sz.batch, kFinishParts), 256, 0, st>>>(a, sns);
+      // 32 CTAs per supernode: the levels near the root hold one supernode whose
+      // finish reads one s x s partial per row chunk of C
+      k_diag_final<T><<<dim3(nsn, a.sz.batch, 32), 256, 0, st>>>(a, sns);
       break;
   }
   return cudaGetLastError();
