@@ -628,12 +628,12 @@ int build_schedule(pselinv_handle* h) {
     tl.per_sn.assign(nsn, Range{});
     tl.var.assign(nsn, (int8_t)var);
     h->schur_gptr.assign(nl + 1, 0);
-    h->schur_fptr.assign(nl + 1, 0);
-    h->schur_grp.clear();
+    h->schur_near.clear();
+    h->schur_far.clear();
     std::vector<uint64_t> used(h->n, 0);  // groups (< 64) holding a supernode with this row in C
     std::vector<int32_t> touched, color;
     for (int32_t l = 0; l < nl; ++l) {
-      h->schur_gptr[l] = (int32_t)h->schur_grp.size();
+      h->schur_gptr[l] = (int32_t)h->schur_near.size();
       const int32_t b = h->level_ptr[l], e = h->level_ptr[l + 1];
       color.assign(e - b, 0);
       int32_t ncol = 0;
@@ -662,13 +662,15 @@ int build_schedule(pselinv_handle* h) {
       // Each supernode's tiles split at np, the number of rows of C inside its
       // parent P: "near" tiles (target columns in P, level l - 1) and "far"
       // tiles (columns above P, levels <= l - 2).  Task.c holds the tile's
-      // column end.  A level's near groups come first, then its far groups.
+      // column end.  Per colour the near tiles, then the far tiles, adjacent:
+      // near and far target different levels, so a colour's two ranges may
+      // also run as one launch.
       Range& lv = tl.per_lv[(size_t)l * kNumVar + var];
       lv.begin = (int64_t)tl.tasks.size();
-      for (int part = 0; part < 2; ++part) {
-        if (part == 1) h->schur_fptr[l] = (int32_t)h->schur_grp.size();
-        for (int32_t c = 0; c < ncol; ++c) {
-          Range g;
+      for (int32_t c = 0; c < ncol; ++c) {
+        Range ng, fg;
+        for (int part = 0; part < 2; ++part) {
+          Range& g = part == 0 ? ng : fg;
           g.begin = (int64_t)tl.tasks.size();
           for (int32_t t = b; t < e; ++t) {
             if (color[t - b] != c) continue;
@@ -688,13 +690,15 @@ int build_schedule(pselinv_handle* h) {
             }
           }
           g.end = (int64_t)tl.tasks.size();
-          if (g.end > g.begin) h->schur_grp.push_back(g);
+        }
+        if (fg.end > ng.begin) {
+          h->schur_near.push_back(ng);
+          h->schur_far.push_back(fg);
         }
       }
       lv.end = (int64_t)tl.tasks.size();
     }
-    h->schur_gptr[nl] = (int32_t)h->schur_grp.size();
-    h->schur_fptr[nl] = h->schur_gptr[nl];
+    h->schur_gptr[nl] = (int32_t)h->schur_near.size();
   }
   // counters of the split step-2 output tiles (one per (supernode, m-tile, n-tile))
   h->tctr_total = 0;

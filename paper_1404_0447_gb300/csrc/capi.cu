@@ -680,10 +680,11 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
   PSI_CUDA(h, cudaStreamWaitEvent(hi, ev[0], 0));
   PSI_CUDA(h, cudaStreamWaitEvent(lo, ev[0], 0));
   const auto* lsn = (const int32_t*)h->d_levelsn;
-  auto schur = [&](int32_t g0, int32_t g1, cudaStream_t s) -> cudaError_t {
+  auto schur = [&](const std::vector<psi::Range>& grp, int32_t g0, int32_t g1, cudaStream_t s) -> cudaError_t {
     for (int side = 0; side < (unsym ? 2 : 1); ++side)
       for (int32_t g = g0; g < g1; ++g) {  // group by group: disjoint targets inside a group, no atomics
-        const psi::Range r = h->schur_grp[g];
+        const psi::Range r = grp[g];
+        if (r.end == r.begin) continue;
         cudaError_t e = psi::launch_tiles(psi::Kern::Schur, h->schur_var, side ? su : sl,
                                           tasks_at(h, h->off_schur, r.begin), r.end - r.begin, s);
         if (e != cudaSuccess) return e;
@@ -715,10 +716,10 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
     }
     PSI_CUDA(h, cudaEventRecord(ev[1 + l], hi));
     PSI_CUDA(h, cudaStreamWaitEvent(lo, ev[1 + l], 0));
-    PSI_CUDA(h, schur(h->schur_fptr[l], h->schur_gptr[l + 1], lo));
+    PSI_CUDA(h, schur(h->schur_far, h->schur_gptr[l], h->schur_gptr[l + 1], lo));
     PSI_CUDA(h, cudaEventRecord(ev[1 + nl + l], lo));
     if (l + 1 < nl) PSI_CUDA(h, cudaStreamWaitEvent(hi, ev[1 + nl + l + 1], 0));
-    PSI_CUDA(h, schur(h->schur_gptr[l], h->schur_fptr[l], hi));
+    PSI_CUDA(h, schur(h->schur_near, h->schur_gptr[l], h->schur_gptr[l + 1], hi));
   }
   PSI_CUDA(h, cudaEventRecord(ev[1 + 2 * nl], hi));
   PSI_CUDA(h, cudaStreamWaitEvent(st, ev[1 + 2 * nl], 0));
@@ -1117,10 +1118,10 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
     PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::Zbar, a, sns, nsl, st));
     PSI_CUDA(h, tiles(AdjKern::Ybar, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Lhbar, h->t_gemm1, h->off_gemm1, l));  // step-2 slices of C
-    for (int32_t g = h->schur_gptr[l]; g < h->schur_gptr[l + 1]; ++g) {  // disjoint targets per group
-      const psi::Range r = h->schur_grp[g];
-      PSI_CUDA(h, psi::launch_adj_tiles(AdjKern::Syr2k, h->schur_var, a, tasks_at(h, h->off_schur, r.begin),
-                                        r.end - r.begin, st));
+    // per Schur group, its near and far tiles (adjacent, different target levels) as one launch
+    for (int32_t g = h->schur_gptr[l]; g < h->schur_gptr[l + 1]; ++g) {
+      const int64_t b0 = h->schur_near[g].begin, b1 = h->schur_far[g].end;
+      PSI_CUDA(h, psi::launch_adj_tiles(AdjKern::Syr2k, h->schur_var, a, tasks_at(h, h->off_schur, b0), b1 - b0, st));
     }
     PSI_CUDA(h, tiles(AdjKern::LbarOff, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Vpart, h->t_gemm2, h->off_gemm2, l));

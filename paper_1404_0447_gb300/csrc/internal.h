@@ -149,11 +149,12 @@ struct pselinv_handle {
   psi::TaskList t_schur;  // factorisation: Schur-complement update tiles
   // Schur groups: the supernodes of a level split into groups whose update
   // targets are disjoint (no two share a row of C), launched one after the
-  // other; level l's groups are schur_grp[schur_gptr[l] .. schur_gptr[l+1]),
-  // those before schur_fptr[l] updating the parents' columns ("near"), the
-  // rest the columns above the parents ("far")
-  std::vector<int32_t> schur_gptr, schur_fptr;
-  std::vector<psi::Range> schur_grp;
+  // other; level l's groups are g = schur_gptr[l] .. schur_gptr[l+1], each
+  // with its tiles updating the parents' columns (schur_near[g]) and those
+  // updating the columns above the parents (schur_far[g]), adjacent in the
+  // task list (far begins where near ends)
+  std::vector<int32_t> schur_gptr;
+  std::vector<psi::Range> schur_near, schur_far;
   int32_t schur_var = 0;  // tile variant of every Schur tile
   std::vector<int8_t> s2var, s3var, trvar;  // step-2 / step-3 / panel-solve tile variant per supernode
   psi::TaskList t_sq;     // s x s tiles of each supernode's diagonal block (adjoint products)
