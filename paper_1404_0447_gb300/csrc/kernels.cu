@@ -574,7 +574,7 @@ __global__ void k_factor_diag_bk(const SnMeta* __restrict__ meta, const int32_t*
     if (t == 0) report_pivot(status, m.f + k, sh_bad == 1);
     return;
   }
-  unit_lower_inverse(Tp, s, Linv + b * sz.linv + m.linv);
+  unit_lower_inverse_blocked(Tp, s, Linv + b * sz.linv + m.linv, reinterpret_cast<T*>(perm + ((s + 3) & ~3)));
   for (int e = t; e < s * s; e += nt) {
     const int i = e % s, j = e / s;
     if (i > j) P[i + (int64_t)j * ld] = Tp[pk(i, j, s)];
@@ -921,6 +921,13 @@ static size_t diag_smem_fd(int maxw) {
   return sizeof(T) * ((size_t)maxw * (maxw + 1) / 2 + (size_t)maxw + 256 * (nb > 1 ? nb - 1 : 1));
 }
 
+// the pivoted diagonal factorisation: diag_smem plus the blocks of the inverse
+template <class T>
+static size_t diag_smem_bk(int maxw) {
+  const size_t nb = (size_t)(maxw + 15) / 16;
+  return diag_smem<T>(maxw) + 16 + sizeof(T) * 256 * (nb > 1 ? nb - 1 : 1);
+}
+
 // two packed triangles of the non-symmetric diagonal factorisation
 template <class T>
 static size_t diag_smem_lu(int maxw) {
@@ -939,7 +946,7 @@ static cudaError_t setup_t() {
                              (int)diag_smem<T>(kMaxWidth));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_factor_diag_bk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)diag_smem<T>(kMaxWidth));
+                             (int)diag_smem_bk<T>(kMaxWidth));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_factor_diag_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)diag_smem_lu<T>(Sc<T>::P == 1 ? kMaxWidth : kMaxWidthLUComplex));
@@ -1079,7 +1086,7 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
                                                                       (T*)a.Linv, (T*)a.Uinv, a.sz, a.status);
       break;
     case Kern::FactorDiagBK:
-      k_factor_diag_bk<T><<<grid, threads > 512 ? 512 : threads, diag_smem<T>(a.maxw), st>>>(
+      k_factor_diag_bk<T><<<grid, threads > 512 ? 512 : threads, diag_smem_bk<T>(a.maxw), st>>>(
           a.meta, sns, (T*)a.L, (T*)a.D, (T*)a.E, (int8_t*)a.ptype, (int32_t*)a.piv, (T*)a.Linv, a.sz, a.status);
       break;
     case Kern::CopyBackBK:
