@@ -526,10 +526,10 @@ __global__ void k_factor_diag_bk(const SnMeta* __restrict__ meta, const int32_t*
       const T d = Tp[pk(k, k, s)];
       for (int i = k + 1 + t; i < s; i += nt) Tp[pk(i, k, s)] = Tp[pk(i, k, s)] / d;
       __syncthreads();
-      const int w = s - k - 1;
-      for (int e = t; e < w * w; e += nt) {
-        const int ii = k + 1 + e % w, jj = k + 1 + e / w;
-        if (ii >= jj) Tp[pk(ii, jj, s)] -= Tp[pk(ii, k, s)] * Tp[pk(jj, k, s)] * d;
+      // trailing lower triangle, one warp per column (no integer division)
+      for (int jj = k + 1 + (t >> 5); jj < s; jj += nt >> 5) {
+        const int cj = pk(jj, jj, s);
+        for (int ii = jj + (t & 31); ii < s; ii += 32) Tp[cj + ii - jj] -= Tp[pk(ii, k, s)] * Tp[pk(jj, k, s)] * d;
       }
       if (t == 0) {
         dd[k] = d;
@@ -546,10 +546,10 @@ __global__ void k_factor_diag_bk(const SnMeta* __restrict__ meta, const int32_t*
         l2[i] = (w2 * a11 - w1 * a21) / det;
       }
       __syncthreads();
-      const int w = s - k - 2;
-      for (int e = t; e < w * w; e += nt) {
-        const int ii = k + 2 + e % w, jj = k + 2 + e / w;
-        if (ii >= jj) Tp[pk(ii, jj, s)] -= l1[ii] * Tp[pk(jj, k, s)] + l2[ii] * Tp[pk(jj, k + 1, s)];
+      for (int jj = k + 2 + (t >> 5); jj < s; jj += nt >> 5) {
+        const int cj = pk(jj, jj, s);
+        for (int ii = jj + (t & 31); ii < s; ii += 32)
+          Tp[cj + ii - jj] -= l1[ii] * Tp[pk(jj, k, s)] + l2[ii] * Tp[pk(jj, k + 1, s)];
       }
       __syncthreads();
       for (int i = k + 2 + t; i < s; i += nt) {
