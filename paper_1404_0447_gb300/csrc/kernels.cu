@@ -257,16 +257,25 @@ __global__ void k_factor_diag_lu(const SnMeta* __restrict__ meta, const int32_t*
       Tu[pk(i, j, s)] = Tu[pk(i, j, s)] / d;
     }
     __syncthreads();
-    const int w = s - j - 1;
-    for (int e = t; e < w * w; e += nt) {
-      const int ii = j + 1 + e % w, kk = j + 1 + e / w;
-      if (ii >= kk) Tl[pk(ii, kk, s)] -= Tl[pk(ii, j, s)] * Tu[pk(kk, j, s)] * d;      // A_{ii,kk}
-      if (ii > kk) Tu[pk(ii, kk, s)] -= Tu[pk(ii, j, s)] * Tl[pk(kk, j, s)] * d;       // A_{kk,ii}
+    // trailing block, one warp per column kk (no integer division)
+    for (int kk = j + 1 + (t >> 5); kk < s; kk += nt >> 5) {
+      const int ck = pk(kk, kk, s);
+      for (int ii = kk + (t & 31); ii < s; ii += 32) {
+        Tl[ck + ii - kk] -= Tl[pk(ii, j, s)] * Tu[pk(kk, j, s)] * d;                      // A_{ii,kk}
+        if (ii > kk) Tu[ck + ii - kk] -= Tu[pk(ii, j, s)] * Tl[pk(kk, j, s)] * d;         // A_{kk,ii}
+      }
     }
     __syncthreads();
   }
-  unit_lower_inverse(Tl, s, Linv + b * sz.linv + m.linv);
-  unit_lower_inverse(Tu, s, Uinv + b * sz.linv + m.linv);
+  if constexpr (Sc<T>::P == 1) {  // real: the blocked inverses (their 16 x 16 scratch after the triangles)
+    T* S = Tu + s * (s + 1) / 2;
+    unit_lower_inverse_blocked(Tl, s, Linv + b * sz.linv + m.linv, S);
+    __syncthreads();
+    unit_lower_inverse_blocked(Tu, s, Uinv + b * sz.linv + m.linv, S);
+  } else {  // complex: both triangles fill the shared memory
+    unit_lower_inverse(Tl, s, Linv + b * sz.linv + m.linv);
+    unit_lower_inverse(Tu, s, Uinv + b * sz.linv + m.linv);
+  }
   for (int e = t; e < s * s; e += nt) {
     const int i = e % s, j = e / s;
     if (i >= j) P[i + (int64_t)j * ld] = Tl[pk(i, j, s)];
@@ -931,7 +940,8 @@ static size_t diag_smem_bk(int maxw) {
 // two packed triangles of the non-symmetric diagonal factorisation
 template <class T>
 static size_t diag_smem_lu(int maxw) {
-  return sizeof(T) * (size_t)maxw * (maxw + 1);
+  const size_t nb = (size_t)(maxw + 15) / 16;
+  return sizeof(T) * ((size_t)maxw * (maxw + 1) + (Sc<T>::P == 1 ? 256 * (nb > 1 ? nb - 1 : 1) : 0));
 }
 
 template <class T>
