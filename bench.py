@@ -63,6 +63,15 @@ def measure_fp64_peak(dev, n=8192, reps=3):
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
+def hbm_peak():
+    """Measured copy bandwidth of this machine's GB300 (GB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def bf16_sustained_peak():
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
         return float(json.load(f)["bf16_tflops_sustained"])
@@ -403,6 +412,23 @@ def run_ours(args):
                     "peak": peak_used, "unit": "TFLOP/s", "frac": fl_factor / (f_med * 1e-3) / 1e12 / peak_used,
                     "flop_count": "sum over supernodes of r(r+1)s + r s^2 + 2/3 s^3"}
 
+    # the index-driven gather of the selected entries at A's positions (HBM-bound):
+    # per entry the int64 value-map offset, the X panel value and the output
+    sel_out = torch.empty(info["nnz_a"], dtype=torch.float64, device=dev)
+    h.selected(out=sel_out, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        h.selected(out=sel_out, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    g_ms = e0.elapsed_time(e1) / 10
+    gather_block = {"kernel": "k_gather_values (selected entries of X at A's nonzeros)", "ms": g_ms,
+                    "bytes": 24 * info["nnz_a"], "achieved_GBps": 24 * info["nnz_a"] / (g_ms * 1e-3) / 1e9,
+                    "peak_GBps": hbm_peak(), "frac": 24 * info["nnz_a"] / (g_ms * 1e-3) / 1e9 / hbm_peak()}
+    del sel_out
+
     # end to end through host buffers: values H2D, factor, selinv, X panels D2H
     e2e = None
     if not args.no_e2e:
@@ -490,7 +516,8 @@ def run_ours(args):
                            "fp64_peak_measured_tflops": peak,
                            "l2": "no flush: the X panels (%.1f GB) exceed L2 (129 MB)" % (info["panel_entries"] * 8 / 1e9),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roofline, "factor": factor_block, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "factor": factor_block, "gather": gather_block, "cpu_baseline": cpu,
+                "e2e": e2e,
                 "gpu_launches": int(round(sum(kl))) * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
