@@ -621,7 +621,6 @@ int build_schedule(pselinv_handle* h) {
     // thread: the factor is bitwise reproducible.
     TaskList& tl = h->t_schur;
     const int var = by_rows(0);
-    const int bn = 8 << var;
     h->schur_var = var;
     tl.tasks.clear();
     tl.per_lv.assign((size_t)nl * kNumVar, Range{});
@@ -630,6 +629,7 @@ int build_schedule(pselinv_handle* h) {
     h->schur_gptr.assign(nl + 1, 0);
     h->schur_near.clear();
     h->schur_far.clear();
+    h->schur_gvar.clear();
     std::vector<uint64_t> used(h->n, 0);  // groups (< 64) holding a supernode with this row in C
     std::vector<int32_t> touched, color;
     for (int32_t l = 0; l < nl; ++l) {
@@ -668,6 +668,16 @@ int build_schedule(pselinv_handle* h) {
       Range& lv = tl.per_lv[(size_t)l * kNumVar + var];
       lv.begin = (int64_t)tl.tasks.size();
       for (int32_t c = 0; c < ncol; ++c) {
+        // a group with few 64 x 64 tiles (under ~4 waves of 4 CTAs per SM)
+        // runs 64 x 8 tiles instead: 8x the tiles, each 8x shorter
+        int64_t ntile = 0;
+        for (int32_t t = b; t < e; ++t) {
+          if (color[t - b] != c) continue;
+          const int64_t rb = (h->meta[h->level_sn[t]].r + kTileM - 1) / kTileM;
+          ntile += rb * (rb + 1) / 2;
+        }
+        const int gvar = ntile < 16 * 152 ? 0 : var;
+        const int bn = 8 << gvar;
         Range ng, fg;
         for (int part = 0; part < 2; ++part) {
           Range& g = part == 0 ? ng : fg;
@@ -694,6 +704,7 @@ int build_schedule(pselinv_handle* h) {
         if (fg.end > ng.begin) {
           h->schur_near.push_back(ng);
           h->schur_far.push_back(fg);
+          h->schur_gvar.push_back((int8_t)gvar);
         }
       }
       lv.end = (int64_t)tl.tasks.size();

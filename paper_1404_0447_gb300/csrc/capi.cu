@@ -685,7 +685,7 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
       for (int32_t g = g0; g < g1; ++g) {  // group by group: disjoint targets inside a group, no atomics
         const psi::Range r = grp[g];
         if (r.end == r.begin) continue;
-        cudaError_t e = psi::launch_tiles(psi::Kern::Schur, h->schur_var, side ? su : sl,
+        cudaError_t e = psi::launch_tiles(psi::Kern::Schur, h->schur_gvar[g], side ? su : sl,
                                           tasks_at(h, h->off_schur, r.begin), r.end - r.begin, s);
         if (e != cudaSuccess) return e;
       }
@@ -1121,7 +1121,7 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
     // per Schur group, its near and far tiles (adjacent, different target levels) as one launch
     for (int32_t g = h->schur_gptr[l]; g < h->schur_gptr[l + 1]; ++g) {
       const int64_t b0 = h->schur_near[g].begin, b1 = h->schur_far[g].end;
-      PSI_CUDA(h, psi::launch_adj_tiles(AdjKern::Syr2k, h->schur_var, a, tasks_at(h, h->off_schur, b0), b1 - b0, st));
+      PSI_CUDA(h, psi::launch_adj_tiles(AdjKern::Syr2k, h->schur_gvar[g], a, tasks_at(h, h->off_schur, b0), b1 - b0, st));
     }
     PSI_CUDA(h, tiles(AdjKern::LbarOff, h->t_rect, h->off_rect, l));
     PSI_CUDA(h, tiles(AdjKern::Vpart, h->t_gemm2, h->off_gemm2, l));

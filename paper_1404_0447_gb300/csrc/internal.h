@@ -155,7 +155,8 @@ struct pselinv_handle {
   // task list (far begins where near ends)
   std::vector<int32_t> schur_gptr;
   std::vector<psi::Range> schur_near, schur_far;
-  int32_t schur_var = 0;  // tile variant of every Schur tile
+  std::vector<int8_t> schur_gvar;  // tile variant of each group (64 x 8 for groups with few tiles)
+  int32_t schur_var = 0;  // tile variant of the Schur tiles of the larger groups
   std::vector<int8_t> s2var, s3var, trvar;  // step-2 / step-3 / panel-solve tile variant per supernode
   psi::TaskList t_sq;     // s x s tiles of each supernode's diagonal block (adjoint products)
   psi::TaskList t_pgemm1; // persistent schedule: step-2 tiles, widths <= 8 << kPersistentMaxVar
