@@ -584,7 +584,27 @@ int build_schedule(pselinv_handle* h) {
       for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, 0});
   };
   build(h->t_lhat, true, by_width, rect);
-  build(h->t_rect, false, by_width, rect);
+  // the adjoint's r x s and s x s tile lists: 64 x 8 tiles on levels whose
+  // tiles are too few to fill the GPU (as for steps 2 and 3)
+  std::vector<int8_t> rvar(nsn), qvar(nsn);
+  {
+    const int64_t target = o.level_tiles > 0 ? o.level_tiles : kTargetTiles;
+    for (int32_t l = 0; l < nl; ++l) {
+      int64_t nr = 0, nq = 0;
+      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+        const SnMeta& m = h->meta[h->level_sn[t]];
+        const int64_t bn = 8 << by_width(h->level_sn[t]);
+        nr += (m.r + kTileM - 1) / kTileM * ((m.s + bn - 1) / bn);
+        nq += (m.s + kTileM - 1) / kTileM * ((m.s + bn - 1) / bn);
+      }
+      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+        const int32_t k = h->level_sn[t];
+        rvar[k] = (int8_t)(nr < target ? 0 : by_width(k));
+        qvar[k] = (int8_t)(nq < target ? 0 : by_width(k));
+      }
+    }
+  }
+  build(h->t_rect, false, [&](int32_t k) { return (int)rvar[k]; }, rect);
   auto step2_tiles = [&](int32_t k, int bn, std::vector<Task>& out) {  // step 2: + k-parts
     const SnMeta& m = h->meta[k];
     for (int32_t c = 0; c < m.ksplit; ++c)
@@ -600,7 +620,7 @@ int build_schedule(pselinv_handle* h) {
   build(h->t_gemm1, false, [&](int32_t k) { return (int)h->s2var[k]; }, step2_tiles);
   build(h->t_trsm, false, [&](int32_t k) { return (int)h->trvar[k]; }, rect);
   build(h->t_gemm2, false, [&](int32_t k) { return (int)h->s3var[k]; }, step3_tiles);
-  build(h->t_sq, false, by_width, [&](int32_t k, int bn, std::vector<Task>& out) {  // s x s, no chunks
+  build(h->t_sq, false, [&](int32_t k) { return (int)qvar[k]; }, [&](int32_t k, int bn, std::vector<Task>& out) {
     const SnMeta& m = h->meta[k];
     for (int32_t m0 = 0; m0 < m.s; m0 += kTileM)
       for (int32_t n0 = 0; n0 < m.s; n0 += bn) out.push_back({k, m0, n0, 0});
