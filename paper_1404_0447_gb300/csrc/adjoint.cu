@@ -323,12 +323,14 @@ __global__ void k_adj_dr2(AdjArgs a, const int32_t* __restrict__ sns) {
   T* Z = (T*)a.Zb + b * sz.linv + m.linv;
   const T* W = (const T*)a.W1 + b * sz.linv + m.linv;
   T* Db = (T*)a.Db + b * sz.n + m.f;
-  for (int t = threadIdx.x; t < s; t += blockDim.x) {
+  // blockIdx.z of gridDim.z CTAs: columns t = z (mod gridDim.z), entries e in blocks of blockDim.x
+  const int zc = blockIdx.z, nz = gridDim.z;
+  for (int t = zc + threadIdx.x * nz; t < s; t += blockDim.x * nz) {
     T acc = Sc<T>::zero();
     for (int j = 0; j < s; ++j) acc += W[t + j * s] * V[t + j * s];
     Db[t] = -(acc / (d[t] * d[t]));
   }
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+  for (int e = threadIdx.x + zc * blockDim.x; e < s * s; e += blockDim.x * nz) {
     const int t = e % s;
     T vb = 2.0 * W[e] / d[t];
     if (m.nchunk > 0) vb += part[e];  // chunk partials already summed into chunk 0
@@ -356,21 +358,23 @@ __global__ void k_adj_df1(AdjArgs a, const int32_t* __restrict__ sns) {
   const T zero = Sc<T>::zero();
   auto R = [&](int i, int j) { return m.nchunk > 0 ? part[i + j * s] : zero; };
   auto Lkk = [&](int i, int j) { return i == j ? Sc<T>::one() : (i > j ? Lp[i + (int64_t)j * ld] : zero); };
-  // one warp per column, lanes along the r rows
+  // blockIdx.z of gridDim.z CTAs: columns t = z (mod gridDim.z), one warp per
+  // column, lanes along the r rows; entries e of W in blocks of blockDim.x
+  const int zc = blockIdx.z, nz = gridDim.z;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-  for (int t = warp; t < s; t += nw) {
+  for (int t = zc + warp * nz; t < s; t += nw * nz) {
     T acc = zero;
     for (int i = lane; i < r; i += 32) acc += Lp[s + i + (int64_t)t * ld] * T1[i + (int64_t)t * r];
     acc = warp_sum(acc);
     if (lane == 0) colsum[t] = acc;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < s; t += blockDim.x) {
+  for (int t = zc + threadIdx.x * nz; t < s; t += blockDim.x * nz) {
     T acc2 = zero;
     for (int j = t; j < s; ++j) acc2 += Lkk(j, t) * R(j, t);
     Db[t] = Db[t] - 0.5 * colsum[t] - acc2;
   }
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+  for (int e = threadIdx.x + zc * blockDim.x; e < s * s; e += blockDim.x * nz) {
     const int i = e % s, j = e / s;
     W[e] = i > j ? Lb[i + (int64_t)j * ld] - R(i, j) * d[j] : zero;
   }
@@ -445,8 +449,8 @@ static cudaError_t adj_sn_t(AdjSn k, const AdjArgs& a, const int32_t* sns, int n
   switch (k) {
     case AdjSn::Seed: k_adj_seed<T><<<grid, 256, 0, st>>>(a); break;
     case AdjSn::Zbar: k_adj_zbar<T><<<grid, 256, 0, st>>>(a, sns); break;
-    case AdjSn::Dr2: k_adj_dr2<T><<<grid, 256, 0, st>>>(a, sns); break;
-    case AdjSn::Df1: k_adj_df1<T><<<grid, 256, 0, st>>>(a, sns); break;
+    case AdjSn::Dr2: k_adj_dr2<T><<<dim3(nsn, a.k.sz.batch, 8), 256, 0, st>>>(a, sns); break;
+    case AdjSn::Df1: k_adj_df1<T><<<dim3(nsn, a.k.sz.batch, 8), 256, 0, st>>>(a, sns); break;
     case AdjSn::Df5: k_adj_df5<T><<<grid, 256, 0, st>>>(a, sns); break;
     case AdjSn::SumParts: k_adj_sum_parts<T><<<dim3(nsn, a.k.sz.batch, 8), 256, 0, st>>>(a, sns); break;
     default: break;
