@@ -16,7 +16,26 @@ binding plus a few plain numpy definitions used as independent pins:
 * ``trace_error`` -- the accuracy measure E of Section 4.3, Eq. (16);
 * ``dense_adjoint`` -- the gradient -(X G X) restricted to A's pattern.
 
-Every function pinned by tests/test_oracle_pins.py; none is "parity unpinned".
+Pins (values fixed independently of this package), per function:
+
+* the C sweeps and symbolic analysis -- listed in ``oracle.c``'s header;
+* ``laplacian_1d_inverse``, ``grid_inverse_entries`` -- multiplied back
+  against A to the identity (test_oracle_pins::test_laplacian_1d_closed_form_and_linear_work,
+  test_grid_closed_form_is_the_inverse);
+* ``convdiff_inverse_entries`` -- the same check for the non-symmetric form
+  (test_oracle_lu_pins::test_convdiff_closed_form_is_the_inverse);
+* ``trace_error`` -- E = 0 for the exact inverse of a 2D grid
+  (test_trace_identity_grid2d_31);
+* ``dense_adjoint`` -- central finite differences of <G, A^{-1}>
+  (test_dense_adjoint_against_finite_differences);
+* ``bk_block``, ``selected_inverse_bk``, ``logdet_bk`` -- scipy.linalg.ldl's
+  Bunch-Kaufman pivots and dense inverses of indefinite matrices
+  (tests/test_oracle_bk_pins.py);
+* ``panels_from_columns``, ``panels_from_dense`` -- each other and numpy's
+  dense inverse on relaxed supernodes (test_panel_layouts_against_the_dense_inverse);
+  ``panels_from_columns_lu`` runs the same ``_panels`` layout twice.
+
+None is "parity unpinned".
 """
 from __future__ import annotations
 

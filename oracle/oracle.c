@@ -27,11 +27,40 @@
  * column and rows sorted; colptr int64, row indices int32.  The L pattern
  * is stored strictly below the diagonal ("struct(j)"), D separately.
  *
- * Parity pins: every function here is checked by tests/test_oracle_pins.py
- * against values fixed independently of this file (dense inverses, exact
- * rational inverses, the closed-form inverse of tridiag(-1,2,-1), the
- * separable closed form of grid Laplacians, the worked example of Figure 1,
- * brute-force boolean elimination, numpy's slogdet).
+ * Parity pins: every function here is checked against values fixed
+ * independently of this file.  Per function, the test that a plausible
+ * mistake in it (a dropped term, a wrong sign or index, an off-by-one in a
+ * threshold) would fail:
+ *   orc_etree, orc_sym_*      brute-force boolean elimination on random
+ *                             patterns (test_oracle_pins::test_symbolic_vs_brute_force),
+ *                             Figure 1's tree (test_figure1_worked_example)
+ *   orc_postorder             random forests: children before parents, subtrees
+ *                             contiguous (test_postorder_of_random_forest)
+ *   orc_supernodes            hand-derived partitions of chains, a 5 x 5 grid and
+ *                             cases on both sides of the 5% zero threshold
+ *                             (tests/golden/relaxed_supernodes.txt,
+ *                             test_supernode_golden); width caps and the
+ *                             zero bound (test_supernode_rule_properties)
+ *   orc_sn_struct, orc_relidx the definition ancestor-row by ancestor-row on
+ *                             random patterns (test_relative_indices_definition),
+ *                             Figure 1 (test_figure1_worked_example)
+ *   orc_ldlt_*, orc_selinv_*  dense inverses of random SPD and complex symmetric
+ *                             matrices (test_tiny_random_vs_dense_inverse), exact
+ *                             rational inverses (test_exact_rational_inverse), the
+ *                             closed form of tridiag(-1,2,-1) and of grid
+ *                             Laplacians (test_laplacian_1d_closed_form_and_linear_work,
+ *                             test_oracle_vs_grid_closed_form_nd_order), the trace
+ *                             identity (test_trace_identity_grid2d_31)
+ *   orc_selinv_omp            bitwise equal to the one-thread sweep
+ *                             (test_oracle_omp)
+ *   orc_solve_*               numpy.linalg.solve (test_solve_vs_numpy)
+ *   orc_logdet_*              numpy.linalg.slogdet (test_logdet_vs_slogdet)
+ *   orc_ldu_*, orc_selinv_lu_*, orc_solve_lu_*
+ *                             tests/test_oracle_lu_pins.py: dense and exact
+ *                             rational inverses, Usmani's closed form for
+ *                             tridiagonal inverses, L D U' reproducing A, the
+ *                             convection-diffusion closed form, bitwise reduction
+ *                             to the symmetric sweep when A is symmetric
  */
 #include <complex.h>
 #include <math.h>

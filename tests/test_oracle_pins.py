@@ -405,3 +405,23 @@ def test_complex_config_small_pole_block_matrix():
         scale = np.abs(Ainv).max()
         assert rel_err(xv, ev, scale) < 1e-13
         assert rel_err(xd, ed, scale) < 1e-13
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_panel_layouts_against_the_dense_inverse(cplx):
+    """``panels_from_columns`` (column-form X of the sweep) and
+    ``panels_from_dense`` (numpy's dense inverse) lay X out on the same
+    supernodal panels: a wrong row, column or mirror index in either would
+    make them differ.  Relaxed supernodes of width <= 4, so the diagonal
+    blocks hold entries mirrored above the diagonal."""
+    n = 40
+    A = random_symmetric(n, 0.15, 321, cplx)
+    cp, ri, v = lower_from_dense(A)
+    sym, lv, d, xv, xd, lcp, lri = oracle.selected_inverse(n, cp, ri, v, 4, 1, "supernodal")
+    post = sym["post"]
+    Ap = np.linalg.inv(A)[np.ix_(post, post)]
+    off, Xc = oracle.panels_from_columns(n, sym["sn_start"], sym["rcount"], sym["rrows"], lcp, xv, xd)
+    Xd = oracle.panels_from_dense(sym, Ap)
+    assert off[-1] == Xd.size
+    assert np.max(np.abs(np.diff(sym["sn_start"]))) > 1          # some supernode has a mirrored block
+    assert rel_err(Xc, Xd, np.abs(Ap).max()) < 1e-13
