@@ -229,7 +229,9 @@ int pselinv_analyze_batch(int32_t k, const int64_t* h_n, const int64_t* const* h
  * the selected inversion.  Per level: the diagonal blocks, the panel solves,
  * then the Schur updates of the ancestors in groups of supernodes whose
  * update targets are disjoint (fixed order, no atomics): L and D, and so X,
- * are bitwise reproducible from run to run.
+ * are bitwise reproducible from run to run.  The handle's X panels serve as
+ * scratch (the panel solve's L_{C,K} D_K): a selected inverse computed before
+ * is gone.
  *
  * d_values   device, batch x nnz_a values of A's lower CSC in the user's
  *            order (dtype of the handle)
@@ -288,6 +290,7 @@ int pselinv_get_pivots(pselinv_handle* h, int32_t* h_piv, int8_t* h_type, void* 
  *          i >= j, of the pattern given to pselinv_analyze (user order)
  * d_upper  device, batch x nnz_a: A_ji at the same positions (the entries
  *          at diagonal positions are not read)
+ * The X and XU panels serve as scratch, as in pselinv_factor.
  * Errors as pselinv_factor; ERR_STATE on a symmetric handle.
  */
 int pselinv_factor_unsym(pselinv_handle* h, const void* d_lower, const void* d_upper, void* stream);

@@ -55,8 +55,20 @@ __device__ __forceinline__ void slice_sum(const Acc<T, BN>& acc, const SnMeta& m
   });
 }
 
+// Occupancy hint per operation: the r^2 s contractions (LHBAR, T1, SYR2K)
+// and Q get the step-2 tile's CTAs per SM (one less for 64-wide T1 tiles and
+// real Q tiles from 32 wide, whose two products would spill under that
+// register cap); the rest keeps the compiler's choice.
 template <class T, int BN, int OP>
-__global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* __restrict__ tasks) {
+constexpr int adj_min_ctas() {
+  if (OP == A_LHBAR || OP == A_SYR2K) return tile_min_ctas<T, BN>();
+  if (OP == A_T1) return BN == 64 ? tile_min_ctas<T, BN>() - 1 : tile_min_ctas<T, BN>();
+  if (OP == A_Q) return BN >= 32 && Sc<T>::P == 1 ? tile_min_ctas<T, BN>() - 1 : tile_min_ctas<T, BN>();
+  return 1;
+}
+
+template <class T, int BN, int OP>
+__global__ void __launch_bounds__(TG_THREADS, (adj_min_ctas<T, BN, OP>())) k_adj_tile(AdjArgs a, const Task* __restrict__ tasks) {
   __shared__ TileSmem<T, BN> sm;
   const Task tk = tasks[blockIdx.x];
   const int b = blockIdx.y;
@@ -128,16 +140,28 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
     });
   } else if constexpr (OP == A_T1) {  // T1 = (W + W^T) L_CK, W gathered from Fb (= Xb), k-slice tk.c
     const int kb = tk.c * m.kchunk, ke = min(r, kb + m.kchunk);
+    // the product runs on the symmetric W (W_ik on both sides of the diagonal,
+    // W_ii once), with no FP64 operation per loaded element; the second W_ii of
+    // (W + W^T)'s diagonal is one more product, diag(W_ii) L_CK[i, :], over the
+    // rows of the tile on the slice's part of the diagonal (at most 64 k)
     auto la = [&](int mm, int kk) {
       const int i = m0 + mm;
       if (i >= r) return zero;
       const int lo = i < kk ? i : kk, hi = i < kk ? kk : i;
       const ColDesc cd = dk[lo];
-      const T w = Xb[cd.col + rel[cd.rel + hi]];
-      return i == kk ? 2.0 * w : w;
+      return Xb[cd.col + rel[cd.rel + hi]];
     };
     auto lb = [&](int kk, int nn) { const int n = n0 + nn; return n < s ? L[m.panel + s + kk + (int64_t)n * ld] : zero; };
     tile_mma<T, BN>(sm, kb, ke, upper_by_k, la, lb, acc, rect);
+    const int db = max(kb, m0), de = min(min(ke, r), m0 + TG_BM);
+    if (db < de) {
+      auto ld_ = [&](int mm, int kk) {
+        if (m0 + mm != kk) return zero;
+        const ColDesc cd = dk[kk];
+        return Xb[cd.col + rel[cd.rel + kk]];
+      };
+      tile_mma<T, BN>(sm, db, de, none, ld_, lb, acc, rect);
+    }
     T* yp = (T*)a.k.ypart + b * sz.ypart + m.ypart;
     T* out = m.ksplit == 1 ? Yb : yp + (int64_t)tk.c * r * s;
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
@@ -145,13 +169,16 @@ __global__ void __launch_bounds__(TG_THREADS) k_adj_tile(AdjArgs a, const Task* 
       if (i < r && n < s) out[i + (int64_t)n * r] = v;
     });
     if (m.ksplit > 1 && a.k.tctr && last_slice<BN>(a.k, m, tk, b)) slice_sum<T, BN>(acc, m, tk, yp, Yb, false);
-  } else if constexpr (OP == A_Q) {  // Q = (Lb_CK E - T1) V -> Fb_CK
-    auto la = [&](int mm, int t) {
-      const int i = m0 + mm;
-      return i < r ? Lb[m.panel + s + i + (int64_t)t * ld] / d[t] - Yb[i + (int64_t)t * r] : zero;
-    };
-    auto lb = [&](int t, int nn) { const int n = n0 + nn; return n < s ? V[t + n * s] : zero; };
-    tile_mma<T, BN>(sm, n0, s, none, la, lb, acc, rect, KLowerB<BN>{n0});
+  } else if constexpr (OP == A_Q) {  // Q = (Lb_CK E - T1) V = Lb_CK (E V) - T1 V -> Fb_CK
+    // E V (rows of V divided by d) in W1 from k_adj_ev: no FP64 operation per loaded element
+    const T* EV = (const T*)a.W1 + b * sz.linv + m.linv;
+    auto la1 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Yb[i + (int64_t)t * r] : zero; };
+    auto lb1 = [&](int t, int nn) { const int n = n0 + nn; return n < s ? V[t + n * s] : zero; };
+    tile_mma<T, BN>(sm, n0, s, none, la1, lb1, acc, rect, KLowerB<BN>{n0});
+    tile_update<T, BN>(acc, [](int, int, T v) { return -v; });
+    auto la2 = [&](int mm, int t) { const int i = m0 + mm; return i < r ? Lb[m.panel + s + i + (int64_t)t * ld] : zero; };
+    auto lb2 = [&](int t, int nn) { const int n = n0 + nn; return n < s ? EV[t + n * s] : zero; };
+    tile_mma<T, BN>(sm, n0, s, none, la2, lb2, acc, rect, KLowerB<BN>{n0});
     tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
       const int i = m0 + mm, n = n0 + nn;
       if (i < r && n < s) Xb[m.panel + s + i + (int64_t)n * ld] = v;
@@ -380,6 +407,21 @@ __global__ void k_adj_df1(AdjArgs a, const int32_t* __restrict__ sns) {
   }
 }
 
+// Start of the LDL^T adjoint, every supernode (blockIdx.x): W1 = E V, the
+// rows of V = (L_KK)^{-1} divided by d (E = D^{-1}), the second operand of Q.
+// W1 is free until the supernode's own DF1.
+template <class T>
+__global__ void k_adj_ev(AdjArgs a) {
+  const int k = blockIdx.x, b = blockIdx.y;
+  const Sizes sz = a.k.sz;
+  const SnMeta m = a.k.meta[k];
+  const int s = m.s;
+  const T* V = (const T*)a.k.Linv + b * sz.linv + m.linv;
+  const T* d = (const T*)a.k.D + b * sz.n + m.f;
+  T* EV = (T*)a.W1 + b * sz.linv + m.linv;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) EV[e] = V[e] / d[e % s];
+}
+
 // LDL^T adjoint, last diagonal part: Fb_KK (stored lower) = Ab_ij + Ab_ji
 // (i > j), Ab_ii with Ab = V^T P V (from DF4, in Zb).
 template <class T>
@@ -448,6 +490,7 @@ static cudaError_t adj_sn_t(AdjSn k, const AdjArgs& a, const int32_t* sns, int n
   const dim3 grid(nsn, a.k.sz.batch);
   switch (k) {
     case AdjSn::Seed: k_adj_seed<T><<<grid, 256, 0, st>>>(a); break;
+    case AdjSn::Ev: k_adj_ev<T><<<grid, 256, 0, st>>>(a); break;
     case AdjSn::Zbar: k_adj_zbar<T><<<grid, 256, 0, st>>>(a, sns); break;
     case AdjSn::Dr2: k_adj_dr2<T><<<dim3(nsn, a.k.sz.batch, 8), 256, 0, st>>>(a, sns); break;
     case AdjSn::Df1: k_adj_df1<T><<<dim3(nsn, a.k.sz.batch, 8), 256, 0, st>>>(a, sns); break;

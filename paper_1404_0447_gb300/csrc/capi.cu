@@ -288,6 +288,7 @@ psi::KArgs kargs(pselinv_handle* h) {
   a.piv = h->pivoted ? (const int32_t*)h->d_piv : nullptr;
   a.ptype = h->pivoted ? (const int8_t*)h->d_ptype : nullptr;
   a.E = h->pivoted ? h->d_E : nullptr;
+  a.W = nullptr;
   return a;
 }
 
@@ -654,8 +655,17 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
   psi::KArgs au = a;
   au.L = h->d_U;
   au.Lhat = h->d_uhat;
+  // pivot-free: the panel solves also keep W = L_{C,K} D_K (and U'_{K,C}^T D_K),
+  // in the X (XU) panels, which a factorisation withdraws, as the Schur
+  // update's first operand
+  if (!bk) {
+    al.W = h->d_X;
+    if (unsym) au.W = h->d_XU;
+  }
   // Schur: L_{C,K} D U'_{K,C} into the L panels, and its strict upper part (transposed) into the U panels
   psi::KArgs sl = a, su = a;
+  sl.W = al.W;
+  su.W = au.W;
   if (unsym) {
     sl.Uhat = h->d_uhat;
     su.L = h->d_U;
@@ -1134,6 +1144,7 @@ int pselinv_selinv_adjoint(pselinv_handle* h, const void* d_G, int32_t g_kind, v
   }
   // adjoint of the supernodal LDL^T, root -> leaves
   PSI_CUDA(h, cudaMemsetAsync(h->d_xb, 0, B * h->panel_total * es, st));
+  PSI_CUDA(h, psi::launch_adj_per_sn(AdjSn::Ev, a, nullptr, h->nsn, st));
   for (int32_t l = 0; l < h->nlevels; ++l) {
     const int32_t* sns = lsn + h->level_ptr[l];
     const int nsl = h->level_ptr[l + 1] - h->level_ptr[l];

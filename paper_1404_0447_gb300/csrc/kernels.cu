@@ -18,6 +18,13 @@ namespace psi {
 // packed lower-triangular index, column-major: (i, j), i >= j, order s
 __device__ __forceinline__ int pk(int i, int j, int s) { return j * s - (j * (j - 1)) / 2 + (i - j); }
 
+// elements of the blocked inverse's scratch S for width s: (ceil(s/16) - 1)
+// blocks of 16 x 16 (at least one)
+__host__ __device__ __forceinline__ int fd_scratch(int s) {
+  const int nb = (s + 15) / 16;
+  return 256 * (nb > 1 ? nb - 1 : 1);
+}
+
 // Status words 0-1 hold one 64-bit key (column << 2 | kind), kind 1 = zero
 // pivot, 2 = non-finite: the minimum is the first bad column and, within
 // it, a zero pivot before its consequences.
@@ -109,29 +116,46 @@ __device__ void unit_lower_inverse(const T* Tp, int s, T* V) {
   }
 }
 
+// Where unit_lower_inverse_blocked keeps V: column-major in global memory
+// (ld s; the upper triangle is written as zeros), or packed lower in shared
+// memory (the pk layout; only the lower triangle exists).
+template <class T>
+struct VGlobal {
+  static constexpr bool kPacked = false;
+  T* p;
+  int s;
+  __device__ __forceinline__ T& operator()(int i, int j) const { return p[i + (int64_t)j * s]; }
+};
+template <class T>
+struct VPacked {
+  static constexpr bool kPacked = true;
+  T* p;
+  int s;
+  __device__ __forceinline__ T& operator()(int i, int j) const { return p[pk(i, j, s)]; }
+};
+
 // V = (L_KK)^{-1} for the unit lower triangle held packed in Tp (shared
 // memory), by 16 x 16 blocks so that the whole CTA works at every step:
 // first the diagonal blocks V_ii = (L_ii)^{-1} (one column per thread),
 // then, for block distance d = 1, 2, ... (all block pairs (i, j) with
 // i - j = d at once), S = sum_{k=j}^{i-1} L_ik V_kj and V_ij = -V_ii S.
-// V is written column-major to global memory (ld s, zeros above the
-// diagonal) and read back by the later steps of this CTA; S (shared) holds
-// (ceil(s/16) - 1) blocks of 16 x 16.
-template <class T>
-__device__ void unit_lower_inverse_blocked(const T* Tp, int s, T* V, T* S) {
+// V (see VGlobal / VPacked) is read back by the later steps of this CTA;
+// S (shared) holds (ceil(s/16) - 1) blocks of 16 x 16.
+template <class T, class VA>
+__device__ void unit_lower_inverse_blocked(const T* Tp, int s, const VA& V, T* S) {
   constexpr int B = 16;
   const int nb = (s + B - 1) / B;
   const int nt = blockDim.x, t = threadIdx.x;
   for (int c = t; c < s; c += nt) {
     const int i1 = min((c / B + 1) * B, s);
-    for (int i = 0; i < c; ++i) V[i + c * s] = Sc<T>::zero();
-    V[c + c * s] = Sc<T>::one();
+    if constexpr (!VA::kPacked)
+      for (int i = 0; i < c; ++i) V(i, c) = Sc<T>::zero();
+    V(c, c) = Sc<T>::one();
     for (int i = c + 1; i < i1; ++i) {
       T acc = Sc<T>::zero();
-      for (int q = c; q < i; ++q) acc += Tp[pk(i, q, s)] * V[q + c * s];
-      V[i + c * s] = -acc;
+      for (int q = c; q < i; ++q) acc += Tp[pk(i, q, s)] * V(q, c);
+      V(i, c) = -acc;
     }
-    for (int i = i1; i < s; ++i) V[i + c * s] = Sc<T>::zero();  // off-diagonal blocks: set below
   }
   __syncthreads();
   for (int d = 1; d < nb; ++d) {
@@ -140,8 +164,8 @@ __device__ void unit_lower_inverse_blocked(const T* Tp, int s, T* V, T* S) {
       const int j = e / (B * B), rr = (e / B) % B, cc = e % B;
       const int row = (j + d) * B + rr, col = j * B + cc;
       T acc = Sc<T>::zero();
-      if (row < s && col < s)
-        for (int q = j * B; q < (j + d) * B; ++q) acc += Tp[pk(row, q, s)] * V[q + col * s];
+      if (row < s && col < s)  // V(q, col) = 0 above the diagonal: q from col
+        for (int q = col; q < (j + d) * B; ++q) acc += Tp[pk(row, q, s)] * V(q, col);
       S[e] = acc;
     }
     __syncthreads();
@@ -150,8 +174,8 @@ __device__ void unit_lower_inverse_blocked(const T* Tp, int s, T* V, T* S) {
       const int i0 = (j + d) * B, row = i0 + rr, col = j * B + cc;
       if (row >= s || col >= s) continue;
       T acc = Sc<T>::zero();
-      for (int q = 0; q <= rr; ++q) acc += V[row + (i0 + q) * s] * S[j * B * B + q * B + cc];
-      V[row + col * s] = -acc;
+      for (int q = 0; q <= rr; ++q) acc += V(row, i0 + q) * S[j * B * B + q * B + cc];
+      V(row, col) = -acc;
     }
     __syncthreads();
   }
@@ -210,7 +234,16 @@ __global__ void k_factor_diag(const SnMeta* __restrict__ meta, const int32_t* __
     }
     __syncthreads();
   }
-  unit_lower_inverse_blocked(Tp, s, Linv + b * sz.linv + m.linv, S);
+  T* Vg = Linv + b * sz.linv + m.linv;
+  if constexpr (Sc<T>::P == 1) {
+    // real: V packed in shared memory after S, then written out with its zeros
+    T* Vs = S + fd_scratch(s);
+    unit_lower_inverse_blocked(Tp, s, VPacked<T>{Vs, s}, S);
+    for (int j = warp; j < s; j += nw)
+      for (int i = lane; i < s; i += 32) Vg[i + (int64_t)j * s] = i < j ? Sc<T>::zero() : Vs[pk(i, j, s)];
+  } else {
+    unit_lower_inverse_blocked(Tp, s, VGlobal<T>{Vg, s}, S);
+  }
   for (int j = warp; j < s; j += nw) {
     const int cb = pk(j, j, s);
     for (int i = j + lane; i < s; i += 32) P[i + (int64_t)j * ld] = Tp[cb + i - j];
@@ -269,9 +302,9 @@ __global__ void k_factor_diag_lu(const SnMeta* __restrict__ meta, const int32_t*
   }
   if constexpr (Sc<T>::P == 1) {  // real: the blocked inverses (their 16 x 16 scratch after the triangles)
     T* S = Tu + s * (s + 1) / 2;
-    unit_lower_inverse_blocked(Tl, s, Linv + b * sz.linv + m.linv, S);
+    unit_lower_inverse_blocked(Tl, s, VGlobal<T>{Linv + b * sz.linv + m.linv, s}, S);
     __syncthreads();
-    unit_lower_inverse_blocked(Tu, s, Uinv + b * sz.linv + m.linv, S);
+    unit_lower_inverse_blocked(Tu, s, VGlobal<T>{Uinv + b * sz.linv + m.linv, s}, S);
   } else {  // complex: both triangles fill the shared memory
     unit_lower_inverse(Tl, s, Linv + b * sz.linv + m.linv);
     unit_lower_inverse(Tu, s, Uinv + b * sz.linv + m.linv);
@@ -583,7 +616,7 @@ __global__ void k_factor_diag_bk(const SnMeta* __restrict__ meta, const int32_t*
     if (t == 0) report_pivot(status, m.f + k, sh_bad == 1);
     return;
   }
-  unit_lower_inverse_blocked(Tp, s, Linv + b * sz.linv + m.linv, reinterpret_cast<T*>(perm + ((s + 3) & ~3)));
+  unit_lower_inverse_blocked(Tp, s, VGlobal<T>{Linv + b * sz.linv + m.linv, s}, reinterpret_cast<T*>(perm + ((s + 3) & ~3)));
   for (int e = t; e < s * s; e += nt) {
     const int i = e % s, j = e / s;
     if (i > j) P[i + (int64_t)j * ld] = Tp[pk(i, j, s)];
@@ -654,14 +687,16 @@ __global__ void k_copyback(const SnMeta* __restrict__ meta, const int32_t* __res
 // tile GEMMs
 // --------------------------------------------------------------------------
 
-// Factorisation panel solve: Ltmp_{C,K} = A_{C,K} (L_KK)^{-T} D_K^{-1}.
+// Factorisation panel solve: Ltmp_{C,K} = A_{C,K} (L_KK)^{-T} D_K^{-1}, and,
+// when W is set, W_{C,K} = A_{C,K} (L_KK)^{-T} itself (the Schur update's
+// L_{C,K} D_K without a product per operand element; KArgs::W).
 // Pivoted factor (piv set): the columns of A_{C,K} are read in pivot order
 // and D^{-1} is left to k_copyback_bk (2x2 blocks can straddle tiles).
 template <class T, int BN>
 __global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_trsm(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
                                                      const T* __restrict__ L, const T* __restrict__ D,
                                                      const T* __restrict__ Linv, T* __restrict__ Ltmp, Sizes sz,
-                                                     const int32_t* __restrict__ piv) {
+                                                     const int32_t* __restrict__ piv, T* __restrict__ W) {
   __shared__ TileSmem<T, BN> sm;
   const Task tk = tasks[blockIdx.x];
   const int b = blockIdx.y;
@@ -685,9 +720,13 @@ __global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_trsm(c
   tile_mma<T, BN>(sm, 0, min(s, tk.n0 + BN), [](int) { return false; }, la, lb, acc,
                   LiveRect{r - tk.m0, s - tk.n0}, KUpperB<BN>{tk.n0});
   T* out = Ltmp + b * sz.lhat + m.lhat;
+  T* wout = W ? W + b * sz.panel + m.panel : nullptr;
   tile_epilogue<T, BN>(acc, [&](int mm, int nn, T v) {
     const int row = tk.m0 + mm, col = tk.n0 + nn;
-    if (row < r && col < s) out[row + (int64_t)col * r] = pv ? v : v / d[col];
+    if (row < r && col < s) {
+      out[row + (int64_t)col * r] = pv ? v : v / d[col];
+      if (wout) wout[row + (int64_t)col * r] = v;
+    }
   });
 }
 
@@ -702,14 +741,18 @@ __global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_trsm(c
 // Non-symmetric factor: Ltmp2 is the second operand (U'_{K,C}^T), giving
 // L_{C,K} D_K U'_{K,C} into the L panels and, called again with the operands
 // swapped and `strict`, (U'_{K,C}^T D_K L_{C,K}^T) below the diagonal into the
-// U panels.
+// U panels.  W set (pivot-free factor): the first operand is W_{C,K} =
+// L_{C,K} D_K (or U'_{K,C}^T D_K) as the panel solve left it, so the loads carry no
+// FP64 product (a product per A element is 64 x 16 FP64 operations per
+// k-tile, 1/8 of the MMA work of a 64 x 8 tile on the same pipe).
 template <class T, int BN>
 __global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_schur(const SnMeta* __restrict__ meta, const Task* __restrict__ tasks,
                                                       const ColDesc* __restrict__ desc,
                                                       const int32_t* __restrict__ relidx, T* __restrict__ L,
                                                       const T* __restrict__ D, const T* __restrict__ Ltmp,
                                                       const T* __restrict__ Ltmp2, int strict, Sizes sz,
-                                                      const int8_t* __restrict__ ptype, const T* __restrict__ E) {
+                                                      const int8_t* __restrict__ ptype, const T* __restrict__ E,
+                                                      const T* __restrict__ W) {
   __shared__ TileSmem<T, BN> sm;
   const Task tk = tasks[blockIdx.x];
   const int b = blockIdx.y;
@@ -722,9 +765,11 @@ __global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_schur(
   acc_zero<T, BN>(acc);
   const int8_t* ty = ptype ? ptype + b * sz.n + m.f : nullptr;
   const T* ee = ptype ? E + b * sz.n + m.f : nullptr;
+  const T* Wc = W ? W + b * sz.panel + m.panel : nullptr;
   auto la = [&](int mm, int kk) {
     const int row = tk.m0 + mm;
     if (row >= r) return Sc<T>::zero();
+    if (Wc) return Wc[row + (int64_t)kk * r];
     T v = Lc[row + (int64_t)kk * r] * d[kk];
     if (ty && ty[kk] == 1) v += Lc[row + (int64_t)(kk + 1) * r] * ee[kk];       // (L D) with a 2x2 block
     if (ty && ty[kk] == 2) v += Lc[row + (int64_t)(kk - 1) * r] * ee[kk - 1];
@@ -926,8 +971,9 @@ static size_t diag_smem(int maxw) {
 // and the 16 x 16 blocks S of the blocked inverse
 template <class T>
 static size_t diag_smem_fd(int maxw) {
-  const size_t nb = (size_t)(maxw + 15) / 16;
-  return sizeof(T) * ((size_t)maxw * (maxw + 1) / 2 + (size_t)maxw + 256 * (nb > 1 ? nb - 1 : 1));
+  // packed L_KK, u, S; real: the packed inverse too (complex keeps it in global memory)
+  const size_t tri = (size_t)maxw * (maxw + 1) / 2;
+  return sizeof(T) * (tri + (size_t)maxw + fd_scratch(maxw) + (Sc<T>::P == 1 ? tri : 0));
 }
 
 // the pivoted diagonal factorisation: diag_smem plus the blocks of the inverse
@@ -1032,12 +1078,12 @@ static cudaError_t tiles_tb(Kern k, const KArgs& a, const Task* t, int64_t n, cu
   switch (k) {
     case Kern::Trsm:
       k_trsm<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.L, (const T*)a.D, (const T*)a.Linv,
-                                                 (T*)a.Lhat, a.sz, a.piv);
+                                                 (T*)a.Lhat, a.sz, a.piv, (T*)a.W);
       break;
     case Kern::Schur:
       k_schur<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, a.desc, a.relidx, (T*)a.L, (const T*)a.D,
                                                   (const T*)a.Lhat, (const T*)(a.Uhat ? a.Uhat : a.Lhat),
-                                                  a.strict, a.sz, a.ptype, (const T*)a.E);
+                                                  a.strict, a.sz, a.ptype, (const T*)a.E, (const T*)a.W);
       break;
     case Kern::Lhat:
       k_lhat<T, BN><<<grid, TG_THREADS, 0, st>>>(a.meta, t, (const T*)a.L, (const T*)a.Linv, (T*)a.Lhat, a.sz);

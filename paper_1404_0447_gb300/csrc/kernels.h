@@ -56,6 +56,11 @@ struct KArgs {
   const int32_t* piv;  // supernode-local original column at each pivot position
   const int8_t* ptype; // 0 = 1x1 pivot, 1 / 2 = first / second column of a 2x2 pivot
   const void* E;       // D_{k+1,k} of a 2x2 pivot, at its first column
+  // pivot-free factor: W_{C,K} = L_{C,K} D_K (U side: U'_{K,C}^T D_K), the
+  // panel solve's product before the D^{-1} scaling, kept for the Schur
+  // update; r x s column-major at each supernode's panel offset of this array
+  // (the X or XU panels, free during the factorisation); nullptr otherwise
+  void* W;
 };
 
 // Original local column of pivot position k of the supernode starting at f.
@@ -173,7 +178,7 @@ struct AdjArgs {
   void* Hb;       // r x s per supernode: Lhat-bar
 };
 enum class AdjKern { Ybar, Lhbar, LbarOff, T1, Q, Vpart, Rpart, Syr2k, Dr1, Dr3, Dr4, Df2, Df3, Df4 };
-enum class AdjSn { Seed, Zbar, Dr2, Df1, Df5, SumParts };
+enum class AdjSn { Seed, Ev, Zbar, Dr2, Df1, Df5, SumParts };
 cudaError_t launch_adj_tiles(AdjKern k, int var, const AdjArgs& a, const Task* tasks, int64_t n, cudaStream_t st);
 cudaError_t launch_adj_per_sn(AdjSn k, const AdjArgs& a, const int32_t* sns, int nsn, cudaStream_t st);
 

@@ -309,4 +309,35 @@ __device__ __forceinline__ void tile_epilogue(const Acc<T, BN>& acc, const F& f)
       }
 }
 
+// acc(mm, nn) = f(mm, nn, acc(mm, nn)) for every element of the tile
+// (tile-local coordinates as in tile_epilogue).
+template <class T, int BN, class F>
+__device__ __forceinline__ void tile_update(Acc<T, BN>& acc, const F& f) {
+  using G = Geo<BN>;
+  const int t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const int wm = (warp % G::WM) * (TG_BM / G::WM), wn = (warp / G::WM) * (BN / G::WN);
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int i = 0; i < G::FM; ++i)
+#pragma unroll
+    for (int j = 0; j < G::FN; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        T v;
+        if constexpr (Sc<T>::P == 1) {
+          v = acc[0][i][j][e];
+        } else {
+          v = T{acc[0][i][j][e], acc[1][i][j][e]};
+        }
+        v = f(wm + 8 * i + g, wn + 8 * j + 2 * q + e, v);
+        if constexpr (Sc<T>::P == 1) {
+          acc[0][i][j][e] = v;
+        } else {
+          acc[0][i][j][e] = v.re;
+          acc[1][i][j][e] = v.im;
+        }
+      }
+}
+
 }  // namespace psi
