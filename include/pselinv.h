@@ -262,7 +262,8 @@ int pselinv_factor(pselinv_handle* h, const void* d_values, void* stream);
  * diagonal on the diagonal slots); the selected inversion undoes the order,
  * so X, pselinv_get_selected, pselinv_logdet and pselinv_logdet_grad are as
  * for pselinv_factor.  pselinv_selinv_adjoint needs the pivot-free factor.
- * d_values as for pselinv_factor.  Errors: ERR_ZERO_PIVOT for a reduced
+ * d_values as for pselinv_factor (the X panels serve as scratch here too).
+ * Errors: ERR_ZERO_PIVOT for a reduced
  * column that is entirely zero or a singular 2x2 block (first column, internal
  * order) and ERR_NONFINITE, both reported as for pselinv_factor (no
  * synchronisation here), ERR_STATE on non-symmetric handles.

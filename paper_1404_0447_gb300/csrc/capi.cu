@@ -655,13 +655,11 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
   psi::KArgs au = a;
   au.L = h->d_U;
   au.Lhat = h->d_uhat;
-  // pivot-free: the panel solves also keep W = L_{C,K} D_K (and U'_{K,C}^T D_K),
-  // in the X (XU) panels, which a factorisation withdraws, as the Schur
-  // update's first operand
-  if (!bk) {
-    al.W = h->d_X;
-    if (unsym) au.W = h->d_XU;
-  }
+  // the panel solves also keep W = L_{C,K} D_K (U'_{K,C}^T D_K; with pivots,
+  // D_K's 1 x 1 and 2 x 2 blocks), in the X (XU) panels, which a factorisation
+  // withdraws, as the Schur update's first operand
+  al.W = h->d_X;
+  if (unsym) au.W = h->d_XU;
   // Schur: L_{C,K} D U'_{K,C} into the L panels, and its strict upper part (transposed) into the U panels
   psi::KArgs sl = a, su = a;
   sl.W = al.W;
@@ -708,10 +706,13 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
     // diagonal factorisation are serial, the work inside each step is not
     int wmax = 0;
     for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) wmax = std::max(wmax, h->meta[h->level_sn[t]].s);
+    // shared memory sized for the level's widest block: several CTAs per SM on levels of narrow supernodes
+    psi::KArgs ad = a;
+    ad.maxw = wmax;
     PSI_CUDA(h, psi::launch_per_sn(unsym ? psi::Kern::FactorDiagLU
                                          : bk  ? psi::Kern::FactorDiagBK
                                                : psi::Kern::FactorDiag,
-                                   a, sns, nsl, hi, wmax >= 64 ? 1024 : 256));
+                                   ad, sns, nsl, hi, wmax >= 64 ? 1024 : 256));
     for (int side = 0; side < (unsym ? 2 : 1); ++side) {
       const psi::KArgs& ka = side ? au : al;
       for (int v = 0; v < psi::kNumVar; ++v) {

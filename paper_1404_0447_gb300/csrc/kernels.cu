@@ -741,8 +741,8 @@ __global__ void __launch_bounds__(TG_THREADS, (tile_min_ctas<T, BN>())) k_trsm(c
 // Non-symmetric factor: Ltmp2 is the second operand (U'_{K,C}^T), giving
 // L_{C,K} D_K U'_{K,C} into the L panels and, called again with the operands
 // swapped and `strict`, (U'_{K,C}^T D_K L_{C,K}^T) below the diagonal into the
-// U panels.  W set (pivot-free factor): the first operand is W_{C,K} =
-// L_{C,K} D_K (or U'_{K,C}^T D_K) as the panel solve left it, so the loads carry no
+// U panels.  W set: the first operand is W_{C,K} = L_{C,K} D_K (or
+// U'_{K,C}^T D_K; pivoted: with D's 2 x 2 blocks) as the panel solve left it, so the loads carry no
 // FP64 product (a product per A element is 64 x 16 FP64 operations per
 // k-tile, 1/8 of the MMA work of a 64 x 8 tile on the same pipe).
 template <class T, int BN>

@@ -56,10 +56,11 @@ struct KArgs {
   const int32_t* piv;  // supernode-local original column at each pivot position
   const int8_t* ptype; // 0 = 1x1 pivot, 1 / 2 = first / second column of a 2x2 pivot
   const void* E;       // D_{k+1,k} of a 2x2 pivot, at its first column
-  // pivot-free factor: W_{C,K} = L_{C,K} D_K (U side: U'_{K,C}^T D_K), the
-  // panel solve's product before the D^{-1} scaling, kept for the Schur
-  // update; r x s column-major at each supernode's panel offset of this array
-  // (the X or XU panels, free during the factorisation); nullptr otherwise
+  // factor: W_{C,K} = L_{C,K} D_K (U side: U'_{K,C}^T D_K; pivoted: D_K's
+  // 1 x 1 and 2 x 2 blocks, columns in pivot order), the panel solve's
+  // product before the D^{-1} scaling, kept for the Schur update; r x s
+  // column-major at each supernode's panel offset of this array (the X or XU
+  // panels, free during the factorisation); nullptr elsewhere
   void* W;
 };
 
