@@ -612,11 +612,37 @@ int ensure_factor_streams(pselinv_handle* h) {
     PSI_CUDA(h, cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, least));
     h->fs_lo = s;
   }
-  const size_t need = 2 * (size_t)h->nlevels + 3;
+  const size_t need = 3 * (size_t)h->nlevels + 3;
   while (h->fev.size() < need) {
     cudaEvent_t e;
     PSI_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     h->fev.push_back(e);
+  }
+  if (h->far_after_near.empty()) {
+    // Per level l: does far(l) wait for near(l), so that level l - 1's
+    // diagonal blocks start beside it?  A diagonal-block CTA does not fit on
+    // an SM beside resident Schur tiles, so when far(l) is already running the
+    // next diagonal blocks wait for its end.  Worth it when far(l) is short
+    // against the next level's diagonal blocks and panel solves (model: FP64
+    // work at 1 TFLOP/s; a diagonal block of width w, 345 us (w / 128)^3 +
+    // 30 us, measured on the 1,024-thread kernel).
+    const int32_t nl = h->nlevels;
+    std::vector<double> t_far(nl, 0.0), t_next(nl, 0.0);
+    for (int32_t l = 0; l < nl; ++l) {
+      double far = 0.0, solve = 0.0;
+      int wmax = 0;
+      for (int32_t t = h->level_ptr[l]; t < h->level_ptr[l + 1]; ++t) {
+        const psi::SnMeta& m = h->meta[h->level_sn[t]];
+        far += (double)m.r * (m.r + 1) * m.s;
+        solve += (double)m.r * m.s * m.s;
+        wmax = std::max(wmax, m.s);
+      }
+      const double w = wmax / 128.0;
+      t_far[l] = far / 1e12;
+      t_next[l] = 345e-6 * w * w * w + 30e-6 + solve / 1e12;
+    }
+    h->far_after_near.assign(nl, 0);
+    for (int32_t l = 1; l < nl; ++l) h->far_after_near[l] = t_far[l] < 4.0 * t_next[l - 1];
   }
   return PSELINV_OK;
 }
@@ -678,11 +704,15 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
   // level l overlaps the diagonal blocks and panel solves of level l - 1.
   // Events keep every target's updates in a fixed order: far(l) waits for
   // the panel solves of l (its operand); near(l) waits for far(l + 1), the
-  // last earlier update of level l - 1's panels.
+  // last earlier update of level l - 1's panels.  On levels whose far update
+  // is short (far_after_near), far(l) waits for near(l) instead, so that the
+  // diagonal blocks of l - 1 get their SMs before far(l)'s tiles fill them;
+  // every target sees its updates in the same order either way.
   int rc;
   if ((rc = ensure_factor_streams(h))) return rc;
   cudaStream_t hi = (cudaStream_t)h->fs_hi, lo = (cudaStream_t)h->fs_lo;
-  cudaEvent_t* ev = (cudaEvent_t*)h->fev.data();  // [0] start, [1 + l] solves of l, [1 + nl + l] far of l
+  // [0] start, [1 + l] solves of l, [1 + nl + l] far of l, [3 + 2 nl + l] near of l
+  cudaEvent_t* ev = (cudaEvent_t*)h->fev.data();
   const int32_t nl = h->nlevels;
   PSI_CUDA(h, cudaEventRecord(ev[0], st));
   PSI_CUDA(h, cudaStreamWaitEvent(hi, ev[0], 0));
@@ -725,12 +755,21 @@ int factor_impl(pselinv_handle* h, const void* d_lower, const void* d_upper, cud
       // factorisation reads L_{C,K} from them): once for all levels, after the loop
       if (bk) PSI_CUDA(h, psi::launch_per_sn(psi::Kern::CopyBackBK, ka, sns, nsl, hi));
     }
-    PSI_CUDA(h, cudaEventRecord(ev[1 + l], hi));
-    PSI_CUDA(h, cudaStreamWaitEvent(lo, ev[1 + l], 0));
-    PSI_CUDA(h, schur(h->schur_far, h->schur_gptr[l], h->schur_gptr[l + 1], lo));
-    PSI_CUDA(h, cudaEventRecord(ev[1 + nl + l], lo));
-    if (l + 1 < nl) PSI_CUDA(h, cudaStreamWaitEvent(hi, ev[1 + nl + l + 1], 0));
-    PSI_CUDA(h, schur(h->schur_near, h->schur_gptr[l], h->schur_gptr[l + 1], hi));
+    if (h->far_after_near[l]) {
+      if (l + 1 < nl) PSI_CUDA(h, cudaStreamWaitEvent(hi, ev[1 + nl + l + 1], 0));
+      PSI_CUDA(h, schur(h->schur_near, h->schur_gptr[l], h->schur_gptr[l + 1], hi));
+      PSI_CUDA(h, cudaEventRecord(ev[3 + 2 * nl + l], hi));
+      PSI_CUDA(h, cudaStreamWaitEvent(lo, ev[3 + 2 * nl + l], 0));
+      PSI_CUDA(h, schur(h->schur_far, h->schur_gptr[l], h->schur_gptr[l + 1], lo));
+      PSI_CUDA(h, cudaEventRecord(ev[1 + nl + l], lo));
+    } else {
+      PSI_CUDA(h, cudaEventRecord(ev[1 + l], hi));
+      PSI_CUDA(h, cudaStreamWaitEvent(lo, ev[1 + l], 0));
+      PSI_CUDA(h, schur(h->schur_far, h->schur_gptr[l], h->schur_gptr[l + 1], lo));
+      PSI_CUDA(h, cudaEventRecord(ev[1 + nl + l], lo));
+      if (l + 1 < nl) PSI_CUDA(h, cudaStreamWaitEvent(hi, ev[1 + nl + l + 1], 0));
+      PSI_CUDA(h, schur(h->schur_near, h->schur_gptr[l], h->schur_gptr[l + 1], hi));
+    }
   }
   PSI_CUDA(h, cudaEventRecord(ev[1 + 2 * nl], hi));
   PSI_CUDA(h, cudaStreamWaitEvent(st, ev[1 + 2 * nl], 0));

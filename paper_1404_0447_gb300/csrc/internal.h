@@ -232,6 +232,7 @@ struct pselinv_handle {
   void* fs_hi = nullptr;
   void* fs_lo = nullptr;
   std::vector<void*> fev;
+  std::vector<uint8_t> far_after_near;  // per level: far(l) waits for near(l) (factor_impl)
 
   // optional kernel timing (pselinv_set_timing)
   bool timing = false;
