@@ -633,6 +633,8 @@ def run_workload(args):
         gam = torch.empty(info["panel_entries"], dtype=torch.complex128, device=dev)
         line["pole_sum_ms"] = _time(lambda: h.pole_sum(wts, out=gam, stream=st), 3, 1, st)
         line["pole_sum_GBps"] = (info["batch"] + 1) * info["panel_entries"] * 16 / (line["pole_sum_ms"] * 1e-3) / 1e9
+        # the same sum accumulated in the sweep's write step: selinv + Gamma in one call
+        line["selinv_pole_sum_fused_ms"] = _time(lambda: h.selinv_pole_sum(wts, out=gam, stream=st), 1, 1, st)
         line["trace_E_per_pole"] = [float(e) for e in h.trace_error(vals.view(-1), stream=st)]
     if w == "indefinite80":
         piv, ty = h.pivots(stream=st)

@@ -400,6 +400,21 @@ int pselinv_logdet_grad(pselinv_handle* h, void* d_out, void* stream);
 int pselinv_pole_sum(pselinv_handle* h, const double* h_weights, void* d_out, void* stream);
 
 /*
+ * The selected inversion of the batch (LEVEL schedule, as pselinv_selinv)
+ * with the pole sum of Section 4.4 accumulated in its write step:
+ * d_out = sum_b w_b X_b in the X panel layout, formed while the sweep runs.
+ * The step-3 finish writes each panel entry last, so the CTA that finishes a
+ * supernode's share for the last member of the batch sums that share over
+ * the members in order b = 0, 1, ... (no value atomics; bitwise
+ * reproducible, the same arithmetic as pselinv_pole_sum).  The X panels of
+ * every member are kept as by pselinv_selinv.  h_weights as for
+ * pselinv_pole_sum.  Errors: ERR_ARG (NULL argument, fp64_emulation set),
+ * ERR_STATE (non-symmetric handle, no factor, a pivoted factor), ERR_OOM,
+ * ERR_CUDA.  Allocates nsn x 32 counters on first use.
+ */
+int pselinv_selinv_pole_sum(pselinv_handle* h, const double* h_weights, void* d_out, void* stream);
+
+/*
  * Trace pairing of Section 4.3, Eq. (16): for every batch member b,
  * S_b = sum over the nonzeros of A_b (both triangles) of X_ij A_ji, so that
  * E_b = |1 - S_b / n|.  d_values: the batch's values of A (as passed to

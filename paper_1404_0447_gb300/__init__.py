@@ -25,7 +25,8 @@ G_SYMMETRIC, G_PANEL = 0, 1
 
 EXPORTED = ["pselinv_default_opts", "pselinv_analyze", "pselinv_analyze_batch", "pselinv_factor",
             "pselinv_factor_unsym", "pselinv_factor_bk", "pselinv_get_pivots", "pselinv_selinv",
-            "pselinv_selinv_to_host", "pselinv_get_panels", "pselinv_pole_sum", "pselinv_trace_sum",
+            "pselinv_selinv_to_host", "pselinv_get_panels", "pselinv_pole_sum", "pselinv_selinv_pole_sum",
+            "pselinv_trace_sum",
             "pselinv_sync_status", "pselinv_set_debug", "pselinv_get_selected", "pselinv_get_selected_upper",
             "pselinv_logdet_grad", "pselinv_logdet",
             "pselinv_selinv_adjoint",
@@ -93,6 +94,7 @@ def load_library():
     L.pselinv_get_panels.argtypes = [vp, ctypes.c_int32, vp, vp]
     L.pselinv_sync_status.argtypes = [vp, vp]
     L.pselinv_pole_sum.argtypes = [vp, vp, vp, vp]
+    L.pselinv_selinv_pole_sum.argtypes = [vp, vp, vp, vp]
     L.pselinv_trace_sum.argtypes = [vp, vp, vp, vp]
     L.pselinv_set_debug.argtypes = [vp, ctypes.c_int32]
     L.pselinv_get_selected.argtypes = [vp, vp, vp]
@@ -275,6 +277,18 @@ class SelInv:
             out = torch.empty(self.info["panel_entries"], dtype=self.torch_dtype, device="cuda")
         self._check(self._lib.pselinv_pole_sum(self._h, ctypes.c_void_p(w.ctypes.data),
                                                ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def selinv_pole_sum(self, weights, out=None, stream=None):
+        """pselinv_selinv_pole_sum: the batch's selected inversion (LEVEL) with
+        sum_b w_b X_b accumulated in its write step (X panel layout)."""
+        import torch
+        w = np.ascontiguousarray(weights, np.complex128 if self.opts.dtype == C128 else np.float64)
+        assert w.size == self.opts.batch
+        if out is None:
+            out = torch.empty(self.info["panel_entries"], dtype=self.torch_dtype, device="cuda")
+        self._check(self._lib.pselinv_selinv_pole_sum(self._h, ctypes.c_void_p(w.ctypes.data),
+                                                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
 
     def trace_error(self, values, stream=None):

@@ -70,7 +70,8 @@ void free_device(pselinv_handle* h) {
                    &h->d_status, &h->d_flipmap, &h->d_U, &h->d_XU, &h->d_uhat, &h->d_uinv,
                    &h->d_piv, &h->d_ptype, &h->d_E, &h->d_snlevel, &h->d_yring, &h->d_pring,
                    &h->d_xb,   &h->d_lb,   &h->d_db,     &h->d_zb,     &h->d_w1,    &h->d_yb,   &h->d_hb,
-                   &h->d_plist, &h->d_pn,  &h->d_pctr, &h->d_xs, &h->d_ls, &h->d_sig, &h->d_lexp, &h->d_gexp, &h->d_crow};
+                   &h->d_plist, &h->d_pn,  &h->d_pctr, &h->d_xs, &h->d_ls, &h->d_sig, &h->d_lexp, &h->d_gexp, &h->d_crow,
+                   &h->d_tctr, &h->d_gctr};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -289,6 +290,9 @@ psi::KArgs kargs(pselinv_handle* h) {
   a.ptype = h->pivoted ? (const int8_t*)h->d_ptype : nullptr;
   a.E = h->pivoted ? h->d_E : nullptr;
   a.W = nullptr;
+  a.gw = nullptr;
+  a.gam = nullptr;
+  a.gctr = nullptr;
   return a;
 }
 
@@ -391,6 +395,13 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
   if (!emul) {
     a2.tctr = a4f.tctr = (int*)h->d_tctr;
   }
+  // step-3 finish; pselinv_selinv_pole_sum: with the pole sum of its entries
+  psi::KArgs af = a;
+  if (h->pole_gam) {
+    af.gw = (const double*)((int*)h->d_status + kStatusWords) + 2 * h->opts.batch;
+    af.gam = h->pole_gam;
+    af.gctr = (int*)h->d_gctr;
+  }
   auto step = [&](const int32_t* sns, int nsn_step, const psi::Range* r1, const psi::Range* r2, bool split,
                   int maxr) {
     int n1 = (split && emul) ? 1 : 0, n2 = 0, e;
@@ -424,7 +435,7 @@ int enqueue_selinv(pselinv_handle* h, int mode, cudaStream_t st, bool record,
          })))
       return e;
     if ((e = tm.run(3, (nsn_step > 0) * (emul ? 2 : 1), [&] {
-           cudaError_t x = psi::launch_per_sn(Kern::DiagFinal, a, sns, nsn_step, st);
+           cudaError_t x = psi::launch_per_sn(Kern::DiagFinal, af, sns, nsn_step, st);
            if (emul && x == cudaSuccess) x = psi::launch_em_split_x(a, em, sns, nsn_step, st);
            return x;
          })))
@@ -1069,6 +1080,31 @@ int pselinv_pole_sum(pselinv_handle* h, const double* h_weights, void* d_out, vo
   const size_t wbytes = sizeof(double) * (h->opts.dtype == PSELINV_C128 ? 2 : 1) * B;
   PSI_CUDA(h, cudaMemcpyAsync(w, h_weights, wbytes, cudaMemcpyHostToDevice, st));
   PSI_CUDA(h, psi::launch_pole_sum(h->opts.dtype, h->d_X, h->panel_total, B, w, d_out, st));
+  return PSELINV_OK;
+}
+
+int pselinv_selinv_pole_sum(pselinv_handle* h, const double* h_weights, void* d_out, void* stream) {
+  if (!h || !h_weights || !d_out) return set_err(h, PSELINV_ERR_ARG, "NULL argument");
+  if (h->opts.unsym) return set_err(h, PSELINV_ERR_STATE, "symmetric handles only");
+  if (!h->factored) return set_err(h, PSELINV_ERR_STATE, "selinv called before a successful factor");
+  if (h->pivoted) return set_err(h, PSELINV_ERR_STATE, "the fused pole sum needs the pivot-free factor");
+  if (h->opts.fp64_emulation) return set_err(h, PSELINV_ERR_ARG, "the fused pole sum runs without fp64_emulation");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if (!h->d_gctr) {
+    const int64_t n = (int64_t)h->nsn * psi::kFinishCtas;
+    if ((rc = alloc(h, &h->d_gctr, (int64_t)sizeof(int) * n))) return rc;
+    PSI_CUDA(h, cudaMemsetAsync(h->d_gctr, 0, sizeof(int) * n, st));
+  }
+  const int B = h->opts.batch;
+  double* w = (double*)((int*)h->d_status + kStatusWords) + 2 * B;
+  const size_t wbytes = sizeof(double) * (h->opts.dtype == PSELINV_C128 ? 2 : 1) * B;
+  PSI_CUDA(h, cudaMemcpyAsync(w, h_weights, wbytes, cudaMemcpyHostToDevice, st));
+  h->pole_gam = d_out;
+  rc = enqueue_selinv(h, PSELINV_LEVEL, st, h->timing);
+  h->pole_gam = nullptr;
+  if (rc) return rc;
+  h->inverted = true;
   return PSELINV_OK;
 }
 

@@ -185,6 +185,8 @@ struct pselinv_handle {
   void* d_part = nullptr;   // step-3 partial products (level-local)
   void* d_ypart = nullptr;  // step-2 partial products (level-local)
   void* d_tctr = nullptr;   // int, batch x tctr_total: slices of a step-2 output tile finished (reset to 0)
+  void* d_gctr = nullptr;   // int, nsn x kFinishCtas: batch members whose finish part is done (pole sum)
+  void* pole_gam = nullptr; // set during pselinv_selinv_pole_sum: its Gamma output
   void* d_status = nullptr; // device status words
   // Bunch-Kaufman pivoted factor (pselinv_factor_bk), batch x n each
   bool pivoted = false;

@@ -663,9 +663,54 @@ __global__ void k_copyback_bk(const SnMeta* __restrict__ meta, const int32_t* __
   }
 }
 
+// Pole sum in the write step (Section 4.4's expansion Gamma = sum_b w_b X_b,
+// batch members b = poles): the finish is the last write of every panel
+// entry (X_{C,K} is final since step 2, X_KK once the finish's CTAs have
+// run), so after CTA `part` of supernode k has finished member b it counts
+// itself on the counter of (k, part); the one that completes the batch forms
+// Gamma over the entries this part owns (its X_KK pairs, both triangles, and
+// a 1/nparts share of X_{C,K}), summing the members in order b = 0, 1, ...:
+// no atomics on values, every Gamma entry written once, the same arithmetic
+// as the separate pass (k_pole_sum).  Pivot-free symmetric factors only.
+template <class T>
+__device__ void pole_share(const KArgs& a, int k, int part, int nparts) {
+  const Sizes& sz = a.sz;
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    int* ctr = a.gctr + (int64_t)k * nparts + part;
+    last = atomicAdd(ctr, 1) == sz.batch - 1;
+    if (last) *ctr = 0;
+    __threadfence();
+  }
+  __syncthreads();
+  if (!last) return;
+  const SnMeta m = a.meta[k];
+  const int s = m.s, r = m.r, ld = s + r;
+  const T* w = (const T*)a.gw;
+  const T* X = (const T*)a.X + m.panel;
+  T* G = (T*)a.gam + m.panel;
+  auto gsum = [&](int64_t idx) {
+    T acc = Sc<T>::zero();
+    for (int q = 0; q < sz.batch; ++q) acc += w[q] * ld_cg(X + q * sz.panel + idx);
+    G[idx] = acc;
+  };
+  for (int e = threadIdx.x + part * blockDim.x; e < s * s; e += nparts * blockDim.x) {
+    const int i = e % s, j = e / s;
+    if (i < j) continue;
+    gsum(i + (int64_t)j * ld);
+    if (i != j) gsum(j + (int64_t)i * ld);
+  }
+  const int64_t rs = (int64_t)r * s;
+  for (int64_t q = threadIdx.x + (int64_t)part * blockDim.x; q < rs; q += (int64_t)nparts * blockDim.x)
+    gsum(s + q % r + (q / r) * ld);
+}
+
 template <class T>
 __global__ void k_diag_final(KArgs a, const int32_t* __restrict__ sns) {
   step3_finish<T>(a, sns[blockIdx.x], blockIdx.y, blockIdx.z, gridDim.z, false);
+  if (a.gam) pole_share<T>(a, sns[blockIdx.x], blockIdx.z, gridDim.z);
 }
 
 // Copy the factor scratch back into the panels of the level's supernodes
@@ -1157,7 +1202,7 @@ static cudaError_t per_sn_t(Kern k, const KArgs& a, const int32_t* sns, int nsn,
     default:
       // 32 CTAs per supernode: the levels near the root hold one supernode whose
       // finish reads one s x s partial per row chunk of C
-      k_diag_final<T><<<dim3(nsn, a.sz.batch, 32), 256, 0, st>>>(a, sns);
+      k_diag_final<T><<<dim3(nsn, a.sz.batch, kFinishCtas), 256, 0, st>>>(a, sns);
       break;
   }
   return cudaGetLastError();

@@ -56,6 +56,12 @@ struct KArgs {
   const int32_t* piv;  // supernode-local original column at each pivot position
   const int8_t* ptype; // 0 = 1x1 pivot, 1 / 2 = first / second column of a 2x2 pivot
   const void* E;       // D_{k+1,k} of a 2x2 pivot, at its first column
+  // pole sum accumulated in the step-3 finish (pselinv_selinv_pole_sum):
+  // weights w_b (batch), Gamma = sum_b w_b X_b (one panel array), counters
+  // (nsn x kFinishCtas, zero between launches); nullptr otherwise
+  const void* gw;
+  void* gam;
+  int* gctr;
   // factor: W_{C,K} = L_{C,K} D_K (U side: U'_{K,C}^T D_K; pivoted: D_K's
   // 1 x 1 and 2 x 2 blocks, columns in pivot order), the panel solve's
   // product before the D^{-1} scaling, kept for the Schur update; r x s
@@ -63,6 +69,9 @@ struct KArgs {
   // panels, free during the factorisation); nullptr elsewhere
   void* W;
 };
+
+// CTAs of the per-level step-3 finish per supernode (blockIdx.z of k_diag_final).
+constexpr int kFinishCtas = 32;
 
 // Original local column of pivot position k of the supernode starting at f.
 __device__ __forceinline__ int pcol(const KArgs& a, int b, int f, int k) {

@@ -111,6 +111,48 @@ def test_pole_sum_and_trace_error_per_pole(P):
         assert E[l] < 1e-12
 
 
+@pytest.mark.parametrize("wmax", [32, 8])
+def test_pole_sum_fused_into_the_sweep(P, wmax):
+    """pselinv_selinv_pole_sum: Gamma accumulated in the write step of the
+    batched sweep (Section 4.4's pole expansion) against the sum over the
+    oracle's selected inverse of each pole, bitwise reproducible, equal to the
+    separate pass over the same X, and the X panels of every pole as a plain
+    selinv leaves them.  Two tile policies (wide and narrow supernodes), so
+    the finish shares cover X_{C,K} rows and diagonal blocks of several sizes."""
+    import torch
+    n, cp, ri, v, z, hv = poles_problem((4, 3, 3), 8, 5, seed=23)
+    h = P.SelInv(n, cp, ri, dtype=P.C128, batch=5, max_sn_width=wmax)
+    h.factor(tvals(v))
+    w = np.random.default_rng(5).normal(size=5) + 1j * np.random.default_rng(6).normal(size=5)
+    G = h.selinv_pole_sum(w).cpu().numpy()
+    X1 = h.panels().cpu().numpy()
+    want = 0
+    for l in range(5):
+        sym, lv, d, xv, xd, lcp, lri = oracle.selected_inverse(n, cp, ri, v[l], wmax, 1)
+        off, Xo = oracle.panels_from_columns(n, sym["sn_start"], sym["rcount"], sym["rrows"], lcp, xv, xd)
+        want = want + w[l] * Xo
+        assert np.max(np.abs(X1[l] - Xo)) <= TOL * np.max(np.abs(Xo))
+    assert np.max(np.abs(G - want)) <= TOL * np.max(np.abs(want))
+    assert np.array_equal(G, h.selinv_pole_sum(w).cpu().numpy())      # fixed pole order: reproducible
+    sep = h.pole_sum(w).cpu().numpy()
+    assert np.max(np.abs(G - sep)) <= 1e-14 * np.max(np.abs(sep))      # same sums as the separate pass
+    h.selinv(P.LEVEL)
+    assert np.array_equal(X1, h.panels().cpu().numpy())               # X as a plain selinv leaves it
+
+
+def test_pole_sum_fused_rejects_pivoted_and_unsym(P):
+    """The fused pole sum needs a pivot-free symmetric factor."""
+    import torch
+    n, cp, ri, v, z, hv = poles_problem((3, 3, 2), 4, 2, seed=29)
+    h = P.SelInv(n, cp, ri, dtype=P.C128, batch=2, max_sn_width=16)
+    w = np.ones(2, np.complex128)
+    with pytest.raises(P.PselinvError, match="ERR_STATE"):
+        h.selinv_pole_sum(w)                                           # no factor yet
+    h.factor_bk(tvals(v))
+    with pytest.raises(P.PselinvError, match="ERR_STATE"):
+        h.selinv_pole_sum(w)
+
+
 @pytest.mark.slow
 def test_full_size_dg_two_poles_trace_identity_and_batch_equivalence(P):
     """The 12^3-element, 48-dof DG-like matrix (n = 82,944) with its first two
