@@ -688,15 +688,17 @@ int build_schedule(pselinv_handle* h) {
       Range& lv = tl.per_lv[(size_t)l * kNumVar + var];
       lv.begin = (int64_t)tl.tasks.size();
       for (int32_t c = 0; c < ncol; ++c) {
-        // a group with few 64 x 64 tiles (under ~4 waves of 4 CTAs per SM)
-        // runs 64 x 8 tiles instead: 8x the tiles, each 8x shorter
+        // real: 64 x 8 tiles (9 CTAs per SM keep the FP64 pipe ~96% busy, and
+        // the tail of a group is 8x shorter than with 64 x 64 tiles);
+        // complex: 64 x 8 only for a group with few wide tiles (under ~4 waves
+        // of its CTAs per SM)
         int64_t ntile = 0;
         for (int32_t t = b; t < e; ++t) {
           if (color[t - b] != c) continue;
           const int64_t rb = (h->meta[h->level_sn[t]].r + kTileM - 1) / kTileM;
           ntile += rb * (rb + 1) / 2;
         }
-        const int gvar = ntile < 16 * 152 ? 0 : var;
+        const int gvar = (!cplx || ntile < 16 * 152) ? 0 : var;
         const int bn = 8 << gvar;
         Range ng, fg;
         for (int part = 0; part < 2; ++part) {
