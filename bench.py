@@ -201,7 +201,7 @@ def time_oracle_selinv(sample, threads=None):
 
 
 def cpu_baseline_block():
-    """The oracle on the GPU machine's host cores: one run on 1 thread and one
+    """The oracle on this host's cores: one run on 1 thread and one
     on all cores (nproc) of the 32^3 sample (~10 s of CPU work in total)."""
     sample = oracle_sample()
     flops = sample[-1]
