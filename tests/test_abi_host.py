@@ -135,3 +135,23 @@ def test_opts_structure_matches_the_c_layout(P):
                                                                                           P.RELAX_AMALG, -1, 1024)
     assert (o.debug_checks, o.unsym, o.spin_limit_ns, o.level_tiles, o.min_slice_rows, o.fp64_emulation) == (
         0, 0, 1000000000, 0, 0, 0)
+
+
+def test_pole_sum_state_checks_run_on_the_host(P):
+    """pselinv_selinv_pole_sum and pselinv_pole_sum check their arguments and
+    the handle's state before any device work (called through the C ABI with
+    a NULL stream, no GPU needed): NULL output -> ERR_ARG, no factor ->
+    ERR_STATE, a non-symmetric handle -> ERR_STATE."""
+    import ctypes
+    lib = P.load_library()
+    cp = np.array([0, 2, 4, 5], np.int64)
+    ri = np.array([0, 1, 1, 2, 2], np.int32)
+    h = P.SelInv(3, cp, ri, dtype=P.C128, batch=2)
+    w = np.ones(4, np.float64)                     # two complex weights as (re, im) pairs
+    out = np.zeros(2 * h.info["panel_entries"], np.float64)
+    wp, op = ctypes.c_void_p(w.ctypes.data), ctypes.c_void_p(out.ctypes.data)
+    for fn in (lib.pselinv_selinv_pole_sum, lib.pselinv_pole_sum):
+        assert fn(h._h, wp, None, None) == -1      # ERR_ARG
+        assert fn(h._h, wp, op, None) == -8        # ERR_STATE: nothing factored / inverted
+    hu = P.SelInv(3, cp, ri, unsym=1)
+    assert lib.pselinv_selinv_pole_sum(hu._h, wp, op, None) == -8
