@@ -163,6 +163,16 @@ typedef struct {
   const int32_t* nblk;      /* [nsn] ancestor blocks of each C */
   const int32_t* level_ptr; /* [nlevels+1] offsets into level_sn */
   const int32_t* level_sn;  /* [nsn] supernodes of level k (k = 0 is sigma 1), costliest first */
+  /* Schur groups of the factorisation (the supernodes of a level whose sets
+     C are pairwise disjoint, so their updates hit disjoint entries and run in
+     one launch without atomics): level k's groups are
+     group_ptr[k] .. group_ptr[k+1]-1, group g's supernodes
+     group_sn[group_sn_ptr[g] .. group_sn_ptr[g+1]-1]; supernodes with an
+     empty C may be absent */
+  int32_t ngroups;
+  const int32_t* group_ptr;     /* [nlevels+1] */
+  const int32_t* group_sn_ptr;  /* [ngroups+1] */
+  const int32_t* group_sn;
 } pselinv_symbolic;
 
 /* Fill *o with defaults: F64, batch 1, w_max 128, RELAX_AMALG, padding-minimal

@@ -65,7 +65,8 @@ class Symbolic(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nsn", ctypes.c_int32), ("nlevels", ctypes.c_int32),
                 ("perm", _P32), ("parent", _P32), ("sn_start", _P32), ("sn_parent", _P32), ("sigma", _P32),
                 ("rowptr", _P64), ("rows", _P32), ("panel_off", _P64), ("relptr", _P64), ("relidx", _P32),
-                ("nblk", _P32), ("level_ptr", _P32), ("level_sn", _P32)]
+                ("nblk", _P32), ("level_ptr", _P32), ("level_sn", _P32),
+                ("ngroups", ctypes.c_int32), ("group_ptr", _P32), ("group_sn_ptr", _P32), ("group_sn", _P32)]
 
 
 _lib = None
@@ -217,7 +218,9 @@ class SelInv:
                     sn_start=arr(v.sn_start, nsn + 1), sn_parent=arr(v.sn_parent, nsn),
                     sigma=arr(v.sigma, nsn), rowptr=rowptr, rows=arr(v.rows, int(rowptr[-1])),
                     panel_off=arr(v.panel_off, nsn + 1), relptr=relptr, relidx=arr(v.relidx, int(relptr[-1])),
-                    nblk=arr(v.nblk, nsn), level_ptr=arr(v.level_ptr, nl + 1), level_sn=arr(v.level_sn, nsn))
+                    nblk=arr(v.nblk, nsn), level_ptr=arr(v.level_ptr, nl + 1), level_sn=arr(v.level_sn, nsn),
+                    group_ptr=arr(v.group_ptr, nl + 1), group_sn_ptr=arr(v.group_sn_ptr, v.ngroups + 1),
+                    group_sn=arr(v.group_sn, int(arr(v.group_sn_ptr, v.ngroups + 1)[-1])))
 
     # ---- numeric ----
     @property

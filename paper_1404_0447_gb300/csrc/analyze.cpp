@@ -650,6 +650,8 @@ int build_schedule(pselinv_handle* h) {
     h->schur_near.clear();
     h->schur_far.clear();
     h->schur_gvar.clear();
+    h->schur_gsn_ptr.assign(1, 0);
+    h->schur_gsn.clear();
     std::vector<uint64_t> used(h->n, 0);  // groups (< 64) holding a supernode with this row in C
     std::vector<int32_t> touched, color;
     for (int32_t l = 0; l < nl; ++l) {
@@ -727,6 +729,9 @@ int build_schedule(pselinv_handle* h) {
           h->schur_near.push_back(ng);
           h->schur_far.push_back(fg);
           h->schur_gvar.push_back((int8_t)gvar);
+          for (int32_t t = b; t < e; ++t)
+            if (color[t - b] == c) h->schur_gsn.push_back(h->level_sn[t]);
+          h->schur_gsn_ptr.push_back((int32_t)h->schur_gsn.size());
         }
       }
       lv.end = (int64_t)tl.tasks.size();

@@ -1423,6 +1423,10 @@ int pselinv_export_symbolic(const pselinv_handle* h, pselinv_symbolic* v) {
   v->nblk = h->nblk.data();
   v->level_ptr = h->level_ptr.data();
   v->level_sn = h->level_sn.data();
+  v->ngroups = (int32_t)h->schur_near.size();
+  v->group_ptr = h->schur_gptr.data();
+  v->group_sn_ptr = h->schur_gsn_ptr.data();
+  v->group_sn = h->schur_gsn.data();
   return PSELINV_OK;
 }
 

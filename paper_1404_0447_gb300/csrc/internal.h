@@ -156,6 +156,7 @@ struct pselinv_handle {
   std::vector<int32_t> schur_gptr;
   std::vector<psi::Range> schur_near, schur_far;
   std::vector<int8_t> schur_gvar;  // tile variant of each group (64 x 8 for groups with few tiles)
+  std::vector<int32_t> schur_gsn_ptr, schur_gsn;  // supernodes of each group (pselinv_export_symbolic)
   int32_t schur_var = 0;  // tile variant of the Schur tiles of the larger groups
   std::vector<int8_t> s2var, s3var, trvar;  // step-2 / step-3 / panel-solve tile variant per supernode
   psi::TaskList t_sq;     // s x s tiles of each supernode's diagonal block (adjoint products)

@@ -155,3 +155,45 @@ def test_pole_sum_state_checks_run_on_the_host(P):
         assert fn(h._h, wp, op, None) == -8        # ERR_STATE: nothing factored / inverted
     hu = P.SelInv(3, cp, ri, unsym=1)
     assert lib.pselinv_selinv_pole_sum(hu._h, wp, op, None) == -8
+
+
+@pytest.mark.parametrize("case", ["grid3d_12", "graphlap_10", "random_perm"])
+def test_schur_groups_have_disjoint_targets(P, case):
+    """The factorisation's Schur update runs the supernodes of a level in
+    groups, each group one launch with plain read-modify-writes (no atomics).
+    That is race-free only if no two supernodes of a group update the same
+    ancestor entry, i.e. (the analysis's sufficient condition) their sets C
+    are disjoint.  Checked on the exported groups: every group lies in one
+    level, its C sets are pairwise disjoint, and every supernode with a
+    non-empty C is in exactly one group of its level."""
+    if case == "grid3d_12":
+        p = synth.grid3d(12)
+        h = P.SelInv(p.n, p.colptr, p.rowind, max_sn_width=16, relax=P.RELAX_AMALG)
+    elif case == "graphlap_10":
+        gl = synth.GraphLaplacian((10, 10, 10))
+        h = P.SelInv(gl.n, gl.colptr, gl.rowind, perm=synth.nd_order(gl.dims), max_sn_width=8)
+    else:
+        p = synth.grid3d(9)
+        perm = np.random.default_rng(4).permutation(p.n).astype(np.int32)
+        h = P.SelInv(p.n, p.colptr, p.rowind, perm=perm, max_sn_width=32)
+    sym = h.symbolic()
+    lp, ls, gp = sym["level_ptr"], sym["level_sn"], sym["group_ptr"]
+    gsp, gsn, rp, rows = sym["group_sn_ptr"], sym["group_sn"], sym["rowptr"], sym["rows"]
+    assert gp[0] == 0 and gp[-1] == len(gsp) - 1
+    seen = np.zeros(sym["nsn"], int)
+    ngroups_max = 0
+    for l in range(sym["nlevels"]):
+        level = set(ls[lp[l]:lp[l + 1]].tolist())
+        ngroups_max = max(ngroups_max, gp[l + 1] - gp[l])
+        for g in range(gp[l], gp[l + 1]):
+            members = gsn[gsp[g]:gsp[g + 1]]
+            assert set(members.tolist()) <= level
+            covered = set()
+            for k in members:
+                C = set(rows[rp[k]:rp[k + 1]].tolist())
+                assert not (C & covered), (l, g, k)
+                covered |= C
+                seen[k] += 1
+    r = np.diff(rp)
+    assert np.all(seen[r > 0] == 1) and np.all(seen <= 1)
+    assert ngroups_max > 1          # the cases do have levels whose supernodes conflict
